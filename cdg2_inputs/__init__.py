@@ -1,0 +1,189 @@
+"""Seeded synthetic inputs shared by the CUDA path and the oracle.
+
+This module holds random-number generation and plain data only (workload
+sizes, coefficient presets, Gaussian centres and amplitudes, manufactured-
+solution phases).  It contains none of the method's arithmetic: evaluating
+and projecting the initial field, the operator and the time stepper live on
+each side separately.
+
+Random draws use SplitMix64 (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014): state += 0x9E3779B97F4A7C15,
+then two xor-shift-multiply rounds and a final xor-shift.  A uniform double
+on [0,1) takes the top 53 bits.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+_MASK = (1 << 64) - 1
+
+
+class SplitMix64:
+    """SplitMix64 generator; ``uniform()`` returns a double in [0, 1)."""
+
+    def __init__(self, seed: int):
+        self.state = seed & _MASK
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+        return z ^ (z >> 31)
+
+    def uniform(self) -> float:
+        return (self.next_u64() >> 11) * (1.0 / 9007199254740992.0)
+
+
+# Species order of the state vector U = (n1, n2, n3, c1, c2, c3) (Sec. 2).
+SPECIES = ("n1", "n2", "n3", "c1", "c2", "c3")
+N_SPECIES = 6
+
+
+def default_params() -> dict:
+    """Builder preset of every model coefficient.
+
+    The paper prints no numeric coefficient values; these are documented
+    defaults chosen for a smooth, positive, diffusion-dominated regime, not
+    the paper's.  Keys follow Eq. (1) and Eq. (3): motilities mu/nu, tactic
+    sensitivities chi(x, y, a, b) = a x / (y + b) with (a, b) = (chi0, chith)
+    for the pairs 11, 13, 21 (n2 towards c1) and 22 (n2 against n1; the paper
+    reuses the 21 constants there, so the defaults are equal), death rates
+    d1, d2, debris constant gamma (< 0), neutralisation alpha1, alpha2,
+    debris-dependent production f1 (taken constant), oxidation rate k_ox,
+    inflow rates beta1, beta2, sigma and thresholds c1_star, c1_star2.
+    ``bc_sign`` = +1 reads the normal in Eq. (3) as the inward one (so the
+    boundary terms are influxes), -1 as the outward one.
+    """
+    return dict(
+        mu=(1e-2, 5e-3, 1e-3),
+        nu=(5e-2, 5e-2, 5e-2),
+        chi0=(1e-2, 5e-3, 5e-3, 5e-3),     # chi11, chi13, chi21, chi22
+        chith=(0.1, 0.1, 0.1, 0.1),
+        d1=0.1, d2=0.05, gamma=-0.1, alpha1=1.0, alpha2=0.5, f1=0.1, k_ox=0.5,
+        beta1=1.0, beta2=0.5, sigma=1.0, c1_star=0.01, c1_star2=0.02,
+        bc_sign=1.0,
+    )
+
+
+# The 8 reaction coefficients a gradient is taken with respect to.
+THETA_NAMES = ("d1", "d2", "gamma", "alpha1", "alpha2", "f1", "k_ox", "beta1")
+
+
+@dataclass
+class Workload:
+    """One named synthetic workload: mesh, degree and stepping sizes."""
+    name: str
+    dim: int
+    cells: tuple
+    extent: tuple
+    periodic: tuple
+    k: int
+    n_gauss: int = 4
+    sigma: float = 0.05
+    floor: float = 1e-3
+    seed: int = 1157
+    steps: int = 0
+    dt: float = 0.0
+    mms: bool = False
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_elem(self) -> int:
+        return math.prod(self.cells[: self.dim])
+
+    @property
+    def n_basis(self) -> int:
+        return (self.k + 1) ** self.dim
+
+    @property
+    def n_dof(self) -> int:
+        return N_SPECIES * self.n_elem * self.n_basis
+
+
+def workload(cfg: int, k: int | None = None) -> Workload:
+    """The five synthetic workloads shaped like the paper's 2D and 3D tests.
+
+    0: 2D 32x8 Q1 (about 6k DOF), 1: 2D 256x64 Q2/Q3 (manufactured
+    solution), 2: 2D 128x32 Q2 (differentiation), 3: 3D 64x16x16 Q3 (6.3M
+    DOF), 4: 3D 128x32x32 Q2 (21.2M DOF).  Domain [0,1]x[0,0.2](x[0,0.2]),
+    y = 0 the lumen side, y = 0.2 the outer wall, periodic in x (and z).
+    """
+    ext2 = (1.0, 0.2, 1.0)
+    ext3 = (1.0, 0.2, 0.2)
+    per2 = (1, 0, 0)
+    per3 = (1, 0, 1)
+    if cfg == 0:
+        return Workload("2D 32x8 Q1 seeded Gaussians", 2, (32, 8, 1), ext2, per2, 1 if k is None else k,
+                        seed=1157, steps=20, dt=1e-3)
+    if cfg == 1:
+        kk = 3 if k is None else k
+        return Workload(f"2D 256x64 Q{kk} manufactured solution", 2, (256, 64, 1), ext2, per2, kk,
+                        seed=1158, steps=20, dt=1e-4, mms=True)
+    if cfg == 2:
+        return Workload("2D 128x32 Q2 seeded Gaussians", 2, (128, 32, 1), ext2, per2, 2 if k is None else k,
+                        seed=1159, steps=50, dt=1e-3, extra=dict(checkpoint=10))
+    if cfg == 3:
+        return Workload("3D 64x16x16 Q3 seeded Gaussians", 3, (64, 16, 16), ext3, per3, 3 if k is None else k,
+                        n_gauss=8, sigma=0.04, seed=1160, steps=10, dt=1e-3)
+    if cfg == 4:
+        return Workload("3D 128x32x32 Q2 seeded Gaussians", 3, (128, 32, 32), ext3, per3, 2 if k is None else k,
+                        n_gauss=8, sigma=0.04, seed=1161, steps=20, dt=1e-3, extra=dict(checkpoint=5))
+    raise ValueError(f"unknown workload {cfg}")
+
+
+def gaussian_draws(dim: int, extent, n_gauss: int, seed: int):
+    """Centres and amplitudes of the seeded Gaussian bumps of every species.
+
+    For each species in order, then each bump: the ``dim`` centre
+    coordinates (uniform in the box), then the amplitude (uniform in [0,1)).
+    Returns (centres[6][n_gauss][dim], amps[6][n_gauss]) as nested lists.
+    """
+    rng = SplitMix64(seed)
+    centres, amps = [], []
+    for _s in range(N_SPECIES):
+        cs, a_s = [], []
+        for _g in range(n_gauss):
+            cs.append([rng.uniform() * extent[j] for j in range(dim)])
+            a_s.append(rng.uniform())
+        centres.append(cs)
+        amps.append(a_s)
+    return centres, amps
+
+
+def mms_phases(seed: int):
+    """Per-species phases in [0, 2 pi) of the manufactured solution."""
+    rng = SplitMix64(seed ^ 0x5EED)
+    return [2.0 * math.pi * rng.uniform() for _ in range(N_SPECIES)]
+
+
+def splitmix64_uniform_array(seed: int, n: int):
+    """The first ``n`` SplitMix64 uniforms of ``seed`` as a float64 numpy array.
+
+    Same stream as ``SplitMix64(seed).uniform()`` called ``n`` times: the
+    i-th state is seed + (i + 1) * 0x9E3779B97F4A7C15 (mod 2^64).
+    """
+    import numpy as np
+    with np.errstate(over="ignore"):
+        i = np.arange(1, n + 1, dtype=np.uint64)
+        z = np.uint64(seed & _MASK) + i * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def random_coefficients(n_elem: int, n_basis: int, seed: int, scale: float = 0.1):
+    """A positive random coefficient field [E][6][n_b] as a float64 numpy array.
+
+    Coefficient 0 (the cell mean for the orthonormal basis) is drawn in
+    [0.5, 1.5); mode i > 0 in +-scale / (1 + i).  Used for parity cases that
+    need arbitrary discrete states rather than smooth ones.
+    """
+    import numpy as np
+    u = splitmix64_uniform_array(seed, n_elem * N_SPECIES * n_basis).reshape(n_elem, N_SPECIES, n_basis)
+    i = np.arange(n_basis, dtype=np.float64)
+    out = scale * (2.0 * u - 1.0) / (1.0 + i)
+    out[:, :, 0] = 0.5 + u[:, :, 0]
+    return out

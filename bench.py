@@ -1,0 +1,339 @@
+"""Benchmark of the CDG2 operator L_h on one GB300 (or N replicas).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference] [--config C] [--k K]
+
+A step is one application of f(U) = M^{-1} L_h(U) (volume terms, face fluxes
+with the CDG2 lifting, boundary influxes, inverse mass matrix) over the whole
+mesh, in FP64, through the C ABI.  The default workload is the 2D 256x64 DG
+Q3 manufactured-solution mesh (1,572,864 DOF).  Its state (12.6 MB) fits in
+L2, so L2 is flushed (a 512 MB write) before every timed step, outside the
+step's CUDA events.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "L_h apply GDOF/s FP64 vs mixed at stated error; VJP GDOF/s; % HBM roofline"
+
+
+def apply_flops_per_element(dim: int, k: int) -> int:
+    """Floating-point operations of one element in the fused apply kernel.
+
+    Counted from the kernel's loops (an FMA is 2 flops, a divide 1):
+    sum-factorised interpolation of U and grad U to the (k+2)^d Gauss points,
+    the transposed test passes, the pointwise volume flux (33 + 34 d per
+    point), and per face axis the normal contraction (own trace, jump,
+    both normal derivatives), tangential interpolation of 4 fields, the
+    pointwise face flux (112 per point and side; each interior face is
+    evaluated from both sides), the tangential test of 2 fields and the
+    normal expansion into the residual.
+    """
+    b, q, d, s = k + 1, k + 2, dim, 6
+    if d == 2:
+        interp = 2 * q * b * b + 3 * q * q * b
+        test = 3 * q * q * b + 2 * q * b * b
+        face_axis = 8 * b ** 2 + 8 * q * b + 4 * q * b + 4 * b ** 2
+    else:
+        interp = 2 * q * b ** 3 + 3 * q * q * b * b + 4 * q ** 3 * b
+        test = 4 * q ** 3 * b + 3 * q * q * b * b + 2 * q * b ** 3
+        face_axis = 8 * b ** 3 + 8 * (q * b * b + q * q * b) + 4 * (b * q * q + b * b * q) + 4 * b ** 3
+    fma = s * (interp + test + d * face_axis)
+    pointwise = q ** d * (33 + 34 * d) + 2 * d * q ** (d - 1) * 112
+    return 2 * fma + pointwise
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_setup(cfg: int, k: int | None):
+    import cdg2_inputs as I
+    w = I.workload(cfg, k)
+    return w, I
+
+
+def make_inputs(G, w, I, mesh, dtype_flag=0):
+    import torch
+    dt = torch.float32 if dtype_flag else torch.float64
+    U = torch.empty(mesh.n_dof, dtype=dt, device="cuda")
+    p = I.default_params()
+    if w.mms:
+        ph = I.mms_phases(w.seed)
+        G.cdg2_project_mms(mesh, G.make_params(p, ph), 0.0, U, dtype_flag)
+    else:
+        cen, amp = I.gaussian_draws(w.dim, w.extent, w.n_gauss, w.seed)
+        G.cdg2_project_gaussians(mesh, cen, amp, w.sigma, w.floor, U, dtype_flag)
+    return U, p
+
+
+def time_applies(G, torch, mesh, p, U, out, flags, steps, warmup, flush):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush.fill_(1)
+        G.cdg2_apply(mesh, p, U, out, flags)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush.fill_(1)
+        a.record(stream)
+        G.cdg2_apply(mesh, p, U, out, flags)
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def cpu_oracle_baseline(w, seconds: float = 12.0):
+    """The oracle (plain FP64 PyTorch CPU) timed on this host on the same workload."""
+    import torch
+
+    import cdg2_inputs as I
+    from oracle import cdg2_oracle as O
+    om = O.Mesh(w.dim, w.cells, w.extent, w.periodic, w.k)
+    p = I.default_params()
+    U = torch.from_numpy(I.random_coefficients(om.E, om.nb, w.seed))
+    O.apply(om, U, p)
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        O.apply(om, U, p)
+        reps += 1
+    dt = time.perf_counter() - t0
+    return {"value": w.n_dof * reps / dt / 1e9, "unit": "GDOF/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{reps} full-mesh applies of {w.name} ({w.n_dof} DOF) in {dt:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, K timed steps (rank 0 only)."""
+    import torch
+
+    import cdg2_inputs as I
+    from oracle import cdg2_oracle as O
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = I.workload(args.config, args.k)
+    om = O.Mesh(w.dim, w.cells, w.extent, w.periodic, w.k)
+    p = I.default_params()
+    U = torch.from_numpy(I.random_coefficients(om.E, om.nb, w.seed))
+    t0 = time.perf_counter()
+    O.apply(om, U, p)
+    t_one = time.perf_counter() - t0
+    # bound the whole run to about two minutes: shrink the sample mesh along y if needed
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    cells = list(w.cells)
+    if t_one > budget:
+        cells[1] = max(2, int(cells[1] * budget / t_one))
+        om = O.Mesh(w.dim, cells, w.extent, w.periodic, w.k)
+        U = torch.from_numpy(I.random_coefficients(om.E, om.nb, w.seed))
+    ndof = 6 * om.E * om.nb
+    for _ in range(args.warmup):
+        O.apply(om, U, p)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.apply(om, U, p)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = ndof * args.steps / total / 1e9
+    sample = f"{args.steps} oracle applies on {cells[:w.dim]} cells of {w.name} ({ndof} DOF each)"
+    line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": w.name, "n_dof": ndof, "sample_cells": cells[:w.dim]},
+            "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--k", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1403_1157_gb300 as G
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w, I = workload_setup(args.config, args.k)
+    mesh = G.cdg2_mesh_create(w.dim, w.cells, w.extent, w.periodic, w.k)
+    U, p = make_inputs(G, w, I, mesh)
+    out = torch.empty_like(U)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    # ---- timed region: K FP64 applies, L2 flushed before each ----
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(uuid)
+    time.sleep(0.4)
+    t_wall = time.perf_counter()
+    ms = time_applies(G, torch, mesh, p, U, out, G.CDG2_MINV, args.steps, args.warmup, flush)
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_step = total_ms / args.steps
+    value = world * w.n_dof * args.steps / (total_ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (the fused FP64 apply kernel) ----
+    fl = apply_flops_per_element(w.dim, w.k) * w.n_elem
+    achieved_tf = fl / (ms_step * 1e-3) / 1e12
+    fp64_peak = 1.25
+    peaks, kind = load_peaks()
+    hbm_bytes = 16 * w.n_dof
+    hbm_frac = hbm_bytes / (ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"]
+
+    # ---- FP32 apply (the inner-solve operator) and its raw error vs FP64 ----
+    U32 = U.float()
+    out32 = torch.empty_like(U32)
+    ms32 = time_applies(G, torch, mesh, p, U32, out32, G.CDG2_MINV | G.CDG2_FP32, max(20, args.steps // 4), 3, flush)
+    ref64 = torch.empty_like(U)
+    G.cdg2_apply(mesh, p, U32.double(), ref64, G.CDG2_MINV)
+    torch.cuda.synchronize()
+    e = out32.double().view(w.n_elem, 6, -1) - ref64.view(w.n_elem, 6, -1)
+    rel32 = float((e.pow(2).sum(dim=(0, 2)).sqrt() / ref64.view(w.n_elem, 6, -1).pow(2).sum(dim=(0, 2)).sqrt()).max())
+    fp32 = {"value": w.n_dof / (statistics.mean(ms32) * 1e-3) / 1e9, "unit": "GDOF/s",
+            "rel_l2_err_vs_fp64_max_species": rel32}
+
+    # ---- end to end through the API: pinned host U -> device, apply, result -> pinned host ----
+    hU = U.cpu().pin_memory()
+    hout = torch.empty_like(hU).pin_memory()
+    dU = torch.empty_like(U)
+    stream = torch.cuda.current_stream()
+    n_e2e = max(10, args.steps // 4)
+    for _ in range(3):
+        dU.copy_(hU, non_blocking=True)
+        G.cdg2_apply(mesh, p, dU, out, G.CDG2_MINV)
+        hout.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(n_e2e):
+        dU.copy_(hU, non_blocking=True)
+        G.cdg2_apply(mesh, p, dU, out, G.CDG2_MINV)
+        hout.copy_(out, non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b) / n_e2e
+    nbytes = U.numel() * U.element_size()
+    e2e = {"value": world * w.n_dof / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_oracle_baseline(w)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_dof": w.n_dof, "n_elem": w.n_elem, "degree": w.k,
+                   "l2": "flushed before every timed step (512 MB write outside the step events)",
+                   "step": "one cdg2_apply (M^-1 L_h, FP64) over the whole mesh"},
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tf / fp64_peak, "traffic": None,
+                     "peak_note": "nominal FP64 FMA rate of GB300 (2 DFMA/clk/SM x 152 SMs); an FMA-loop probe measured 1.253",
+                     "flops_per_launch": fl, "kernel": f"apply_kernel<{w.dim},{w.k},double>",
+                     "hbm_frac": hbm_frac, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_kind": kind},
+        "fp32": fp32,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "wall_s_timed_region": t_wall,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

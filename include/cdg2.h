@@ -1,0 +1,139 @@
+/*
+ * cdg2.h -- C ABI of the GB300 CDG2 library for the six-species
+ * atherosclerosis model of Girke, Kloefkorn and Ohlberger (arXiv 1403.1157).
+ *
+ * The library applies the discontinuous Galerkin spatial operator
+ *   f(U) = M^{-1} L_h(U),     <phi, L_h(U)> = <phi, K_h(U)> + <phi, I_h(U)>
+ * (Sec. 3.1 Eq. convDiscr with the element integrals of Eq. elementint and the
+ * surface integrals of Eq. surfaceint; Sec. 3.2 Eq. ode for M^{-1}), its
+ * derivatives, and SDIRK time steps solved by Jacobian-free Newton-GMRES
+ * (Sec. 3.2).  Every entry point runs its arithmetic in hand-written CUDA
+ * kernels for sm_103a on the caller's stream.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * Mesh: uniform Cartesian cells of the box [0,L0]x[0,L1](x[0,L2]), numbered
+ *   lexicographically with x fastest.  Axis 1 (y) is the wall: y = 0 is
+ *   Gamma_1 (lumen side), y = L1 is Gamma_2 (outer wall) unless periodic.
+ * Basis: on each cell the tensor Legendre basis
+ *   phi_i(x) = prod_j sqrt(2 a_j + 1) P_{a_j}(2 xi_j - 1),  xi = (x - x_K)/h,
+ *   degree k in each direction (Q_k), multi-index a lexicographic, x fastest;
+ *   orthonormal on the unit cell, so M_K = |K| I.
+ * Coefficients: U[e][s][i], e < n_elem, s < 6 in the species order
+ *   (n1, n2, n3, c1, c2, c3), i < n_basis = (k+1)^dim; contiguous.
+ *   float64, or float32 with CDG2_FP32.
+ * Pointers: "device" arrays live in GPU memory owned by the caller; the
+ *   library never frees them.  Host structs are read during the call only.
+ * stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Calls are asynchronous with respect to the host unless stated.
+ * Errors: every int-returning call returns CDG2_OK (0) or a negative code;
+ *   cdg2_last_error() then describes it.  No call aborts or throws.
+ */
+#ifndef CDG2_H
+#define CDG2_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CDG2_OK 0
+#define CDG2_ERR_INVALID_ARG (-1)   /* a NULL pointer, bad size or unsupported option */
+#define CDG2_ERR_CUDA (-2)          /* a CUDA runtime call or kernel launch failed */
+#define CDG2_ERR_NOT_CONVERGED (-3) /* Newton or GMRES hit its iteration cap */
+#define CDG2_ERR_NONFINITE (-4)     /* a NaN or Inf appeared in a solver residual */
+
+/* flags of cdg2_apply / cdg2_jvp / cdg2_vjp */
+#define CDG2_MINV 1      /* return M^{-1} L_h (else the residual <phi, L_h>) */
+#define CDG2_FORCING 2   /* add the manufactured-solution forcing at time t */
+#define CDG2_FP32 4      /* arrays are float32 and the kernel computes in FP32 */
+
+typedef struct cdg2_mesh cdg2_mesh;
+
+/* Mesh description.
+ * dim: 2 or 3.  cells[d] >= 1, extent[d] > 0, periodic[d] in {0,1} for d < dim.
+ * k: polynomial degree 1..3 (Q_k, Sec. 3.1 "P_k(K)" read as Q_k on boxes).
+ * q1: Gauss points per direction; 0 selects k+2 (the only supported value).
+ * chi_e: CDG2 lifting factor (Sec. 3.1: half the faces per element);
+ *   <= 0 selects dim (2 for quads, 3 for hexes).
+ * gamma1_in: x-range [x0, x1] of the LDL inflow part Gamma_{1,in} of Gamma_1. */
+typedef struct cdg2_mesh_desc {
+    int dim;
+    int cells[3];
+    double extent[3];
+    int periodic[3];
+    int k;
+    int q1;
+    double chi_e;
+    double gamma1_in[2];
+} cdg2_mesh_desc;
+
+/* Model coefficients of Eq. (1) and Eq. (3) (Sec. 2).
+ * mu, nu: motilities (A = diag(mu1,mu2,mu3,nu1,nu2,nu3)).
+ * chi0/chith: tactic sensitivities chi(x,y,a,b) = a x / (y + b) with
+ *   (a, b) = (chi0[j], chith[j]) for j = 0: n1 up c1, 1: n1 up c3,
+ *   2: n2 up c1, 3: n2 down n1.
+ * d1, d2 death rates; gamma = F < 0 the debris term; alpha1, alpha2
+ *   neutralisation; f1 the (constant) debris production; k_ox oxidation.
+ * beta1, beta2, sigma inflow rates; c1_star, c1_star2 thresholds c1*, c1**.
+ * bc_sign: +1 reads the normal of Eq. (3) as inward (influx), -1 outward.
+ * mms_phase: phases of the manufactured solution used by CDG2_FORCING,
+ *   U*_s = 1 + cos(2 pi x + mms_phase[s]) cos(pi y / L1) exp(-t) / 2. */
+typedef struct cdg2_params {
+    double mu[3];
+    double nu[3];
+    double chi0[4];
+    double chith[4];
+    double d1, d2, gamma, alpha1, alpha2, f1, k_ox;
+    double beta1, beta2, sigma, c1_star, c1_star2;
+    double bc_sign;
+    double mms_phase[6];
+} cdg2_params;
+
+/* Build a mesh (host call, synchronous).  Tabulates the 1D basis and Gauss
+ * rule on the host.  *out receives an opaque handle owned by the caller
+ * until cdg2_mesh_destroy.  Errors: INVALID_ARG for an unsupported desc. */
+int cdg2_mesh_create(const cdg2_mesh_desc* desc, cdg2_mesh** out);
+
+/* Free a mesh and every device workspace it owns (synchronises the device
+ * work queued on those buffers).  NULL is ignored. */
+void cdg2_mesh_destroy(cdg2_mesh* mesh);
+
+/* Sizes: elements, basis functions per species per element, total DOF
+ * (= 6 * n_elem * n_basis).  Any output pointer may be NULL. */
+int cdg2_mesh_info(const cdg2_mesh* mesh, long long* n_elem, int* n_basis, long long* n_dof);
+
+/* out = M^{-1} L_h(U) (flags & CDG2_MINV) or out = <phi, L_h(U)>.
+ * Sec. 3.1 Eq. convDiscr: element integrals int_K (F - A grad U):grad phi
+ * + S.phi; interior faces: symmetric terms {A grad phi}:[U], consistency
+ * {A grad U}:[phi], local Lax-Friedrichs F^ and the CDG2 diffusion flux
+ * 2 chi_e A r_e([U]) on K^-_e (the lower-coordinate cell); boundary faces:
+ * the influxes of Eq. (3).  Sec. 3.2: M^{-1} of the orthonormal basis.
+ * U, out: device arrays [n_elem][6][n_basis] (float64, or float32 with
+ * CDG2_FP32); they must not overlap.  t: time of the CDG2_FORCING term. */
+int cdg2_apply(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, void* out,
+               int flags, double t, void* stream);
+
+/* Initial data: out = L2 projection onto V_h of
+ *   u0_s(x) = floor_value + sum_b amps[s][b] exp(-|x - centres[s][b]|^2 / (2 sigma^2))
+ * (Sec. 3.2: U(0) is the projection of U_0), distances taken as minimum
+ * images along periodic axes, with the q1-point Gauss rule of the mesh.
+ * centres: host [6][n_gauss][dim], amps: host [6][n_gauss] (read during the
+ * call), 0 <= n_gauss <= 16, sigma > 0.  out: device [n_elem][6][n_basis],
+ * float64 or float32 (flags = CDG2_FP32). */
+int cdg2_project_gaussians(const cdg2_mesh* mesh, int n_gauss, const double* centres, const double* amps,
+                           double sigma, double floor_value, void* out, int flags, void* stream);
+
+/* out = L2 projection of the manufactured solution
+ *   U*_s = 1 + cos(2 pi x + params->mms_phase[s]) cos(pi y / L1) exp(-t) / 2
+ * (a smooth positive field with zero normal derivative on y = 0, L1).
+ * out: device [n_elem][6][n_basis], float64 or float32 (CDG2_FP32). */
+int cdg2_project_mms(const cdg2_mesh* mesh, const cdg2_params* params, double t, void* out, int flags,
+                     void* stream);
+
+/* Human-readable description of the last error on this thread. */
+const char* cdg2_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CDG2_H */

@@ -1,0 +1,230 @@
+"""Python binding of the CDG2 CUDA library (``include/cdg2.h``).
+
+Argument marshalling only: every step of the operator, its derivatives and
+the time stepper runs in the library's CUDA kernels.  PyTorch tensors supply
+device memory and streams.  There is no CPU fallback: importing works
+without a GPU, but every call needs the built ``libcdg2.so`` and a CUDA
+device, and raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+__all__ = [
+    "CDG2_MINV", "CDG2_FORCING", "CDG2_FP32", "Cdg2Error", "Mesh", "load_library", "library_path",
+    "make_params", "cdg2_mesh_create", "cdg2_mesh_destroy", "cdg2_mesh_info", "cdg2_apply", "cdg2_last_error",
+    "cdg2_project_gaussians", "cdg2_project_mms",
+]
+
+CDG2_MINV = 1
+CDG2_FORCING = 2
+CDG2_FP32 = 4
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+class Cdg2Error(RuntimeError):
+    """A CDG2 call returned a negative status."""
+
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"CDG2 error {code}: {msg}")
+        self.code = code
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("cells", ctypes.c_int * 3),
+        ("extent", ctypes.c_double * 3),
+        ("periodic", ctypes.c_int * 3),
+        ("k", ctypes.c_int),
+        ("q1", ctypes.c_int),
+        ("chi_e", ctypes.c_double),
+        ("gamma1_in", ctypes.c_double * 2),
+    ]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("mu", ctypes.c_double * 3),
+        ("nu", ctypes.c_double * 3),
+        ("chi0", ctypes.c_double * 4),
+        ("chith", ctypes.c_double * 4),
+        ("d1", ctypes.c_double), ("d2", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("alpha1", ctypes.c_double), ("alpha2", ctypes.c_double), ("f1", ctypes.c_double),
+        ("k_ox", ctypes.c_double),
+        ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("sigma", ctypes.c_double),
+        ("c1_star", ctypes.c_double), ("c1_star2", ctypes.c_double),
+        ("bc_sign", ctypes.c_double),
+        ("mms_phase", ctypes.c_double * 6),
+    ]
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libcdg2.so")
+
+
+def load_library():
+    """Load ``libcdg2.so`` (built in-tree by ``build.py``); raise if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CDG2 CUDA library not built ({path} missing); run paper_1403_1157_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.cdg2_mesh_create.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(vp)]
+    lib.cdg2_mesh_create.restype = i
+    lib.cdg2_mesh_destroy.argtypes = [vp]
+    lib.cdg2_mesh_destroy.restype = None
+    lib.cdg2_mesh_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i),
+                                   ctypes.POINTER(ctypes.c_longlong)]
+    lib.cdg2_mesh_info.restype = i
+    lib.cdg2_apply.argtypes = [vp, ctypes.POINTER(Params), vp, vp, i, d, vp]
+    lib.cdg2_apply.restype = i
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.cdg2_project_gaussians.argtypes = [vp, i, dp, dp, d, d, vp, i, vp]
+    lib.cdg2_project_gaussians.restype = i
+    lib.cdg2_project_mms.argtypes = [vp, ctypes.POINTER(Params), d, vp, i, vp]
+    lib.cdg2_project_mms.restype = i
+    lib.cdg2_last_error.argtypes = []
+    lib.cdg2_last_error.restype = ctypes.c_char_p
+    _LIB = lib
+    return lib
+
+
+def cdg2_last_error() -> str:
+    return load_library().cdg2_last_error().decode()
+
+
+def _check(code: int):
+    if code != 0:
+        raise Cdg2Error(code, cdg2_last_error())
+
+
+def make_params(p: dict, mms_phase=None) -> Params:
+    """cdg2_params from a coefficient dict (keys of ``cdg2_inputs.default_params``)."""
+    out = Params()
+    for j in range(3):
+        out.mu[j] = float(p["mu"][j])
+        out.nu[j] = float(p["nu"][j])
+    for j in range(4):
+        out.chi0[j] = float(p["chi0"][j])
+        out.chith[j] = float(p["chith"][j])
+    for key in ("d1", "d2", "gamma", "alpha1", "alpha2", "f1", "k_ox", "beta1", "beta2", "sigma",
+                "c1_star", "c1_star2", "bc_sign"):
+        setattr(out, key, float(p[key]))
+    ph = mms_phase if mms_phase is not None else p.get("mms_phase", (0.0,) * 6)
+    for j in range(6):
+        out.mms_phase[j] = float(ph[j])
+    return out
+
+
+class Mesh:
+    """Owning handle of a cdg2_mesh."""
+
+    def __init__(self, handle: int, desc: MeshDesc):
+        self.handle = handle
+        self.desc = desc
+        lib = load_library()
+        ne, nb, nd = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_longlong()
+        _check(lib.cdg2_mesh_info(handle, ctypes.byref(ne), ctypes.byref(nb), ctypes.byref(nd)))
+        self.n_elem, self.n_basis, self.n_dof = ne.value, nb.value, nd.value
+        self.dim, self.k = desc.dim, desc.k
+
+    @property
+    def shape(self):
+        return (self.n_elem, 6, self.n_basis)
+
+    def close(self):
+        if self.handle:
+            load_library().cdg2_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cdg2_mesh_create(dim, cells, extent, periodic, k, q1=0, chi_e=0.0, gamma1_in=(0.375, 0.625)) -> Mesh:
+    desc = MeshDesc()
+    desc.dim = int(dim)
+    for a in range(3):
+        desc.cells[a] = int(cells[a]) if a < len(cells) else 1
+        desc.extent[a] = float(extent[a]) if a < len(extent) else 1.0
+        desc.periodic[a] = int(periodic[a]) if a < len(periodic) else 1
+    desc.k = int(k)
+    desc.q1 = int(q1)
+    desc.chi_e = float(chi_e)
+    desc.gamma1_in[0], desc.gamma1_in[1] = float(gamma1_in[0]), float(gamma1_in[1])
+    h = ctypes.c_void_p()
+    _check(load_library().cdg2_mesh_create(ctypes.byref(desc), ctypes.byref(h)))
+    return Mesh(h.value, desc)
+
+
+def cdg2_mesh_destroy(mesh: Mesh):
+    mesh.close()
+
+
+def cdg2_mesh_info(mesh: Mesh):
+    return mesh.n_elem, mesh.n_basis, mesh.n_dof
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, mesh: Mesh, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous() or t.numel() != mesh.n_dof:
+        raise ValueError(f"{name} must be contiguous with {mesh.n_dof} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _params(params):
+    return params if isinstance(params, Params) else make_params(params)
+
+
+def cdg2_apply(mesh: Mesh, params, U: torch.Tensor, out: torch.Tensor, flags: int = CDG2_MINV, t: float = 0.0,
+               stream=None) -> torch.Tensor:
+    """out = M^{-1} L_h(U) (CDG2_MINV) on the given (default: current) stream."""
+    dt = torch.float32 if flags & CDG2_FP32 else torch.float64
+    p = _params(params)
+    _check(load_library().cdg2_apply(mesh.handle, ctypes.byref(p), _dev(U, mesh, dt, "U"),
+                                     _dev(out, mesh, dt, "out"), int(flags), float(t), _stream_ptr(stream)))
+    return out
+
+
+def cdg2_project_gaussians(mesh: Mesh, centres, amps, sigma: float, floor_value: float, out: torch.Tensor,
+                           flags: int = 0, stream=None) -> torch.Tensor:
+    """out = L2 projection of floor + sum of Gaussian bumps (centres[6][n][dim], amps[6][n])."""
+    n = len(amps[0])
+    flat_c = [float(v) for s in range(6) for b in range(n) for v in centres[s][b][: mesh.dim]]
+    flat_a = [float(v) for s in range(6) for v in amps[s]]
+    cc = (ctypes.c_double * max(1, len(flat_c)))(*flat_c)
+    aa = (ctypes.c_double * max(1, len(flat_a)))(*flat_a)
+    dt = torch.float32 if flags & CDG2_FP32 else torch.float64
+    _check(load_library().cdg2_project_gaussians(mesh.handle, n, cc, aa, float(sigma), float(floor_value),
+                                                 _dev(out, mesh, dt, "out"), int(flags), _stream_ptr(stream)))
+    return out
+
+
+def cdg2_project_mms(mesh: Mesh, params, t: float, out: torch.Tensor, flags: int = 0, stream=None) -> torch.Tensor:
+    """out = L2 projection of the manufactured solution at time t (phases from params)."""
+    dt = torch.float32 if flags & CDG2_FP32 else torch.float64
+    p = _params(params)
+    _check(load_library().cdg2_project_mms(mesh.handle, ctypes.byref(p), float(t), _dev(out, mesh, dt, "out"),
+                                           int(flags), _stream_ptr(stream)))
+    return out

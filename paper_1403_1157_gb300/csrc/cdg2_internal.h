@@ -1,0 +1,69 @@
+// Internal types shared by the host layer and the kernels of the CDG2 library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "cdg2.h"
+
+namespace cdg2 {
+
+constexpr int NS = 6;      // species (n1, n2, n3, c1, c2, c3), Sec. 2
+constexpr int MAXK = 3;    // highest supported degree
+constexpr int MAXQ = MAXK + 2;
+
+// 1D tables on the reference interval [0,1] for degree k and q1 = k+2 Gauss
+// points: psi_a(xi) = sqrt(2a+1) P_a(2 xi - 1) and its derivative.
+struct Tab1D {
+    double B[MAXQ][MAXK + 1];   // psi_a(xi_q)
+    double D[MAXQ][MAXK + 1];   // d psi_a / d xi at xi_q
+    double w[MAXQ];             // Gauss weights on [0,1] (sum 1)
+    double xi[MAXQ];            // Gauss points on [0,1]
+    double e[2][MAXK + 1];      // psi_a(0), psi_a(1)
+    double d[2][MAXK + 1];      // psi'_a(0), psi'_a(1)
+};
+
+// Uniform Cartesian geometry (Sec. 3.1 tessellation, read as boxes).
+struct Geo {
+    int dim, k;
+    int n[3];          // cells per axis (1 beyond dim)
+    int periodic[3];
+    double h[3];       // cell sizes (1 beyond dim)
+    double L[3];
+    double vol;        // |K|
+    double chi_e;      // CDG2 lifting factor
+    double g1in[2];    // Gamma_{1,in} x-range
+    long long E;       // elements
+};
+
+// Model coefficients in kernel-argument form (copied from cdg2_params).
+struct Coef {
+    double A[NS];                  // diag(mu1, mu2, mu3, nu1, nu2, nu3)
+    double chi0[4], chith[4];
+    double d1, d2, gamma, alpha1, alpha2, f1, k_ox;
+    double beta1, beta2, sigma, c1s, c1ss, bc_sign;
+    double phase[NS];
+};
+
+Coef make_coef(const cdg2_params& p);
+
+}  // namespace cdg2
+
+struct cdg2_mesh {
+    cdg2::Geo geo;
+    cdg2::Tab1D tab;
+    int nb;            // basis per species per element
+    long long ndof;
+};
+
+namespace cdg2 {
+
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// Kernel launchers (apply.cu).  Return a cudaError_t of the launch.
+cudaError_t launch_apply(const cdg2_mesh& m, const Coef& c, const void* U, void* out, int flags, double t,
+                         cudaStream_t stream);
+
+}  // namespace cdg2

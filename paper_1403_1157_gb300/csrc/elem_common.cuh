@@ -1,0 +1,170 @@
+// Building blocks shared by the element-centric kernels (apply, JVP, VJP):
+// compile-time shapes, shared-memory tables, sum-factorised tensor
+// contractions and the neighbour lookup of the structured mesh.
+#pragma once
+
+#include "cdg2_internal.h"
+
+namespace cdg2 {
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+// Sizes of one element for dimension D and degree K (q1 = K + 2 points).
+template <int D, int K>
+struct Shape {
+    static constexpr int NB1 = K + 1;                 // 1D basis
+    static constexpr int NQ1 = K + 2;                 // 1D Gauss points
+    static constexpr int NB = ipow(NB1, D);           // basis per species
+    static constexpr int NQ = ipow(NQ1, D);           // volume points
+    static constexpr int NBT = ipow(NB1, D - 1);      // tangential basis on a face
+    static constexpr int NQT = ipow(NQ1, D - 1);      // face points
+};
+
+// 1D tables in shared memory in the kernel's precision.
+template <int K, typename T>
+struct STab {
+    T B[K + 2][K + 1];   // psi_a(xi_q)
+    T D[K + 2][K + 1];   // psi'_a(xi_q)
+    T w[K + 2];
+    T xi[K + 2];
+    T e[2][K + 1];       // psi_a(0), psi_a(1)
+    T d[2][K + 1];       // psi'_a(0), psi'_a(1)
+};
+
+template <int K, typename T>
+__device__ __forceinline__ void load_tab(STab<K, T>& s, const Tab1D& t) {
+    for (int i = threadIdx.x; i < (K + 2) * (K + 1); i += blockDim.x) {
+        int q = i / (K + 1), a = i % (K + 1);
+        s.B[q][a] = (T)t.B[q][a];
+        s.D[q][a] = (T)t.D[q][a];
+    }
+    for (int i = threadIdx.x; i < K + 2; i += blockDim.x) {
+        s.w[i] = (T)t.w[i];
+        s.xi[i] = (T)t.xi[i];
+    }
+    for (int i = threadIdx.x; i < 2 * (K + 1); i += blockDim.x) {
+        int f = i / (K + 1), a = i % (K + 1);
+        s.e[f][a] = (T)t.e[f][a];
+        s.d[f][a] = (T)t.d[f][a];
+    }
+}
+
+template <typename T>
+struct Ident {
+    using type = T;
+};
+
+// One sum-factorisation pass over nt tensors stored back to back.
+// Input tensors have extents (I0, I1, I2) (x fastest); axis AX (extent NI)
+// is replaced by NO in the output:
+//     out[t][..o..] = sum_i M1(o,i) in1[t][..i..]  (+ M2(o,i) in2[t][..i..])
+// M(o,i) = M[o][i] (TR = false) or M[i][o] (TR = true), row length LD.
+template <int AX, int I0, int I1, int I2, int NO, bool TR, int LD, bool TWO, typename T>
+__device__ __forceinline__ void sf_pass(const T* __restrict__ in1, const T* __restrict__ M1,
+                                        const typename Ident<T>::type* __restrict__ in2,
+                                        const typename Ident<T>::type* __restrict__ M2, int in_stride,
+                                        T* __restrict__ out, int out_stride, int nt) {
+    constexpr int NI = AX == 0 ? I0 : (AX == 1 ? I1 : I2);
+    constexpr int O0 = AX == 0 ? NO : I0;
+    constexpr int O1 = AX == 1 ? NO : I1;
+    constexpr int O2 = AX == 2 ? NO : I2;
+    constexpr int OSZ = O0 * O1 * O2;
+    constexpr int SI = AX == 0 ? 1 : (AX == 1 ? I0 : I0 * I1);
+    const int total = nt * OSZ;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int tt = idx / OSZ;
+        const int r = idx - tt * OSZ;
+        const int o0 = r % O0;
+        const int o1 = (r / O0) % O1;
+        const int o2 = r / (O0 * O1);
+        const int o = AX == 0 ? o0 : (AX == 1 ? o1 : o2);
+        const int base = (AX == 0 ? 0 : o0) + (AX == 1 ? 0 : o1) * I0 + (AX == 2 ? 0 : o2) * I0 * I1;
+        const T* s1 = in1 + tt * in_stride + base;
+        T acc = T(0);
+#pragma unroll
+        for (int i = 0; i < NI; ++i) acc = fma(TR ? M1[i * LD + o] : M1[o * LD + i], s1[i * SI], acc);
+        if constexpr (TWO) {
+            const T* s2 = in2 + tt * in_stride + base;
+#pragma unroll
+            for (int i = 0; i < NI; ++i) acc = fma(TR ? M2[i * LD + o] : M2[o * LD + i], s2[i * SI], acc);
+        }
+        out[tt * out_stride + r] = acc;
+    }
+}
+
+// Index of the element coefficient with normal index m along axis A and
+// tangential multi-index (b0, b1) over the remaining axes in increasing order.
+template <int D, int K, int A>
+__device__ __forceinline__ int coef_index(int m, int b0, int b1) {
+    constexpr int N = K + 1;
+    if constexpr (D == 2) {
+        return A == 0 ? (m + N * b0) : (b0 + N * m);
+    } else {
+        if constexpr (A == 0) return m + N * (b0 + N * b1);
+        if constexpr (A == 1) return b0 + N * (m + N * b1);
+        return b0 + N * (b1 + N * m);
+    }
+}
+
+// Neighbour of element e across face f (0: low side, 1: high side) of axis
+// a; -1 on a non-periodic boundary.
+__device__ __forceinline__ long long neighbour(const Geo& g, long long e, int a, int f) {
+    long long ix = e % g.n[0];
+    long long r = e / g.n[0];
+    long long iy = r % g.n[1];
+    long long iz = r / g.n[1];
+    long long c[3] = {ix, iy, iz};
+    long long v = c[a] + (f ? 1 : -1);
+    if (v < 0 || v >= g.n[a]) {
+        if (!g.periodic[a]) return -1;
+        v = (v + g.n[a]) % g.n[a];
+    }
+    c[a] = v;
+    return c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+}
+
+// Manufactured solution U*_s = 1 + cos(2 pi x + phase_s) cos(pi y / Ly) e^{-t} / 2
+// and its forcing g = dU*/dt - (-div(F(U*) - A grad U*) + S(U*)), written out
+// by hand: for chi-type fluxes n kappa(c) grad c with kappa(c) = a / (c + b),
+// div(n kappa grad c) = kappa grad n . grad c + n kappa' |grad c|^2 + n kappa lap c.
+template <typename T>
+__device__ __forceinline__ void mms_forcing(T x, T y, T t, T Ly, const Coef& c, T g[NS]) {
+    const T pi = T(3.14159265358979323846);
+    const T et = exp(-t);
+    const T ky = pi / Ly;
+    const T Cy = cos(ky * y), Sy = sin(ky * y);
+    T u[NS], ux[NS], uy[NS], lap[NS];
+    for (int s = 0; s < NS; ++s) {
+        const T arg = T(2) * pi * x + T(c.phase[s]);
+        const T cx = cos(arg), sx = sin(arg);
+        u[s] = T(1) + T(0.5) * cx * Cy * et;
+        ux[s] = -pi * sx * Cy * et;
+        uy[s] = -T(0.5) * cx * ky * Sy * et;
+        lap[s] = -T(2) * pi * pi * cx * Cy * et - T(0.5) * cx * ky * ky * Cy * et;
+    }
+    auto div_chem = [&](int n, int cc, int j) -> T {
+        const T a = T(c.chi0[j]), b = T(c.chith[j]);
+        const T kap = a / (u[cc] + b);
+        const T dkap = -a / ((u[cc] + b) * (u[cc] + b));
+        const T gng = ux[n] * ux[cc] + uy[n] * uy[cc];
+        const T gg = ux[cc] * ux[cc] + uy[cc] * uy[cc];
+        return kap * gng + u[n] * dkap * gg + u[n] * kap * lap[cc];
+    };
+    T divF[NS] = {div_chem(0, 3, 0) + div_chem(0, 5, 1), div_chem(1, 3, 2) - div_chem(1, 0, 3), 0, 0, 0, 0};
+    const T n1 = u[0], n2 = u[1], n3 = u[2], c1 = u[3], c2 = u[4];
+    T S[NS];
+    S[0] = -T(c.d1) * n1;
+    S[1] = -T(c.d2) * n2;
+    S[2] = T(c.d1) * n1 + T(c.d2) * n2 - T(c.gamma) * n1;
+    S[3] = -T(c.alpha1) * n1 * c1 - T(c.alpha2) * n2 * c1 + T(c.f1) * n3;
+    S[4] = -T(c.k_ox) * c2;
+    S[5] = T(c.k_ox) * c2;
+    for (int s = 0; s < NS; ++s) {
+        const T ut = -(u[s] - T(1));
+        const T rhs = -divF[s] + T(c.A[s]) * lap[s] + S[s];
+        g[s] = ut - rhs;
+    }
+}
+
+}  // namespace cdg2

@@ -321,7 +321,13 @@ def face_residual(mesh: Mesh, U, p):
         UP = torch.einsum("pi,fsi->sfp", phiP, U[ep])
         GM = torch.einsum("jpi,fsi->sjfp", gradM, U[em])
         GP = torch.einsum("jpi,fsi->sjfp", gradP, U[ep])
-        Delta = UM - UP                                          # (6, F, P)
+        # The jump Delta = U^- - U^+ at each face point, summed over the basis
+        # as sum_i (phi_i^- U_i^- - phi_i^+ U_i^+): each basis function's two
+        # contributions are differenced before the sum, so the rounding error
+        # scales with the jump instead of with U (both traces are O(1) while
+        # the jump of a smooth field is tiny).
+        pair = phiM[None, None, :, :] * U[em][:, :, None, :] - phiP[None, None, :, :] * U[ep][:, :, None, :]
+        Delta = pair.sum(-1).permute(1, 0, 2)                    # (6, F, P)
 
         avg_dn = 0.5 * torch.einsum("j,sjfp->sfp", nvec, GM + GP)
         FnM = torch.einsum("j,sjfp->sfp", nvec, flux_F(UM, GM, p))

@@ -95,7 +95,13 @@ def test_apply_forcing_parity(G, k):
     ref = O.apply(om, U, p, forcing=lambda xx, tt: gx, t=t)
     out = torch.empty_like(U.cuda())
     G.cdg2_apply(gm, G.make_params(p, ph), U.cuda(), out, G.CDG2_MINV | G.CDG2_FORCING, t)
-    assert rel_l2_per_species(out, ref) <= FP64_TOL
+    # For the manufactured solution the forcing cancels most of L_h(U) (by up to
+    # 16x here), so the bar applies relative to the size of the terms, not of
+    # their sum: ||out - ref||_s <= tol * max(||ref||_s, ||M^-1 L_h(U)||_s).
+    lh = O.apply(om, U, p)
+    d = ((out.cpu().reshape(ref.shape) - ref) ** 2).sum(dim=(0, 2)).sqrt()
+    scale = torch.maximum((ref ** 2).sum(dim=(0, 2)).sqrt(), (lh ** 2).sum(dim=(0, 2)).sqrt())
+    assert float((d / scale).max()) <= FP64_TOL
 
 
 @pytest.mark.parametrize("cfg", [0, 1, 3])

@@ -113,6 +113,33 @@ int cdg2_mesh_info(const cdg2_mesh* mesh, long long* n_elem, int* n_basis, long 
 int cdg2_apply(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, void* out,
                int flags, double t, void* stream);
 
+/* Directional derivative of cdg2_apply (the Jacobian-vector product of the
+ * Jacobian-free Newton-Krylov solver, Sec. 3.2):
+ *   out = J(U) dU + (d f / d theta) dtheta,   f = M^{-1} L_h (CDG2_MINV) or L_h.
+ * Linearised pointwise terms: d|x|/dx = sign(x) with sign(0) = 0, the LLF
+ * maximum differentiated on the K^- side at a tie, H' = 0, and the forcing
+ * (independent of U) drops out.  theta = (d1, d2, gamma, alpha1, alpha2, f1,
+ * k_ox, beta1) (the reaction coefficients of Eq. (1) and the immune-cell
+ * inflow rate of Eq. (3)); dtheta is a HOST array of 8 doubles or NULL.
+ * U, dU, out: device [n_elem][6][n_basis], float64 or float32 (CDG2_FP32);
+ * out must not overlap U or dU.  t is accepted for symmetry and unused. */
+int cdg2_jvp(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, const void* dU,
+             const double* dtheta, void* out, int flags, double t, void* stream);
+
+/* Transpose of cdg2_jvp (vector-Jacobian product, for the adjoint of the
+ * implicit steps):
+ *   gU = J(U)^T lam,   gtheta = (d f / d theta)^T lam  (when gtheta != NULL),
+ * f = M^{-1} L_h (CDG2_MINV) or L_h, theta as in cdg2_jvp, same derivative
+ * conventions.  Each element gathers the adjoint contributions of its own
+ * volume and faces (no atomics); gtheta is reduced in a fixed order, so the
+ * result is bitwise reproducible.  U, lam, gU: device [n_elem][6][n_basis],
+ * float64 or float32 (CDG2_FP32; gtheta is float64 either way); gU must not
+ * overlap U or lam.  gtheta: DEVICE array of 8 doubles or NULL.  The first
+ * call with gtheta allocates a per-mesh workspace (8 doubles per CTA,
+ * cudaMalloc); calls sharing a mesh must then be ordered on one stream. */
+int cdg2_vjp(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, const void* lam, void* gU,
+             double* gtheta, int flags, double t, void* stream);
+
 /* Initial data: out = L2 projection onto V_h of
  *   u0_s(x) = floor_value + sum_b amps[s][b] exp(-|x - centres[s][b]|^2 / (2 sigma^2))
  * (Sec. 3.2: U(0) is the projection of U_0), distances taken as minimum

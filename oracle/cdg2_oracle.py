@@ -434,6 +434,13 @@ def jvp(mesh: Mesh, U, dU, params: dict):
     return torch.func.jvp(lambda V: apply(mesh, V, params), (U,), (dU,))[1]
 
 
+def jvp_theta(mesh: Mesh, U, dU, params: dict, theta_names, dtheta):
+    """J(U) dU + (df/dtheta) dtheta (torch.func forward mode over U and theta)."""
+    theta = torch.tensor([float(params[n]) for n in theta_names], dtype=F64)
+    dth = torch.as_tensor(dtheta, dtype=F64)
+    return torch.func.jvp(lambda V, th: apply_theta(mesh, V, params, theta_names, th), (U, theta), (dU, dth))[1]
+
+
 def vjp(mesh: Mesh, U, lam, params: dict, theta_names=()):
     """(J(U)^T lam, (df/dtheta)^T lam) via torch.func reverse mode."""
     theta = torch.tensor([float(params[n]) for n in theta_names], dtype=F64)

@@ -16,7 +16,7 @@ import torch
 __all__ = [
     "CDG2_MINV", "CDG2_FORCING", "CDG2_FP32", "Cdg2Error", "Mesh", "load_library", "library_path",
     "make_params", "cdg2_mesh_create", "cdg2_mesh_destroy", "cdg2_mesh_info", "cdg2_apply", "cdg2_last_error",
-    "cdg2_project_gaussians", "cdg2_project_mms",
+    "cdg2_project_gaussians", "cdg2_project_mms", "cdg2_jvp", "cdg2_vjp",
 ]
 
 CDG2_MINV = 1
@@ -88,6 +88,10 @@ def load_library():
     lib.cdg2_apply.argtypes = [vp, ctypes.POINTER(Params), vp, vp, i, d, vp]
     lib.cdg2_apply.restype = i
     dp = ctypes.POINTER(ctypes.c_double)
+    lib.cdg2_jvp.argtypes = [vp, ctypes.POINTER(Params), vp, vp, dp, vp, i, d, vp]
+    lib.cdg2_jvp.restype = i
+    lib.cdg2_vjp.argtypes = [vp, ctypes.POINTER(Params), vp, vp, vp, vp, i, d, vp]
+    lib.cdg2_vjp.restype = i
     lib.cdg2_project_gaussians.argtypes = [vp, i, dp, dp, d, d, vp, i, vp]
     lib.cdg2_project_gaussians.restype = i
     lib.cdg2_project_mms.argtypes = [vp, ctypes.POINTER(Params), d, vp, i, vp]
@@ -228,3 +232,38 @@ def cdg2_project_mms(mesh: Mesh, params, t: float, out: torch.Tensor, flags: int
     _check(load_library().cdg2_project_mms(mesh.handle, ctypes.byref(p), float(t), _dev(out, mesh, dt, "out"),
                                            int(flags), _stream_ptr(stream)))
     return out
+
+
+def _theta_ptr(dtheta):
+    if dtheta is None:
+        return None
+    vals = [float(v) for v in dtheta]
+    if len(vals) != 8:
+        raise ValueError("dtheta must hold 8 values (d1, d2, gamma, alpha1, alpha2, f1, k_ox, beta1)")
+    return (ctypes.c_double * 8)(*vals)
+
+
+def cdg2_jvp(mesh: Mesh, params, U: torch.Tensor, dU: torch.Tensor, out: torch.Tensor, flags: int = CDG2_MINV,
+             dtheta=None, t: float = 0.0, stream=None) -> torch.Tensor:
+    """out = J(U) dU (+ df/dtheta dtheta) on the given (default: current) stream."""
+    dt = torch.float32 if flags & CDG2_FP32 else torch.float64
+    p = _params(params)
+    _check(load_library().cdg2_jvp(mesh.handle, ctypes.byref(p), _dev(U, mesh, dt, "U"), _dev(dU, mesh, dt, "dU"),
+                                   _theta_ptr(dtheta), _dev(out, mesh, dt, "out"), int(flags), float(t),
+                                   _stream_ptr(stream)))
+    return out
+
+
+def cdg2_vjp(mesh: Mesh, params, U: torch.Tensor, lam: torch.Tensor, gU: torch.Tensor, gtheta: torch.Tensor = None,
+             flags: int = CDG2_MINV, t: float = 0.0, stream=None) -> torch.Tensor:
+    """gU = J(U)^T lam; gtheta (a CUDA float64 tensor of 8, optional) = (df/dtheta)^T lam."""
+    dt = torch.float32 if flags & CDG2_FP32 else torch.float64
+    gth = None
+    if gtheta is not None:
+        if not (gtheta.is_cuda and gtheta.dtype == torch.float64 and gtheta.numel() == 8 and gtheta.is_contiguous()):
+            raise ValueError("gtheta must be a contiguous CUDA float64 tensor of 8 values")
+        gth = ctypes.c_void_p(gtheta.data_ptr())
+    p = _params(params)
+    _check(load_library().cdg2_vjp(mesh.handle, ctypes.byref(p), _dev(U, mesh, dt, "U"), _dev(lam, mesh, dt, "lam"),
+                                   _dev(gU, mesh, dt, "gU"), gth, int(flags), float(t), _stream_ptr(stream)))
+    return gU

@@ -168,7 +168,11 @@ int cdg2_mesh_create(const cdg2_mesh_desc* d, cdg2_mesh** out) {
     return CDG2_OK;
 }
 
-void cdg2_mesh_destroy(cdg2_mesh* m) { delete m; }
+void cdg2_mesh_destroy(cdg2_mesh* m) {
+    if (!m) return;
+    if (m->theta_part) cudaFree(m->theta_part);   // synchronises work queued on it
+    delete m;
+}
 
 int cdg2_mesh_info(const cdg2_mesh* m, long long* n_elem, int* n_basis, long long* n_dof) {
     if (!m) {
@@ -198,6 +202,61 @@ int cdg2_apply(const cdg2_mesh* m, const cdg2_params* p, const void* U, void* ou
     Coef c = make_coef(*p);
     cudaError_t e = launch_apply(*m, c, U, out, flags, t, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cdg2_apply");
+    return CDG2_OK;
+}
+
+int cdg2_jvp(const cdg2_mesh* m, const cdg2_params* p, const void* U, const void* dU, const double* dtheta,
+             void* out, int flags, double t, void* stream) {
+    (void)t;   // the forcing does not depend on U or on the coefficients
+    if (!m || !p || !U || !dU || !out) {
+        set_error("cdg2_jvp: NULL argument");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (out == U || out == dU) {
+        set_error("cdg2_jvp: out must not overlap U or dU");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (flags & ~(CDG2_MINV | CDG2_FORCING | CDG2_FP32)) {
+        set_error("cdg2_jvp: unknown flag bits");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    Coef c = make_coef(*p);
+    cudaError_t e = launch_jvp(*m, c, U, dU, dtheta, out, flags, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cdg2_jvp");
+    return CDG2_OK;
+}
+
+int cdg2_vjp(const cdg2_mesh* m, const cdg2_params* p, const void* U, const void* lam, void* gU, double* gtheta,
+             int flags, double t, void* stream) {
+    (void)t;
+    if (!m || !p || !U || !lam || !gU) {
+        set_error("cdg2_vjp: NULL argument");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (gU == U || gU == lam) {
+        set_error("cdg2_vjp: gU must not overlap U or lam");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (flags & ~(CDG2_MINV | CDG2_FORCING | CDG2_FP32)) {
+        set_error("cdg2_vjp: unknown flag bits");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    double* part = nullptr;
+    if (gtheta) {
+        const long long need = vjp_grid(*m) * 8;
+        if (m->theta_part_n < need) {
+            if (m->theta_part) cudaFree(m->theta_part);
+            m->theta_part = nullptr;
+            m->theta_part_n = 0;
+            cudaError_t e = cudaMalloc(&m->theta_part, sizeof(double) * need);
+            if (e != cudaSuccess) return cuda_fail(e, "cdg2_vjp: workspace");
+            m->theta_part_n = need;
+        }
+        part = m->theta_part;
+    }
+    Coef c = make_coef(*p);
+    cudaError_t e = launch_vjp(*m, c, U, lam, gU, part, gtheta, flags, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cdg2_vjp");
     return CDG2_OK;
 }
 

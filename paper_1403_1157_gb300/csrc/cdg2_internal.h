@@ -55,6 +55,10 @@ struct cdg2_mesh {
     cdg2::Tab1D tab;
     int nb;            // basis per species per element
     long long ndof;
+    // Device workspace owned by the mesh, allocated on first use and freed by
+    // cdg2_mesh_destroy: per-CTA partial sums of the VJP's theta gradient.
+    mutable double* theta_part = nullptr;
+    mutable long long theta_part_n = 0;
 };
 
 namespace cdg2 {
@@ -62,8 +66,15 @@ namespace cdg2 {
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
-// Kernel launchers (apply.cu).  Return a cudaError_t of the launch.
+// Kernel launchers (operator.cu).  Return the cudaError_t of the launch.
 cudaError_t launch_apply(const cdg2_mesh& m, const Coef& c, const void* U, void* out, int flags, double t,
                          cudaStream_t stream);
+cudaError_t launch_jvp(const cdg2_mesh& m, const Coef& c, const void* U, const void* dU, const double* dtheta,
+                       void* out, int flags, cudaStream_t stream);
+// VJP: gU = (df/dU)^T lam; when gtheta is non-null also (df/dtheta)^T lam via
+// theta_part ([vjp_grid(m)][8] doubles of scratch) and a fixed-order reduction.
+cudaError_t launch_vjp(const cdg2_mesh& m, const Coef& c, const void* U, const void* lam, void* gU,
+                       double* theta_part, double* gtheta, int flags, cudaStream_t stream);
+long long vjp_grid(const cdg2_mesh& m);
 
 }  // namespace cdg2

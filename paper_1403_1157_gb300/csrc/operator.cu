@@ -1,0 +1,901 @@
+// Fused element-centric kernels for f(U) = M^{-1} L_h(U) (Sec. 3.1, Eq.
+// convDiscr; Sec. 3.2, Eq. ode) and its directional derivative J(U) dU
+// (the Jacobian-vector product of the Jacobian-free Newton-Krylov solver,
+// Sec. 3.2).
+//
+// One CTA owns EPB consecutive elements (a contiguous slab of U), computes
+// their volume integrals (Eq. elementint) with sum factorisation, then
+// visits their 2*dim faces: it evaluates its own trace and the neighbour's
+// trace (read from global memory, mostly L2 hits), forms the face fluxes of
+// Eq. surfaceint at every face point, tests them against its own basis and
+// accumulates.  Every interior face is thus evaluated by both adjacent
+// elements; in exchange there are no atomics, no face buffer in HBM and a
+// single pass over U and out.
+//
+// The kernel has three modes.  MODE 0 applies the operator to U.  MODE 1
+// (JVP) carries the primal field U and a tangent dU through the same
+// contraction passes and evaluates the linearised pointwise fluxes (the
+// contractions are linear, so only the pointwise terms change).  MODE 2
+// (VJP) carries U and the cotangent mu: interpolating mu with the forward
+// operators gives exactly the transposed test operators' inputs, the
+// pointwise maps are replaced by their adjoints, and testing the adjoints
+// gives (dR/dU)^T mu.  Each element gathers the adjoint contributions of its
+// own faces from both traces, so the transposed face scatter needs no atomics.
+//
+// The CDG2 lifting r_e on K^- is taken in closed form: on a Cartesian cell
+// with the orthonormal tensor basis and a Q_k trace Delta,
+//     r_e([U]) . n^- = -(k+1)^2 |e| / (2 |K^-|) Delta   on e,
+// because the lifting solve only needs the mass-inverse projection of Delta
+// onto the trace space of K^- (exact for a Q_k trace with k+2 Gauss points)
+// times sum_m psi_m(1)^2 = (k+1)^2 in the normal direction.
+#include <cstdio>
+
+#include "elem_common.cuh"
+
+namespace cdg2 {
+
+template <int D, int K, int F>
+struct OpPlan {
+    using S = Shape<D, K>;
+    static constexpr int NT = 128;
+    static constexpr int EPB = D == 3 ? (K == 1 ? 4 : (K == 2 ? 2 : 1)) : (F == 1 ? (K == 1 ? 16 : 8) : (K == 1 ? 8 : 4));
+    static constexpr int NB1 = S::NB1, NQ1 = S::NQ1;
+    // volume phase: per-field sizes for the whole CTA (all F input fields)
+    static constexpr int XSZ = F * EPB * NS * NQ1 * ipow(NB1, D - 1);
+    static constexpr int YSZ = D == 3 ? F * EPB * NS * NQ1 * NQ1 * NB1 : 0;
+    static constexpr int QSZ = F * EPB * NS * S::NQ;
+    static constexpr int VOL = (D + 1) * QSZ + 2 * XSZ + 3 * YSZ;
+    // face phase (the two faces normal to one axis)
+    static constexpr int FC = F * EPB * 2 * 4 * NS * S::NBT;
+    static constexpr int FT = D == 3 ? F * EPB * 2 * 4 * NS * NQ1 * NB1 : 0;
+    static constexpr int FP = F * EPB * 2 * 4 * NS * S::NQT;
+    static constexpr int FS = EPB * 2 * 2 * NS * S::NQT;
+    static constexpr int TS1 = D == 3 ? EPB * 2 * 2 * NS * NB1 * NQ1 : 0;
+    static constexpr int TS = EPB * 2 * 2 * NS * S::NBT;
+    static constexpr int FACE = FC + FT + FP + FS + TS1 + TS;
+    static constexpr int WORK = cmax(VOL, FACE);
+    static constexpr int UR = EPB * NS * S::NB;   // one field's slab
+    template <typename T>
+    static constexpr size_t tab_bytes() {
+        return (sizeof(STab<K, T>) + 15) / 16 * 16;
+    }
+    template <typename T>
+    static constexpr size_t smem_bytes() {
+        return tab_bytes<T>() + sizeof(T) * (size_t)((F + 1) * UR + WORK);
+    }
+};
+
+// Arguments of one launch.
+template <typename T>
+struct OpArgs {
+    const T* U[2];      // U, and the tangent dU when F = 2
+    T* out;
+    int flags;
+    double t;
+    int has_dtheta;
+    double dtheta[8];   // tangent of (d1, d2, gamma, alpha1, alpha2, f1, k_ox, beta1)
+    double* theta_part; // VJP: per-CTA partial sums of (df/dtheta)^T lambda, [gridDim.x][8], or null
+};
+
+constexpr int MODE_APPLY = 0, MODE_JVP = 1, MODE_VJP = 2;
+constexpr int fields_of(int mode) { return mode == MODE_APPLY ? 1 : 2; }
+
+// ---------------------------------------------------------------------------
+// Pointwise physics (Sec. 2)
+// ---------------------------------------------------------------------------
+
+// Volume flux at one quadrature point (Eq. elementint): Phi_s = F_s(U, grad U)
+// - A_s grad U_s and S(U) (Reading: the c1 row of S follows Eq. (1),
+// -alpha1 n1 c1 - alpha2 n2 c1 + f1 n3).
+template <int D, typename T>
+__device__ __forceinline__ void volume_point(const Coef& c, const T u[NS], const T g[NS][D], T Phi[NS][D],
+                                             T S[NS]) {
+    const T k11 = T(c.chi0[0]) / (u[3] + T(c.chith[0]));
+    const T k13 = T(c.chi0[1]) / (u[5] + T(c.chith[1]));
+    const T k21 = T(c.chi0[2]) / (u[3] + T(c.chith[2]));
+    const T k22 = T(c.chi0[3]) / (u[0] + T(c.chith[3]));
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const T v1 = k11 * g[3][j] + k13 * g[5][j];
+        const T v2 = k21 * g[3][j] - k22 * g[0][j];
+        Phi[0][j] = u[0] * v1 - T(c.A[0]) * g[0][j];
+        Phi[1][j] = u[1] * v2 - T(c.A[1]) * g[1][j];
+#pragma unroll
+        for (int s = 2; s < NS; ++s) Phi[s][j] = -T(c.A[s]) * g[s][j];
+    }
+    const T n1 = u[0], n2 = u[1], n3 = u[2], c1 = u[3], c2 = u[4];
+    S[0] = -T(c.d1) * n1;
+    S[1] = -T(c.d2) * n2;
+    S[2] = T(c.d1) * n1 + T(c.d2) * n2 - T(c.gamma) * n1;
+    S[3] = -T(c.alpha1) * n1 * c1 - T(c.alpha2) * n2 * c1 + T(c.f1) * n3;
+    S[4] = -T(c.k_ox) * c2;
+    S[5] = T(c.k_ox) * c2;
+}
+
+// Linearisation of volume_point along (du, dg), plus the derivative of S
+// along a tangent of the reaction coefficients (dth = d(d1, d2, gamma,
+// alpha1, alpha2, f1, k_ox, .)), when has_dth.  With kappa = a / (c + b):
+// d kappa = -kappa / (c + b) dc.
+template <int D, typename T>
+__device__ __forceinline__ void volume_point_lin(const Coef& c, const T u[NS], const T g[NS][D], const T du[NS],
+                                                 const T dg[NS][D], bool has_dth, const double* dth, T dPhi[NS][D],
+                                                 T dS[NS]) {
+    const T r11 = T(1) / (u[3] + T(c.chith[0]));
+    const T r13 = T(1) / (u[5] + T(c.chith[1]));
+    const T r21 = T(1) / (u[3] + T(c.chith[2]));
+    const T r22 = T(1) / (u[0] + T(c.chith[3]));
+    const T k11 = T(c.chi0[0]) * r11, k13 = T(c.chi0[1]) * r13;
+    const T k21 = T(c.chi0[2]) * r21, k22 = T(c.chi0[3]) * r22;
+    const T dk11 = -k11 * r11 * du[3], dk13 = -k13 * r13 * du[5];
+    const T dk21 = -k21 * r21 * du[3], dk22 = -k22 * r22 * du[0];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const T v1 = k11 * g[3][j] + k13 * g[5][j];
+        const T v2 = k21 * g[3][j] - k22 * g[0][j];
+        const T dv1 = dk11 * g[3][j] + k11 * dg[3][j] + dk13 * g[5][j] + k13 * dg[5][j];
+        const T dv2 = dk21 * g[3][j] + k21 * dg[3][j] - dk22 * g[0][j] - k22 * dg[0][j];
+        dPhi[0][j] = du[0] * v1 + u[0] * dv1 - T(c.A[0]) * dg[0][j];
+        dPhi[1][j] = du[1] * v2 + u[1] * dv2 - T(c.A[1]) * dg[1][j];
+#pragma unroll
+        for (int s = 2; s < NS; ++s) dPhi[s][j] = -T(c.A[s]) * dg[s][j];
+    }
+    dS[0] = -T(c.d1) * du[0];
+    dS[1] = -T(c.d2) * du[1];
+    dS[2] = T(c.d1) * du[0] + T(c.d2) * du[1] - T(c.gamma) * du[0];
+    dS[3] = -T(c.alpha1) * (du[0] * u[3] + u[0] * du[3]) - T(c.alpha2) * (du[1] * u[3] + u[1] * du[3]) +
+            T(c.f1) * du[2];
+    dS[4] = -T(c.k_ox) * du[4];
+    dS[5] = T(c.k_ox) * du[4];
+    if (has_dth) {
+        const T n1 = u[0], n2 = u[1], n3 = u[2], c1 = u[3], c2 = u[4];
+        dS[0] += -T(dth[0]) * n1;
+        dS[1] += -T(dth[1]) * n2;
+        dS[2] += T(dth[0]) * n1 + T(dth[1]) * n2 - T(dth[2]) * n1;
+        dS[3] += -T(dth[3]) * n1 * c1 - T(dth[4]) * n2 * c1 + T(dth[5]) * n3;
+        dS[4] += -T(dth[6]) * c2;
+        dS[5] += T(dth[6]) * c2;
+    }
+}
+
+// Interior-face flux at one face point (Eq. surfaceint), n^- = +e_a, with the
+// jump Delta = U^- - U^+ passed in (formed from coefficient differences):
+//   sigma_s = A_s {d_n U_s} - F^_s.n^- + A^_s.n^-   (multiplies phi^- - phi^+)
+//   tau_s   = A_s Delta_s / 2                       (multiplies d_n phi^- + d_n phi^+)
+// F^ local Lax-Friedrichs with lambda_s = max(|v_s^-.n|, |v_s^+.n|);
+// A^ = 2 chi_e A r_e on K^-, r_e.n^- = -(k+1)^2 Delta / (2 h_a).
+template <typename T>
+__device__ __forceinline__ void face_point(const Coef& c, T pen, const T uM[NS], const T dM[NS], const T uP[NS],
+                                           const T dP[NS], const T del[NS], T sig[NS], T tau[NS]) {
+    T Fh[2];
+    {
+        const T vM = T(c.chi0[0]) / (uM[3] + T(c.chith[0])) * dM[3] + T(c.chi0[1]) / (uM[5] + T(c.chith[1])) * dM[5];
+        const T vP = T(c.chi0[0]) / (uP[3] + T(c.chith[0])) * dP[3] + T(c.chi0[1]) / (uP[5] + T(c.chith[1])) * dP[5];
+        const T lam = fmax(fabs(vM), fabs(vP));
+        Fh[0] = T(0.5) * (uM[0] * vM + uP[0] * vP) + T(0.5) * lam * del[0];
+    }
+    {
+        const T vM = T(c.chi0[2]) / (uM[3] + T(c.chith[2])) * dM[3] - T(c.chi0[3]) / (uM[0] + T(c.chith[3])) * dM[0];
+        const T vP = T(c.chi0[2]) / (uP[3] + T(c.chith[2])) * dP[3] - T(c.chi0[3]) / (uP[0] + T(c.chith[3])) * dP[0];
+        const T lam = fmax(fabs(vM), fabs(vP));
+        Fh[1] = T(0.5) * (uM[1] * vM + uP[1] * vP) + T(0.5) * lam * del[1];
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const T A = T(c.A[s]);
+        T sg = A * T(0.5) * (dM[s] + dP[s]) - pen * A * del[s];
+        if (s < 2) sg -= Fh[s];
+        sig[s] = sg;
+        tau[s] = T(0.5) * A * del[s];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T sgn0(T x) {
+    return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0));
+}
+
+// One side's chemotactic normal velocity of species 0 or 1 and its derivative:
+// v_0 = kappa11(c1) d_n c1 + kappa13(c3) d_n c3,  v_1 = kappa21(c1) d_n c1 - kappa22(n1) d_n n1.
+template <typename T>
+__device__ __forceinline__ void velocity_lin(const Coef& c, int sp, const T u[NS], const T dn[NS], const T du[NS],
+                                             const T ddn[NS], T& v, T& dv) {
+    if (sp == 0) {
+        const T r1 = T(1) / (u[3] + T(c.chith[0])), r3 = T(1) / (u[5] + T(c.chith[1]));
+        const T k1 = T(c.chi0[0]) * r1, k3 = T(c.chi0[1]) * r3;
+        v = k1 * dn[3] + k3 * dn[5];
+        dv = -k1 * r1 * du[3] * dn[3] + k1 * ddn[3] - k3 * r3 * du[5] * dn[5] + k3 * ddn[5];
+    } else {
+        const T r1 = T(1) / (u[3] + T(c.chith[2])), r0 = T(1) / (u[0] + T(c.chith[3]));
+        const T k1 = T(c.chi0[2]) * r1, k0 = T(c.chi0[3]) * r0;
+        v = k1 * dn[3] - k0 * dn[0];
+        dv = -k1 * r1 * du[3] * dn[3] + k1 * ddn[3] + k0 * r0 * du[0] * dn[0] - k0 * ddn[0];
+    }
+}
+
+// Linearisation of face_point along the tangent traces.  Reading: d|x|/dx =
+// sign(x) with sign(0) = 0; at a tie |v^-| = |v^+| the K^- side is taken.
+template <typename T>
+__device__ __forceinline__ void face_point_lin(const Coef& c, T pen, const T uM[NS], const T dM[NS], const T uP[NS],
+                                               const T dP[NS], const T del[NS], const T duM[NS], const T ddM[NS],
+                                               const T duP[NS], const T ddP[NS], const T ddel[NS], T dsig[NS],
+                                               T dtau[NS]) {
+    T dFh[2];
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+        T vM, dvM, vP, dvP;
+        velocity_lin<T>(c, sp, uM, dM, duM, ddM, vM, dvM);
+        velocity_lin<T>(c, sp, uP, dP, duP, ddP, vP, dvP);
+        const T aM = fabs(vM), aP = fabs(vP);
+        const bool takeM = aM >= aP;
+        const T lam = takeM ? aM : aP;
+        const T dlam = takeM ? sgn0(vM) * dvM : sgn0(vP) * dvP;
+        dFh[sp] = T(0.5) * (duM[sp] * vM + uM[sp] * dvM + duP[sp] * vP + uP[sp] * dvP) +
+                  T(0.5) * (dlam * del[sp] + lam * ddel[sp]);
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const T A = T(c.A[s]);
+        T sg = A * T(0.5) * (ddM[s] + ddP[s]) - pen * A * ddel[s];
+        if (s < 2) sg -= dFh[s];
+        dsig[s] = sg;
+        dtau[s] = T(0.5) * A * ddel[s];
+    }
+}
+
+// Adjoint of volume_point: given the weighted cotangents sb = W mu (of S) and
+// gb[s][j] = W d_j mu (of Phi_s,j), the cotangents of the inputs,
+//   ub_t = sum_s sb_s dS_s/du_t + sum_{s,j} gb_sj dPhi_sj/du_t,
+//   Gb_tj = sum_s gb_sj dPhi_sj/dg_tj,
+// and th[0..6] += the cotangents of (d1, d2, gamma, alpha1, alpha2, f1, k_ox).
+template <int D, typename T>
+__device__ __forceinline__ void volume_point_adj(const Coef& c, const T u[NS], const T g[NS][D], const T sb[NS],
+                                                 const T gb[NS][D], T ub[NS], T Gb[NS][D], double th[8]) {
+    const T r11 = T(1) / (u[3] + T(c.chith[0]));
+    const T r13 = T(1) / (u[5] + T(c.chith[1]));
+    const T r21 = T(1) / (u[3] + T(c.chith[2]));
+    const T r22 = T(1) / (u[0] + T(c.chith[3]));
+    const T k11 = T(c.chi0[0]) * r11, k13 = T(c.chi0[1]) * r13;
+    const T k21 = T(c.chi0[2]) * r21, k22 = T(c.chi0[3]) * r22;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) ub[s] = T(0);
+    T kb11 = 0, kb13 = 0, kb21 = 0, kb22 = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const T v1 = k11 * g[3][j] + k13 * g[5][j];
+        const T v2 = k21 * g[3][j] - k22 * g[0][j];
+        ub[0] += gb[0][j] * v1;
+        ub[1] += gb[1][j] * v2;
+        const T vb1 = gb[0][j] * u[0];
+        const T vb2 = gb[1][j] * u[1];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) Gb[s][j] = -T(c.A[s]) * gb[s][j];
+        Gb[3][j] += vb1 * k11 + vb2 * k21;
+        Gb[5][j] += vb1 * k13;
+        Gb[0][j] -= vb2 * k22;
+        kb11 += vb1 * g[3][j];
+        kb13 += vb1 * g[5][j];
+        kb21 += vb2 * g[3][j];
+        kb22 -= vb2 * g[0][j];
+    }
+    ub[3] += -k11 * r11 * kb11 - k21 * r21 * kb21;
+    ub[5] += -k13 * r13 * kb13;
+    ub[0] += -k22 * r22 * kb22;
+    // reaction source
+    ub[0] += -T(c.d1) * sb[0] + (T(c.d1) - T(c.gamma)) * sb[2] - T(c.alpha1) * u[3] * sb[3];
+    ub[1] += -T(c.d2) * sb[1] + T(c.d2) * sb[2] - T(c.alpha2) * u[3] * sb[3];
+    ub[2] += T(c.f1) * sb[3];
+    ub[3] += (-T(c.alpha1) * u[0] - T(c.alpha2) * u[1]) * sb[3];
+    ub[4] += -T(c.k_ox) * sb[4] + T(c.k_ox) * sb[5];
+    th[0] += double(u[0] * (sb[2] - sb[0]));
+    th[1] += double(u[1] * (sb[2] - sb[1]));
+    th[2] += double(-u[0] * sb[2]);
+    th[3] += double(-u[0] * u[3] * sb[3]);
+    th[4] += double(-u[1] * u[3] * sb[3]);
+    th[5] += double(u[2] * sb[3]);
+    th[6] += double(u[4] * (sb[5] - sb[4]));
+}
+
+// Adjoint of face_point with respect to the traces of one side X (the own
+// cell: K^- when ownM, else K^+), given the cotangents sb = W (mu^- - mu^+)
+// of sigma and tb = W (d_n mu^- + d_n mu^+) of tau.  Returns the cotangents
+// of X's value trace (ub) and normal-derivative trace (db).  Delta depends on
+// both sides: dDelta/du^X = +1 for K^-, -1 for K^+.  Same derivative
+// conventions as face_point_lin.
+template <typename T>
+__device__ __forceinline__ void face_point_adj(const Coef& c, T pen, bool ownM, const T uM[NS], const T dM[NS],
+                                               const T uP[NS], const T dP[NS], const T del[NS], const T sb[NS],
+                                               const T tb[NS], T ub[NS], T db[NS]) {
+    const T sX = ownM ? T(1) : T(-1);
+    const T* uX = ownM ? uM : uP;
+    const T* dX = ownM ? dM : dP;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        ub[s] = sX * T(c.A[s]) * (T(0.5) * tb[s] - pen * sb[s]);
+        db[s] = T(0.5) * T(c.A[s]) * sb[s];
+    }
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+        T vM, vP, dummy;
+        const T zero[NS] = {0, 0, 0, 0, 0, 0};
+        velocity_lin<T>(c, sp, uM, dM, zero, zero, vM, dummy);
+        velocity_lin<T>(c, sp, uP, dP, zero, zero, vP, dummy);
+        const bool takeM = fabs(vM) >= fabs(vP);
+        const T lam = takeM ? fabs(vM) : fabs(vP);
+        const T vX = ownM ? vM : vP;
+        const bool fromX = ownM ? takeM : !takeM;
+        const T Fb = -sb[sp];                       // sigma_sp contains -F^_sp
+        ub[sp] += Fb * (T(0.5) * vX + T(0.5) * lam * sX);
+        const T vb = Fb * (T(0.5) * uX[sp] + (fromX ? T(0.5) * del[sp] * sgn0(vX) : T(0)));
+        if (sp == 0) {
+            const T r1 = T(1) / (uX[3] + T(c.chith[0])), r3 = T(1) / (uX[5] + T(c.chith[1]));
+            const T k1 = T(c.chi0[0]) * r1, k3 = T(c.chi0[1]) * r3;
+            ub[3] += vb * (-k1 * r1 * dX[3]);
+            ub[5] += vb * (-k3 * r3 * dX[5]);
+            db[3] += vb * k1;
+            db[5] += vb * k3;
+        } else {
+            const T r1 = T(1) / (uX[3] + T(c.chith[2])), r0 = T(1) / (uX[0] + T(c.chith[3]));
+            const T k1 = T(c.chi0[2]) * r1, k0 = T(c.chi0[3]) * r0;
+            ub[3] += vb * (-k1 * r1 * dX[3]);
+            ub[0] += vb * (k0 * r0 * dX[0]);
+            db[3] += vb * k1;
+            db[0] -= vb * k0;
+        }
+    }
+}
+
+// Boundary data of Eq. (3) at one face point of the own cell (Reading: the
+// normal is inward, so the data are influxes times bc_sign):
+// Gamma_1 (y = 0): n1 mu1 beta1 H(c1 - c1*), c2 nu2 sigma on Gamma_{1,in};
+// Gamma_2 (y = L1): n2 mu2 beta2 H(c1 - c1**).  H(0) = 0.  With beta1 scaled
+// by `b1` (1 for the data, the tangent d beta1 for their derivative).
+template <typename T>
+__device__ __forceinline__ void boundary_point(const Coef& c, int f, T x, const Geo& g, const T uo[NS], T sig[NS],
+                                               T b1, bool other_terms) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) sig[s] = T(0);
+    const T bs = T(c.bc_sign);
+    if (f == 0) {
+        sig[0] = (uo[3] - T(c.c1s) > T(0)) ? bs * T(c.A[0]) * b1 : T(0);
+        if (other_terms)
+            sig[4] = (x >= T(g.g1in[0]) && x <= T(g.g1in[1])) ? bs * T(c.A[4]) * T(c.sigma) : T(0);
+    } else if (other_terms) {
+        sig[1] = (uo[3] - T(c.c1ss) > T(0)) ? bs * T(c.A[1]) * T(c.beta2) : T(0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The two faces normal to axis A of every element of the CTA
+// ---------------------------------------------------------------------------
+template <int D, int K, int MODE, int A, typename T>
+__device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, const Coef& c, const OpArgs<T>& args,
+                                         const T* sU, T* sR, T* W, long long e0, long long (*nbr)[2],
+                                         double th[8]) {
+    constexpr int F = fields_of(MODE);
+    using P = OpPlan<D, K, F>;
+    using S = Shape<D, K>;
+    constexpr int EPB = P::EPB, NB = S::NB, NB1 = S::NB1, NQ1 = S::NQ1, NBT = S::NBT, NQT = S::NQT;
+    T* FC = W;
+    T* FT = FC + P::FC;
+    T* FP = FT + P::FT;
+    T* FS = FP + P::FP;
+    T* TS1 = FS + P::FS;
+    T* TS = TS1 + P::TS1;
+    const T invh = T(1.0 / g.h[A]);
+
+    if (threadIdx.x < EPB * 2) {
+        const int e = threadIdx.x / 2, f = threadIdx.x % 2;
+        const long long ge = e0 + e;
+        nbr[e][f] = ge < g.E ? neighbour(g, ge, A, f) : -1;
+    }
+    __syncthreads();
+
+    // Normal contraction.  Fields per (input field, face, species, tangential mode):
+    //   0: own trace at xi_A = f,  1: jump Delta = U^- - U^+,
+    //   2: own normal derivative,  3: neighbour normal derivative (at xi_A = 1 - f).
+    // The jump is formed difference-first, (U^-_0 - U^+_0) + sum_{m>0} (psi_m(1) U^-_m - psi_m(0) U^+_m),
+    // so the rounding error scales with Delta rather than with U (this matters in FP32).
+    for (int idx = threadIdx.x; idx < F * EPB * 2 * NS * NBT; idx += blockDim.x) {
+        const int t = idx % NBT;
+        const int s = (idx / NBT) % NS;
+        const int f = (idx / (NBT * NS)) % 2;
+        const int e = (idx / (NBT * NS * 2)) % EPB;
+        const int fi = idx / (NBT * NS * 2 * EPB);
+        const int b0 = t % NB1, b1 = t / NB1;
+        const T* own = sU + fi * P::UR + (e * NS + s) * NB;
+        T uo = 0, dO = 0, del = 0, dn = 0;
+#pragma unroll
+        for (int m = 0; m < NB1; ++m) {
+            const T v = own[coef_index<D, K, A>(m, b0, b1)];
+            uo = fma(tb.e[f][m], v, uo);
+            dO = fma(tb.d[f][m], v, dO);
+        }
+        const long long nb = nbr[e][f];
+        if (nb >= 0) {
+            const T* nbp = args.U[fi] + (nb * NS + s) * NB;
+            const T* um = f ? own : nbp;     // K^- coefficients
+            const T* up = f ? nbp : own;     // K^+ coefficients
+            del = um[coef_index<D, K, A>(0, b0, b1)] - up[coef_index<D, K, A>(0, b0, b1)];
+#pragma unroll
+            for (int m = 1; m < NB1; ++m) {
+                const int ci = coef_index<D, K, A>(m, b0, b1);
+                del = fma(tb.e[1][m], um[ci], del);
+                del = fma(-tb.e[0][m], up[ci], del);
+            }
+#pragma unroll
+            for (int m = 0; m < NB1; ++m) dn = fma(tb.d[1 - f][m], nbp[coef_index<D, K, A>(m, b0, b1)], dn);
+        }
+        T* o = FC + (((fi * EPB + e) * 2 + f) * 4) * NS * NBT + s * NBT + t;
+        o[0 * NS * NBT] = uo;
+        o[1 * NS * NBT] = del;
+        o[2 * NS * NBT] = dO * invh;
+        o[3 * NS * NBT] = dn * invh;
+    }
+    __syncthreads();
+
+    // tangential interpolation to the face points
+    if constexpr (D == 2) {
+        sf_pass<0, NB1, 1, 1, NQ1, false, K + 1, false>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FP, NQT,
+                                                         F * EPB * 2 * 4 * NS);
+    } else {
+        sf_pass<0, NB1, NB1, 1, NQ1, false, K + 1, false>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT, NQ1 * NB1,
+                                                           F * EPB * 2 * 4 * NS);
+        __syncthreads();
+        sf_pass<1, NQ1, NB1, 1, NQ1, false, K + 1, false>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, FP, NQT,
+                                                           F * EPB * 2 * 4 * NS);
+    }
+    __syncthreads();
+
+    // pointwise fluxes, weighted: W_p = w_p |e|, |e| = |K| / h_A
+    const T pen = T(g.chi_e) * T((K + 1) * (K + 1)) * invh;
+    for (int idx = threadIdx.x; idx < EPB * 2 * NQT; idx += blockDim.x) {
+        const int p = idx % NQT;
+        const int f = (idx / NQT) % 2;
+        const int e = idx / (NQT * 2);
+        T uo[NS], del[NS], dO[NS], dn[NS], sig[NS], tau[NS];
+        {
+            const T* base = FP + ((e * 2 + f) * 4) * NS * NQT + p;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                uo[s] = base[(0 * NS + s) * NQT];
+                del[s] = base[(1 * NS + s) * NQT];
+                dO[s] = base[(2 * NS + s) * NQT];
+                dn[s] = base[(3 * NS + s) * NQT];
+            }
+        }
+        const int p0 = p % NQ1, p1 = p / NQ1;
+        T wp = tb.w[p0];
+        if constexpr (D == 3) wp *= tb.w[p1];
+        const T Wp = wp * T(g.vol) * invh;
+        const long long nb = nbr[e][f];
+        if (nb >= 0) {
+            T uN[NS];   // neighbour trace recovered from the jump
+#pragma unroll
+            for (int s = 0; s < NS; ++s) uN[s] = f == 1 ? uo[s] - del[s] : uo[s] + del[s];
+            if constexpr (MODE == MODE_APPLY) {
+                if (f == 1)
+                    face_point<T>(c, pen, uo, dO, uN, dn, del, sig, tau);
+                else
+                    face_point<T>(c, pen, uN, dn, uo, dO, del, sig, tau);
+            } else if constexpr (MODE == MODE_VJP) {
+                // cotangents of sigma and tau from the traces of mu (second field)
+                T sb[NS], tbr[NS];
+                const T* base = FP + (((EPB + e) * 2 + f) * 4) * NS * NQT + p;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    sb[s] = Wp * base[(1 * NS + s) * NQT];
+                    tbr[s] = Wp * (base[(2 * NS + s) * NQT] + base[(3 * NS + s) * NQT]);
+                }
+                if (f == 1)
+                    face_point_adj<T>(c, pen, true, uo, dO, uN, dn, del, sb, tbr, sig, tau);
+                else
+                    face_point_adj<T>(c, pen, false, uN, dn, uo, dO, del, sb, tbr, sig, tau);
+            } else {
+                T tuo[NS], tdel[NS], tdO[NS], tdn[NS], tuN[NS];
+                const T* base = FP + (((EPB + e) * 2 + f) * 4) * NS * NQT + p;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    tuo[s] = base[(0 * NS + s) * NQT];
+                    tdel[s] = base[(1 * NS + s) * NQT];
+                    tdO[s] = base[(2 * NS + s) * NQT];
+                    tdn[s] = base[(3 * NS + s) * NQT];
+                    tuN[s] = f == 1 ? tuo[s] - tdel[s] : tuo[s] + tdel[s];
+                }
+                if (f == 1)
+                    face_point_lin<T>(c, pen, uo, dO, uN, dn, del, tuo, tdO, tuN, tdn, tdel, sig, tau);
+                else
+                    face_point_lin<T>(c, pen, uN, dn, uo, dO, del, tuN, tdn, tuo, tdO, tdel, sig, tau);
+            }
+            if constexpr (MODE != MODE_VJP) {
+                const T sgn = f == 1 ? T(1) : T(-1);
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    sig[s] = sgn * Wp * sig[s];
+                    tau[s] = Wp * tau[s];
+                }
+            }
+        } else {
+            if (A == 1) {
+                const long long ge = e0 + e;
+                const T x = T((ge % g.n[0]) * g.h[0]) + T(g.h[0]) * tb.xi[p0];
+                if constexpr (MODE == MODE_APPLY) {
+                    boundary_point<T>(c, f, x, g, uo, sig, T(c.beta1), true);
+                } else if constexpr (MODE == MODE_JVP) {
+                    // H' = 0: only a tangent of beta1 moves the boundary data
+                    boundary_point<T>(c, f, x, g, uo, sig, args.has_dtheta ? T(args.dtheta[7]) : T(0), false);
+                } else {
+                    // H' = 0: the boundary data do not depend on U; their beta1
+                    // derivative, tested with mu's own trace, feeds the theta gradient
+                    boundary_point<T>(c, f, x, g, uo, sig, T(1), false);
+                    const T* base = FP + (((EPB + e) * 2 + f) * 4) * NS * NQT + p;
+                    th[7] += double(Wp * sig[0] * base[0]);
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) sig[s] = T(0);
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < NS; ++s) sig[s] = T(0);
+            }
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                sig[s] = Wp * sig[s];
+                tau[s] = T(0);
+            }
+        }
+        T* o = FS + ((e * 2 + f) * 2) * NS * NQT + p;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            o[(0 * NS + s) * NQT] = sig[s];
+            o[(1 * NS + s) * NQT] = tau[s];
+        }
+    }
+    __syncthreads();
+
+    // tangential test against the own basis
+    if constexpr (D == 2) {
+        sf_pass<0, NQ1, 1, 1, NB1, true, K + 1, false>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS, NBT,
+                                                        EPB * 2 * 2 * NS);
+    } else {
+        sf_pass<0, NQ1, NQ1, 1, NB1, true, K + 1, false>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1, NB1 * NQ1,
+                                                          EPB * 2 * 2 * NS);
+        __syncthreads();
+        sf_pass<1, NB1, NQ1, 1, NB1, true, K + 1, false>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1, TS, NBT,
+                                                          EPB * 2 * 2 * NS);
+    }
+    __syncthreads();
+
+    // normal expansion: phi_i = psi_{i_A}(f) (tangential part), d_A phi_i = psi'_{i_A}(f) / h_A (...)
+    for (int idx = threadIdx.x; idx < EPB * NS * NB; idx += blockDim.x) {
+        const int i = idx % NB;
+        const int es = idx / NB;          // e * NS + s
+        const int e = es / NS, s = es % NS;
+        int m, t;
+        if constexpr (D == 2) {
+            m = A == 0 ? i % NB1 : i / NB1;
+            t = A == 0 ? i / NB1 : i % NB1;
+        } else {
+            if constexpr (A == 0) {
+                m = i % NB1;
+                t = i / NB1;
+            } else if constexpr (A == 1) {
+                m = (i / NB1) % NB1;
+                t = i % NB1 + NB1 * (i / (NB1 * NB1));
+            } else {
+                m = i / (NB1 * NB1);
+                t = i % (NB1 * NB1);
+            }
+        }
+        T acc = sR[idx];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const T* ts = TS + ((e * 2 + f) * 2) * NS * NBT + s * NBT + t;
+            acc = fma(tb.e[f][m], ts[0], acc);
+            acc = fma(tb.d[f][m] * invh, ts[NS * NBT], acc);
+        }
+        sR[idx] = acc;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// The kernel
+// ---------------------------------------------------------------------------
+template <int D, int K, int MODE, typename T>
+__global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, const Coef c, const OpArgs<T> args) {
+    constexpr int F = fields_of(MODE);
+    using P = OpPlan<D, K, F>;
+    using S = Shape<D, K>;
+    constexpr int EPB = P::EPB, NB = S::NB, NQ = S::NQ, NB1 = S::NB1, NQ1 = S::NQ1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    STab<K, T>& tb = *reinterpret_cast<STab<K, T>*>(smem_raw);
+    T* sU = reinterpret_cast<T*>(smem_raw + P::template tab_bytes<T>());   // F slabs
+    T* sR = sU + F * P::UR;
+    T* W = sR + P::UR;
+    __shared__ long long nbr[EPB][2];
+
+    const long long e0 = (long long)blockIdx.x * EPB;
+    double th[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // VJP: this thread's theta cotangent partials
+    load_tab<K, T>(tb, tab);
+    for (int i = threadIdx.x; i < F * P::UR; i += blockDim.x) {
+        const int fi = i / P::UR, r = i % P::UR;
+        const long long ge = e0 + r / (NS * NB);
+        sU[i] = ge < g.E ? args.U[fi][e0 * NS * NB + r] : T(0);
+    }
+    __syncthreads();
+
+    // ---- volume: U, grad U (of every input field) at the Gauss points ----
+    T* X0 = W;
+    T* X1 = X0 + P::XSZ;
+    T* Y = X1 + P::XSZ;
+    T* Q = Y + 3 * P::YSZ;   // D + 1 slots of F*EPB*NS tensors: u, g_0, .., g_{D-1}
+    const int nt = F * EPB * NS;
+    if constexpr (D == 2) {
+        sf_pass<0, NB1, NB1, 1, NQ1, false, K + 1, false>(sU, &tb.B[0][0], nullptr, nullptr, NB, X0, NQ1 * NB1, nt);
+        sf_pass<0, NB1, NB1, 1, NQ1, false, K + 1, false>(sU, &tb.D[0][0], nullptr, nullptr, NB, X1, NQ1 * NB1, nt);
+        __syncthreads();
+        sf_pass<1, NQ1, NB1, 1, NQ1, false, K + 1, false>(X0, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, Q, NQ, nt);
+        sf_pass<1, NQ1, NB1, 1, NQ1, false, K + 1, false>(X1, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1,
+                                                           Q + P::QSZ, NQ, nt);
+        sf_pass<1, NQ1, NB1, 1, NQ1, false, K + 1, false>(X0, &tb.D[0][0], nullptr, nullptr, NQ1 * NB1,
+                                                           Q + 2 * P::QSZ, NQ, nt);
+    } else {
+        constexpr int XS = NQ1 * NB1 * NB1, YS = NQ1 * NQ1 * NB1;
+        sf_pass<0, NB1, NB1, NB1, NQ1, false, K + 1, false>(sU, &tb.B[0][0], nullptr, nullptr, NB, X0, XS, nt);
+        sf_pass<0, NB1, NB1, NB1, NQ1, false, K + 1, false>(sU, &tb.D[0][0], nullptr, nullptr, NB, X1, XS, nt);
+        __syncthreads();
+        sf_pass<1, NQ1, NB1, NB1, NQ1, false, K + 1, false>(X0, &tb.B[0][0], nullptr, nullptr, XS, Y, YS, nt);
+        sf_pass<1, NQ1, NB1, NB1, NQ1, false, K + 1, false>(X1, &tb.B[0][0], nullptr, nullptr, XS, Y + P::YSZ, YS,
+                                                             nt);
+        sf_pass<1, NQ1, NB1, NB1, NQ1, false, K + 1, false>(X0, &tb.D[0][0], nullptr, nullptr, XS,
+                                                             Y + 2 * P::YSZ, YS, nt);
+        __syncthreads();
+        sf_pass<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false>(Y, &tb.B[0][0], nullptr, nullptr, YS, Q, NQ, nt);
+        sf_pass<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false>(Y + P::YSZ, &tb.B[0][0], nullptr, nullptr, YS,
+                                                             Q + P::QSZ, NQ, nt);
+        sf_pass<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false>(Y + 2 * P::YSZ, &tb.B[0][0], nullptr, nullptr, YS,
+                                                             Q + 2 * P::QSZ, NQ, nt);
+        sf_pass<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false>(Y, &tb.D[0][0], nullptr, nullptr, YS, Q + 3 * P::QSZ,
+                                                             NQ, nt);
+    }
+    __syncthreads();
+
+    // ---- volume: pointwise fluxes, weighted by w_q |K| (and 1/h_j for gradients) ----
+    // The result goes to the slots of the last input field (the only one tested).
+    const T invh[3] = {T(1.0 / g.h[0]), T(1.0 / g.h[1]), T(1.0 / g.h[2])};
+    constexpr int OFF = (F - 1) * EPB * NS * NQ;
+    for (int idx = threadIdx.x; idx < EPB * NQ; idx += blockDim.x) {
+        const int q = idx % NQ, e = idx / NQ;
+        T u[NS], gr[NS][D], Phi[NS][D], Sr[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            u[s] = Q[(e * NS + s) * NQ + q];
+#pragma unroll
+            for (int j = 0; j < D; ++j) gr[s][j] = Q[(j + 1) * P::QSZ + (e * NS + s) * NQ + q] * invh[j];
+        }
+        const int q0 = q % NQ1, q1 = (q / NQ1) % NQ1, q2 = q / (NQ1 * NQ1);
+        T wq = tb.w[q0] * tb.w[q1];
+        if constexpr (D == 3) wq *= tb.w[q2];
+        const T Wq = wq * T(g.vol);
+        if constexpr (MODE == MODE_APPLY) {
+            volume_point<D, T>(c, u, gr, Phi, Sr);
+        } else {
+            T du[NS], dg[NS][D];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                du[s] = Q[OFF + (e * NS + s) * NQ + q];
+#pragma unroll
+                for (int j = 0; j < D; ++j) dg[s][j] = Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q] * invh[j];
+            }
+            if constexpr (MODE == MODE_JVP) {
+                volume_point_lin<D, T>(c, u, gr, du, dg, args.has_dtheta != 0, args.dtheta, Phi, Sr);
+            } else {
+                // du, dg are mu and grad mu here; weighted they are the cotangents of S and Phi
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    du[s] *= Wq;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) dg[s][j] *= Wq;
+                }
+                // (padding elements of a ragged last CTA hold mu = 0 and add nothing)
+                volume_point_adj<D, T>(c, u, gr, du, dg, Sr, Phi, th);
+                // the adjoints are already weighted: store them unscaled (gradients / h_j for the test)
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    Q[OFF + (e * NS + s) * NQ + q] = Sr[s];
+#pragma unroll
+                    for (int j = 0; j < D; ++j) Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q] = Phi[s][j] * invh[j];
+                }
+                continue;
+            }
+        }
+        if constexpr (MODE == MODE_APPLY) {
+            if (args.flags & CDG2_FORCING) {
+                const long long ge = e0 + e;
+                const long long ix = ge % g.n[0], iy = (ge / g.n[0]) % g.n[1];
+                const T x = T(ix * g.h[0]) + T(g.h[0]) * tb.xi[q0];
+                const T y = T(iy * g.h[1]) + T(g.h[1]) * tb.xi[q1];
+                T gf[NS];
+                mms_forcing<T>(x, y, T(args.t), T(g.L[1]), c, gf);
+#pragma unroll
+                for (int s = 0; s < NS; ++s) Sr[s] += gf[s];
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            Q[OFF + (e * NS + s) * NQ + q] = Wq * Sr[s];
+#pragma unroll
+            for (int j = 0; j < D; ++j) Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q] = Wq * Phi[s][j] * invh[j];
+        }
+    }
+    __syncthreads();
+
+    // ---- volume: test with phi and grad phi (transposed sum factorisation) ----
+    const int nto = EPB * NS;
+    T* Qo = Q + OFF;
+    if constexpr (D == 2) {
+        // Y0 = B^T_y S' + D^T_y Phi_y',  Y1 = B^T_y Phi_x'
+        T* Y0 = X0;
+        T* Y1 = X1;
+        sf_pass<1, NQ1, NQ1, 1, NB1, true, K + 1, true>(Qo, &tb.B[0][0], Qo + 2 * P::QSZ, &tb.D[0][0], NQ, Y0,
+                                                         NQ1 * NB1, nto);
+        sf_pass<1, NQ1, NQ1, 1, NB1, true, K + 1, false>(Qo + P::QSZ, &tb.B[0][0], nullptr, nullptr, NQ, Y1,
+                                                          NQ1 * NB1, nto);
+        __syncthreads();
+        sf_pass<0, NQ1, NB1, 1, NB1, true, K + 1, true>(Y0, &tb.B[0][0], Y1, &tb.D[0][0], NQ1 * NB1, sR, NB, nto);
+    } else {
+        constexpr int ZS = NQ1 * NQ1 * NB1, XS = NQ1 * NB1 * NB1;
+        T* Z0 = Y;
+        T* Z1 = Y + P::YSZ;
+        T* Z2 = Y + 2 * P::YSZ;
+        sf_pass<2, NQ1, NQ1, NQ1, NB1, true, K + 1, true>(Qo, &tb.B[0][0], Qo + 3 * P::QSZ, &tb.D[0][0], NQ, Z0, ZS,
+                                                           nto);
+        sf_pass<2, NQ1, NQ1, NQ1, NB1, true, K + 1, false>(Qo + 2 * P::QSZ, &tb.B[0][0], nullptr, nullptr, NQ, Z1,
+                                                            ZS, nto);
+        sf_pass<2, NQ1, NQ1, NQ1, NB1, true, K + 1, false>(Qo + P::QSZ, &tb.B[0][0], nullptr, nullptr, NQ, Z2, ZS,
+                                                            nto);
+        __syncthreads();
+        T* Y0 = X0;
+        T* Y1 = X1;
+        sf_pass<1, NQ1, NQ1, NB1, NB1, true, K + 1, true>(Z0, &tb.B[0][0], Z1, &tb.D[0][0], ZS, Y0, XS, nto);
+        sf_pass<1, NQ1, NQ1, NB1, NB1, true, K + 1, false>(Z2, &tb.B[0][0], nullptr, nullptr, ZS, Y1, XS, nto);
+        __syncthreads();
+        sf_pass<0, NQ1, NB1, NB1, NB1, true, K + 1, true>(Y0, &tb.B[0][0], Y1, &tb.D[0][0], XS, sR, NB, nto);
+    }
+    __syncthreads();
+
+    // ---- faces ----
+    op_faces<D, K, MODE, 0, T>(g, tb, c, args, sU, sR, W, e0, nbr, th);
+    op_faces<D, K, MODE, 1, T>(g, tb, c, args, sU, sR, W, e0, nbr, th);
+    if constexpr (D == 3) op_faces<D, K, MODE, 2, T>(g, tb, c, args, sU, sR, W, e0, nbr, th);
+
+    // ---- M^{-1} = I / |K| for the orthonormal basis; coalesced store ----
+    const T scale = (args.flags & CDG2_MINV) ? T(1.0 / g.vol) : T(1);
+    for (int i = threadIdx.x; i < P::UR; i += blockDim.x) {
+        const long long ge = e0 + i / (NS * NB);
+        if (ge < g.E) args.out[e0 * NS * NB + i] = sR[i] * scale;
+    }
+
+    // ---- VJP: deterministic per-CTA reduction of the theta cotangent ----
+    if constexpr (MODE == MODE_VJP) {
+        if (args.theta_part != nullptr) {
+            __syncthreads();   // W is free again: reuse it as a double buffer
+            double* red = reinterpret_cast<double*>(W);
+            for (int j = 0; j < 8; ++j) red[j * blockDim.x + threadIdx.x] = th[j];
+            __syncthreads();
+            for (int stride = blockDim.x / 2; stride > 0; stride >>= 1) {
+                if ((int)threadIdx.x < stride)
+                    for (int j = 0; j < 8; ++j) red[j * blockDim.x + threadIdx.x] += red[j * blockDim.x + threadIdx.x + stride];
+                __syncthreads();
+            }
+            if (threadIdx.x < 8) args.theta_part[(long long)blockIdx.x * 8 + threadIdx.x] = red[threadIdx.x * blockDim.x] * double(scale);
+        }
+    }
+}
+
+// Fixed-order sum of the per-CTA theta partials: one CTA of 256 threads, each
+// thread sums a strided subset in index order, then a tree reduction.
+__global__ void __launch_bounds__(256) theta_reduce_kernel(const double* __restrict__ part, long long nblocks,
+                                                           double* __restrict__ gtheta) {
+    __shared__ double red[8][256];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int j = 0; j < 8; ++j) acc[j] += part[b * 8 + j];
+    for (int j = 0; j < 8; ++j) red[j][threadIdx.x] = acc[j];
+    __syncthreads();
+    for (int stride = blockDim.x / 2; stride > 0; stride >>= 1) {
+        if ((int)threadIdx.x < stride)
+            for (int j = 0; j < 8; ++j) red[j][threadIdx.x] += red[j][threadIdx.x + stride];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) gtheta[threadIdx.x] = red[threadIdx.x][0];
+}
+
+template <int MODE>
+static long long grid_of(const cdg2_mesh& m) {
+    constexpr int F = fields_of(MODE);
+    const int d = m.geo.dim, k = m.geo.k;
+    int epb = 1;
+    if (d == 2 && k == 1) epb = OpPlan<2, 1, F>::EPB;
+    if (d == 2 && k == 2) epb = OpPlan<2, 2, F>::EPB;
+    if (d == 2 && k == 3) epb = OpPlan<2, 3, F>::EPB;
+    if (d == 3 && k == 1) epb = OpPlan<3, 1, F>::EPB;
+    if (d == 3 && k == 2) epb = OpPlan<3, 2, F>::EPB;
+    if (d == 3 && k == 3) epb = OpPlan<3, 3, F>::EPB;
+    return (m.geo.E + epb - 1) / epb;
+}
+
+template <int D, int K, int MODE, typename T>
+static cudaError_t launch_one(const cdg2_mesh& m, const Coef& c, const OpArgs<T>& a, cudaStream_t st) {
+    using P = OpPlan<D, K, fields_of(MODE)>;
+    constexpr size_t smem = P::template smem_bytes<T>();
+    static_assert(smem <= 227 * 1024, "operator kernel shared memory exceeds 227 KB");
+    static_assert(MODE != MODE_VJP || sizeof(T) * P::WORK >= 8 * 128 * sizeof(double),
+                  "theta reduction buffer does not fit the work area");
+    static bool attr_done = false;   // per instantiation; benign race: both writers set the same value
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(op_kernel<D, K, MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const long long blocks = grid_of<MODE>(m);
+    op_kernel<D, K, MODE, T><<<(unsigned)blocks, P::NT, smem, st>>>(m.geo, m.tab, c, a);
+    return cudaGetLastError();
+}
+
+template <int MODE, typename T>
+static cudaError_t dispatch(const cdg2_mesh& m, const Coef& c, const OpArgs<T>& a, cudaStream_t st) {
+    const int d = m.geo.dim, k = m.geo.k;
+    if (d == 2 && k == 1) return launch_one<2, 1, MODE, T>(m, c, a, st);
+    if (d == 2 && k == 2) return launch_one<2, 2, MODE, T>(m, c, a, st);
+    if (d == 2 && k == 3) return launch_one<2, 3, MODE, T>(m, c, a, st);
+    if (d == 3 && k == 1) return launch_one<3, 1, MODE, T>(m, c, a, st);
+    if (d == 3 && k == 2) return launch_one<3, 2, MODE, T>(m, c, a, st);
+    if (d == 3 && k == 3) return launch_one<3, 3, MODE, T>(m, c, a, st);
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static OpArgs<T> make_args(const void* U, const void* dU, void* out, int flags, double t, const double* dtheta,
+                           double* theta_part) {
+    OpArgs<T> a{};
+    a.U[0] = (const T*)U;
+    a.U[1] = (const T*)dU;
+    a.out = (T*)out;
+    a.flags = flags;
+    a.t = t;
+    a.has_dtheta = dtheta != nullptr;
+    for (int i = 0; i < 8; ++i) a.dtheta[i] = dtheta ? dtheta[i] : 0.0;
+    a.theta_part = theta_part;
+    return a;
+}
+
+long long vjp_grid(const cdg2_mesh& m) { return grid_of<MODE_VJP>(m); }
+
+cudaError_t launch_apply(const cdg2_mesh& m, const Coef& c, const void* U, void* out, int flags, double t,
+                         cudaStream_t st) {
+    if (flags & CDG2_FP32)
+        return dispatch<MODE_APPLY, float>(m, c, make_args<float>(U, U, out, flags, t, nullptr, nullptr), st);
+    return dispatch<MODE_APPLY, double>(m, c, make_args<double>(U, U, out, flags, t, nullptr, nullptr), st);
+}
+
+cudaError_t launch_jvp(const cdg2_mesh& m, const Coef& c, const void* U, const void* dU, const double* dtheta,
+                       void* out, int flags, cudaStream_t st) {
+    if (flags & CDG2_FP32)
+        return dispatch<MODE_JVP, float>(m, c, make_args<float>(U, dU, out, flags, 0.0, dtheta, nullptr), st);
+    return dispatch<MODE_JVP, double>(m, c, make_args<double>(U, dU, out, flags, 0.0, dtheta, nullptr), st);
+}
+
+cudaError_t launch_vjp(const cdg2_mesh& m, const Coef& c, const void* U, const void* lam, void* gU,
+                       double* theta_part, double* gtheta, int flags, cudaStream_t st) {
+    cudaError_t e;
+    if (flags & CDG2_FP32)
+        e = dispatch<MODE_VJP, float>(m, c, make_args<float>(U, lam, gU, flags, 0.0, nullptr, theta_part), st);
+    else
+        e = dispatch<MODE_VJP, double>(m, c, make_args<double>(U, lam, gU, flags, 0.0, nullptr, theta_part), st);
+    if (e != cudaSuccess || gtheta == nullptr) return e;
+    theta_reduce_kernel<<<1, 256, 0, st>>>(theta_part, grid_of<MODE_VJP>(m), gtheta);
+    return cudaGetLastError();
+}
+
+}  // namespace cdg2

@@ -140,6 +140,27 @@ int cdg2_jvp(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, co
 int cdg2_vjp(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, const void* lam, void* gU,
              double* gtheta, int flags, double t, void* stream);
 
+/* cdg2_vjp for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is a library-interface addition).  cdg2_vjp cudaMallocs
+ * a per-mesh workspace the first time gtheta is requested; a caller whose
+ * device memory is wholly managed by its own pool allocator, or whose loop
+ * must never incur the implicit device synchronisation of cudaMalloc /
+ * cudaFree, cannot accept that.  This entry point computes the same gU and
+ * gtheta with its scratch in a fixed 1 MiB device array inside the library
+ * (held on every GPU that loads the library until the process exits) and
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ * Limit: with gtheta != NULL the mesh may need at most 16384 VJP thread
+ * blocks (elements per block: 2D 8/4/4 for k = 1/2/3, 3D 4/2/1; e.g. 16384
+ * 3D Q3 elements); larger meshes return CDG2_ERR_INVALID_ARG.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and nothing in it
+ * needs to start at zero (each block overwrites its own slots), but calls
+ * that overlap on the GPU race on it: order them on one stream.
+ * Arguments, layouts and results are those of cdg2_vjp. */
+int cdg2_vjp_noalloc(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, const void* lam, void* gU,
+                     double* gtheta, int flags, double t, void* stream);
+
 /* Initial data: out = L2 projection onto V_h of
  *   u0_s(x) = floor_value + sum_b amps[s][b] exp(-|x - centres[s][b]|^2 / (2 sigma^2))
  * (Sec. 3.2: U(0) is the projection of U_0), distances taken as minimum

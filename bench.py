@@ -56,7 +56,7 @@ def apply_flops_per_element(dim: int, k: int) -> int:
 # from one ncu capture (profiles/), keyed by workload and valid only for the
 # kernel sources the counters were taken with (first 16 hex of their sha256).
 NCU_TRAFFIC = {("2D 256x64 Q3 manufactured solution", "double"): (12756736, "2c371327bd3f5910")}
-KERNEL_SOURCES = ("paper_1403_1157_gb300/csrc/apply.cu", "paper_1403_1157_gb300/csrc/elem_common.cuh")
+KERNEL_SOURCES = ("paper_1403_1157_gb300/csrc/operator.cu", "paper_1403_1157_gb300/csrc/elem_common.cuh")
 
 
 def kernel_source_hash() -> str:

@@ -47,6 +47,10 @@ extern "C" {
 #define CDG2_FORCING 2   /* add the manufactured-solution forcing at time t */
 #define CDG2_FP32 4      /* arrays are float32 and the kernel computes in FP32 */
 
+/* time-stepping schemes of cdg2_step */
+#define CDG2_SDIRK2 2    /* Alexander's 2-stage L-stable SDIRK, order 2 */
+#define CDG2_SDIRK3 3    /* Alexander's 3-stage L-stable SDIRK, order 3 */
+
 typedef struct cdg2_mesh cdg2_mesh;
 
 /* Mesh description.
@@ -89,6 +93,40 @@ typedef struct cdg2_params {
     double mms_phase[6];
 } cdg2_params;
 
+/* Options of cdg2_step.
+ * scheme: CDG2_SDIRK2 or CDG2_SDIRK3 (Sec. 3.2 names DIRK of order 2, 3 or 4
+ *   without tableaux; Reading: Alexander's L-stable stiffly accurate SDIRK).
+ * mixed: 0 = FP64 Krylov vectors and FP64 JVP; 1 = FP32 Krylov vectors, FP32
+ *   JVP about an FP32 copy of the stage iterate, FP64 Newton residual and
+ *   update (iterative refinement).
+ * flags: 0 or CDG2_FORCING (manufactured-solution forcing at stage times).
+ * Newton stops when ||G||_2 <= max(newton_rtol ||G(Y^0)||_2, newton_atol),
+ *   G(Y) = Y - dt a_ii f(Y) - rhs_i, Y^0 the previous stage value (U_n first);
+ *   at most max_newton corrections per stage.
+ * GMRES(gmres_restart) with CGS2 stops at ||r||_2 <= gmres_rtol ||G||_2 or
+ *   after max_gmres iterations per Newton correction; 1 <= gmres_restart <= 64. */
+typedef struct cdg2_solver_opts {
+    int scheme;
+    int mixed;
+    int flags;
+    int max_newton;
+    int gmres_restart;
+    int max_gmres;
+    double newton_rtol;
+    double newton_atol;
+    double gmres_rtol;
+} cdg2_solver_opts;
+
+/* Statistics of one cdg2_step call. */
+typedef struct cdg2_stats {
+    int stages;           /* stages of the scheme */
+    int newton_iters;     /* Newton corrections, all stages */
+    int gmres_iters;      /* GMRES iterations (JVP launches in Arnoldi), all stages */
+    double residual0[4];  /* ||G(Y^0)||_2 per stage */
+    double residual[4];   /* final ||G||_2 per stage */
+    double seconds;       /* host wall time of the call */
+} cdg2_stats;
+
 /* Build a mesh (host call, synchronous).  Tabulates the 1D basis and Gauss
  * rule on the host.  *out receives an opaque handle owned by the caller
  * until cdg2_mesh_destroy.  Errors: INVALID_ARG for an unsupported desc. */
@@ -125,6 +163,19 @@ int cdg2_apply(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, 
  * out must not overlap U or dU.  t is accepted for symmetry and unused. */
 int cdg2_jvp(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, const void* dU,
              const double* dtheta, void* out, int flags, double t, void* stream);
+
+/* One SDIRK step U_n -> U_{n+1} of U' = f(U, t) = M^{-1} L_h(U) (+ forcing)
+ * (Sec. 3.2, Eq. ode), each stage solved by Jacobian-free Newton-Krylov with
+ * GMRES (Sec. 3.2) on the GPU; JVPs come from cdg2_jvp's kernel.
+ * U: device float64 [n_elem][6][n_basis], overwritten with U_{n+1}.
+ * t, dt: time and step (dt > 0).  opts: see cdg2_solver_opts.  stats: may be
+ * NULL.  Synchronous: returns after the step has completed on `stream`.
+ * The first call allocates a per-mesh workspace (cudaMalloc; 8 state vectors
+ * plus gmres_restart + 5 Krylov vectors); calls sharing a mesh must be
+ * ordered.  Errors: NOT_CONVERGED (U unchanged, stats filled), NONFINITE
+ * (a NaN/Inf residual), INVALID_ARG, CUDA. */
+int cdg2_step(const cdg2_mesh* mesh, const cdg2_params* params, double* U, double t, double dt,
+              const cdg2_solver_opts* opts, cdg2_stats* stats, void* stream);
 
 /* Transpose of cdg2_jvp (vector-Jacobian product, for the adjoint of the
  * implicit steps):

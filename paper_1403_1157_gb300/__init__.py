@@ -16,12 +16,15 @@ import torch
 __all__ = [
     "CDG2_MINV", "CDG2_FORCING", "CDG2_FP32", "Cdg2Error", "Mesh", "load_library", "library_path",
     "make_params", "cdg2_mesh_create", "cdg2_mesh_destroy", "cdg2_mesh_info", "cdg2_apply", "cdg2_last_error",
-    "cdg2_project_gaussians", "cdg2_project_mms", "cdg2_jvp", "cdg2_vjp",
+    "cdg2_project_gaussians", "cdg2_project_mms", "cdg2_jvp", "cdg2_vjp", "cdg2_step",
+    "CDG2_SDIRK2", "CDG2_SDIRK3", "SolverOpts", "Stats", "make_opts",
 ]
 
 CDG2_MINV = 1
 CDG2_FORCING = 2
 CDG2_FP32 = 4
+CDG2_SDIRK2 = 2
+CDG2_SDIRK3 = 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
@@ -64,6 +67,26 @@ class Params(ctypes.Structure):
     ]
 
 
+class SolverOpts(ctypes.Structure):
+    _fields_ = [
+        ("scheme", ctypes.c_int), ("mixed", ctypes.c_int), ("flags", ctypes.c_int), ("max_newton", ctypes.c_int),
+        ("gmres_restart", ctypes.c_int), ("max_gmres", ctypes.c_int),
+        ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double), ("gmres_rtol", ctypes.c_double),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("stages", ctypes.c_int), ("newton_iters", ctypes.c_int), ("gmres_iters", ctypes.c_int),
+        ("residual0", ctypes.c_double * 4), ("residual", ctypes.c_double * 4), ("seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {"stages": self.stages, "newton_iters": self.newton_iters, "gmres_iters": self.gmres_iters,
+                "residual0": list(self.residual0)[: self.stages], "residual": list(self.residual)[: self.stages],
+                "seconds": self.seconds}
+
+
 def library_path() -> str:
     return os.path.join(_HERE, "libcdg2.so")
 
@@ -92,6 +115,9 @@ def load_library():
     lib.cdg2_jvp.restype = i
     lib.cdg2_vjp.argtypes = [vp, ctypes.POINTER(Params), vp, vp, vp, vp, i, d, vp]
     lib.cdg2_vjp.restype = i
+    lib.cdg2_step.argtypes = [vp, ctypes.POINTER(Params), vp, d, d, ctypes.POINTER(SolverOpts), ctypes.POINTER(Stats),
+                              vp]
+    lib.cdg2_step.restype = i
     lib.cdg2_project_gaussians.argtypes = [vp, i, dp, dp, d, d, vp, i, vp]
     lib.cdg2_project_gaussians.restype = i
     lib.cdg2_project_mms.argtypes = [vp, ctypes.POINTER(Params), d, vp, i, vp]
@@ -267,3 +293,25 @@ def cdg2_vjp(mesh: Mesh, params, U: torch.Tensor, lam: torch.Tensor, gU: torch.T
     _check(load_library().cdg2_vjp(mesh.handle, ctypes.byref(p), _dev(U, mesh, dt, "U"), _dev(lam, mesh, dt, "lam"),
                                    _dev(gU, mesh, dt, "gU"), gth, int(flags), float(t), _stream_ptr(stream)))
     return gU
+
+
+def make_opts(scheme=CDG2_SDIRK2, mixed=False, flags=0, max_newton=20, gmres_restart=30, max_gmres=300,
+              newton_rtol=1e-10, newton_atol=0.0, gmres_rtol=1e-3) -> SolverOpts:
+    o = SolverOpts()
+    o.scheme, o.mixed, o.flags, o.max_newton = int(scheme), int(bool(mixed)), int(flags), int(max_newton)
+    o.gmres_restart, o.max_gmres = int(gmres_restart), int(max_gmres)
+    o.newton_rtol, o.newton_atol, o.gmres_rtol = float(newton_rtol), float(newton_atol), float(gmres_rtol)
+    return o
+
+
+def cdg2_step(mesh: Mesh, params, U: torch.Tensor, t: float, dt: float, opts: SolverOpts = None, stream=None,
+              raise_on_error: bool = True):
+    """One SDIRK step in place on the float64 CUDA tensor U; returns (status, stats dict)."""
+    p = _params(params)
+    o = opts if opts is not None else make_opts()
+    st = Stats()
+    rc = load_library().cdg2_step(mesh.handle, ctypes.byref(p), _dev(U, mesh, torch.float64, "U"), float(t), float(dt),
+                                  ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream))
+    if rc != 0 and raise_on_error:
+        _check(rc)
+    return rc, st.as_dict()

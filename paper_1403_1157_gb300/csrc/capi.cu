@@ -171,6 +171,7 @@ int cdg2_mesh_create(const cdg2_mesh_desc* d, cdg2_mesh** out) {
 void cdg2_mesh_destroy(cdg2_mesh* m) {
     if (!m) return;
     if (m->theta_part) cudaFree(m->theta_part);   // synchronises work queued on it
+    if (m->step_ws) cudaFree(m->step_ws);
     delete m;
 }
 

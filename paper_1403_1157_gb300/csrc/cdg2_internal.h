@@ -59,6 +59,9 @@ struct cdg2_mesh {
     // cdg2_mesh_destroy: per-CTA partial sums of the VJP's theta gradient.
     mutable double* theta_part = nullptr;
     mutable long long theta_part_n = 0;
+    // Workspace of cdg2_step: 8 FP64 state vectors, the Krylov basis, reduction scratch.
+    mutable void* step_ws = nullptr;
+    mutable size_t step_ws_bytes = 0;
 };
 
 namespace cdg2 {
@@ -71,6 +74,9 @@ cudaError_t launch_apply(const cdg2_mesh& m, const Coef& c, const void* U, void*
                          cudaStream_t stream);
 cudaError_t launch_jvp(const cdg2_mesh& m, const Coef& c, const void* U, const void* dU, const double* dtheta,
                        void* out, int flags, cudaStream_t stream);
+// out = alpha dU + beta J(U) dU (the Krylov operator v - gamma dt J v in one pass)
+cudaError_t launch_jvp_axpby(const cdg2_mesh& m, const Coef& c, const void* U, const void* dU, double alpha,
+                             double beta, void* out, int flags, cudaStream_t stream);
 // VJP: gU = (df/dU)^T lam; when gtheta is non-null also (df/dtheta)^T lam via
 // theta_part ([vjp_grid(m)][8] doubles of scratch) and a fixed-order reduction.
 cudaError_t launch_vjp(const cdg2_mesh& m, const Coef& c, const void* U, const void* lam, void* gU,

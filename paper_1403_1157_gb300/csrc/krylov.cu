@@ -1,0 +1,196 @@
+// Vector kernels of the Newton-GMRES solver (Sec. 3.2: the DIRK stages are
+// solved by a Jacobian-free Newton-Krylov method with GMRES).  All are
+// bandwidth-bound passes over DOF-length vectors with grid-stride loops;
+// every reduction is two-stage with a fixed partition and a fixed tree, so
+// results are bitwise reproducible (no atomics).  Dot products of FP32
+// vectors accumulate in FP64.
+#include "krylov.h"
+
+namespace cdg2 {
+
+constexpr int VT = 256;                       // threads per block of the vector kernels
+constexpr int RED_BLOCKS = 4 * 152;           // blocks of every partial reduction (4 per SM)
+
+// y = a x + b y
+template <typename T>
+__global__ void __launch_bounds__(VT) k_axpby(long long n, double a, const T* __restrict__ x, double b,
+                                               T* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
+        y[i] = T(a * double(x[i]) + b * double(y[i]));
+}
+
+// out = x + sum_j c_j V_j (j < nv), V_j double vectors with leading dimension ldv
+// (x and out may alias: each element is read before it is written by the same thread)
+__global__ void __launch_bounds__(VT) k_lincomb(long long n, const double* x, int nv,
+                                                 const double* __restrict__ V, long long ldv, Coeffs c,
+                                                 double* out) {
+    for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) {
+        double acc = x[i];
+        for (int j = 0; j < nv; ++j) acc = fma(c.v[j], V[j * ldv + i], acc);
+        out[i] = acc;
+    }
+}
+
+// G = Y - gdt * fY - rhs
+__global__ void __launch_bounds__(VT) k_newton_residual(long long n, const double* __restrict__ Y,
+                                                         const double* __restrict__ fY, double gdt,
+                                                         const double* __restrict__ rhs, double* __restrict__ G) {
+    for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
+        G[i] = Y[i] - gdt * fY[i] - rhs[i];
+}
+
+// dst = (T) src   /   Y += (double) x
+// (src and dst may alias)
+template <typename S, typename D>
+__global__ void __launch_bounds__(VT) k_convert(long long n, const S* src, double scale, D* dst) {
+    for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
+        dst[i] = D(scale * double(src[i]));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VT) k_add_into(long long n, const T* __restrict__ x, double* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
+        y[i] += double(x[i]);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = VT / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    return sh[0];
+}
+
+// part[j][blockIdx.x] = sum over this block's slice of V_j . w   (blockIdx.y = j)
+template <typename T>
+__global__ void __launch_bounds__(VT) k_mdot_partial(long long n, const T* __restrict__ V, long long ldv,
+                                                      const T* __restrict__ w, double* __restrict__ part) {
+    __shared__ double sh[VT];
+    const int j = blockIdx.y;
+    const T* v = V + j * ldv;
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
+        acc = fma(double(v[i]), double(w[i]), acc);
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(long long)j * gridDim.x + blockIdx.x] = s;
+}
+
+// out[j] = sum_b part[j][b] in a fixed order (blockIdx.x = j)
+__global__ void __launch_bounds__(VT) k_rows_sum(const double* __restrict__ part, int nparts,
+                                                 double* __restrict__ out) {
+    __shared__ double sh[VT];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += VT) acc += part[(long long)blockIdx.x * nparts + b];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// w -= sum_j h_j V_j  (h on the device)
+template <typename T>
+__global__ void __launch_bounds__(VT) k_mgs_update(long long n, int nv, const T* __restrict__ V, long long ldv,
+                                                   const double* __restrict__ h, T* __restrict__ w) {
+    for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) {
+        double acc = double(w[i]);
+        for (int j = 0; j < nv; ++j) acc = fma(-h[j], double(V[j * ldv + i]), acc);
+        w[i] = T(acc);
+    }
+}
+
+// x += sum_j y_j V_j  (y passed by value)
+template <typename T>
+__global__ void __launch_bounds__(VT) k_basis_combine(long long n, int nv, const T* __restrict__ V, long long ldv,
+                                                      Coeffs y, T* __restrict__ x) {
+    for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) {
+        double acc = double(x[i]);
+        for (int j = 0; j < nv; ++j) acc = fma(y.v[j], double(V[j * ldv + i]), acc);
+        x[i] = T(acc);
+    }
+}
+
+static unsigned grid_for(long long n) {
+    long long b = (n + VT - 1) / VT;
+    const long long cap = 152LL * 16;   // enough blocks to saturate HBM; loops cover the rest
+    return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t vec_axpby(long long n, double a, const T* x, double b, T* y, cudaStream_t st) {
+    k_axpby<T><<<grid_for(n), VT, 0, st>>>(n, a, x, b, y);
+    return cudaGetLastError();
+}
+
+cudaError_t vec_lincomb(long long n, const double* x, int nv, const double* V, long long ldv, const Coeffs& c,
+                        double* out, cudaStream_t st) {
+    k_lincomb<<<grid_for(n), VT, 0, st>>>(n, x, nv, V, ldv, c, out);
+    return cudaGetLastError();
+}
+
+cudaError_t vec_newton_residual(long long n, const double* Y, const double* fY, double gdt, const double* rhs,
+                                double* G, cudaStream_t st) {
+    k_newton_residual<<<grid_for(n), VT, 0, st>>>(n, Y, fY, gdt, rhs, G);
+    return cudaGetLastError();
+}
+
+template <typename S, typename D>
+cudaError_t vec_convert(long long n, const S* src, double scale, D* dst, cudaStream_t st) {
+    k_convert<S, D><<<grid_for(n), VT, 0, st>>>(n, src, scale, dst);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t vec_add_into(long long n, const T* x, double* y, cudaStream_t st) {
+    k_add_into<T><<<grid_for(n), VT, 0, st>>>(n, x, y);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t vec_mdot(long long n, int nv, const T* V, long long ldv, const T* w, double* part, double* out,
+                     cudaStream_t st) {
+    dim3 grid(RED_BLOCKS, nv);
+    k_mdot_partial<T><<<grid, VT, 0, st>>>(n, V, ldv, w, part);
+    k_rows_sum<<<nv, VT, 0, st>>>(part, RED_BLOCKS, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t vec_mgs_update(long long n, int nv, const T* V, long long ldv, const double* h, T* w, cudaStream_t st) {
+    k_mgs_update<T><<<grid_for(n), VT, 0, st>>>(n, nv, V, ldv, h, w);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t vec_basis_combine(long long n, int nv, const T* V, long long ldv, const Coeffs& y, T* x,
+                              cudaStream_t st) {
+    k_basis_combine<T><<<grid_for(n), VT, 0, st>>>(n, nv, V, ldv, y, x);
+    return cudaGetLastError();
+}
+
+long long reduction_scratch_doubles(int max_vectors) { return (long long)RED_BLOCKS * max_vectors; }
+
+template cudaError_t vec_axpby<double>(long long, double, const double*, double, double*, cudaStream_t);
+template cudaError_t vec_axpby<float>(long long, double, const float*, double, float*, cudaStream_t);
+template cudaError_t vec_convert<double, float>(long long, const double*, double, float*, cudaStream_t);
+template cudaError_t vec_convert<float, double>(long long, const float*, double, double*, cudaStream_t);
+template cudaError_t vec_convert<double, double>(long long, const double*, double, double*, cudaStream_t);
+template cudaError_t vec_convert<float, float>(long long, const float*, double, float*, cudaStream_t);
+template cudaError_t vec_add_into<double>(long long, const double*, double*, cudaStream_t);
+template cudaError_t vec_add_into<float>(long long, const float*, double*, cudaStream_t);
+template cudaError_t vec_mdot<double>(long long, int, const double*, long long, const double*, double*, double*,
+                                      cudaStream_t);
+template cudaError_t vec_mdot<float>(long long, int, const float*, long long, const float*, double*, double*,
+                                     cudaStream_t);
+template cudaError_t vec_mgs_update<double>(long long, int, const double*, long long, const double*, double*,
+                                            cudaStream_t);
+template cudaError_t vec_mgs_update<float>(long long, int, const float*, long long, const double*, float*,
+                                           cudaStream_t);
+template cudaError_t vec_basis_combine<double>(long long, int, const double*, long long, const Coeffs&, double*,
+                                               cudaStream_t);
+template cudaError_t vec_basis_combine<float>(long long, int, const float*, long long, const Coeffs&, float*,
+                                              cudaStream_t);
+
+}  // namespace cdg2

@@ -1,0 +1,36 @@
+// Launchers of the Krylov vector kernels (krylov.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace cdg2 {
+
+constexpr int MAX_KRYLOV = 64;   // largest GMRES restart length
+
+// Coefficients passed by value to a kernel (at most MAX_KRYLOV + 1).
+struct Coeffs {
+    double v[MAX_KRYLOV + 1];
+};
+
+template <typename T>
+cudaError_t vec_axpby(long long n, double a, const T* x, double b, T* y, cudaStream_t st);
+cudaError_t vec_lincomb(long long n, const double* x, int nv, const double* V, long long ldv, const Coeffs& c,
+                        double* out, cudaStream_t st);
+cudaError_t vec_newton_residual(long long n, const double* Y, const double* fY, double gdt, const double* rhs,
+                                double* G, cudaStream_t st);
+template <typename S, typename D>
+cudaError_t vec_convert(long long n, const S* src, double scale, D* dst, cudaStream_t st);
+template <typename T>
+cudaError_t vec_add_into(long long n, const T* x, double* y, cudaStream_t st);
+// out[j] = V_j . w for j < nv (V_j = V + j * ldv); part: reduction_scratch_doubles(nv) doubles
+template <typename T>
+cudaError_t vec_mdot(long long n, int nv, const T* V, long long ldv, const T* w, double* part, double* out,
+                     cudaStream_t st);
+template <typename T>
+cudaError_t vec_mgs_update(long long n, int nv, const T* V, long long ldv, const double* h, T* w, cudaStream_t st);
+template <typename T>
+cudaError_t vec_basis_combine(long long n, int nv, const T* V, long long ldv, const Coeffs& y, T* x,
+                              cudaStream_t st);
+long long reduction_scratch_doubles(int max_vectors);
+
+}  // namespace cdg2

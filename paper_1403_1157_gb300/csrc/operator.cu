@@ -75,6 +75,7 @@ struct OpArgs {
     int has_dtheta;
     double dtheta[8];   // tangent of (d1, d2, gamma, alpha1, alpha2, f1, k_ox, beta1)
     double* theta_part; // VJP: per-CTA partial sums of (df/dtheta)^T lambda, [gridDim.x][8], or null
+    double alpha, beta; // JVP epilogue: out = alpha dU + beta J dU (0, 1 for the plain JVP)
 };
 
 constexpr int MODE_APPLY = 0, MODE_JVP = 1, MODE_VJP = 2;
@@ -772,7 +773,12 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
     const T scale = (args.flags & CDG2_MINV) ? T(1.0 / g.vol) : T(1);
     for (int i = threadIdx.x; i < P::UR; i += blockDim.x) {
         const long long ge = e0 + i / (NS * NB);
-        if (ge < g.E) args.out[e0 * NS * NB + i] = sR[i] * scale;
+        if (ge < g.E) {
+            if constexpr (MODE == MODE_JVP)
+                args.out[e0 * NS * NB + i] = T(args.alpha) * sU[P::UR + i] + T(args.beta) * (sR[i] * scale);
+            else
+                args.out[e0 * NS * NB + i] = sR[i] * scale;
+        }
     }
 
     // ---- VJP: deterministic per-CTA reduction of the theta cotangent ----
@@ -867,6 +873,8 @@ static OpArgs<T> make_args(const void* U, const void* dU, void* out, int flags, 
     a.has_dtheta = dtheta != nullptr;
     for (int i = 0; i < 8; ++i) a.dtheta[i] = dtheta ? dtheta[i] : 0.0;
     a.theta_part = theta_part;
+    a.alpha = 0.0;
+    a.beta = 1.0;
     return a;
 }
 
@@ -884,6 +892,20 @@ cudaError_t launch_jvp(const cdg2_mesh& m, const Coef& c, const void* U, const v
     if (flags & CDG2_FP32)
         return dispatch<MODE_JVP, float>(m, c, make_args<float>(U, dU, out, flags, 0.0, dtheta, nullptr), st);
     return dispatch<MODE_JVP, double>(m, c, make_args<double>(U, dU, out, flags, 0.0, dtheta, nullptr), st);
+}
+
+cudaError_t launch_jvp_axpby(const cdg2_mesh& m, const Coef& c, const void* U, const void* dU, double alpha,
+                             double beta, void* out, int flags, cudaStream_t st) {
+    if (flags & CDG2_FP32) {
+        OpArgs<float> a = make_args<float>(U, dU, out, flags, 0.0, nullptr, nullptr);
+        a.alpha = alpha;
+        a.beta = beta;
+        return dispatch<MODE_JVP, float>(m, c, a, st);
+    }
+    OpArgs<double> a = make_args<double>(U, dU, out, flags, 0.0, nullptr, nullptr);
+    a.alpha = alpha;
+    a.beta = beta;
+    return dispatch<MODE_JVP, double>(m, c, a, st);
 }
 
 cudaError_t launch_vjp(const cdg2_mesh& m, const Coef& c, const void* U, const void* lam, void* gU,

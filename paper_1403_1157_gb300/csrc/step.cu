@@ -1,0 +1,351 @@
+// cdg2_step: one diagonally implicit Runge-Kutta step of U' = f(U, t) =
+// M^{-1} L_h(U) (+ forcing) (Sec. 3.2, Eq. ode), each stage solved by a
+// Jacobian-free Newton-Krylov method with GMRES (Sec. 3.2).
+//
+// Reading: the paper names DIRK methods of order 2, 3 or 4 without tableaux;
+// this uses Alexander's L-stable, stiffly accurate SDIRK2 and SDIRK3.
+//
+// Stage i solves G(Y) = Y - dt a_ii f(Y, t + c_i dt) - rhs_i = 0 with
+// rhs_i = U_n + dt sum_{j<i} a_ij K_j.  Newton: the residual G is always
+// formed in FP64; the correction solves (I - dt a_ii J(Y)) d = -G by
+// restarted GMRES with classical Gram-Schmidt applied twice (CGS2), whose
+// matrix-vector product is one JVP launch (J from the kernel, not a finite
+// difference).  In the mixed mode the Krylov vectors, the JVP and the
+// primal state it linearises about are FP32 while G, Y and the convergence
+// test stay FP64: iterative refinement, so the converged stage agrees with
+// the FP64 solve to the Newton tolerance.
+//
+// The driver runs on the host; it synchronises the stream to read each
+// reduction (Newton residual norms, Gram-Schmidt coefficients).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cdg2_internal.h"
+#include "krylov.h"
+
+namespace cdg2 {
+
+struct Tableau {
+    int s;
+    double A[3][3];
+    double b[3];
+    double c[3];
+};
+
+// Alexander (1977): SDIRK2 with gamma = 1 - 1/sqrt(2); SDIRK3 with gamma the
+// root in (1/6, 1/2) of 6 g^3 - 18 g^2 + 9 g - 1 (found by Newton's method),
+// c2 = (1 + g)/2, b1 = -(6 g^2 - 16 g + 1)/4, b2 = (6 g^2 - 20 g + 5)/4.
+static Tableau sdirk_tableau(int scheme) {
+    Tableau T;
+    std::memset(&T, 0, sizeof(T));
+    if (scheme == CDG2_SDIRK2) {
+        const double g = 1.0 - 1.0 / std::sqrt(2.0);
+        T.s = 2;
+        T.A[0][0] = g;
+        T.A[1][0] = 1.0 - g;
+        T.A[1][1] = g;
+    } else {
+        double g = 0.43;
+        for (int it = 0; it < 60; ++it) {
+            const double p = ((6.0 * g - 18.0) * g + 9.0) * g - 1.0;
+            const double dp = (18.0 * g - 36.0) * g + 9.0;
+            g -= p / dp;
+        }
+        const double c2 = 0.5 * (1.0 + g);
+        T.s = 3;
+        T.A[0][0] = g;
+        T.A[1][0] = c2 - g;
+        T.A[1][1] = g;
+        T.A[2][0] = -(6.0 * g * g - 16.0 * g + 1.0) / 4.0;
+        T.A[2][1] = (6.0 * g * g - 20.0 * g + 5.0) / 4.0;
+        T.A[2][2] = g;
+    }
+    for (int i = 0; i < T.s; ++i) {
+        T.b[i] = T.A[T.s - 1][i];
+        double c = 0.0;
+        for (int j = 0; j <= i; ++j) c += T.A[i][j];
+        T.c[i] = c;
+    }
+    return T;
+}
+
+// Views into the step workspace.
+struct Work {
+    long long n;
+    int m;
+    double* rhs;
+    double* Y;
+    double* fY;
+    double* G;
+    double* b64;
+    double* K[3];
+    void* basis;      // (m + 2) vectors of the Krylov precision: V_0..V_m, w
+    void* dx;         // the Krylov correction
+    void* Yk;         // primal state in the Krylov precision (mixed) / unused
+    void* bk;         // right-hand side in the Krylov precision (mixed)
+    double* red;      // reduction partials
+    double* red_out;  // reduction results (MAX_KRYLOV + 1)
+};
+
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+static int ensure_work(const cdg2_mesh& m, int kdim, bool mixed, Work& w) {
+    const long long n = m.ndof;
+    const size_t ks = mixed ? sizeof(float) : sizeof(double);
+    const size_t vec64 = align256(sizeof(double) * n);
+    const size_t veck = align256(ks * n);
+    const size_t red = align256(sizeof(double) * reduction_scratch_doubles(MAX_KRYLOV + 1));
+    const size_t out = align256(sizeof(double) * (MAX_KRYLOV + 1));
+    // 8 FP64 vectors; basis (kdim + 2) + dx + Yk + bk in the Krylov precision
+    const size_t need = 8 * vec64 + (size_t)(kdim + 5) * veck + red + out;
+    if (m.step_ws_bytes < need) {
+        if (m.step_ws) cudaFree(m.step_ws);
+        m.step_ws = nullptr;
+        m.step_ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&m.step_ws, need);
+        if (e != cudaSuccess) return cuda_fail(e, "cdg2_step: workspace");
+        m.step_ws_bytes = need;
+    }
+    char* p = static_cast<char*>(m.step_ws);
+    w.n = n;
+    w.m = kdim;
+    double** v64[8] = {&w.rhs, &w.Y, &w.fY, &w.G, &w.b64, &w.K[0], &w.K[1], &w.K[2]};
+    for (auto* q : v64) {
+        *q = reinterpret_cast<double*>(p);
+        p += vec64;
+    }
+    w.basis = p;
+    p += (size_t)(kdim + 2) * veck;
+    w.dx = p;
+    p += veck;
+    w.Yk = p;
+    p += veck;
+    w.bk = p;
+    p += veck;
+    w.red = reinterpret_cast<double*>(p);
+    p += red;
+    w.red_out = reinterpret_cast<double*>(p);
+    return CDG2_OK;
+}
+
+#define CDG2_TRY(...)                                              \
+    do {                                                           \
+        cudaError_t e_ = (__VA_ARGS__);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, "cdg2_step"); \
+    } while (0)
+
+// ||x||_2 of a vector, read back to the host.
+template <typename T>
+static int norm2(const Work& w, const T* x, cudaStream_t st, double* out) {
+    CDG2_TRY(vec_mdot<T>(w.n, 1, x, w.n, x, w.red, w.red_out, st));
+    double v = 0.0;
+    CDG2_TRY(cudaMemcpyAsync(&v, w.red_out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CDG2_TRY(cudaStreamSynchronize(st));
+    *out = std::sqrt(v);
+    return CDG2_OK;
+}
+
+// A cycle ends early (done) on convergence, breakdown or the iteration cap;
+// otherwise it used all kdim vectors and GMRES restarts from the true residual.
+static bool done_cycle_needs_restart(bool done, int jlast, int kdim) { return !done && jlast == kdim - 1; }
+
+// Restarted GMRES(m) with CGS2 for (I - gdt J(Yop)) x = b, x0 = 0.
+// Stops when ||b - A x||_2 <= rtol ||b||_2 (the Arnoldi estimate) or after
+// maxit inner iterations.  T is the Krylov precision.
+template <typename T>
+static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, const T* b, T* x, double rtol,
+                 int maxit, const Work& w, cudaStream_t st, int flags, int* iters, double* relres) {
+    const long long n = w.n;
+    const int kdim = w.m;
+    T* V = static_cast<T*>(w.basis);
+    T* wv = V + (size_t)(kdim + 1) * n;
+    const int jflags = CDG2_MINV | ((sizeof(T) == 4) ? CDG2_FP32 : 0) | (flags & CDG2_FORCING);
+    CDG2_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
+    double beta0 = 0.0;
+    if (int rc = norm2<T>(w, b, st, &beta0)) return rc;
+    *iters = 0;
+    *relres = 0.0;
+    if (beta0 == 0.0) return CDG2_OK;
+    if (!std::isfinite(beta0)) {
+        set_error("cdg2_step: non-finite Newton residual");
+        return CDG2_ERR_NONFINITE;
+    }
+    std::vector<double> H((size_t)(kdim + 1) * kdim), cs(kdim), sn(kdim), g(kdim + 1), y(kdim), hcol(kdim + 1);
+    double beta = beta0;
+    CDG2_TRY(vec_convert<T, T>(n, b, 1.0 / beta, V, st));   // V_0 = b / ||b||
+    int total = 0;
+    double resid = beta;
+    while (true) {
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jlast = -1;
+        bool done = false;
+        for (int j = 0; j < kdim; ++j) {
+            T* vj = V + (size_t)j * n;
+            CDG2_TRY(launch_jvp_axpby(m, c, Yop, vj, 1.0, -gdt, wv, jflags, st));   // w = (I - gdt J) v_j
+            std::fill(hcol.begin(), hcol.end(), 0.0);
+            for (int pass = 0; pass < 2; ++pass) {                                // CGS2
+                CDG2_TRY(vec_mdot<T>(n, j + 1, V, n, wv, w.red, w.red_out, st));
+                CDG2_TRY(vec_mgs_update<T>(n, j + 1, V, n, w.red_out, wv, st));
+                std::vector<double> hp(j + 1);
+                CDG2_TRY(cudaMemcpyAsync(hp.data(), w.red_out, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
+                CDG2_TRY(cudaStreamSynchronize(st));
+                for (int i = 0; i <= j; ++i) hcol[i] += hp[i];
+            }
+            double hn = 0.0;
+            if (int rc = norm2<T>(w, wv, st, &hn)) return rc;
+            hcol[j + 1] = hn;
+            // previous Givens rotations, then a new one zeroing hcol[j + 1]
+            for (int i = 0; i < j; ++i) {
+                const double a = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+                hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+                hcol[i] = a;
+            }
+            const double r = std::hypot(hcol[j], hcol[j + 1]);
+            cs[j] = r > 0.0 ? hcol[j] / r : 1.0;
+            sn[j] = r > 0.0 ? hcol[j + 1] / r : 0.0;
+            hcol[j] = r;
+            hcol[j + 1] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            for (int i = 0; i <= j; ++i) H[(size_t)i * kdim + j] = hcol[i];
+            ++total;
+            resid = std::fabs(g[j + 1]);
+            jlast = j;
+            if (!std::isfinite(resid)) {
+                set_error("cdg2_step: non-finite GMRES residual");
+                return CDG2_ERR_NONFINITE;
+            }
+            if (hn == 0.0 || resid <= rtol * beta0 || total >= maxit) {
+                done = true;
+                break;
+            }
+            CDG2_TRY(vec_convert<T, T>(n, wv, 1.0 / hn, V + (size_t)(j + 1) * n, st));
+        }
+        // y = R^{-1} g (upper triangular), x += V y
+        for (int i = jlast; i >= 0; --i) {
+            double acc = g[i];
+            for (int k = i + 1; k <= jlast; ++k) acc -= H[(size_t)i * kdim + k] * y[k];
+            y[i] = acc / H[(size_t)i * kdim + i];
+        }
+        Coeffs yc;
+        for (int i = 0; i <= jlast; ++i) yc.v[i] = y[i];
+        CDG2_TRY(vec_basis_combine<T>(n, jlast + 1, V, n, yc, x, st));
+        if (resid <= rtol * beta0 || total >= maxit || !done_cycle_needs_restart(done, jlast, kdim)) break;
+        // restart: r = b - A x into V_0
+        CDG2_TRY(launch_jvp_axpby(m, c, Yop, x, 1.0, -gdt, wv, jflags, st));
+        CDG2_TRY(vec_convert<T, T>(n, b, 1.0, V, st));
+        CDG2_TRY(vec_axpby<T>(n, -1.0, wv, 1.0, V, st));
+        if (int rc = norm2<T>(w, V, st, &beta)) return rc;
+        if (beta <= rtol * beta0) {
+            resid = beta;
+            break;
+        }
+        CDG2_TRY(vec_convert<T, T>(n, V, 1.0 / beta, V, st));
+    }
+    *iters = total;
+    *relres = resid / beta0;
+    return CDG2_OK;
+}
+
+}  // namespace cdg2
+
+using namespace cdg2;
+
+extern "C" int cdg2_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double t, double dt,
+                         const cdg2_solver_opts* o, cdg2_stats* stats, void* stream) {
+    const auto t_start = std::chrono::steady_clock::now();
+    if (!m || !p || !U || !o) {
+        set_error("cdg2_step: NULL argument");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if ((o->scheme != CDG2_SDIRK2 && o->scheme != CDG2_SDIRK3) || o->gmres_restart < 1 ||
+        o->gmres_restart > MAX_KRYLOV || o->max_newton < 1 || o->max_gmres < 1 || !(dt > 0.0) ||
+        (o->flags & ~CDG2_FORCING)) {
+        set_error("cdg2_step: invalid options (scheme 2|3, 1 <= gmres_restart <= 64, max_newton, max_gmres >= 1, "
+                  "dt > 0, flags in {0, CDG2_FORCING})");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool mixed = o->mixed != 0;
+    Work w;
+    if (int rc = ensure_work(*m, o->gmres_restart, mixed, w)) return rc;
+    const Coef c = make_coef(*p);
+    const Tableau T = sdirk_tableau(o->scheme);
+    const long long n = w.n;
+    cdg2_stats S;
+    std::memset(&S, 0, sizeof(S));
+    S.stages = T.s;
+    int status = CDG2_OK;
+
+    CDG2_TRY(cudaMemcpyAsync(w.Y, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    for (int i = 0; i < T.s && status == CDG2_OK; ++i) {
+        const double ti = t + T.c[i] * dt;
+        const double gdt = dt * T.A[i][i];
+        Coeffs a;
+        for (int j = 0; j < i; ++j) a.v[j] = dt * T.A[i][j];
+        // rhs_i = U_n + dt sum_{j<i} a_ij K_j  (K_j are stored back to back)
+        CDG2_TRY(vec_lincomb(n, U, i, w.K[0], w.K[1] - w.K[0], a, w.rhs, st));
+        double g0 = 0.0;
+        bool converged = false;
+        for (int it = 0; it <= o->max_newton; ++it) {
+            CDG2_TRY(launch_apply(*m, c, w.Y, w.fY, CDG2_MINV | (o->flags & CDG2_FORCING), ti, st));
+            CDG2_TRY(vec_newton_residual(n, w.Y, w.fY, gdt, w.rhs, w.G, st));
+            double gn = 0.0;
+            if (int rc = norm2<double>(w, w.G, st, &gn)) return rc;
+            if (!std::isfinite(gn)) {
+                set_error("cdg2_step: non-finite Newton residual");
+                status = CDG2_ERR_NONFINITE;
+                break;
+            }
+            if (it == 0) g0 = gn;
+            S.residual0[i] = g0;
+            S.residual[i] = gn;
+            if (gn <= std::fmax(o->newton_rtol * g0, o->newton_atol)) {
+                converged = true;
+                break;
+            }
+            if (it == o->max_newton) break;
+            ++S.newton_iters;
+            int its = 0;
+            double rr = 0.0;
+            int rc;
+            if (!mixed) {
+                CDG2_TRY(vec_convert<double, double>(n, w.G, -1.0, w.b64, st));
+                rc = gmres<double>(*m, c, w.Y, gdt, w.b64, static_cast<double*>(w.dx), o->gmres_rtol, o->max_gmres, w,
+                                   st, o->flags, &its, &rr);
+                if (rc == CDG2_OK) CDG2_TRY(vec_add_into<double>(n, static_cast<double*>(w.dx), w.Y, st));
+            } else {
+                CDG2_TRY(vec_convert<double, float>(n, w.Y, 1.0, static_cast<float*>(w.Yk), st));
+                CDG2_TRY(vec_convert<double, float>(n, w.G, -1.0, static_cast<float*>(w.bk), st));
+                rc = gmres<float>(*m, c, static_cast<float*>(w.Yk), gdt, static_cast<float*>(w.bk),
+                                  static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, o->flags, &its, &rr);
+                if (rc == CDG2_OK) CDG2_TRY(vec_add_into<float>(n, static_cast<float*>(w.dx), w.Y, st));
+            }
+            S.gmres_iters += its;
+            if (rc != CDG2_OK) {
+                status = rc;
+                break;
+            }
+        }
+        if (status != CDG2_OK) break;
+        if (!converged) {
+            set_error("cdg2_step: Newton did not reach the tolerance within max_newton iterations");
+            status = CDG2_ERR_NOT_CONVERGED;
+            break;
+        }
+        // K_i = f(Y_i): the last residual evaluation was at the converged Y_i
+        CDG2_TRY(cudaMemcpyAsync(w.K[i], w.fY, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    }
+    if (status == CDG2_OK) {
+        Coeffs bb;
+        for (int i = 0; i < T.s; ++i) bb.v[i] = dt * T.b[i];
+        CDG2_TRY(vec_lincomb(n, U, T.s, w.K[0], w.K[1] - w.K[0], bb, U, st));   // U_{n+1} = U_n + dt sum b_i K_i
+        CDG2_TRY(cudaStreamSynchronize(st));
+    }
+    S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (stats) *stats = S;
+    return status;
+}

@@ -160,6 +160,79 @@ def time_applies(G, torch, mesh, p, U, out, flags, steps, warmup, flush):
     return [a.elapsed_time(b) for a, b in ev]
 
 
+def time_op(G, torch, fn, steps, warmup, flush):
+    """Mean CUDA-event time (ms) of fn() over `steps` calls, L2 flushed before each."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush.fill_(1)
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush.fill_(1)
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+
+def measure_derivatives(G, torch, w, mesh, p, U, flush, steps):
+    """JVP and VJP throughput (GDOF/s) in FP64 and FP32 on the bench workload."""
+    out = {}
+    lam = torch.sin(torch.arange(U.numel(), device="cuda", dtype=torch.float64) * 0.37)
+    res = torch.empty_like(U)
+    gth = torch.zeros(8, dtype=torch.float64, device="cuda")
+    U32, lam32, res32 = U.float(), lam.float(), torch.empty_like(U, dtype=torch.float32)
+    cases = {
+        "jvp_fp64": lambda: G.cdg2_jvp(mesh, p, U, lam, res, G.CDG2_MINV),
+        "jvp_fp32": lambda: G.cdg2_jvp(mesh, p, U32, lam32, res32, G.CDG2_MINV | G.CDG2_FP32),
+        "vjp_fp64": lambda: G.cdg2_vjp(mesh, p, U, lam, res, gth, G.CDG2_MINV),
+        "vjp_fp32": lambda: G.cdg2_vjp(mesh, p, U32, lam32, res32, gth, G.CDG2_MINV | G.CDG2_FP32),
+    }
+    for name, fn in cases.items():
+        ms = time_op(G, torch, fn, steps, 3, flush)
+        out[name] = {"value": w.n_dof / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "ms": ms}
+    return out
+
+
+def measure_solve(G, torch, cfg: int, steps: int):
+    """Implicit SDIRK steps to Newton relative residual 1e-10: FP64 Krylov vs FP32 Krylov + FP64 refinement."""
+    import cdg2_inputs as I
+    w = I.workload(cfg)
+    mesh = G.cdg2_mesh_create(w.dim, w.cells, w.extent, w.periodic, w.k)
+    U0, p = make_inputs(G, w, I, mesh)
+    scheme = G.CDG2_SDIRK2 if w.k == 1 else G.CDG2_SDIRK3
+    result = {"workload": w.name, "n_dof": w.n_dof, "dt": w.dt, "steps": steps, "scheme": f"SDIRK{scheme}",
+              "newton_rtol": 1e-10}
+    finals = {}
+    for mode, mixed, eta in (("fp64", False, 1e-3), ("mixed", True, 1e-4)):
+        U = U0.clone()
+        # one untimed step warms up the kernels and allocates the workspace
+        G.cdg2_step(mesh, p, U.clone(), 0.0, w.dt, G.make_opts(scheme=scheme, mixed=mixed, newton_rtol=1e-10,
+                                                                 gmres_rtol=eta))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        newton = gm = 0
+        worst = 0.0
+        for i in range(steps):
+            rc, st = G.cdg2_step(mesh, p, U, i * w.dt, w.dt, G.make_opts(scheme=scheme, mixed=mixed, newton_rtol=1e-10,
+                                                                          gmres_rtol=eta))
+            newton += st["newton_iters"]
+            gm += st["gmres_iters"]
+            worst = max([worst] + [r / r0 for r, r0 in zip(st["residual"], st["residual0"]) if r0 > 0])
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        finals[mode] = U
+        result[mode] = {"s_per_step": sec / steps, "newton_iters": newton, "gmres_iters": gm,
+                        "gmres_rtol": eta, "max_final_rel_residual": worst,
+                        "dof_steps_per_s": w.n_dof * steps / sec}
+    d = finals["mixed"] - finals["fp64"]
+    result["mixed_vs_fp64_rel_l2"] = float(d.norm() / finals["fp64"].norm())
+    result["speedup_mixed_over_fp64"] = result["fp64"]["s_per_step"] / result["mixed"]["s_per_step"]
+    return result
+
+
 def cpu_oracle_baseline(w, seconds: float = 12.0):
     """The oracle (plain FP64 PyTorch CPU) timed on this host on the same workload."""
     import torch
@@ -233,6 +306,8 @@ def main():
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve-config", type=int, default=3, help="workload of the implicit-solve comparison")
+    ap.add_argument("--solve-steps", type=int, default=2, help="timed implicit steps per precision (0: skip)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -300,7 +375,8 @@ def main():
     e = out32.double().view(w.n_elem, 6, -1) - ref64.view(w.n_elem, 6, -1)
     rel32 = float((e.pow(2).sum(dim=(0, 2)).sqrt() / ref64.view(w.n_elem, 6, -1).pow(2).sum(dim=(0, 2)).sqrt()).max())
     fp32 = {"value": w.n_dof / (statistics.mean(ms32) * 1e-3) / 1e9, "unit": "GDOF/s",
-            "rel_l2_err_vs_fp64_max_species": rel32}
+            "rel_l2_err_vs_fp64_max_species": rel32,
+            "hbm_frac": 8 * w.n_dof / (statistics.mean(ms32) * 1e-3) / 1e9 / peaks["hbm_gbs"]}
 
     # ---- end to end through the API: pinned host U -> device, apply, result -> pinned host ----
     hU = U.cpu().pin_memory()
@@ -326,6 +402,9 @@ def main():
     e2e = {"value": world * w.n_dof / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
 
+    derivs = measure_derivatives(G, torch, w, mesh, p, U, flush, max(10, args.steps // 8))
+    solve = measure_solve(G, torch, args.solve_config, args.solve_steps) if args.solve_steps > 0 else None
+
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -345,6 +424,8 @@ def main():
                      "flops_per_launch": fl, "kernel": f"apply_kernel<{w.dim},{w.k},double>",
                      "hbm_frac": hbm_frac, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_kind": kind},
         "fp32": fp32,
+        "derivatives": derivs,
+        "solve": solve,
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clk,

@@ -50,6 +50,17 @@ __device__ __forceinline__ void load_tab(STab<K, T>& s, const Tab1D& t) {
     }
 }
 
+// a / b: IEEE division in FP64; the fast reciprocal-based divide in FP32
+// (2 ulp), which the FP32 path's 1e-5 error budget allows.
+template <typename T>
+__device__ __forceinline__ T qdiv(T a, T b) {
+    return a / b;
+}
+template <>
+__device__ __forceinline__ float qdiv<float>(float a, float b) {
+    return __fdividef(a, b);
+}
+
 template <typename T>
 struct Ident {
     using type = T;
@@ -60,36 +71,63 @@ struct Ident {
 // is replaced by NO in the output:
 //     out[t][..o..] = sum_i M1(o,i) in1[t][..i..]  (+ M2(o,i) in2[t][..i..])
 // M(o,i) = M[o][i] (TR = false) or M[i][o] (TR = true), row length LD.
+// One thread computes one whole line along AX: its index arithmetic is done
+// once per line, the 1D matrices are held in registers, and each input is
+// loaded once for NO outputs (shared-memory traffic, not FMA issue, limits
+// these passes).  The sums run over i in increasing order.
 template <int AX, int I0, int I1, int I2, int NO, bool TR, int LD, bool TWO, typename T>
 __device__ __forceinline__ void sf_pass(const T* __restrict__ in1, const T* __restrict__ M1,
                                         const typename Ident<T>::type* __restrict__ in2,
                                         const typename Ident<T>::type* __restrict__ M2, int in_stride,
                                         T* __restrict__ out, int out_stride, int nt) {
     constexpr int NI = AX == 0 ? I0 : (AX == 1 ? I1 : I2);
-    constexpr int O0 = AX == 0 ? NO : I0;
-    constexpr int O1 = AX == 1 ? NO : I1;
-    constexpr int O2 = AX == 2 ? NO : I2;
-    constexpr int OSZ = O0 * O1 * O2;
-    constexpr int SI = AX == 0 ? 1 : (AX == 1 ? I0 : I0 * I1);
-    const int total = nt * OSZ;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int tt = idx / OSZ;
-        const int r = idx - tt * OSZ;
-        const int o0 = r % O0;
-        const int o1 = (r / O0) % O1;
-        const int o2 = r / (O0 * O1);
-        const int o = AX == 0 ? o0 : (AX == 1 ? o1 : o2);
-        const int base = (AX == 0 ? 0 : o0) + (AX == 1 ? 0 : o1) * I0 + (AX == 2 ? 0 : o2) * I0 * I1;
-        const T* s1 = in1 + tt * in_stride + base;
-        T acc = T(0);
+    constexpr int NL = I0 * I1 * I2 / NI;                       // lines per tensor
+    constexpr int ST = AX == 0 ? 1 : (AX == 1 ? I0 : I0 * I1);  // stride along AX (input and output)
+    T m1[NO][NI], m2[TWO ? NO : 1][TWO ? NI : 1];
 #pragma unroll
-        for (int i = 0; i < NI; ++i) acc = fma(TR ? M1[i * LD + o] : M1[o * LD + i], s1[i * SI], acc);
-        if constexpr (TWO) {
-            const T* s2 = in2 + tt * in_stride + base;
+    for (int o = 0; o < NO; ++o)
 #pragma unroll
-            for (int i = 0; i < NI; ++i) acc = fma(TR ? M2[i * LD + o] : M2[o * LD + i], s2[i * SI], acc);
+        for (int i = 0; i < NI; ++i) {
+            m1[o][i] = TR ? M1[i * LD + o] : M1[o * LD + i];
+            if constexpr (TWO) m2[o][i] = TR ? M2[i * LD + o] : M2[o * LD + i];
         }
-        out[tt * out_stride + r] = acc;
+    const int total = nt * NL;
+    for (int line = threadIdx.x; line < total; line += blockDim.x) {
+        const int tt = line / NL;
+        const int r = line - tt * NL;
+        int ib, ob;
+        if constexpr (AX == 0) {
+            ib = r * I0;
+            ob = r * NO;
+        } else if constexpr (AX == 1) {
+            const int a = r % I0, b = r / I0;
+            ib = a + b * I0 * I1;
+            ob = a + b * I0 * NO;
+        } else {
+            ib = r;
+            ob = r;
+        }
+        const T* s1 = in1 + tt * in_stride + ib;
+        T v1[NI], v2[TWO ? NI : 1];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) v1[i] = s1[i * ST];
+        if constexpr (TWO) {
+            const T* s2 = in2 + tt * in_stride + ib;
+#pragma unroll
+            for (int i = 0; i < NI; ++i) v2[i] = s2[i * ST];
+        }
+        T* d = out + tt * out_stride + ob;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+            T acc = T(0);
+#pragma unroll
+            for (int i = 0; i < NI; ++i) acc = fma(m1[o][i], v1[i], acc);
+            if constexpr (TWO) {
+#pragma unroll
+                for (int i = 0; i < NI; ++i) acc = fma(m2[o][i], v2[i], acc);
+            }
+            d[o * ST] = acc;
+        }
     }
 }
 

@@ -91,10 +91,10 @@ constexpr int fields_of(int mode) { return mode == MODE_APPLY ? 1 : 2; }
 template <int D, typename T>
 __device__ __forceinline__ void volume_point(const Coef& c, const T u[NS], const T g[NS][D], T Phi[NS][D],
                                              T S[NS]) {
-    const T k11 = T(c.chi0[0]) / (u[3] + T(c.chith[0]));
-    const T k13 = T(c.chi0[1]) / (u[5] + T(c.chith[1]));
-    const T k21 = T(c.chi0[2]) / (u[3] + T(c.chith[2]));
-    const T k22 = T(c.chi0[3]) / (u[0] + T(c.chith[3]));
+    const T k11 = qdiv<T>(T(c.chi0[0]), u[3] + T(c.chith[0]));
+    const T k13 = qdiv<T>(T(c.chi0[1]), u[5] + T(c.chith[1]));
+    const T k21 = qdiv<T>(T(c.chi0[2]), u[3] + T(c.chith[2]));
+    const T k22 = qdiv<T>(T(c.chi0[3]), u[0] + T(c.chith[3]));
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const T v1 = k11 * g[3][j] + k13 * g[5][j];
@@ -121,10 +121,10 @@ template <int D, typename T>
 __device__ __forceinline__ void volume_point_lin(const Coef& c, const T u[NS], const T g[NS][D], const T du[NS],
                                                  const T dg[NS][D], bool has_dth, const double* dth, T dPhi[NS][D],
                                                  T dS[NS]) {
-    const T r11 = T(1) / (u[3] + T(c.chith[0]));
-    const T r13 = T(1) / (u[5] + T(c.chith[1]));
-    const T r21 = T(1) / (u[3] + T(c.chith[2]));
-    const T r22 = T(1) / (u[0] + T(c.chith[3]));
+    const T r11 = qdiv<T>(T(1), u[3] + T(c.chith[0]));
+    const T r13 = qdiv<T>(T(1), u[5] + T(c.chith[1]));
+    const T r21 = qdiv<T>(T(1), u[3] + T(c.chith[2]));
+    const T r22 = qdiv<T>(T(1), u[0] + T(c.chith[3]));
     const T k11 = T(c.chi0[0]) * r11, k13 = T(c.chi0[1]) * r13;
     const T k21 = T(c.chi0[2]) * r21, k22 = T(c.chi0[3]) * r22;
     const T dk11 = -k11 * r11 * du[3], dk13 = -k13 * r13 * du[5];
@@ -169,14 +169,14 @@ __device__ __forceinline__ void face_point(const Coef& c, T pen, const T uM[NS],
                                            const T dP[NS], const T del[NS], T sig[NS], T tau[NS]) {
     T Fh[2];
     {
-        const T vM = T(c.chi0[0]) / (uM[3] + T(c.chith[0])) * dM[3] + T(c.chi0[1]) / (uM[5] + T(c.chith[1])) * dM[5];
-        const T vP = T(c.chi0[0]) / (uP[3] + T(c.chith[0])) * dP[3] + T(c.chi0[1]) / (uP[5] + T(c.chith[1])) * dP[5];
+        const T vM = qdiv<T>(T(c.chi0[0]), uM[3] + T(c.chith[0])) * dM[3] + qdiv<T>(T(c.chi0[1]), uM[5] + T(c.chith[1])) * dM[5];
+        const T vP = qdiv<T>(T(c.chi0[0]), uP[3] + T(c.chith[0])) * dP[3] + qdiv<T>(T(c.chi0[1]), uP[5] + T(c.chith[1])) * dP[5];
         const T lam = fmax(fabs(vM), fabs(vP));
         Fh[0] = T(0.5) * (uM[0] * vM + uP[0] * vP) + T(0.5) * lam * del[0];
     }
     {
-        const T vM = T(c.chi0[2]) / (uM[3] + T(c.chith[2])) * dM[3] - T(c.chi0[3]) / (uM[0] + T(c.chith[3])) * dM[0];
-        const T vP = T(c.chi0[2]) / (uP[3] + T(c.chith[2])) * dP[3] - T(c.chi0[3]) / (uP[0] + T(c.chith[3])) * dP[0];
+        const T vM = qdiv<T>(T(c.chi0[2]), uM[3] + T(c.chith[2])) * dM[3] - qdiv<T>(T(c.chi0[3]), uM[0] + T(c.chith[3])) * dM[0];
+        const T vP = qdiv<T>(T(c.chi0[2]), uP[3] + T(c.chith[2])) * dP[3] - qdiv<T>(T(c.chi0[3]), uP[0] + T(c.chith[3])) * dP[0];
         const T lam = fmax(fabs(vM), fabs(vP));
         Fh[1] = T(0.5) * (uM[1] * vM + uP[1] * vP) + T(0.5) * lam * del[1];
     }
@@ -201,12 +201,12 @@ template <typename T>
 __device__ __forceinline__ void velocity_lin(const Coef& c, int sp, const T u[NS], const T dn[NS], const T du[NS],
                                              const T ddn[NS], T& v, T& dv) {
     if (sp == 0) {
-        const T r1 = T(1) / (u[3] + T(c.chith[0])), r3 = T(1) / (u[5] + T(c.chith[1]));
+        const T r1 = qdiv<T>(T(1), u[3] + T(c.chith[0])), r3 = qdiv<T>(T(1), u[5] + T(c.chith[1]));
         const T k1 = T(c.chi0[0]) * r1, k3 = T(c.chi0[1]) * r3;
         v = k1 * dn[3] + k3 * dn[5];
         dv = -k1 * r1 * du[3] * dn[3] + k1 * ddn[3] - k3 * r3 * du[5] * dn[5] + k3 * ddn[5];
     } else {
-        const T r1 = T(1) / (u[3] + T(c.chith[2])), r0 = T(1) / (u[0] + T(c.chith[3]));
+        const T r1 = qdiv<T>(T(1), u[3] + T(c.chith[2])), r0 = qdiv<T>(T(1), u[0] + T(c.chith[3]));
         const T k1 = T(c.chi0[2]) * r1, k0 = T(c.chi0[3]) * r0;
         v = k1 * dn[3] - k0 * dn[0];
         dv = -k1 * r1 * du[3] * dn[3] + k1 * ddn[3] + k0 * r0 * du[0] * dn[0] - k0 * ddn[0];
@@ -251,10 +251,10 @@ __device__ __forceinline__ void face_point_lin(const Coef& c, T pen, const T uM[
 template <int D, typename T>
 __device__ __forceinline__ void volume_point_adj(const Coef& c, const T u[NS], const T g[NS][D], const T sb[NS],
                                                  const T gb[NS][D], T ub[NS], T Gb[NS][D], double th[8]) {
-    const T r11 = T(1) / (u[3] + T(c.chith[0]));
-    const T r13 = T(1) / (u[5] + T(c.chith[1]));
-    const T r21 = T(1) / (u[3] + T(c.chith[2]));
-    const T r22 = T(1) / (u[0] + T(c.chith[3]));
+    const T r11 = qdiv<T>(T(1), u[3] + T(c.chith[0]));
+    const T r13 = qdiv<T>(T(1), u[5] + T(c.chith[1]));
+    const T r21 = qdiv<T>(T(1), u[3] + T(c.chith[2]));
+    const T r22 = qdiv<T>(T(1), u[0] + T(c.chith[3]));
     const T k11 = T(c.chi0[0]) * r11, k13 = T(c.chi0[1]) * r13;
     const T k21 = T(c.chi0[2]) * r21, k22 = T(c.chi0[3]) * r22;
 #pragma unroll
@@ -328,14 +328,14 @@ __device__ __forceinline__ void face_point_adj(const Coef& c, T pen, bool ownM, 
         ub[sp] += Fb * (T(0.5) * vX + T(0.5) * lam * sX);
         const T vb = Fb * (T(0.5) * uX[sp] + (fromX ? T(0.5) * del[sp] * sgn0(vX) : T(0)));
         if (sp == 0) {
-            const T r1 = T(1) / (uX[3] + T(c.chith[0])), r3 = T(1) / (uX[5] + T(c.chith[1]));
+            const T r1 = qdiv<T>(T(1), uX[3] + T(c.chith[0])), r3 = qdiv<T>(T(1), uX[5] + T(c.chith[1]));
             const T k1 = T(c.chi0[0]) * r1, k3 = T(c.chi0[1]) * r3;
             ub[3] += vb * (-k1 * r1 * dX[3]);
             ub[5] += vb * (-k3 * r3 * dX[5]);
             db[3] += vb * k1;
             db[5] += vb * k3;
         } else {
-            const T r1 = T(1) / (uX[3] + T(c.chith[2])), r0 = T(1) / (uX[0] + T(c.chith[3]));
+            const T r1 = qdiv<T>(T(1), uX[3] + T(c.chith[2])), r0 = qdiv<T>(T(1), uX[0] + T(c.chith[3]));
             const T k1 = T(c.chi0[2]) * r1, k0 = T(c.chi0[3]) * r0;
             ub[3] += vb * (-k1 * r1 * dX[3]);
             ub[0] += vb * (k0 * r0 * dX[0]);

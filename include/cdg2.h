@@ -104,7 +104,12 @@ typedef struct cdg2_params {
  *   G(Y) = Y - dt a_ii f(Y) - rhs_i, Y^0 the previous stage value (U_n first);
  *   at most max_newton corrections per stage.
  * GMRES(gmres_restart) with CGS2 stops at ||r||_2 <= gmres_rtol ||G||_2 or
- *   after max_gmres iterations per Newton correction; 1 <= gmres_restart <= 64. */
+ *   after max_gmres iterations per Newton correction; 1 <= gmres_restart <= 64.
+ * precond: 0 = none; 1 = right preconditioning by the modal diagonal
+ *   P = 1 - dt a_ii A_s d_i of the diffusion part (for an orthonormal mode on
+ *   a Cartesian cell the volume and consistency terms cancel on the
+ *   diagonal, leaving the CDG2 penalty: d_i = -chi_e (k+1)^2 sum_j
+ *   (psi_{a_j}(0)^2 + psi_{a_j}(1)^2) / h_j^2), applied inside the JVP. */
 typedef struct cdg2_solver_opts {
     int scheme;
     int mixed;
@@ -115,6 +120,7 @@ typedef struct cdg2_solver_opts {
     double newton_rtol;
     double newton_atol;
     double gmres_rtol;
+    int precond;
 } cdg2_solver_opts;
 
 /* Statistics of one cdg2_step call. */

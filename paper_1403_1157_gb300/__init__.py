@@ -72,6 +72,7 @@ class SolverOpts(ctypes.Structure):
         ("scheme", ctypes.c_int), ("mixed", ctypes.c_int), ("flags", ctypes.c_int), ("max_newton", ctypes.c_int),
         ("gmres_restart", ctypes.c_int), ("max_gmres", ctypes.c_int),
         ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double), ("gmres_rtol", ctypes.c_double),
+        ("precond", ctypes.c_int),
     ]
 
 
@@ -296,11 +297,12 @@ def cdg2_vjp(mesh: Mesh, params, U: torch.Tensor, lam: torch.Tensor, gU: torch.T
 
 
 def make_opts(scheme=CDG2_SDIRK2, mixed=False, flags=0, max_newton=20, gmres_restart=30, max_gmres=300,
-              newton_rtol=1e-10, newton_atol=0.0, gmres_rtol=1e-3) -> SolverOpts:
+              newton_rtol=1e-10, newton_atol=0.0, gmres_rtol=1e-3, precond=1) -> SolverOpts:
     o = SolverOpts()
     o.scheme, o.mixed, o.flags, o.max_newton = int(scheme), int(bool(mixed)), int(flags), int(max_newton)
     o.gmres_restart, o.max_gmres = int(gmres_restart), int(max_gmres)
     o.newton_rtol, o.newton_atol, o.gmres_rtol = float(newton_rtol), float(newton_atol), float(gmres_rtol)
+    o.precond = int(precond)
     return o
 
 

@@ -74,9 +74,11 @@ cudaError_t launch_apply(const cdg2_mesh& m, const Coef& c, const void* U, void*
                          cudaStream_t stream);
 cudaError_t launch_jvp(const cdg2_mesh& m, const Coef& c, const void* U, const void* dU, const double* dtheta,
                        void* out, int flags, cudaStream_t stream);
-// out = alpha dU + beta J(U) dU (the Krylov operator v - gamma dt J v in one pass)
+// out = alpha w + beta J(U) w with w = pscale . dU (pscale: [6][n_basis] per-mode
+// scale on the device, or null): the right-preconditioned Krylov operator
+// (I - gamma dt J) P^{-1} v in one pass.
 cudaError_t launch_jvp_axpby(const cdg2_mesh& m, const Coef& c, const void* U, const void* dU, double alpha,
-                             double beta, void* out, int flags, cudaStream_t stream);
+                             double beta, const double* pscale, void* out, int flags, cudaStream_t stream);
 // VJP: gU = (df/dU)^T lam; when gtheta is non-null also (df/dtheta)^T lam via
 // theta_part ([vjp_grid(m)][8] doubles of scratch) and a fixed-order reduction.
 cudaError_t launch_vjp(const cdg2_mesh& m, const Coef& c, const void* U, const void* lam, void* gU,

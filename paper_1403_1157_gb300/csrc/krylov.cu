@@ -109,6 +109,14 @@ __global__ void __launch_bounds__(VT) k_basis_combine(long long n, int nv, const
     }
 }
 
+// x[i] *= table[i % period]  (a per-(species, mode) diagonal on element-major vectors)
+template <typename T>
+__global__ void __launch_bounds__(VT) k_scale_modes(long long n, const double* __restrict__ table, int period,
+                                                    T* __restrict__ x) {
+    for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
+        x[i] = T(double(x[i]) * table[i % period]);
+}
+
 static unsigned grid_for(long long n) {
     long long b = (n + VT - 1) / VT;
     const long long cap = 152LL * 16;   // enough blocks to saturate HBM; loops cover the rest
@@ -170,8 +178,16 @@ cudaError_t vec_basis_combine(long long n, int nv, const T* V, long long ldv, co
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t vec_scale_modes(long long n, const double* table, int period, T* x, cudaStream_t st) {
+    k_scale_modes<T><<<grid_for(n), VT, 0, st>>>(n, table, period, x);
+    return cudaGetLastError();
+}
+
 long long reduction_scratch_doubles(int max_vectors) { return (long long)RED_BLOCKS * max_vectors; }
 
+template cudaError_t vec_scale_modes<double>(long long, const double*, int, double*, cudaStream_t);
+template cudaError_t vec_scale_modes<float>(long long, const double*, int, float*, cudaStream_t);
 template cudaError_t vec_axpby<double>(long long, double, const double*, double, double*, cudaStream_t);
 template cudaError_t vec_axpby<float>(long long, double, const float*, double, float*, cudaStream_t);
 template cudaError_t vec_convert<double, float>(long long, const double*, double, float*, cudaStream_t);

@@ -31,6 +31,8 @@ cudaError_t vec_mgs_update(long long n, int nv, const T* V, long long ldv, const
 template <typename T>
 cudaError_t vec_basis_combine(long long n, int nv, const T* V, long long ldv, const Coeffs& y, T* x,
                               cudaStream_t st);
+template <typename T>
+cudaError_t vec_scale_modes(long long n, const double* table, int period, T* x, cudaStream_t st);
 long long reduction_scratch_doubles(int max_vectors);
 
 }  // namespace cdg2

@@ -76,6 +76,7 @@ struct OpArgs {
     double dtheta[8];   // tangent of (d1, d2, gamma, alpha1, alpha2, f1, k_ox, beta1)
     double* theta_part; // VJP: per-CTA partial sums of (df/dtheta)^T lambda, [gridDim.x][8], or null
     double alpha, beta; // JVP epilogue: out = alpha dU + beta J dU (0, 1 for the plain JVP)
+    const double* pscale; // JVP: optional [6][n_basis] scale of the tangent (right preconditioner), or null
 };
 
 constexpr int MODE_APPLY = 0, MODE_JVP = 1, MODE_VJP = 2;
@@ -413,18 +414,27 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
         }
         const long long nb = nbr[e][f];
         if (nb >= 0) {
-            const T* nbp = args.U[fi] + (nb * NS + s) * NB;
-            const T* um = f ? own : nbp;     // K^- coefficients
-            const T* up = f ? nbp : own;     // K^+ coefficients
-            del = um[coef_index<D, K, A>(0, b0, b1)] - up[coef_index<D, K, A>(0, b0, b1)];
+            const T* nbg = args.U[fi] + (nb * NS + s) * NB;
+            T nbv[NB1];   // the neighbour's coefficients along the normal line (tangent: preconditioned)
+            const bool scaled = MODE == MODE_JVP && fi == 1 && args.pscale != nullptr;
+#pragma unroll
+            for (int m = 0; m < NB1; ++m) {
+                const int ci = coef_index<D, K, A>(m, b0, b1);
+                nbv[m] = scaled ? nbg[ci] * T(args.pscale[s * NB + ci]) : nbg[ci];
+            }
+            T ov[NB1];
+#pragma unroll
+            for (int m = 0; m < NB1; ++m) ov[m] = own[coef_index<D, K, A>(m, b0, b1)];
+            const T* um = f ? ov : nbv;     // K^- coefficients
+            const T* up = f ? nbv : ov;     // K^+ coefficients
+            del = um[0] - up[0];
 #pragma unroll
             for (int m = 1; m < NB1; ++m) {
-                const int ci = coef_index<D, K, A>(m, b0, b1);
-                del = fma(tb.e[1][m], um[ci], del);
-                del = fma(-tb.e[0][m], up[ci], del);
+                del = fma(tb.e[1][m], um[m], del);
+                del = fma(-tb.e[0][m], up[m], del);
             }
 #pragma unroll
-            for (int m = 0; m < NB1; ++m) dn = fma(tb.d[1 - f][m], nbp[coef_index<D, K, A>(m, b0, b1)], dn);
+            for (int m = 0; m < NB1; ++m) dn = fma(tb.d[1 - f][m], nbv[m], dn);
         }
         T* o = FC + (((fi * EPB + e) * 2 + f) * 4) * NS * NBT + s * NBT + t;
         o[0 * NS * NBT] = uo;
@@ -620,7 +630,9 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
     for (int i = threadIdx.x; i < F * P::UR; i += blockDim.x) {
         const int fi = i / P::UR, r = i % P::UR;
         const long long ge = e0 + r / (NS * NB);
-        sU[i] = ge < g.E ? args.U[fi][e0 * NS * NB + r] : T(0);
+        T v = ge < g.E ? args.U[fi][e0 * NS * NB + r] : T(0);
+        if (MODE == MODE_JVP && fi == 1 && args.pscale) v *= T(args.pscale[r % (NS * NB)]);
+        sU[i] = v;
     }
     __syncthreads();
 
@@ -875,6 +887,7 @@ static OpArgs<T> make_args(const void* U, const void* dU, void* out, int flags, 
     a.theta_part = theta_part;
     a.alpha = 0.0;
     a.beta = 1.0;
+    a.pscale = nullptr;
     return a;
 }
 
@@ -895,16 +908,18 @@ cudaError_t launch_jvp(const cdg2_mesh& m, const Coef& c, const void* U, const v
 }
 
 cudaError_t launch_jvp_axpby(const cdg2_mesh& m, const Coef& c, const void* U, const void* dU, double alpha,
-                             double beta, void* out, int flags, cudaStream_t st) {
+                             double beta, const double* pscale, void* out, int flags, cudaStream_t st) {
     if (flags & CDG2_FP32) {
         OpArgs<float> a = make_args<float>(U, dU, out, flags, 0.0, nullptr, nullptr);
         a.alpha = alpha;
         a.beta = beta;
+        a.pscale = pscale;
         return dispatch<MODE_JVP, float>(m, c, a, st);
     }
     OpArgs<double> a = make_args<double>(U, dU, out, flags, 0.0, nullptr, nullptr);
     a.alpha = alpha;
     a.beta = beta;
+    a.pscale = pscale;
     return dispatch<MODE_JVP, double>(m, c, a, st);
 }
 

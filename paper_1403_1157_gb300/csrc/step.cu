@@ -87,6 +87,7 @@ struct Work {
     void* bk;         // right-hand side in the Krylov precision (mixed)
     double* red;      // reduction partials
     double* red_out;  // reduction results (MAX_KRYLOV + 1)
+    double* pinv;     // [6][n_basis] right preconditioner P^{-1}
 };
 
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -98,8 +99,9 @@ static int ensure_work(const cdg2_mesh& m, int kdim, bool mixed, Work& w) {
     const size_t veck = align256(ks * n);
     const size_t red = align256(sizeof(double) * reduction_scratch_doubles(MAX_KRYLOV + 1));
     const size_t out = align256(sizeof(double) * (MAX_KRYLOV + 1));
+    const size_t tab = align256(sizeof(double) * NS * m.nb);
     // 8 FP64 vectors; basis (kdim + 2) + dx + Yk + bk in the Krylov precision
-    const size_t need = 8 * vec64 + (size_t)(kdim + 5) * veck + red + out;
+    const size_t need = 8 * vec64 + (size_t)(kdim + 5) * veck + red + out + tab;
     if (m.step_ws_bytes < need) {
         if (m.step_ws) cudaFree(m.step_ws);
         m.step_ws = nullptr;
@@ -127,7 +129,39 @@ static int ensure_work(const cdg2_mesh& m, int kdim, bool mixed, Work& w) {
     w.red = reinterpret_cast<double*>(p);
     p += red;
     w.red_out = reinterpret_cast<double*>(p);
+    p += out;
+    w.pinv = reinterpret_cast<double*>(p);
     return CDG2_OK;
+}
+
+// P^{-1} for every (species, mode): P = 1 - gdt A_s d_i with d_i the modal
+// diagonal of the diffusion part of M^{-1} L_h on an interior Cartesian cell:
+// sum_j h_j^{-2} (-int psi'^2 + [psi' psi]_0^1 - chi_e (k+1)^2 (psi(0)^2 + psi(1)^2))
+// (the first two cancel for Legendre modes; they are kept as computed).
+static void modal_pinv(const cdg2_mesh& m, const Coef& c, double gdt, std::vector<double>& out) {
+    const Geo& g = m.geo;
+    const Tab1D& t = m.tab;
+    const int k = g.k, nb1 = k + 1;
+    double d1[MAXK + 1];
+    for (int a = 0; a <= k; ++a) {
+        double vol = 0.0;
+        for (int q = 0; q < k + 2; ++q) vol += t.w[q] * t.D[q][a] * t.D[q][a];
+        const double face = t.d[1][a] * t.e[1][a] - t.d[0][a] * t.e[0][a];
+        const double pen = g.chi_e * (k + 1) * (k + 1) * (t.e[0][a] * t.e[0][a] + t.e[1][a] * t.e[1][a]);
+        d1[a] = -vol + face - pen;
+    }
+    out.assign((size_t)NS * m.nb, 1.0);
+    for (int s = 0; s < NS; ++s)
+        for (int i = 0; i < m.nb; ++i) {
+            int r = i;
+            double d = 0.0;
+            for (int j = 0; j < g.dim; ++j) {
+                const int a = r % nb1;
+                r /= nb1;
+                d += d1[a] / (g.h[j] * g.h[j]);
+            }
+            out[(size_t)s * m.nb + i] = 1.0 / (1.0 - gdt * c.A[s] * d);
+        }
 }
 
 #define CDG2_TRY(...)                                              \
@@ -156,7 +190,8 @@ static bool done_cycle_needs_restart(bool done, int jlast, int kdim) { return !d
 // maxit inner iterations.  T is the Krylov precision.
 template <typename T>
 static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, const T* b, T* x, double rtol,
-                 int maxit, const Work& w, cudaStream_t st, int flags, int* iters, double* relres) {
+                 int maxit, const Work& w, cudaStream_t st, int flags, const double* pinv, int* iters,
+                 double* relres) {
     const long long n = w.n;
     const int kdim = w.m;
     T* V = static_cast<T*>(w.basis);
@@ -184,7 +219,7 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
         bool done = false;
         for (int j = 0; j < kdim; ++j) {
             T* vj = V + (size_t)j * n;
-            CDG2_TRY(launch_jvp_axpby(m, c, Yop, vj, 1.0, -gdt, wv, jflags, st));   // w = (I - gdt J) v_j
+            CDG2_TRY(launch_jvp_axpby(m, c, Yop, vj, 1.0, -gdt, pinv, wv, jflags, st));   // w = (I - gdt J) P^-1 v_j
             std::fill(hcol.begin(), hcol.end(), 0.0);
             for (int pass = 0; pass < 2; ++pass) {                                // CGS2
                 CDG2_TRY(vec_mdot<T>(n, j + 1, V, n, wv, w.red, w.red_out, st));
@@ -235,7 +270,7 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
         CDG2_TRY(vec_basis_combine<T>(n, jlast + 1, V, n, yc, x, st));
         if (resid <= rtol * beta0 || total >= maxit || !done_cycle_needs_restart(done, jlast, kdim)) break;
         // restart: r = b - A x into V_0
-        CDG2_TRY(launch_jvp_axpby(m, c, Yop, x, 1.0, -gdt, wv, jflags, st));
+        CDG2_TRY(launch_jvp_axpby(m, c, Yop, x, 1.0, -gdt, pinv, wv, jflags, st));
         CDG2_TRY(vec_convert<T, T>(n, b, 1.0, V, st));
         CDG2_TRY(vec_axpby<T>(n, -1.0, wv, 1.0, V, st));
         if (int rc = norm2<T>(w, V, st, &beta)) return rc;
@@ -245,6 +280,8 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
         }
         CDG2_TRY(vec_convert<T, T>(n, V, 1.0 / beta, V, st));
     }
+    // right preconditioning: the Krylov iterate lives in P-space, x = P^{-1} y
+    if (pinv) CDG2_TRY(vec_scale_modes<T>(n, pinv, NS * m.nb, x, st));
     *iters = total;
     *relres = resid / beta0;
     return CDG2_OK;
@@ -268,6 +305,10 @@ extern "C" int cdg2_step(const cdg2_mesh* m, const cdg2_params* p, double* U, do
                   "dt > 0, flags in {0, CDG2_FORCING})");
         return CDG2_ERR_INVALID_ARG;
     }
+    if (o->precond != 0 && o->precond != 1) {
+        set_error("cdg2_step: precond must be 0 or 1");
+        return CDG2_ERR_INVALID_ARG;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const bool mixed = o->mixed != 0;
     Work w;
@@ -275,6 +316,13 @@ extern "C" int cdg2_step(const cdg2_mesh* m, const cdg2_params* p, double* U, do
     const Coef c = make_coef(*p);
     const Tableau T = sdirk_tableau(o->scheme);
     const long long n = w.n;
+    const double* pinv = nullptr;
+    std::vector<double> ptab;
+    if (o->precond == 1) {   // SDIRK: one diagonal coefficient for all stages
+        modal_pinv(*m, c, dt * T.A[0][0], ptab);
+        CDG2_TRY(cudaMemcpy(w.pinv, ptab.data(), sizeof(double) * ptab.size(), cudaMemcpyHostToDevice));
+        pinv = w.pinv;
+    }
     cdg2_stats S;
     std::memset(&S, 0, sizeof(S));
     S.stages = T.s;
@@ -315,13 +363,13 @@ extern "C" int cdg2_step(const cdg2_mesh* m, const cdg2_params* p, double* U, do
             if (!mixed) {
                 CDG2_TRY(vec_convert<double, double>(n, w.G, -1.0, w.b64, st));
                 rc = gmres<double>(*m, c, w.Y, gdt, w.b64, static_cast<double*>(w.dx), o->gmres_rtol, o->max_gmres, w,
-                                   st, o->flags, &its, &rr);
+                                   st, o->flags, pinv, &its, &rr);
                 if (rc == CDG2_OK) CDG2_TRY(vec_add_into<double>(n, static_cast<double*>(w.dx), w.Y, st));
             } else {
                 CDG2_TRY(vec_convert<double, float>(n, w.Y, 1.0, static_cast<float*>(w.Yk), st));
                 CDG2_TRY(vec_convert<double, float>(n, w.G, -1.0, static_cast<float*>(w.bk), st));
                 rc = gmres<float>(*m, c, static_cast<float*>(w.Yk), gdt, static_cast<float*>(w.bk),
-                                  static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, o->flags, &its, &rr);
+                                  static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, o->flags, pinv, &its, &rr);
                 if (rc == CDG2_OK) CDG2_TRY(vec_add_into<float>(n, static_cast<float*>(w.dx), w.Y, st));
             }
             S.gmres_iters += its;

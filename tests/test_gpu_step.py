@@ -148,3 +148,19 @@ def test_step_rejects_bad_options(G):
         assert rc == -1
     rc, _ = G.cdg2_step(gm, I.default_params(), U, 0.0, 0.0, G.make_opts(), raise_on_error=False)
     assert rc == -1
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_preconditioner_changes_iterations_not_the_solution(G, mixed):
+    om, gm = _pair(G, 3, (8, 4, 4), 3)
+    p = I.default_params()
+    U0 = gaussian_state(om, n_gauss=8, sigma=0.04, seed=1160).cuda()
+    out, its = {}, {}
+    for pc in (0, 1):
+        U = U0.clone()
+        rc, st = G.cdg2_step(gm, p, U, 0.0, 1e-3, G.make_opts(scheme=3, mixed=mixed, precond=pc, newton_rtol=1e-11,
+                                                               gmres_rtol=1e-4))
+        assert rc == 0
+        out[pc], its[pc] = U, st["gmres_iters"]
+    assert float((out[1] - out[0]).norm() / out[0].norm()) <= 1e-10
+    assert its[1] < its[0]

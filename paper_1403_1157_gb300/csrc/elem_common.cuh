@@ -162,12 +162,64 @@ __device__ __forceinline__ long long neighbour(const Geo& g, long long e, int a,
     return c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
 }
 
+// The model coefficients converted once, on the host, to the kernel's
+// precision, so the pointwise code does no double -> float conversions (on
+// GB300 those run on the narrow FP64 pipe).  Same member names as Coef, plus derived
+// geometry and the optional parameter tangent.
+template <typename T>
+struct CoefT {
+    T A[NS];
+    T chi0[4], chith[4];
+    T d1, d2, gamma, alpha1, alpha2, f1, k_ox;
+    T beta1, beta2, sigma, c1s, c1ss, bc_sign;
+    T phase[NS];
+    T dth[8];       // tangent of (d1, d2, gamma, alpha1, alpha2, f1, k_ox, beta1)
+    T vol;          // |K|
+    T inv_vol;      // 1 / |K| (M^{-1} of the orthonormal basis)
+    T invh[3];      // 1 / h_j
+    T chi_e;        // CDG2 lifting factor
+};
+
+// Host-side conversion (kernel parameters live in the constant bank, so the
+// pointwise code reads these without conversions or shared-memory loads).
+template <typename T>
+inline CoefT<T> make_coefT(const Coef& c, const Geo& g, const double* dtheta) {
+    CoefT<T> d;
+    for (int s = 0; s < NS; ++s) {
+        d.A[s] = T(c.A[s]);
+        d.phase[s] = T(c.phase[s]);
+    }
+    for (int j = 0; j < 4; ++j) {
+        d.chi0[j] = T(c.chi0[j]);
+        d.chith[j] = T(c.chith[j]);
+    }
+    d.d1 = T(c.d1);
+    d.d2 = T(c.d2);
+    d.gamma = T(c.gamma);
+    d.alpha1 = T(c.alpha1);
+    d.alpha2 = T(c.alpha2);
+    d.f1 = T(c.f1);
+    d.k_ox = T(c.k_ox);
+    d.beta1 = T(c.beta1);
+    d.beta2 = T(c.beta2);
+    d.sigma = T(c.sigma);
+    d.c1s = T(c.c1s);
+    d.c1ss = T(c.c1ss);
+    d.bc_sign = T(c.bc_sign);
+    for (int j = 0; j < 8; ++j) d.dth[j] = T(dtheta ? dtheta[j] : 0.0);
+    d.vol = T(g.vol);
+    d.inv_vol = T(1.0 / g.vol);
+    for (int j = 0; j < 3; ++j) d.invh[j] = T(1.0 / g.h[j]);
+    d.chi_e = T(g.chi_e);
+    return d;
+}
+
 // Manufactured solution U*_s = 1 + cos(2 pi x + phase_s) cos(pi y / Ly) e^{-t} / 2
 // and its forcing g = dU*/dt - (-div(F(U*) - A grad U*) + S(U*)), written out
 // by hand: for chi-type fluxes n kappa(c) grad c with kappa(c) = a / (c + b),
 // div(n kappa grad c) = kappa grad n . grad c + n kappa' |grad c|^2 + n kappa lap c.
-template <typename T>
-__device__ __forceinline__ void mms_forcing(T x, T y, T t, T Ly, const Coef& c, T g[NS]) {
+template <typename T, typename C>
+__device__ __forceinline__ void mms_forcing(T x, T y, T t, T Ly, const C& c, T g[NS]) {
     const T pi = T(3.14159265358979323846);
     const T et = exp(-t);
     const T ky = pi / Ly;

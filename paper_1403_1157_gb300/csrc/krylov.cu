@@ -3,7 +3,11 @@
 // bandwidth-bound passes over DOF-length vectors with grid-stride loops;
 // every reduction is two-stage with a fixed partition and a fixed tree, so
 // results are bitwise reproducible (no atomics).  Dot products of FP32
-// vectors accumulate in FP64.
+// vectors accumulate in FP32 within a thread and in FP64 across threads and
+// blocks (FP64 arithmetic per element would bind these kernels on GB300,
+// whose FP64 rate is 1/61 of its FP32 rate).
+#include <type_traits>
+
 #include "krylov.h"
 
 namespace cdg2 {
@@ -15,8 +19,9 @@ constexpr int RED_BLOCKS = 4 * 152;           // blocks of every partial reducti
 template <typename T>
 __global__ void __launch_bounds__(VT) k_axpby(long long n, double a, const T* __restrict__ x, double b,
                                                T* __restrict__ y) {
+    const T aa = T(a), bb = T(b);
     for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
-        y[i] = T(a * double(x[i]) + b * double(y[i]));
+        y[i] = aa * x[i] + bb * y[i];
 }
 
 // out = x + sum_j c_j V_j (j < nv), V_j double vectors with leading dimension ldv
@@ -43,8 +48,11 @@ __global__ void __launch_bounds__(VT) k_newton_residual(long long n, const doubl
 // (src and dst may alias)
 template <typename S, typename D>
 __global__ void __launch_bounds__(VT) k_convert(long long n, const S* src, double scale, D* dst) {
+    // the narrower of the two types carries the arithmetic
+    using C = typename std::conditional<(sizeof(S) < sizeof(D)), S, D>::type;
+    const C sc = C(scale);
     for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
-        dst[i] = D(scale * double(src[i]));
+        dst[i] = D(sc * C(src[i]));
 }
 
 template <typename T>
@@ -63,18 +71,33 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return sh[0];
 }
 
-// part[j][blockIdx.x] = sum over this block's slice of V_j . w   (blockIdx.y = j)
+// part[j][blockIdx.x] = this block's slice of V_j . w for the NVC vectors of
+// chunk blockIdx.y (j = NVC * blockIdx.y + jj): w is read once per chunk and
+// the NVC independent loads per element keep enough bytes in flight.
+constexpr int NVC = 8;
 template <typename T>
-__global__ void __launch_bounds__(VT) k_mdot_partial(long long n, const T* __restrict__ V, long long ldv,
+__global__ void __launch_bounds__(VT) k_mdot_partial(long long n, int nv, const T* __restrict__ V, long long ldv,
                                                       const T* __restrict__ w, double* __restrict__ part) {
     __shared__ double sh[VT];
-    const int j = blockIdx.y;
-    const T* v = V + j * ldv;
-    double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
-        acc = fma(double(v[i]), double(w[i]), acc);
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[(long long)j * gridDim.x + blockIdx.x] = s;
+    const int j0 = blockIdx.y * NVC;
+    const int nj = nv - j0 < NVC ? nv - j0 : NVC;
+    T acc[NVC];
+#pragma unroll
+    for (int jj = 0; jj < NVC; ++jj) acc[jj] = T(0);
+    const long long stride = (long long)gridDim.x * VT;
+    for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += stride) {
+        const T wi = w[i];
+        T v[NVC];
+#pragma unroll
+        for (int jj = 0; jj < NVC; ++jj) v[jj] = jj < nj ? V[(j0 + jj) * ldv + i] : T(0);
+#pragma unroll
+        for (int jj = 0; jj < NVC; ++jj) acc[jj] = fma(v[jj], wi, acc[jj]);
+    }
+    for (int jj = 0; jj < nj; ++jj) {
+        const double s = block_sum(double(acc[jj]), sh);
+        if (threadIdx.x == 0) part[(long long)(j0 + jj) * gridDim.x + blockIdx.x] = s;
+        __syncthreads();
+    }
 }
 
 // out[j] = sum_b part[j][b] in a fixed order (blockIdx.x = j)
@@ -87,14 +110,25 @@ __global__ void __launch_bounds__(VT) k_rows_sum(const double* __restrict__ part
     if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
-// w -= sum_j h_j V_j  (h on the device)
+// w -= sum_j h_j V_j  (h on the device): NVC independent loads per step
 template <typename T>
 __global__ void __launch_bounds__(VT) k_mgs_update(long long n, int nv, const T* __restrict__ V, long long ldv,
                                                    const double* __restrict__ h, T* __restrict__ w) {
+    __shared__ T hs[MAX_KRYLOV + 1];
+    for (int j = threadIdx.x; j < nv; j += VT) hs[j] = T(-h[j]);
+    __syncthreads();
     for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) {
-        double acc = double(w[i]);
-        for (int j = 0; j < nv; ++j) acc = fma(-h[j], double(V[j * ldv + i]), acc);
-        w[i] = T(acc);
+        T acc = w[i];
+        int j = 0;
+        for (; j + NVC <= nv; j += NVC) {
+            T v[NVC];
+#pragma unroll
+            for (int jj = 0; jj < NVC; ++jj) v[jj] = V[(j + jj) * ldv + i];
+#pragma unroll
+            for (int jj = 0; jj < NVC; ++jj) acc = fma(hs[j + jj], v[jj], acc);
+        }
+        for (; j < nv; ++j) acc = fma(hs[j], V[j * ldv + i], acc);
+        w[i] = acc;
     }
 }
 
@@ -102,10 +136,21 @@ __global__ void __launch_bounds__(VT) k_mgs_update(long long n, int nv, const T*
 template <typename T>
 __global__ void __launch_bounds__(VT) k_basis_combine(long long n, int nv, const T* __restrict__ V, long long ldv,
                                                       Coeffs y, T* __restrict__ x) {
+    __shared__ T ys[MAX_KRYLOV + 1];
+    for (int j = threadIdx.x; j < nv; j += VT) ys[j] = T(y.v[j]);
+    __syncthreads();
     for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) {
-        double acc = double(x[i]);
-        for (int j = 0; j < nv; ++j) acc = fma(y.v[j], double(V[j * ldv + i]), acc);
-        x[i] = T(acc);
+        T acc = x[i];
+        int j = 0;
+        for (; j + NVC <= nv; j += NVC) {
+            T v[NVC];
+#pragma unroll
+            for (int jj = 0; jj < NVC; ++jj) v[jj] = V[(j + jj) * ldv + i];
+#pragma unroll
+            for (int jj = 0; jj < NVC; ++jj) acc = fma(ys[j + jj], v[jj], acc);
+        }
+        for (; j < nv; ++j) acc = fma(ys[j], V[j * ldv + i], acc);
+        x[i] = acc;
     }
 }
 
@@ -159,8 +204,8 @@ cudaError_t vec_add_into(long long n, const T* x, double* y, cudaStream_t st) {
 template <typename T>
 cudaError_t vec_mdot(long long n, int nv, const T* V, long long ldv, const T* w, double* part, double* out,
                      cudaStream_t st) {
-    dim3 grid(RED_BLOCKS, nv);
-    k_mdot_partial<T><<<grid, VT, 0, st>>>(n, V, ldv, w, part);
+    dim3 grid(RED_BLOCKS, (nv + NVC - 1) / NVC);
+    k_mdot_partial<T><<<grid, VT, 0, st>>>(n, nv, V, ldv, w, part);
     k_rows_sum<<<nv, VT, 0, st>>>(part, RED_BLOCKS, out);
     return cudaGetLastError();
 }

@@ -77,6 +77,7 @@ struct OpArgs {
     double* theta_part; // VJP: per-CTA partial sums of (df/dtheta)^T lambda, [gridDim.x][8], or null
     double alpha, beta; // JVP epilogue: out = alpha dU + beta J dU (0, 1 for the plain JVP)
     const double* pscale; // JVP: optional [6][n_basis] scale of the tangent (right preconditioner), or null
+    CoefT<T> c;           // coefficients and geometry in the kernel's precision
 };
 
 constexpr int MODE_APPLY = 0, MODE_JVP = 1, MODE_VJP = 2;
@@ -90,7 +91,7 @@ constexpr int fields_of(int mode) { return mode == MODE_APPLY ? 1 : 2; }
 // - A_s grad U_s and S(U) (Reading: the c1 row of S follows Eq. (1),
 // -alpha1 n1 c1 - alpha2 n2 c1 + f1 n3).
 template <int D, typename T>
-__device__ __forceinline__ void volume_point(const Coef& c, const T u[NS], const T g[NS][D], T Phi[NS][D],
+__device__ __forceinline__ void volume_point(const CoefT<T>& c, const T u[NS], const T g[NS][D], T Phi[NS][D],
                                              T S[NS]) {
     const T k11 = qdiv<T>(T(c.chi0[0]), u[3] + T(c.chith[0]));
     const T k13 = qdiv<T>(T(c.chi0[1]), u[5] + T(c.chith[1]));
@@ -119,8 +120,8 @@ __device__ __forceinline__ void volume_point(const Coef& c, const T u[NS], const
 // alpha1, alpha2, f1, k_ox, .)), when has_dth.  With kappa = a / (c + b):
 // d kappa = -kappa / (c + b) dc.
 template <int D, typename T>
-__device__ __forceinline__ void volume_point_lin(const Coef& c, const T u[NS], const T g[NS][D], const T du[NS],
-                                                 const T dg[NS][D], bool has_dth, const double* dth, T dPhi[NS][D],
+__device__ __forceinline__ void volume_point_lin(const CoefT<T>& c, const T u[NS], const T g[NS][D], const T du[NS],
+                                                 const T dg[NS][D], bool has_dth, T dPhi[NS][D],
                                                  T dS[NS]) {
     const T r11 = qdiv<T>(T(1), u[3] + T(c.chith[0]));
     const T r13 = qdiv<T>(T(1), u[5] + T(c.chith[1]));
@@ -150,12 +151,12 @@ __device__ __forceinline__ void volume_point_lin(const Coef& c, const T u[NS], c
     dS[5] = T(c.k_ox) * du[4];
     if (has_dth) {
         const T n1 = u[0], n2 = u[1], n3 = u[2], c1 = u[3], c2 = u[4];
-        dS[0] += -T(dth[0]) * n1;
-        dS[1] += -T(dth[1]) * n2;
-        dS[2] += T(dth[0]) * n1 + T(dth[1]) * n2 - T(dth[2]) * n1;
-        dS[3] += -T(dth[3]) * n1 * c1 - T(dth[4]) * n2 * c1 + T(dth[5]) * n3;
-        dS[4] += -T(dth[6]) * c2;
-        dS[5] += T(dth[6]) * c2;
+        dS[0] += -c.dth[0] * n1;
+        dS[1] += -c.dth[1] * n2;
+        dS[2] += c.dth[0] * n1 + c.dth[1] * n2 - c.dth[2] * n1;
+        dS[3] += -c.dth[3] * n1 * c1 - c.dth[4] * n2 * c1 + c.dth[5] * n3;
+        dS[4] += -c.dth[6] * c2;
+        dS[5] += c.dth[6] * c2;
     }
 }
 
@@ -166,7 +167,7 @@ __device__ __forceinline__ void volume_point_lin(const Coef& c, const T u[NS], c
 // F^ local Lax-Friedrichs with lambda_s = max(|v_s^-.n|, |v_s^+.n|);
 // A^ = 2 chi_e A r_e on K^-, r_e.n^- = -(k+1)^2 Delta / (2 h_a).
 template <typename T>
-__device__ __forceinline__ void face_point(const Coef& c, T pen, const T uM[NS], const T dM[NS], const T uP[NS],
+__device__ __forceinline__ void face_point(const CoefT<T>& c, T pen, const T uM[NS], const T dM[NS], const T uP[NS],
                                            const T dP[NS], const T del[NS], T sig[NS], T tau[NS]) {
     T Fh[2];
     {
@@ -199,7 +200,7 @@ __device__ __forceinline__ T sgn0(T x) {
 // One side's chemotactic normal velocity of species 0 or 1 and its derivative:
 // v_0 = kappa11(c1) d_n c1 + kappa13(c3) d_n c3,  v_1 = kappa21(c1) d_n c1 - kappa22(n1) d_n n1.
 template <typename T>
-__device__ __forceinline__ void velocity_lin(const Coef& c, int sp, const T u[NS], const T dn[NS], const T du[NS],
+__device__ __forceinline__ void velocity_lin(const CoefT<T>& c, int sp, const T u[NS], const T dn[NS], const T du[NS],
                                              const T ddn[NS], T& v, T& dv) {
     if (sp == 0) {
         const T r1 = qdiv<T>(T(1), u[3] + T(c.chith[0])), r3 = qdiv<T>(T(1), u[5] + T(c.chith[1]));
@@ -217,7 +218,7 @@ __device__ __forceinline__ void velocity_lin(const Coef& c, int sp, const T u[NS
 // Linearisation of face_point along the tangent traces.  Reading: d|x|/dx =
 // sign(x) with sign(0) = 0; at a tie |v^-| = |v^+| the K^- side is taken.
 template <typename T>
-__device__ __forceinline__ void face_point_lin(const Coef& c, T pen, const T uM[NS], const T dM[NS], const T uP[NS],
+__device__ __forceinline__ void face_point_lin(const CoefT<T>& c, T pen, const T uM[NS], const T dM[NS], const T uP[NS],
                                                const T dP[NS], const T del[NS], const T duM[NS], const T ddM[NS],
                                                const T duP[NS], const T ddP[NS], const T ddel[NS], T dsig[NS],
                                                T dtau[NS]) {
@@ -250,8 +251,8 @@ __device__ __forceinline__ void face_point_lin(const Coef& c, T pen, const T uM[
 //   Gb_tj = sum_s gb_sj dPhi_sj/dg_tj,
 // and th[0..6] += the cotangents of (d1, d2, gamma, alpha1, alpha2, f1, k_ox).
 template <int D, typename T>
-__device__ __forceinline__ void volume_point_adj(const Coef& c, const T u[NS], const T g[NS][D], const T sb[NS],
-                                                 const T gb[NS][D], T ub[NS], T Gb[NS][D], double th[8]) {
+__device__ __forceinline__ void volume_point_adj(const CoefT<T>& c, const T u[NS], const T g[NS][D], const T sb[NS],
+                                                 const T gb[NS][D], T ub[NS], T Gb[NS][D], T th[8]) {
     const T r11 = qdiv<T>(T(1), u[3] + T(c.chith[0]));
     const T r13 = qdiv<T>(T(1), u[5] + T(c.chith[1]));
     const T r21 = qdiv<T>(T(1), u[3] + T(c.chith[2]));
@@ -288,13 +289,13 @@ __device__ __forceinline__ void volume_point_adj(const Coef& c, const T u[NS], c
     ub[2] += T(c.f1) * sb[3];
     ub[3] += (-T(c.alpha1) * u[0] - T(c.alpha2) * u[1]) * sb[3];
     ub[4] += -T(c.k_ox) * sb[4] + T(c.k_ox) * sb[5];
-    th[0] += double(u[0] * (sb[2] - sb[0]));
-    th[1] += double(u[1] * (sb[2] - sb[1]));
-    th[2] += double(-u[0] * sb[2]);
-    th[3] += double(-u[0] * u[3] * sb[3]);
-    th[4] += double(-u[1] * u[3] * sb[3]);
-    th[5] += double(u[2] * sb[3]);
-    th[6] += double(u[4] * (sb[5] - sb[4]));
+    th[0] += u[0] * (sb[2] - sb[0]);
+    th[1] += u[1] * (sb[2] - sb[1]);
+    th[2] += -u[0] * sb[2];
+    th[3] += -u[0] * u[3] * sb[3];
+    th[4] += -u[1] * u[3] * sb[3];
+    th[5] += u[2] * sb[3];
+    th[6] += u[4] * (sb[5] - sb[4]);
 }
 
 // Adjoint of face_point with respect to the traces of one side X (the own
@@ -304,7 +305,7 @@ __device__ __forceinline__ void volume_point_adj(const Coef& c, const T u[NS], c
 // both sides: dDelta/du^X = +1 for K^-, -1 for K^+.  Same derivative
 // conventions as face_point_lin.
 template <typename T>
-__device__ __forceinline__ void face_point_adj(const Coef& c, T pen, bool ownM, const T uM[NS], const T dM[NS],
+__device__ __forceinline__ void face_point_adj(const CoefT<T>& c, T pen, bool ownM, const T uM[NS], const T dM[NS],
                                                const T uP[NS], const T dP[NS], const T del[NS], const T sb[NS],
                                                const T tb[NS], T ub[NS], T db[NS]) {
     const T sX = ownM ? T(1) : T(-1);
@@ -352,7 +353,7 @@ __device__ __forceinline__ void face_point_adj(const Coef& c, T pen, bool ownM, 
 // Gamma_2 (y = L1): n2 mu2 beta2 H(c1 - c1**).  H(0) = 0.  With beta1 scaled
 // by `b1` (1 for the data, the tangent d beta1 for their derivative).
 template <typename T>
-__device__ __forceinline__ void boundary_point(const Coef& c, int f, T x, const Geo& g, const T uo[NS], T sig[NS],
+__device__ __forceinline__ void boundary_point(const CoefT<T>& c, int f, T x, const Geo& g, const T uo[NS], T sig[NS],
                                                T b1, bool other_terms) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) sig[s] = T(0);
@@ -370,9 +371,9 @@ __device__ __forceinline__ void boundary_point(const Coef& c, int f, T x, const 
 // The two faces normal to axis A of every element of the CTA
 // ---------------------------------------------------------------------------
 template <int D, int K, int MODE, int A, typename T>
-__device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, const Coef& c, const OpArgs<T>& args,
+__device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, const CoefT<T>& c, const OpArgs<T>& args,
                                          const T* sU, T* sR, T* W, long long e0, long long (*nbr)[2],
-                                         double th[8]) {
+                                         T th[8], const T* ps) {
     constexpr int F = fields_of(MODE);
     using P = OpPlan<D, K, F>;
     using S = Shape<D, K>;
@@ -383,7 +384,7 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
     T* FS = FP + P::FP;
     T* TS1 = FS + P::FS;
     T* TS = TS1 + P::TS1;
-    const T invh = T(1.0 / g.h[A]);
+    const T invh = c.invh[A];
 
     if (threadIdx.x < EPB * 2) {
         const int e = threadIdx.x / 2, f = threadIdx.x % 2;
@@ -416,11 +417,11 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
         if (nb >= 0) {
             const T* nbg = args.U[fi] + (nb * NS + s) * NB;
             T nbv[NB1];   // the neighbour's coefficients along the normal line (tangent: preconditioned)
-            const bool scaled = MODE == MODE_JVP && fi == 1 && args.pscale != nullptr;
+            const bool scaled = MODE == MODE_JVP && fi == 1 && ps != nullptr;
 #pragma unroll
             for (int m = 0; m < NB1; ++m) {
                 const int ci = coef_index<D, K, A>(m, b0, b1);
-                nbv[m] = scaled ? nbg[ci] * T(args.pscale[s * NB + ci]) : nbg[ci];
+                nbv[m] = scaled ? nbg[ci] * ps[s * NB + ci] : nbg[ci];
             }
             T ov[NB1];
 #pragma unroll
@@ -458,7 +459,7 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
     __syncthreads();
 
     // pointwise fluxes, weighted: W_p = w_p |e|, |e| = |K| / h_A
-    const T pen = T(g.chi_e) * T((K + 1) * (K + 1)) * invh;
+    const T pen = c.chi_e * T((K + 1) * (K + 1)) * invh;
     for (int idx = threadIdx.x; idx < EPB * 2 * NQT; idx += blockDim.x) {
         const int p = idx % NQT;
         const int f = (idx / NQT) % 2;
@@ -477,7 +478,7 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
         const int p0 = p % NQ1, p1 = p / NQ1;
         T wp = tb.w[p0];
         if constexpr (D == 3) wp *= tb.w[p1];
-        const T Wp = wp * T(g.vol) * invh;
+        const T Wp = wp * c.vol * invh;
         const long long nb = nbr[e][f];
         if (nb >= 0) {
             T uN[NS];   // neighbour trace recovered from the jump
@@ -530,16 +531,16 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
                 const long long ge = e0 + e;
                 const T x = T((ge % g.n[0]) * g.h[0]) + T(g.h[0]) * tb.xi[p0];
                 if constexpr (MODE == MODE_APPLY) {
-                    boundary_point<T>(c, f, x, g, uo, sig, T(c.beta1), true);
+                    boundary_point<T>(c, f, x, g, uo, sig, c.beta1, true);
                 } else if constexpr (MODE == MODE_JVP) {
                     // H' = 0: only a tangent of beta1 moves the boundary data
-                    boundary_point<T>(c, f, x, g, uo, sig, args.has_dtheta ? T(args.dtheta[7]) : T(0), false);
+                    boundary_point<T>(c, f, x, g, uo, sig, c.dth[7], false);
                 } else {
                     // H' = 0: the boundary data do not depend on U; their beta1
                     // derivative, tested with mu's own trace, feeds the theta gradient
                     boundary_point<T>(c, f, x, g, uo, sig, T(1), false);
                     const T* base = FP + (((EPB + e) * 2 + f) * 4) * NS * NQT + p;
-                    th[7] += double(Wp * sig[0] * base[0]);
+                    th[7] += Wp * sig[0] * base[0];
 #pragma unroll
                     for (int s = 0; s < NS; ++s) sig[s] = T(0);
                 }
@@ -612,7 +613,7 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
 // The kernel
 // ---------------------------------------------------------------------------
 template <int D, int K, int MODE, typename T>
-__global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, const Coef c, const OpArgs<T> args) {
+__global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, const OpArgs<T> args) {
     constexpr int F = fields_of(MODE);
     using P = OpPlan<D, K, F>;
     using S = Shape<D, K>;
@@ -623,15 +624,25 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
     T* sR = sU + F * P::UR;
     T* W = sR + P::UR;
     __shared__ long long nbr[EPB][2];
+    __shared__ T psT[MODE == MODE_JVP ? NS * NB : 1];   // tangent pre-scale in the kernel's precision
 
     const long long e0 = (long long)blockIdx.x * EPB;
-    double th[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // VJP: this thread's theta cotangent partials
+    T th[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // VJP: this thread's theta cotangent partials
     load_tab<K, T>(tb, tab);
+    const T* ps = nullptr;
+    if constexpr (MODE == MODE_JVP) {
+        if (args.pscale) {
+            for (int i = threadIdx.x; i < NS * NB; i += blockDim.x) psT[i] = T(args.pscale[i]);
+            ps = psT;
+        }
+    }
+    __syncthreads();
+    const CoefT<T>& c = args.c;
     for (int i = threadIdx.x; i < F * P::UR; i += blockDim.x) {
         const int fi = i / P::UR, r = i % P::UR;
         const long long ge = e0 + r / (NS * NB);
         T v = ge < g.E ? args.U[fi][e0 * NS * NB + r] : T(0);
-        if (MODE == MODE_JVP && fi == 1 && args.pscale) v *= T(args.pscale[r % (NS * NB)]);
+        if (MODE == MODE_JVP && fi == 1 && ps) v *= ps[r % (NS * NB)];
         sU[i] = v;
     }
     __syncthreads();
@@ -674,7 +685,7 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
 
     // ---- volume: pointwise fluxes, weighted by w_q |K| (and 1/h_j for gradients) ----
     // The result goes to the slots of the last input field (the only one tested).
-    const T invh[3] = {T(1.0 / g.h[0]), T(1.0 / g.h[1]), T(1.0 / g.h[2])};
+    const T invh[3] = {c.invh[0], c.invh[1], c.invh[2]};
     constexpr int OFF = (F - 1) * EPB * NS * NQ;
     for (int idx = threadIdx.x; idx < EPB * NQ; idx += blockDim.x) {
         const int q = idx % NQ, e = idx / NQ;
@@ -688,7 +699,7 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
         const int q0 = q % NQ1, q1 = (q / NQ1) % NQ1, q2 = q / (NQ1 * NQ1);
         T wq = tb.w[q0] * tb.w[q1];
         if constexpr (D == 3) wq *= tb.w[q2];
-        const T Wq = wq * T(g.vol);
+        const T Wq = wq * c.vol;
         if constexpr (MODE == MODE_APPLY) {
             volume_point<D, T>(c, u, gr, Phi, Sr);
         } else {
@@ -700,7 +711,7 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
                 for (int j = 0; j < D; ++j) dg[s][j] = Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q] * invh[j];
             }
             if constexpr (MODE == MODE_JVP) {
-                volume_point_lin<D, T>(c, u, gr, du, dg, args.has_dtheta != 0, args.dtheta, Phi, Sr);
+                volume_point_lin<D, T>(c, u, gr, du, dg, args.has_dtheta != 0, Phi, Sr);
             } else {
                 // du, dg are mu and grad mu here; weighted they are the cotangents of S and Phi
 #pragma unroll
@@ -777,17 +788,18 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
     __syncthreads();
 
     // ---- faces ----
-    op_faces<D, K, MODE, 0, T>(g, tb, c, args, sU, sR, W, e0, nbr, th);
-    op_faces<D, K, MODE, 1, T>(g, tb, c, args, sU, sR, W, e0, nbr, th);
-    if constexpr (D == 3) op_faces<D, K, MODE, 2, T>(g, tb, c, args, sU, sR, W, e0, nbr, th);
+    op_faces<D, K, MODE, 0, T>(g, tb, c, args, sU, sR, W, e0, nbr, th, ps);
+    op_faces<D, K, MODE, 1, T>(g, tb, c, args, sU, sR, W, e0, nbr, th, ps);
+    if constexpr (D == 3) op_faces<D, K, MODE, 2, T>(g, tb, c, args, sU, sR, W, e0, nbr, th, ps);
 
     // ---- M^{-1} = I / |K| for the orthonormal basis; coalesced store ----
-    const T scale = (args.flags & CDG2_MINV) ? T(1.0 / g.vol) : T(1);
+    const T scale = (args.flags & CDG2_MINV) ? c.inv_vol : T(1);
+    const T alphaT = T(args.alpha), betaT = T(args.beta);
     for (int i = threadIdx.x; i < P::UR; i += blockDim.x) {
         const long long ge = e0 + i / (NS * NB);
         if (ge < g.E) {
             if constexpr (MODE == MODE_JVP)
-                args.out[e0 * NS * NB + i] = T(args.alpha) * sU[P::UR + i] + T(args.beta) * (sR[i] * scale);
+                args.out[e0 * NS * NB + i] = alphaT * sU[P::UR + i] + betaT * (sR[i] * scale);
             else
                 args.out[e0 * NS * NB + i] = sR[i] * scale;
         }
@@ -798,7 +810,7 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
         if (args.theta_part != nullptr) {
             __syncthreads();   // W is free again: reuse it as a double buffer
             double* red = reinterpret_cast<double*>(W);
-            for (int j = 0; j < 8; ++j) red[j * blockDim.x + threadIdx.x] = th[j];
+            for (int j = 0; j < 8; ++j) red[j * blockDim.x + threadIdx.x] = double(th[j]);
             __syncthreads();
             for (int stride = blockDim.x / 2; stride > 0; stride >>= 1) {
                 if ((int)threadIdx.x < stride)
@@ -843,7 +855,7 @@ static long long grid_of(const cdg2_mesh& m) {
 }
 
 template <int D, int K, int MODE, typename T>
-static cudaError_t launch_one(const cdg2_mesh& m, const Coef& c, const OpArgs<T>& a, cudaStream_t st) {
+static cudaError_t launch_one(const cdg2_mesh& m, const Coef& c, OpArgs<T> a, cudaStream_t st) {
     using P = OpPlan<D, K, fields_of(MODE)>;
     constexpr size_t smem = P::template smem_bytes<T>();
     static_assert(smem <= 227 * 1024, "operator kernel shared memory exceeds 227 KB");
@@ -857,7 +869,8 @@ static cudaError_t launch_one(const cdg2_mesh& m, const Coef& c, const OpArgs<T>
         attr_done = true;
     }
     const long long blocks = grid_of<MODE>(m);
-    op_kernel<D, K, MODE, T><<<(unsigned)blocks, P::NT, smem, st>>>(m.geo, m.tab, c, a);
+    a.c = make_coefT<T>(c, m.geo, a.has_dtheta ? a.dtheta : nullptr);
+    op_kernel<D, K, MODE, T><<<(unsigned)blocks, P::NT, smem, st>>>(m.geo, m.tab, a);
     return cudaGetLastError();
 }
 

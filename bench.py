@@ -27,35 +27,37 @@ METRIC = "L_h apply GDOF/s FP64 vs mixed at stated error; VJP GDOF/s; % HBM roof
 
 
 def apply_flops_per_element(dim: int, k: int) -> int:
-    """Floating-point operations of one element in the fused apply kernel.
+    """Floating-point operations per element of one FP64 apply (face-once path).
 
-    Counted from the kernel's loops (an FMA is 2 flops, a divide 1):
-    sum-factorised interpolation of U and grad U to the (k+2)^d Gauss points,
-    the transposed test passes, the pointwise volume flux (33 + 34 d per
-    point), and per face axis the normal contraction (own trace, jump,
-    both normal derivatives), tangential interpolation of 4 fields, the
-    pointwise face flux (112 per point and side; each interior face is
-    evaluated from both sides), the tangential test of 2 fields and the
-    normal expansion into the residual.
+    Counted from the kernels' loops (an FMA is 2 flops, a divide 1).  Element
+    kernel: sum-factorised interpolation of U and grad U to the (k+2)^d Gauss
+    points, the pointwise volume flux (33 + 34 d per point), the transposed
+    test passes, and per axis the normal expansion of its two faces' tested
+    fluxes.  Face kernel, one face per element and axis: normal contraction
+    (owning trace, jump, both normal derivatives), tangential interpolation
+    of 4 fields, the pointwise face flux (112 per point), tangential test of
+    2 fields.
     """
     b, q, d, s = k + 1, k + 2, dim, 6
     if d == 2:
         interp = 2 * q * b * b + 3 * q * q * b
         test = 3 * q * q * b + 2 * q * b * b
-        face_axis = 8 * b ** 2 + 8 * q * b + 4 * q * b + 4 * b ** 2
+        face = 4 * b ** 2 + 4 * q * b + 2 * q * b
     else:
         interp = 2 * q * b ** 3 + 3 * q * q * b * b + 4 * q ** 3 * b
         test = 4 * q ** 3 * b + 3 * q * q * b * b + 2 * q * b ** 3
-        face_axis = 8 * b ** 3 + 8 * (q * b * b + q * q * b) + 4 * (b * q * q + b * b * q) + 4 * b ** 3
-    fma = s * (interp + test + d * face_axis)
-    pointwise = q ** d * (33 + 34 * d) + 2 * d * q ** (d - 1) * 112
+        face = 4 * b ** 3 + 4 * (q * b * b + q * q * b) + 2 * (b * q * q + b * b * q)
+    expand = 4 * b ** d
+    fma = s * (interp + test + d * (face + expand))
+    pointwise = q ** d * (33 + 34 * d) + d * q ** (d - 1) * 112
     return 2 * fma + pointwise
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel,
-# from one ncu capture (profiles/), keyed by workload and valid only for the
-# kernel sources the counters were taken with (first 16 hex of their sha256).
-NCU_TRAFFIC = {("2D 256x64 Q3 manufactured solution", "double"): (12756736, "2c371327bd3f5910")}
+# dram__bytes_read.sum + dram__bytes_write.sum of one FP64 apply (its face and
+# element kernels), from one ncu capture (profiles/), keyed by workload and
+# valid only for the kernel sources the counters were taken with (first 16 hex
+# of their sha256).
+NCU_TRAFFIC = {("2D 256x64 Q3 manufactured solution", "double"): (50657792, "ef09e5ba5f7f13d7")}
 KERNEL_SOURCES = ("paper_1403_1157_gb300/csrc/operator.cu", "paper_1403_1157_gb300/csrc/elem_common.cuh")
 
 
@@ -420,14 +422,15 @@ def main():
                    "step": "one cdg2_apply (M^-1 L_h, FP64) over the whole mesh"},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": achieved_tf / fp64_peak, "traffic": ncu_traffic(w.name, "double"),
-                     "peak_note": "nominal FP64 FMA rate of GB300 (2 DFMA/clk/SM x 152 SMs); an FMA-loop probe measured 1.253",
-                     "flops_per_launch": fl, "kernel": f"apply_kernel<{w.dim},{w.k},double>",
+                     "peak_note": "nominal FP64 FMA rate of GB300 (2 DFMA/clk/SM x 152 SMs); an FMA-loop probe measured 1.253; achieved = counted flops of one apply / its event time (all its launches)",
+                     "flops_per_apply": fl,
+                     "kernels": f"{w.dim} x face_kernel<{w.dim},{w.k},0,A,double> + op_kernel<{w.dim},{w.k},0,double> (one apply)",
                      "hbm_frac": hbm_frac, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_kind": kind},
         "fp32": fp32,
         "derivatives": derivs,
         "solve": solve,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (1 + w.dim),
         "clocks": clk,
         "wall_s_timed_region": t_wall,
     }

@@ -153,7 +153,11 @@ int cdg2_mesh_info(const cdg2_mesh* mesh, long long* n_elem, int* n_basis, long 
  * 2 chi_e A r_e([U]) on K^-_e (the lower-coordinate cell); boundary faces:
  * the influxes of Eq. (3).  Sec. 3.2: M^{-1} of the orthonormal basis.
  * U, out: device arrays [n_elem][6][n_basis] (float64, or float32 with
- * CDG2_FP32); they must not overlap.  t: time of the CDG2_FORCING term. */
+ * CDG2_FP32); they must not overlap.  t: time of the CDG2_FORCING term.
+ * Each face is evaluated once into a per-mesh face buffer that the first
+ * cdg2_apply or cdg2_jvp on the mesh allocates (cudaMalloc, about
+ * 2*6*(k+1)^(dim-1) doubles per face); calls sharing a mesh must therefore
+ * be ordered on one stream. */
 int cdg2_apply(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, void* out,
                int flags, double t, void* stream);
 

@@ -172,6 +172,7 @@ void cdg2_mesh_destroy(cdg2_mesh* m) {
     if (!m) return;
     if (m->theta_part) cudaFree(m->theta_part);   // synchronises work queued on it
     if (m->step_ws) cudaFree(m->step_ws);
+    if (m->fbuf) cudaFree(m->fbuf);
     delete m;
 }
 

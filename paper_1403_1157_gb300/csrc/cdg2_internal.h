@@ -55,6 +55,10 @@ struct cdg2_mesh {
     cdg2::Tab1D tab;
     int nb;            // basis per species per element
     long long ndof;
+    // Face buffer of the face-once apply/JVP path (allocated by the first
+    // apply or JVP on the mesh, freed by cdg2_mesh_destroy).
+    mutable void* fbuf = nullptr;
+    mutable size_t fbuf_bytes = 0;
     // Device workspace owned by the mesh, allocated on first use and freed by
     // cdg2_mesh_destroy: per-CTA partial sums of the VJP's theta gradient.
     mutable double* theta_part = nullptr;
@@ -84,5 +88,6 @@ cudaError_t launch_jvp_axpby(const cdg2_mesh& m, const Coef& c, const void* U, c
 cudaError_t launch_vjp(const cdg2_mesh& m, const Coef& c, const void* U, const void* lam, void* gU,
                        double* theta_part, double* gtheta, int flags, cudaStream_t stream);
 long long vjp_grid(const cdg2_mesh& m);
+size_t face_buffer_bytes(const Geo& g);
 
 }  // namespace cdg2

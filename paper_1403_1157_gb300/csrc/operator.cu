@@ -78,6 +78,8 @@ struct OpArgs {
     double alpha, beta; // JVP epilogue: out = alpha dU + beta J dU (0, 1 for the plain JVP)
     const double* pscale; // JVP: optional [6][n_basis] scale of the tangent (right preconditioner), or null
     CoefT<T> c;           // coefficients and geometry in the kernel's precision
+    T* fbuf;              // face-once path: tested face fluxes, per axis at fb_off[axis], or null
+    long long fb_off[3];
 };
 
 constexpr int MODE_APPLY = 0, MODE_JVP = 1, MODE_VJP = 2;
@@ -612,6 +614,317 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
 // ---------------------------------------------------------------------------
 // The kernel
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Face-once path (apply and JVP): every face is evaluated by one CTA of the
+// face kernel, which writes its tested fluxes; the element kernel then adds
+// them to both adjacent cells with the normal expansion.  This halves the
+// face work of the fused path (where both cells evaluate every face); the
+// face buffer costs HBM traffic, which the FP64 path has in abundance.
+// Faces of axis A: id < E is the high face of cell id (interior, or the
+// high boundary); id >= E are the low-boundary faces of the first cell
+// layer (non-periodic axes only).  Stored per face: the tangential tests of
+// sigma and tau, [2][6][n_bt].  A low-boundary face stores -sigma so that
+// the element's low-face expansion (-psi(0) sigma + psi'(0)/h tau) applies.
+// ---------------------------------------------------------------------------
+template <int D, int K, int F>
+struct FacePlan {
+    using S = Shape<D, K>;
+    static constexpr int NT = 128;
+    static constexpr int FPB = D == 3 ? (K == 1 ? 8 : (K == 2 ? 4 : 2)) : (F == 1 ? (K == 1 ? 16 : 8) : (K == 1 ? 8 : 4));
+    static constexpr int NB1 = S::NB1, NQ1 = S::NQ1;
+    static constexpr int UB = FPB * NS * S::NB;                       // one side, one field
+    static constexpr int FC = F * FPB * 4 * NS * S::NBT;
+    static constexpr int FT = D == 3 ? F * FPB * 4 * NS * NQ1 * NB1 : 0;
+    static constexpr int FP = F * FPB * 4 * NS * S::NQT;
+    static constexpr int FS = FPB * 2 * NS * S::NQT;
+    static constexpr int TS1 = D == 3 ? FPB * 2 * NS * NB1 * NQ1 : 0;
+    static constexpr int TS = FPB * 2 * NS * S::NBT;
+    template <typename T>
+    static constexpr size_t smem_bytes() {
+        return (sizeof(STab<K, T>) + 15) / 16 * 16 + sizeof(T) * (size_t)(2 * F * UB + FC + FT + FP + FS + TS1 + TS);
+    }
+};
+
+__host__ __device__ inline long long faces_of_axis(const Geo& g, int a) {
+    return g.E + (g.periodic[a] ? 0 : g.E / g.n[a]);
+}
+
+// Index of the low-boundary face of a cell in the first layer of axis a.
+__device__ __forceinline__ long long low_layer_index(const Geo& g, long long e, int a) {
+    const long long ix = e % g.n[0], iy = (e / g.n[0]) % g.n[1], iz = e / ((long long)g.n[0] * g.n[1]);
+    if (a == 0) return iy + (long long)g.n[1] * iz;
+    if (a == 1) return ix + (long long)g.n[0] * iz;
+    return ix + (long long)g.n[0] * iy;
+}
+
+template <int D, int K, int MODE, int A, typename T>
+__global__ void __launch_bounds__(128) face_kernel(const Geo g, const Tab1D tab, const OpArgs<T> args) {
+    constexpr int F = fields_of(MODE);
+    using P = FacePlan<D, K, F>;
+    using S = Shape<D, K>;
+    constexpr int FPB = P::FPB, NB = S::NB, NB1 = S::NB1, NQ1 = S::NQ1, NBT = S::NBT, NQT = S::NQT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    STab<K, T>& tb = *reinterpret_cast<STab<K, T>*>(smem_raw);
+    T* sM = reinterpret_cast<T*>(smem_raw + (sizeof(STab<K, T>) + 15) / 16 * 16);   // [F][FPB][NS][NB] minus cells
+    T* sP = sM + F * P::UB;                                                       // plus cells
+    T* FC = sP + F * P::UB;
+    T* FT = FC + P::FC;
+    T* FPt = FT + P::FT;
+    T* FS = FPt + P::FP;
+    T* TS1 = FS + P::FS;
+    T* TS = TS1 + P::TS1;
+    __shared__ long long cm[FPB], cp[FPB];   // minus / plus cell (-1: none)
+    __shared__ int kind[FPB];                // -1 unused, 0 interior, 1 high boundary, 2 low boundary
+    __shared__ T psT[MODE == MODE_JVP ? NS * NB : 1];
+    const CoefT<T>& c = args.c;
+    const long long nf = faces_of_axis(g, A);
+    const long long f0 = (long long)blockIdx.x * FPB;
+
+    load_tab<K, T>(tb, tab);
+    const T* ps = nullptr;
+    if constexpr (MODE == MODE_JVP) {
+        if (args.pscale) {
+            for (int i = threadIdx.x; i < NS * NB; i += blockDim.x) psT[i] = T(args.pscale[i]);
+            ps = psT;
+        }
+    }
+    if (threadIdx.x < FPB) {
+        const long long fid = f0 + threadIdx.x;
+        int kd = -1;
+        long long em = -1, ep = -1;
+        if (fid < g.E) {
+            em = fid;
+            ep = neighbour(g, fid, A, 1);
+            kd = ep >= 0 ? 0 : 1;
+        } else if (fid < nf) {
+            const long long l = fid - g.E;
+            long long ix = 0, iy = 0, iz = 0;
+            if (A == 0) { iy = l % g.n[1]; iz = l / g.n[1]; }
+            else if (A == 1) { ix = l % g.n[0]; iz = l / g.n[0]; }
+            else { ix = l % g.n[0]; iy = l / g.n[0]; }
+            ep = ix + (long long)g.n[0] * (iy + (long long)g.n[1] * iz);
+            kd = 2;
+        }
+        cm[threadIdx.x] = em;
+        cp[threadIdx.x] = ep;
+        kind[threadIdx.x] = kd;
+    }
+    __syncthreads();
+    // coalesced loads of both cells of every face (the tangent pre-scaled)
+    for (int i = threadIdx.x; i < 2 * F * P::UB; i += blockDim.x) {
+        const int side = i / (F * P::UB);
+        const int r0 = i % (F * P::UB);
+        const int fi = r0 / P::UB, r = r0 % P::UB;
+        const int j = r / (NS * NB), q = r % (NS * NB);
+        const long long cell = side ? cp[j] : cm[j];
+        T v = cell >= 0 ? args.U[fi][cell * NS * NB + q] : T(0);
+        if (MODE == MODE_JVP && fi == 1 && ps) v *= ps[q];
+        (side ? sP : sM)[r0] = v;
+    }
+    __syncthreads();
+
+    const T invh = c.invh[A];
+    // normal contraction: 0 the owning trace (K^- at xi = 1, or K^+ at xi = 0 on a
+    // low boundary), 1 the jump (difference-first), 2 d_n U^-, 3 d_n U^+
+    for (int idx = threadIdx.x; idx < F * FPB * NS * NBT; idx += blockDim.x) {
+        const int t = idx % NBT;
+        const int s = (idx / NBT) % NS;
+        const int j = (idx / (NBT * NS)) % FPB;
+        const int fi = idx / (NBT * NS * FPB);
+        const int b0 = t % NB1, b1 = t / NB1;
+        const T* um = sM + (fi * FPB + j) * NS * NB + s * NB;
+        const T* up = sP + (fi * FPB + j) * NS * NB + s * NB;
+        T vm[NB1], vp[NB1];
+#pragma unroll
+        for (int m = 0; m < NB1; ++m) {
+            vm[m] = um[coef_index<D, K, A>(m, b0, b1)];
+            vp[m] = up[coef_index<D, K, A>(m, b0, b1)];
+        }
+        const int kd = kind[j];
+        T uo = 0, del = 0, dm = 0, dp = 0;
+        if (kd == 2) {
+#pragma unroll
+            for (int m = 0; m < NB1; ++m) uo = fma(tb.e[0][m], vp[m], uo);
+        } else {
+#pragma unroll
+            for (int m = 0; m < NB1; ++m) uo = fma(tb.e[1][m], vm[m], uo);
+        }
+        if (kd == 0) {
+            del = vm[0] - vp[0];
+#pragma unroll
+            for (int m = 1; m < NB1; ++m) {
+                del = fma(tb.e[1][m], vm[m], del);
+                del = fma(-tb.e[0][m], vp[m], del);
+            }
+#pragma unroll
+            for (int m = 0; m < NB1; ++m) {
+                dm = fma(tb.d[1][m], vm[m], dm);
+                dp = fma(tb.d[0][m], vp[m], dp);
+            }
+        }
+        T* o = FC + ((fi * FPB + j) * 4) * NS * NBT + s * NBT + t;
+        o[0 * NS * NBT] = uo;
+        o[1 * NS * NBT] = del;
+        o[2 * NS * NBT] = dm * invh;
+        o[3 * NS * NBT] = dp * invh;
+    }
+    __syncthreads();
+    if constexpr (D == 2) {
+        sf_pass<0, NB1, 1, 1, NQ1, false, K + 1, false>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FPt, NQT,
+                                                         F * FPB * 4 * NS);
+    } else {
+        sf_pass<0, NB1, NB1, 1, NQ1, false, K + 1, false>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT, NQ1 * NB1,
+                                                           F * FPB * 4 * NS);
+        __syncthreads();
+        sf_pass<1, NQ1, NB1, 1, NQ1, false, K + 1, false>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, FPt, NQT,
+                                                           F * FPB * 4 * NS);
+    }
+    __syncthreads();
+
+    const T pen = c.chi_e * T((K + 1) * (K + 1)) * invh;
+    for (int idx = threadIdx.x; idx < FPB * NQT; idx += blockDim.x) {
+        const int p = idx % NQT, j = idx / NQT;
+        const int kd = kind[j];
+        T sig[NS], tau[NS];
+        const int p0 = p % NQ1, p1 = p / NQ1;
+        T wp = tb.w[p0];
+        if constexpr (D == 3) wp *= tb.w[p1];
+        const T Wp = wp * c.vol * invh;
+        T uo[NS], del[NS], dm[NS], dp[NS];
+        {
+            const T* base = FPt + (j * 4) * NS * NQT + p;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                uo[s] = base[(0 * NS + s) * NQT];
+                del[s] = base[(1 * NS + s) * NQT];
+                dm[s] = base[(2 * NS + s) * NQT];
+                dp[s] = base[(3 * NS + s) * NQT];
+            }
+        }
+        if (kd == 0) {
+            T uP[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) uP[s] = uo[s] - del[s];
+            if constexpr (MODE == MODE_APPLY) {
+                face_point<T>(c, pen, uo, dm, uP, dp, del, sig, tau);
+            } else {
+                T tuo[NS], tdel[NS], tdm[NS], tdp[NS], tuP[NS];
+                const T* base = FPt + ((FPB + j) * 4) * NS * NQT + p;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    tuo[s] = base[(0 * NS + s) * NQT];
+                    tdel[s] = base[(1 * NS + s) * NQT];
+                    tdm[s] = base[(2 * NS + s) * NQT];
+                    tdp[s] = base[(3 * NS + s) * NQT];
+                    tuP[s] = tuo[s] - tdel[s];
+                }
+                face_point_lin<T>(c, pen, uo, dm, uP, dp, del, tuo, tdm, tuP, tdp, tdel, sig, tau);
+            }
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                sig[s] = Wp * sig[s];
+                tau[s] = Wp * tau[s];
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                sig[s] = T(0);
+                tau[s] = T(0);
+            }
+            if (A == 1 && kd > 0) {
+                const int f = kd == 2 ? 0 : 1;             // Gamma_1 (y = 0) or Gamma_2 (y = L1)
+                const long long cell = kd == 2 ? cp[j] : cm[j];
+                const T x = T((cell % g.n[0]) * g.h[0]) + T(g.h[0]) * tb.xi[p0];
+                if constexpr (MODE == MODE_APPLY)
+                    boundary_point<T>(c, f, x, g, uo, sig, c.beta1, true);
+                else
+                    boundary_point<T>(c, f, x, g, uo, sig, c.dth[7], false);
+                const T sg = kd == 2 ? -Wp : Wp;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) sig[s] = sg * sig[s];
+            }
+        }
+        T* o = FS + (j * 2) * NS * NQT + p;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            o[(0 * NS + s) * NQT] = sig[s];
+            o[(1 * NS + s) * NQT] = tau[s];
+        }
+    }
+    __syncthreads();
+    if constexpr (D == 2) {
+        sf_pass<0, NQ1, 1, 1, NB1, true, K + 1, false>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS, NBT,
+                                                        FPB * 2 * NS);
+    } else {
+        sf_pass<0, NQ1, NQ1, 1, NB1, true, K + 1, false>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1, NB1 * NQ1,
+                                                          FPB * 2 * NS);
+        __syncthreads();
+        sf_pass<1, NB1, NQ1, 1, NB1, true, K + 1, false>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1, TS, NBT,
+                                                          FPB * 2 * NS);
+    }
+    __syncthreads();
+    // coalesced store of the faces' tested fluxes
+    T* dst = args.fbuf + args.fb_off[A];
+    for (int i = threadIdx.x; i < P::TS; i += blockDim.x) {
+        const long long fid = f0 + i / (2 * NS * NBT);
+        if (fid < nf) dst[f0 * 2 * NS * NBT + i] = TS[i];
+    }
+}
+
+// Element side of the face-once path: add the tested fluxes of the two faces
+// normal to axis A to the residual of every cell of the CTA.
+template <int D, int K, int A, typename T>
+__device__ __forceinline__ void faces_expand(const Geo& g, const STab<K, T>& tb, const CoefT<T>& c,
+                                             const T* __restrict__ fb, T* sR, long long e0, int epb,
+                                             long long (*fid)[2]) {
+    using S = Shape<D, K>;
+    constexpr int NB = S::NB, NB1 = S::NB1, NBT = S::NBT;
+    if (threadIdx.x < epb) {
+        const long long ge = e0 + threadIdx.x;
+        long long hi = -1, lo = -1;
+        if (ge < g.E) {
+            hi = ge;
+            const long long nb = neighbour(g, ge, A, 0);
+            lo = nb >= 0 ? nb : g.E + low_layer_index(g, ge, A);
+        }
+        fid[threadIdx.x][0] = lo;
+        fid[threadIdx.x][1] = hi;
+    }
+    __syncthreads();
+    const T invh = c.invh[A];
+    for (int idx = threadIdx.x; idx < epb * NS * NB; idx += blockDim.x) {
+        const int i = idx % NB;
+        const int es = idx / NB;
+        const int e = es / NS, s = es % NS;
+        if (fid[e][1] < 0) continue;
+        int m, t;
+        if constexpr (D == 2) {
+            m = A == 0 ? i % NB1 : i / NB1;
+            t = A == 0 ? i / NB1 : i % NB1;
+        } else {
+            if constexpr (A == 0) {
+                m = i % NB1;
+                t = i / NB1;
+            } else if constexpr (A == 1) {
+                m = (i / NB1) % NB1;
+                t = i % NB1 + NB1 * (i / (NB1 * NB1));
+            } else {
+                m = i / (NB1 * NB1);
+                t = i % (NB1 * NB1);
+            }
+        }
+        const T* lo = fb + fid[e][0] * 2 * NS * NBT + s * NBT + t;
+        const T* hi = fb + fid[e][1] * 2 * NS * NBT + s * NBT + t;
+        T acc = sR[idx];
+        acc = fma(-tb.e[0][m], lo[0], acc);
+        acc = fma(tb.d[0][m] * invh, lo[NS * NBT], acc);
+        acc = fma(tb.e[1][m], hi[0], acc);
+        acc = fma(tb.d[1][m] * invh, hi[NS * NBT], acc);
+        sR[idx] = acc;
+    }
+    __syncthreads();
+}
+
 template <int D, int K, int MODE, typename T>
 __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, const OpArgs<T> args) {
     constexpr int F = fields_of(MODE);
@@ -788,9 +1101,15 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
     __syncthreads();
 
     // ---- faces ----
-    op_faces<D, K, MODE, 0, T>(g, tb, c, args, sU, sR, W, e0, nbr, th, ps);
-    op_faces<D, K, MODE, 1, T>(g, tb, c, args, sU, sR, W, e0, nbr, th, ps);
-    if constexpr (D == 3) op_faces<D, K, MODE, 2, T>(g, tb, c, args, sU, sR, W, e0, nbr, th, ps);
+    if (MODE != MODE_VJP && args.fbuf != nullptr) {
+        faces_expand<D, K, 0, T>(g, tb, c, args.fbuf + args.fb_off[0], sR, e0, EPB, nbr);
+        faces_expand<D, K, 1, T>(g, tb, c, args.fbuf + args.fb_off[1], sR, e0, EPB, nbr);
+        if constexpr (D == 3) faces_expand<D, K, 2, T>(g, tb, c, args.fbuf + args.fb_off[2], sR, e0, EPB, nbr);
+    } else {
+        op_faces<D, K, MODE, 0, T>(g, tb, c, args, sU, sR, W, e0, nbr, th, ps);
+        op_faces<D, K, MODE, 1, T>(g, tb, c, args, sU, sR, W, e0, nbr, th, ps);
+        if constexpr (D == 3) op_faces<D, K, MODE, 2, T>(g, tb, c, args, sU, sR, W, e0, nbr, th, ps);
+    }
 
     // ---- M^{-1} = I / |K| for the orthonormal basis; coalesced store ----
     const T scale = (args.flags & CDG2_MINV) ? c.inv_vol : T(1);
@@ -870,6 +1189,47 @@ static cudaError_t launch_one(const cdg2_mesh& m, const Coef& c, OpArgs<T> a, cu
     }
     const long long blocks = grid_of<MODE>(m);
     a.c = make_coefT<T>(c, m.geo, a.has_dtheta ? a.dtheta : nullptr);
+    a.fbuf = nullptr;
+    // Face-once for FP64 (bound by the FP64 pipe: halving the face arithmetic
+    // pays) and for 2D; the fused path stays for FP32 in 3D, where the extra
+    // launches and face loads cost more than the arithmetic they save.
+    constexpr bool face_once = MODE != MODE_VJP && (sizeof(T) == 8 || D == 2);
+    if constexpr (face_once) {
+        if (!m.fbuf) {
+            const size_t bytes = face_buffer_bytes(m.geo);
+            cudaError_t e = cudaMalloc(&m.fbuf, bytes);
+            if (e != cudaSuccess) return e;
+            m.fbuf_bytes = bytes;
+        }
+        {
+            using FPl = FacePlan<D, K, fields_of(MODE)>;
+            constexpr size_t fsmem = FPl::template smem_bytes<T>();
+            static_assert(fsmem <= 227 * 1024, "face kernel shared memory exceeds 227 KB");
+            static bool fattr_done = false;
+            if (!fattr_done) {
+                cudaError_t e = cudaSuccess;
+                e = cudaFuncSetAttribute(face_kernel<D, K, MODE, 0, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(face_kernel<D, K, MODE, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+                if (e == cudaSuccess && D == 3)
+                    e = cudaFuncSetAttribute(face_kernel<D, K, MODE, D == 3 ? 2 : 1, T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+                if (e != cudaSuccess) return e;
+                fattr_done = true;
+            }
+            a.fbuf = static_cast<T*>(m.fbuf);
+            constexpr long long per_face = 2LL * NS * Shape<D, K>::NBT;
+            long long off = 0;
+            for (int ax = 0; ax < 3; ++ax) {
+                a.fb_off[ax] = off;
+                if (ax < D) off += faces_of_axis(m.geo, ax) * per_face;
+            }
+            auto fgrid = [&](int ax) { return (unsigned)((faces_of_axis(m.geo, ax) + FPl::FPB - 1) / FPl::FPB); };
+            face_kernel<D, K, MODE, 0, T><<<fgrid(0), FPl::NT, fsmem, st>>>(m.geo, m.tab, a);
+            face_kernel<D, K, MODE, 1, T><<<fgrid(1), FPl::NT, fsmem, st>>>(m.geo, m.tab, a);
+            if constexpr (D == 3) face_kernel<D, K, MODE, 2, T><<<fgrid(2), FPl::NT, fsmem, st>>>(m.geo, m.tab, a);
+        }
+    }
     op_kernel<D, K, MODE, T><<<(unsigned)blocks, P::NT, smem, st>>>(m.geo, m.tab, a);
     return cudaGetLastError();
 }
@@ -901,10 +1261,20 @@ static OpArgs<T> make_args(const void* U, const void* dU, void* out, int flags, 
     a.alpha = 0.0;
     a.beta = 1.0;
     a.pscale = nullptr;
+    a.fbuf = nullptr;
+    for (int i = 0; i < 3; ++i) a.fb_off[i] = 0;
     return a;
 }
 
 long long vjp_grid(const cdg2_mesh& m) { return grid_of<MODE_VJP>(m); }
+
+size_t face_buffer_bytes(const Geo& g) {
+    long long nbt = 1;
+    for (int a = 0; a < g.dim - 1; ++a) nbt *= g.k + 1;
+    long long faces = 0;
+    for (int a = 0; a < g.dim; ++a) faces += faces_of_axis(g, a);
+    return (size_t)faces * 2 * NS * nbt * sizeof(double);
+}
 
 cudaError_t launch_apply(const cdg2_mesh& m, const Coef& c, const void* U, void* out, int flags, double t,
                          cudaStream_t st) {

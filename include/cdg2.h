@@ -187,6 +187,27 @@ int cdg2_jvp(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, co
 int cdg2_step(const cdg2_mesh* mesh, const cdg2_params* params, double* U, double t, double dt,
               const cdg2_solver_opts* opts, cdg2_stats* stats, void* stream);
 
+/* cdg2_step that also stores the converged stage values Y_1..Y_s, the
+ * linearisation points of the step's discrete adjoint.
+ * stages: device float64 [s][n_elem][6][n_basis] (s = 2 or 3 for the scheme). */
+int cdg2_step_stages(const cdg2_mesh* mesh, const cdg2_params* params, double* U, double t, double dt,
+                     const cdg2_solver_opts* opts, double* stages, cdg2_stats* stats, void* stream);
+
+/* Discrete adjoint of one SDIRK step (Sec. 3.2 stepping, differentiated):
+ * lam <- (dU_{n+1}/dU_n)^T lam and gtheta += (dU_{n+1}/dtheta)^T lam, theta
+ * as in cdg2_jvp.  With K_i = f(Y_i): backwards over the stages,
+ *   r_i = dt b_i lam + dt sum_{j>i} a_ji ybar_j,  (I - dt a_ii J(Y_i)^T) g_i = r_i,
+ *   ybar_i = J(Y_i)^T g_i,  gtheta += (df/dtheta)(Y_i)^T g_i,  lam_n = lam + sum_i ybar_i.
+ * stages: the output of cdg2_step_stages for this step.  Each stage system
+ * is solved to ||residual||_2 <= max(newton_rtol ||r_i||_2, newton_atol) by
+ * refinement (FP64 residual via cdg2_vjp's kernel; corrections by GMRES in
+ * FP64, or FP32 with opts->mixed); max_newton bounds the refinements.
+ * lam: device float64, in/out.  gtheta: device float64 [8], accumulated, or
+ * NULL.  opts->flags must be 0 (the forcing's coefficient dependence is not
+ * differentiated).  Synchronous; workspace as cdg2_step (+ cdg2_vjp's). */
+int cdg2_step_adjoint(const cdg2_mesh* mesh, const cdg2_params* params, const double* stages, double t, double dt,
+                      const cdg2_solver_opts* opts, double* lam, double* gtheta, cdg2_stats* stats, void* stream);
+
 /* Transpose of cdg2_jvp (vector-Jacobian product, for the adjoint of the
  * implicit steps):
  *   gU = J(U)^T lam,   gtheta = (d f / d theta)^T lam  (when gtheta != NULL),

@@ -606,3 +606,60 @@ def step(mesh: Mesh, U, params: dict, t: float, dt: float, scheme="sdirk2", forc
     for i in range(s):
         out = out + dt * b[i] * K[i]
     return out
+
+
+def step_stages(mesh: Mesh, U, params: dict, t: float, dt: float, scheme="sdirk2", **kw):
+    """step() that also returns the converged stage values Y_1..Y_s."""
+    A, b, c = sdirk_tableau(scheme)
+    stages = []
+    s = len(b)
+    K = []
+    Y = U.clone()
+    for i in range(s):
+        ti = t + c[i] * dt
+        rhs = U.clone()
+        for j in range(i):
+            rhs = rhs + dt * A[i, j] * K[j]
+        gdt = dt * A[i, i]
+        scale = max(1.0, float(torch.linalg.norm(rhs)))
+        for _it in range(kw.get("max_newton", 30)):
+            fY = apply(mesh, Y, params, kw.get("forcing"), ti)
+            G = Y - gdt * fY - rhs
+            if float(torch.linalg.norm(G)) <= kw.get("newton_tol", 1e-13) * scale:
+                break
+            Yc = Y
+            Y = Y + _gmres(lambda v, Yc=Yc: v - gdt * jvp(mesh, Yc, v, params), -G, kw.get("gmres_tol", 1e-13))
+        stages.append(Y.clone())
+        K.append(apply(mesh, Y, params, kw.get("forcing"), ti))
+    out = U.clone()
+    for i in range(s):
+        out = out + dt * b[i] * K[i]
+    return out, stages
+
+
+def step_adjoint(mesh: Mesh, stages, params: dict, dt: float, scheme, lam, theta_names=()):
+    """Discrete adjoint of one SDIRK step with dense Jacobians (tiny meshes only).
+
+    With K_i = f(Y_i), Y_i = U_n + dt sum_j a_ij K_j, U_{n+1} = U_n + dt sum_i b_i K_i,
+    the chain rule gives, backwards over the stages:
+      r_i = dt b_i lam + dt sum_{j>i} a_ji ybar_j,   (I - dt a_ii J_i)^T g_i = r_i,
+      ybar_i = J_i^T g_i,   gtheta += (df/dtheta)(Y_i)^T g_i,   lam_n = lam + sum_i ybar_i,
+    with J_i = df/dU at Y_i formed densely by forward-mode differentiation.
+    """
+    A, b, _c = sdirk_tableau(scheme)
+    s = len(b)
+    n = lam.numel()
+    ybar = [None] * s
+    gth = torch.zeros(len(theta_names), dtype=F64)
+    for i in reversed(range(s)):
+        r = dt * b[i] * lam.reshape(-1)
+        for j in range(i + 1, s):
+            r = r + dt * A[j, i] * ybar[j]
+        J = torch.func.jacfwd(lambda V: apply(mesh, V, params))(stages[i]).reshape(n, n)
+        g = torch.linalg.solve((torch.eye(n, dtype=F64) - dt * A[i, i] * J).T, r)
+        ybar[i] = J.T @ g
+        if theta_names:
+            _gU, gt = vjp(mesh, stages[i], g.reshape(lam.shape), params, theta_names)
+            gth = gth + gt
+    lam_n = lam.reshape(-1) + sum(ybar)
+    return lam_n.reshape(lam.shape), gth

@@ -17,7 +17,8 @@ __all__ = [
     "CDG2_MINV", "CDG2_FORCING", "CDG2_FP32", "Cdg2Error", "Mesh", "load_library", "library_path",
     "make_params", "cdg2_mesh_create", "cdg2_mesh_destroy", "cdg2_mesh_info", "cdg2_apply", "cdg2_last_error",
     "cdg2_project_gaussians", "cdg2_project_mms", "cdg2_jvp", "cdg2_vjp", "cdg2_step",
-    "CDG2_SDIRK2", "CDG2_SDIRK3", "SolverOpts", "Stats", "make_opts",
+    "CDG2_SDIRK2", "CDG2_SDIRK3", "SolverOpts", "Stats", "make_opts", "cdg2_step_stages", "cdg2_step_adjoint",
+    "stages_of",
 ]
 
 CDG2_MINV = 1
@@ -119,6 +120,12 @@ def load_library():
     lib.cdg2_step.argtypes = [vp, ctypes.POINTER(Params), vp, d, d, ctypes.POINTER(SolverOpts), ctypes.POINTER(Stats),
                               vp]
     lib.cdg2_step.restype = i
+    lib.cdg2_step_stages.argtypes = [vp, ctypes.POINTER(Params), vp, d, d, ctypes.POINTER(SolverOpts), vp,
+                                     ctypes.POINTER(Stats), vp]
+    lib.cdg2_step_stages.restype = i
+    lib.cdg2_step_adjoint.argtypes = [vp, ctypes.POINTER(Params), vp, d, d, ctypes.POINTER(SolverOpts), vp, vp,
+                                      ctypes.POINTER(Stats), vp]
+    lib.cdg2_step_adjoint.restype = i
     lib.cdg2_project_gaussians.argtypes = [vp, i, dp, dp, d, d, vp, i, vp]
     lib.cdg2_project_gaussians.restype = i
     lib.cdg2_project_mms.argtypes = [vp, ctypes.POINTER(Params), d, vp, i, vp]
@@ -317,3 +324,39 @@ def cdg2_step(mesh: Mesh, params, U: torch.Tensor, t: float, dt: float, opts: So
     if rc != 0 and raise_on_error:
         _check(rc)
     return rc, st.as_dict()
+
+
+def stages_of(opts: SolverOpts) -> int:
+    return 2 if opts.scheme == CDG2_SDIRK2 else 3
+
+
+def cdg2_step_stages(mesh: Mesh, params, U: torch.Tensor, t: float, dt: float, stages: torch.Tensor,
+                     opts: SolverOpts = None, stream=None):
+    """cdg2_step that also stores the stage values into stages (float64 CUDA, [s * n_dof])."""
+    p = _params(params)
+    o = opts if opts is not None else make_opts()
+    if not (stages.is_cuda and stages.dtype == torch.float64 and stages.is_contiguous()
+            and stages.numel() == stages_of(o) * mesh.n_dof):
+        raise ValueError("stages must be a contiguous CUDA float64 tensor of s * n_dof values")
+    st = Stats()
+    _check(load_library().cdg2_step_stages(mesh.handle, ctypes.byref(p), _dev(U, mesh, torch.float64, "U"), float(t),
+                                           float(dt), ctypes.byref(o), ctypes.c_void_p(stages.data_ptr()),
+                                           ctypes.byref(st), _stream_ptr(stream)))
+    return st.as_dict()
+
+
+def cdg2_step_adjoint(mesh: Mesh, params, stages: torch.Tensor, t: float, dt: float, lam: torch.Tensor,
+                      gtheta: torch.Tensor = None, opts: SolverOpts = None, stream=None):
+    """lam <- (dU_{n+1}/dU_n)^T lam; gtheta += (dU_{n+1}/dtheta)^T lam (in place)."""
+    p = _params(params)
+    o = opts if opts is not None else make_opts()
+    gth = None
+    if gtheta is not None:
+        if not (gtheta.is_cuda and gtheta.dtype == torch.float64 and gtheta.numel() == 8):
+            raise ValueError("gtheta must be a CUDA float64 tensor of 8 values")
+        gth = ctypes.c_void_p(gtheta.data_ptr())
+    st = Stats()
+    _check(load_library().cdg2_step_adjoint(mesh.handle, ctypes.byref(p), ctypes.c_void_p(stages.data_ptr()),
+                                            float(t), float(dt), ctypes.byref(o), _dev(lam, mesh, torch.float64, "lam"),
+                                            gth, ctypes.byref(st), _stream_ptr(stream)))
+    return st.as_dict()

@@ -83,6 +83,9 @@ cudaError_t launch_jvp(const cdg2_mesh& m, const Coef& c, const void* U, const v
 // (I - gamma dt J) P^{-1} v in one pass.
 cudaError_t launch_jvp_axpby(const cdg2_mesh& m, const Coef& c, const void* U, const void* dU, double alpha,
                              double beta, const double* pscale, void* out, int flags, cudaStream_t stream);
+// out = alpha w + beta J(U)^T w with w = pscale . lam (the transposed Krylov operator)
+cudaError_t launch_vjp_axpby(const cdg2_mesh& m, const Coef& c, const void* U, const void* lam, double alpha,
+                             double beta, const double* pscale, void* out, int flags, cudaStream_t stream);
 // VJP: gU = (df/dU)^T lam; when gtheta is non-null also (df/dtheta)^T lam via
 // theta_part ([vjp_grid(m)][8] doubles of scratch) and a fixed-order reduction.
 cudaError_t launch_vjp(const cdg2_mesh& m, const Coef& c, const void* U, const void* lam, void* gU,

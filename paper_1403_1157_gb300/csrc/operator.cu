@@ -419,7 +419,7 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
         if (nb >= 0) {
             const T* nbg = args.U[fi] + (nb * NS + s) * NB;
             T nbv[NB1];   // the neighbour's coefficients along the normal line (tangent: preconditioned)
-            const bool scaled = MODE == MODE_JVP && fi == 1 && ps != nullptr;
+            const bool scaled = MODE != MODE_APPLY && fi == 1 && ps != nullptr;
 #pragma unroll
             for (int m = 0; m < NB1; ++m) {
                 const int ci = coef_index<D, K, A>(m, b0, b1);
@@ -937,13 +937,13 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
     T* sR = sU + F * P::UR;
     T* W = sR + P::UR;
     __shared__ long long nbr[EPB][2];
-    __shared__ T psT[MODE == MODE_JVP ? NS * NB : 1];   // tangent pre-scale in the kernel's precision
+    __shared__ T psT[MODE != MODE_APPLY ? NS * NB : 1];   // tangent/cotangent pre-scale in the kernel's precision
 
     const long long e0 = (long long)blockIdx.x * EPB;
     T th[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // VJP: this thread's theta cotangent partials
     load_tab<K, T>(tb, tab);
     const T* ps = nullptr;
-    if constexpr (MODE == MODE_JVP) {
+    if constexpr (MODE != MODE_APPLY) {
         if (args.pscale) {
             for (int i = threadIdx.x; i < NS * NB; i += blockDim.x) psT[i] = T(args.pscale[i]);
             ps = psT;
@@ -955,7 +955,7 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
         const int fi = i / P::UR, r = i % P::UR;
         const long long ge = e0 + r / (NS * NB);
         T v = ge < g.E ? args.U[fi][e0 * NS * NB + r] : T(0);
-        if (MODE == MODE_JVP && fi == 1 && ps) v *= ps[r % (NS * NB)];
+        if (MODE != MODE_APPLY && fi == 1 && ps) v *= ps[r % (NS * NB)];
         sU[i] = v;
     }
     __syncthreads();
@@ -1117,7 +1117,7 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
     for (int i = threadIdx.x; i < P::UR; i += blockDim.x) {
         const long long ge = e0 + i / (NS * NB);
         if (ge < g.E) {
-            if constexpr (MODE == MODE_JVP)
+            if constexpr (MODE != MODE_APPLY)
                 args.out[e0 * NS * NB + i] = alphaT * sU[P::UR + i] + betaT * (sR[i] * scale);
             else
                 args.out[e0 * NS * NB + i] = sR[i] * scale;
@@ -1304,6 +1304,22 @@ cudaError_t launch_jvp_axpby(const cdg2_mesh& m, const Coef& c, const void* U, c
     a.beta = beta;
     a.pscale = pscale;
     return dispatch<MODE_JVP, double>(m, c, a, st);
+}
+
+cudaError_t launch_vjp_axpby(const cdg2_mesh& m, const Coef& c, const void* U, const void* lam, double alpha,
+                             double beta, const double* pscale, void* out, int flags, cudaStream_t st) {
+    if (flags & CDG2_FP32) {
+        OpArgs<float> a = make_args<float>(U, lam, out, flags, 0.0, nullptr, nullptr);
+        a.alpha = alpha;
+        a.beta = beta;
+        a.pscale = pscale;
+        return dispatch<MODE_VJP, float>(m, c, a, st);
+    }
+    OpArgs<double> a = make_args<double>(U, lam, out, flags, 0.0, nullptr, nullptr);
+    a.alpha = alpha;
+    a.beta = beta;
+    a.pscale = pscale;
+    return dispatch<MODE_VJP, double>(m, c, a, st);
 }
 
 cudaError_t launch_vjp(const cdg2_mesh& m, const Coef& c, const void* U, const void* lam, void* gU,

@@ -20,6 +20,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "cdg2_internal.h"
@@ -188,10 +189,18 @@ static bool done_cycle_needs_restart(bool done, int jlast, int kdim) { return !d
 // Restarted GMRES(m) with CGS2 for (I - gdt J(Yop)) x = b, x0 = 0.
 // Stops when ||b - A x||_2 <= rtol ||b||_2 (the Arnoldi estimate) or after
 // maxit inner iterations.  T is the Krylov precision.
+// The operator's matvec: w = (I - gdt J) P^{-1} v, or with J^T (adjoint).
+template <typename T>
+static cudaError_t matvec(bool adjoint, const cdg2_mesh& m, const Coef& c, const T* Yop, const T* v, double gdt,
+                          const double* pinv, T* out, int flags, cudaStream_t st) {
+    if (adjoint) return launch_vjp_axpby(m, c, Yop, v, 1.0, -gdt, pinv, out, flags, st);
+    return launch_jvp_axpby(m, c, Yop, v, 1.0, -gdt, pinv, out, flags, st);
+}
+
 template <typename T>
 static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, const T* b, T* x, double rtol,
                  int maxit, const Work& w, cudaStream_t st, int flags, const double* pinv, int* iters,
-                 double* relres) {
+                 double* relres, bool adjoint = false) {
     const long long n = w.n;
     const int kdim = w.m;
     T* V = static_cast<T*>(w.basis);
@@ -219,7 +228,7 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
         bool done = false;
         for (int j = 0; j < kdim; ++j) {
             T* vj = V + (size_t)j * n;
-            CDG2_TRY(launch_jvp_axpby(m, c, Yop, vj, 1.0, -gdt, pinv, wv, jflags, st));   // w = (I - gdt J) P^-1 v_j
+            CDG2_TRY(matvec<T>(adjoint, m, c, Yop, vj, gdt, pinv, wv, jflags, st));   // w = (I - gdt J) P^-1 v_j
             std::fill(hcol.begin(), hcol.end(), 0.0);
             for (int pass = 0; pass < 2; ++pass) {                                // CGS2
                 CDG2_TRY(vec_mdot<T>(n, j + 1, V, n, wv, w.red, w.red_out, st));
@@ -270,7 +279,7 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
         CDG2_TRY(vec_basis_combine<T>(n, jlast + 1, V, n, yc, x, st));
         if (resid <= rtol * beta0 || total >= maxit || !done_cycle_needs_restart(done, jlast, kdim)) break;
         // restart: r = b - A x into V_0
-        CDG2_TRY(launch_jvp_axpby(m, c, Yop, x, 1.0, -gdt, pinv, wv, jflags, st));
+        CDG2_TRY(matvec<T>(adjoint, m, c, Yop, x, gdt, pinv, wv, jflags, st));
         CDG2_TRY(vec_convert<T, T>(n, b, 1.0, V, st));
         CDG2_TRY(vec_axpby<T>(n, -1.0, wv, 1.0, V, st));
         if (int rc = norm2<T>(w, V, st, &beta)) return rc;
@@ -291,24 +300,25 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
 
 using namespace cdg2;
 
-extern "C" int cdg2_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double t, double dt,
-                         const cdg2_solver_opts* o, cdg2_stats* stats, void* stream) {
+static int check_opts(const cdg2_solver_opts* o, double dt, const char* who) {
+    if ((o->scheme != CDG2_SDIRK2 && o->scheme != CDG2_SDIRK3) || o->gmres_restart < 1 ||
+        o->gmres_restart > MAX_KRYLOV || o->max_newton < 1 || o->max_gmres < 1 || !(dt > 0.0) ||
+        (o->flags & ~CDG2_FORCING) || (o->precond != 0 && o->precond != 1)) {
+        set_error(std::string(who) + ": invalid options (scheme 2|3, 1 <= gmres_restart <= 64, max_newton, "
+                  "max_gmres >= 1, dt > 0, flags in {0, CDG2_FORCING}, precond in {0, 1})");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    return CDG2_OK;
+}
+
+static int run_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double t, double dt,
+                    const cdg2_solver_opts* o, cdg2_stats* stats, double* stages_out, void* stream) {
     const auto t_start = std::chrono::steady_clock::now();
     if (!m || !p || !U || !o) {
         set_error("cdg2_step: NULL argument");
         return CDG2_ERR_INVALID_ARG;
     }
-    if ((o->scheme != CDG2_SDIRK2 && o->scheme != CDG2_SDIRK3) || o->gmres_restart < 1 ||
-        o->gmres_restart > MAX_KRYLOV || o->max_newton < 1 || o->max_gmres < 1 || !(dt > 0.0) ||
-        (o->flags & ~CDG2_FORCING)) {
-        set_error("cdg2_step: invalid options (scheme 2|3, 1 <= gmres_restart <= 64, max_newton, max_gmres >= 1, "
-                  "dt > 0, flags in {0, CDG2_FORCING})");
-        return CDG2_ERR_INVALID_ARG;
-    }
-    if (o->precond != 0 && o->precond != 1) {
-        set_error("cdg2_step: precond must be 0 or 1");
-        return CDG2_ERR_INVALID_ARG;
-    }
+    if (int rc = check_opts(o, dt, "cdg2_step")) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const bool mixed = o->mixed != 0;
     Work w;
@@ -386,6 +396,8 @@ extern "C" int cdg2_step(const cdg2_mesh* m, const cdg2_params* p, double* U, do
         }
         // K_i = f(Y_i): the last residual evaluation was at the converged Y_i
         CDG2_TRY(cudaMemcpyAsync(w.K[i], w.fY, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        if (stages_out)
+            CDG2_TRY(cudaMemcpyAsync(stages_out + (size_t)i * n, w.Y, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     }
     if (status == CDG2_OK) {
         Coeffs bb;
@@ -396,4 +408,144 @@ extern "C" int cdg2_step(const cdg2_mesh* m, const cdg2_params* p, double* U, do
     S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = S;
     return status;
+}
+
+extern "C" int cdg2_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double t, double dt,
+                         const cdg2_solver_opts* o, cdg2_stats* stats, void* stream) {
+    return run_step(m, p, U, t, dt, o, stats, nullptr, stream);
+}
+
+extern "C" int cdg2_step_stages(const cdg2_mesh* m, const cdg2_params* p, double* U, double t, double dt,
+                                const cdg2_solver_opts* o, double* stages, cdg2_stats* stats, void* stream) {
+    if (!stages) {
+        set_error("cdg2_step_stages: NULL stages");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    return run_step(m, p, U, t, dt, o, stats, stages, stream);
+}
+
+// Discrete adjoint of one SDIRK step (the transpose of the linearised step map):
+// with K_i = f(Y_i), Y_i = U_n + dt sum_{j<=i} a_ij K_j, U_{n+1} = U_n + dt sum b_i K_i,
+// backwards over the stages
+//   r_i = dt b_i lam + dt sum_{j>i} a_ji ybar_j,  (I - dt a_ii J_i^T) g_i = r_i,
+//   ybar_i = J_i^T g_i,  gtheta += (df/dtheta)(Y_i)^T g_i,
+// and lam_n = lam + sum_i ybar_i.  Each stage system is solved by refinement:
+// the residual r_i - (I - dt a_ii J_i^T) g in FP64, the correction by GMRES
+// (FP64, or FP32 in the mixed mode), until ||residual|| <= newton_rtol ||r_i||.
+extern "C" int cdg2_step_adjoint(const cdg2_mesh* m, const cdg2_params* p, const double* stages, double t, double dt,
+                                 const cdg2_solver_opts* o, double* lam, double* gtheta, cdg2_stats* stats,
+                                 void* stream) {
+    (void)t;
+    const auto t_start = std::chrono::steady_clock::now();
+    if (!m || !p || !stages || !o || !lam) {
+        set_error("cdg2_step_adjoint: NULL argument");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (int rc = check_opts(o, dt, "cdg2_step_adjoint")) return rc;
+    if (o->flags & CDG2_FORCING) {
+        set_error("cdg2_step_adjoint: the forcing's dependence on the coefficients is not differentiated");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool mixed = o->mixed != 0;
+    Work w;
+    if (int rc = ensure_work(*m, o->gmres_restart, mixed, w)) return rc;
+    const Coef c = make_coef(*p);
+    const Tableau T = sdirk_tableau(o->scheme);
+    const long long n = w.n;
+    const long long ldk = w.K[1] - w.K[0];
+    double* gth = w.red_out + (MAX_KRYLOV + 1) - 8;   // 8 doubles at the end of the result area
+    double* part = nullptr;
+    if (gtheta) {
+        const long long need = vjp_grid(*m) * 8;
+        if (m->theta_part_n < need) {
+            if (m->theta_part) cudaFree(m->theta_part);
+            m->theta_part = nullptr;
+            m->theta_part_n = 0;
+            CDG2_TRY(cudaMalloc(&m->theta_part, sizeof(double) * need));
+            m->theta_part_n = need;
+        }
+        part = m->theta_part;
+    }
+    const double* pinv = nullptr;
+    std::vector<double> ptab;
+    if (o->precond == 1) {
+        modal_pinv(*m, c, dt * T.A[0][0], ptab);
+        CDG2_TRY(cudaMemcpy(w.pinv, ptab.data(), sizeof(double) * ptab.size(), cudaMemcpyHostToDevice));
+        pinv = w.pinv;
+    }
+    cdg2_stats S;
+    std::memset(&S, 0, sizeof(S));
+    S.stages = T.s;
+    for (int i = T.s - 1; i >= 0; --i) {
+        const double* Yi = stages + (size_t)i * n;
+        const double gdt = dt * T.A[i][i];
+        // r_i = dt b_i lam + dt sum_{j>i} a_ji ybar_j   (ybar_j kept in K[j])
+        CDG2_TRY(vec_convert<double, double>(n, lam, dt * T.b[i], w.rhs, st));
+        Coeffs a;
+        for (int j = i + 1; j < T.s; ++j) a.v[j - i - 1] = dt * T.A[j][i];
+        if (i + 1 < T.s) CDG2_TRY(vec_lincomb(n, w.rhs, T.s - 1 - i, w.K[i + 1], ldk, a, w.rhs, st));
+        double r0 = 0.0;
+        if (int rc = norm2<double>(w, w.rhs, st, &r0)) return rc;
+        S.residual0[i] = r0;
+        CDG2_TRY(cudaMemsetAsync(w.Y, 0, sizeof(double) * n, st));            // g_i = 0
+        bool converged = r0 == 0.0;
+        for (int it = 0; it < o->max_newton && !converged; ++it) {
+            // residual rr = r_i - (I - gdt J_i^T) g   (FP64)
+            CDG2_TRY(launch_vjp_axpby(*m, c, Yi, w.Y, 1.0, -gdt, nullptr, w.G, CDG2_MINV, st));
+            CDG2_TRY(vec_axpby<double>(n, 1.0, w.rhs, -1.0, w.G, st));
+            double rn = 0.0;
+            if (int rc = norm2<double>(w, w.G, st, &rn)) return rc;
+            S.residual[i] = rn;
+            if (!std::isfinite(rn)) {
+                set_error("cdg2_step_adjoint: non-finite residual");
+                return CDG2_ERR_NONFINITE;
+            }
+            if (rn <= std::fmax(o->newton_rtol * r0, o->newton_atol)) {
+                converged = true;
+                break;
+            }
+            ++S.newton_iters;
+            int its = 0, rc;
+            double rr = 0.0;
+            if (!mixed) {
+                rc = gmres<double>(*m, c, Yi, gdt, w.G, static_cast<double*>(w.dx), o->gmres_rtol, o->max_gmres, w, st,
+                                   0, pinv, &its, &rr, true);
+                if (rc == CDG2_OK) CDG2_TRY(vec_add_into<double>(n, static_cast<double*>(w.dx), w.Y, st));
+            } else {
+                CDG2_TRY(vec_convert<double, float>(n, Yi, 1.0, static_cast<float*>(w.Yk), st));
+                CDG2_TRY(vec_convert<double, float>(n, w.G, 1.0, static_cast<float*>(w.bk), st));
+                rc = gmres<float>(*m, c, static_cast<float*>(w.Yk), gdt, static_cast<float*>(w.bk),
+                                  static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, 0, pinv, &its, &rr,
+                                  true);
+                if (rc == CDG2_OK) CDG2_TRY(vec_add_into<float>(n, static_cast<float*>(w.dx), w.Y, st));
+            }
+            S.gmres_iters += its;
+            if (rc != CDG2_OK) return rc;
+        }
+        if (!converged) {
+            // the last correction was not checked: check once more
+            CDG2_TRY(launch_vjp_axpby(*m, c, Yi, w.Y, 1.0, -gdt, nullptr, w.G, CDG2_MINV, st));
+            CDG2_TRY(vec_axpby<double>(n, 1.0, w.rhs, -1.0, w.G, st));
+            double rn = 0.0;
+            if (int rc = norm2<double>(w, w.G, st, &rn)) return rc;
+            S.residual[i] = rn;
+            if (!(rn <= std::fmax(o->newton_rtol * r0, o->newton_atol))) {
+                set_error("cdg2_step_adjoint: a stage system did not reach the tolerance within max_newton refinements");
+                if (stats) *stats = S;
+                return CDG2_ERR_NOT_CONVERGED;
+            }
+        }
+        // ybar_i = J_i^T g_i (into K[i]) and the coefficient gradient of this stage
+        CDG2_TRY(launch_vjp(*m, c, Yi, w.Y, w.K[i], part, gtheta ? gth : nullptr, CDG2_MINV, st));
+        if (gtheta) CDG2_TRY(vec_axpby<double>(8, 1.0, gth, 1.0, gtheta, st));
+    }
+    // lam_n = lam + sum_i ybar_i
+    Coeffs ones;
+    for (int i = 0; i < T.s; ++i) ones.v[i] = 1.0;
+    CDG2_TRY(vec_lincomb(n, lam, T.s, w.K[0], ldk, ones, lam, st));
+    CDG2_TRY(cudaStreamSynchronize(st));
+    S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (stats) *stats = S;
+    return CDG2_OK;
 }

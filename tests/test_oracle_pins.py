@@ -421,3 +421,30 @@ def test_projection_reproduces_qk_polynomials():
     f = lambda x: torch.stack([(x[..., 0] ** 2) * x[..., 1] + s for s in range(6)])
     U = O.project(mesh, f)
     assert float(O.l2_error(mesh, U, f).max()) < 1e-14
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk3"])
+def test_step_adjoint_matches_finite_differences_of_the_step(scheme):
+    mesh = O.Mesh(2, (2, 2), (1.0, 0.2), (1, 0), 1)
+    p = I.default_params()
+    p["chi0"] = (0.05, 0.02, 0.03, 0.02)
+    U = smooth_state(mesh, seed=2)
+    U[:, 3, 0] += 0.05
+    dt = 2e-3
+    U1, stages = O.step_stages(mesh, U, p, 0.0, dt, scheme)
+    assert torch.allclose(U1, O.step(mesh, U, p, 0.0, dt, scheme), atol=1e-12)
+    rng = np.random.default_rng(4)
+    lam = torch.from_numpy(rng.standard_normal(U.shape))
+    v = torch.from_numpy(rng.standard_normal(U.shape))
+    lam0, gth = O.step_adjoint(mesh, stages, p, dt, scheme, lam, I.THETA_NAMES)
+    eps = 1e-6
+    fd = float((lam * (O.step(mesh, U + eps * v, p, 0.0, dt, scheme) - O.step(mesh, U - eps * v, p, 0.0, dt, scheme))).sum()) / (2 * eps)
+    assert abs(fd - float((lam0 * v).sum())) <= 1e-7 * max(1.0, abs(fd))
+    for i in (0, 2, 6, 7):                      # d1, gamma, k_ox, beta1
+        name = I.THETA_NAMES[i]
+        h = 1e-6 * max(1.0, abs(p[name]))
+        pp, pm = dict(p), dict(p)
+        pp[name] += h
+        pm[name] -= h
+        fdt = float((lam * (O.step(mesh, U, pp, 0.0, dt, scheme) - O.step(mesh, U, pm, 0.0, dt, scheme))).sum()) / (2 * h)
+        assert abs(fdt - float(gth[i])) <= 1e-6 * max(1.0, abs(fdt)), name

@@ -235,6 +235,38 @@ def measure_solve(G, torch, cfg: int, steps: int):
     return result
 
 
+def measure_gradient(G, torch, cfg: int, steps: int | None, mixed: bool):
+    """Forward + checkpointed discrete-adjoint backward of J = int n3(T) w.r.t. (U0, theta)."""
+    import numpy as np
+
+    import cdg2_inputs as I
+    from paper_1403_1157_gb300 import adjoint as Adj
+    w = I.workload(cfg)
+    nsteps = steps or w.steps
+    cp = w.extra.get("checkpoint", 10)
+    mesh = G.cdg2_mesh_create(w.dim, w.cells, w.extent, w.periodic, w.k)
+    U0, p = make_inputs(G, w, I, mesh)
+    theta = torch.tensor([p[n] for n in Adj.THETA_NAMES], dtype=torch.float64, device="cuda")
+    scheme = G.CDG2_SDIRK2 if w.k == 1 else G.CDG2_SDIRK3
+    opts = G.make_opts(scheme=scheme, mixed=mixed, newton_rtol=1e-10, gmres_rtol=1e-4 if mixed else 1e-3)
+    vol = float(np.prod([e / c for e, c in zip(w.extent[: w.dim], w.cells[: w.dim])]))
+    U = U0.clone().requires_grad_(True)
+    th = theta.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    UT = Adj.steps(U, th, mesh, p, 0.0, w.dt, nsteps, cp, opts)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J = vol * UT.view(mesh.n_elem, 6, mesh.n_basis)[:, 2, 0].sum()
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return {"workload": w.name, "n_dof": w.n_dof, "steps": nsteps, "checkpoint": cp, "dt": w.dt,
+            "precision": "mixed" if mixed else "fp64", "forward_s": t1 - t0, "backward_s": t2 - t1,
+            "functional": "int n3(T)", "dJ_dtheta": [float(v) for v in th.grad],
+            "dJ_dU0_norm": float(U.grad.norm())}
+
+
 def cpu_oracle_baseline(w, seconds: float = 12.0):
     """The oracle (plain FP64 PyTorch CPU) timed on this host on the same workload."""
     import torch
@@ -310,11 +342,29 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve-config", type=int, default=3, help="workload of the implicit-solve comparison")
     ap.add_argument("--solve-steps", type=int, default=2, help="timed implicit steps per precision (0: skip)")
+    ap.add_argument("--grad-config", type=int, default=2, help="workload of the gradient-through-steps timing")
+    ap.add_argument("--profile-solve", choices=["mixed", "fp64"], default=None,
+                    help="run one implicit step of the solve workload and exit (for ncu launch lists)")
+    ap.add_argument("--grad-steps", type=int, default=-1, help="steps of the gradient timing (-1: the workload's; 0: skip)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_solve:
+        import torch
+
+        import cdg2_inputs as I
+        import paper_1403_1157_gb300 as G
+        w = I.workload(args.solve_config)
+        mesh = G.cdg2_mesh_create(w.dim, w.cells, w.extent, w.periodic, w.k)
+        U, p = make_inputs(G, w, I, mesh)
+        mixed = args.profile_solve == "mixed"
+        scheme = G.CDG2_SDIRK2 if w.k == 1 else G.CDG2_SDIRK3
+        rc, st = G.cdg2_step(mesh, p, U, 0.0, w.dt, G.make_opts(scheme=scheme, mixed=mixed, newton_rtol=1e-10,
+                                                                 gmres_rtol=1e-4 if mixed else 1e-3))
+        print(json.dumps({"profile_solve": args.profile_solve, "workload": w.name, "stats": st}))
         return
 
     import torch
@@ -406,6 +456,9 @@ def main():
 
     derivs = measure_derivatives(G, torch, w, mesh, p, U, flush, max(10, args.steps // 8))
     solve = measure_solve(G, torch, args.solve_config, args.solve_steps) if args.solve_steps > 0 else None
+    grad = None
+    if args.grad_steps != 0:
+        grad = measure_gradient(G, torch, args.grad_config, None if args.grad_steps < 0 else args.grad_steps, True)
 
     if rank != 0:
         if world > 1:
@@ -429,6 +482,7 @@ def main():
         "fp32": fp32,
         "derivatives": derivs,
         "solve": solve,
+        "gradient": grad,
         "e2e": e2e,
         "gpu_launches": args.steps * (1 + w.dim),
         "clocks": clk,

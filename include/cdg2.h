@@ -50,6 +50,7 @@ extern "C" {
 /* time-stepping schemes of cdg2_step */
 #define CDG2_SDIRK2 2    /* Alexander's 2-stage L-stable SDIRK, order 2 */
 #define CDG2_SDIRK3 3    /* Alexander's 3-stage L-stable SDIRK, order 3 */
+#define CDG2_SDIRK4 4    /* Hairer and Wanner's 5-stage L-stable SDIRK, gamma = 1/4, order 4 */
 
 typedef struct cdg2_mesh cdg2_mesh;
 
@@ -81,7 +82,12 @@ typedef struct cdg2_mesh_desc {
  * beta1, beta2, sigma inflow rates; c1_star, c1_star2 thresholds c1*, c1**.
  * bc_sign: +1 reads the normal of Eq. (3) as inward (influx), -1 outward.
  * mms_phase: phases of the manufactured solution used by CDG2_FORCING,
- *   U*_s = 1 + cos(2 pi x + mms_phase[s]) cos(pi y / L1) exp(-t) / 2. */
+ *   U*_s = 1 + cos(2 pi x + mms_phase[s]) cos(pi y / L1) exp(-t) / 2.
+ * model: 0 = the six-species system of Eq. (1); 1 = the reduced model of
+ *   Eq. (2) (Sec. 4.2): only n1, n3, c1 evolve; n2, c2, c3 are inactive and
+ *   must be zero fields (their rows of f are zero); n1 has no c3-taxis and no
+ *   death term, n3 keeps d1 n1 - gamma n1, c1 has no alpha2 term, and only
+ *   the n1 inflow of Eq. (3) remains.  Other values are read as 0. */
 typedef struct cdg2_params {
     double mu[3];
     double nu[3];
@@ -91,11 +97,13 @@ typedef struct cdg2_params {
     double beta1, beta2, sigma, c1_star, c1_star2;
     double bc_sign;
     double mms_phase[6];
+    int model;
 } cdg2_params;
 
 /* Options of cdg2_step.
- * scheme: CDG2_SDIRK2 or CDG2_SDIRK3 (Sec. 3.2 names DIRK of order 2, 3 or 4
- *   without tableaux; Reading: Alexander's L-stable stiffly accurate SDIRK).
+ * scheme: CDG2_SDIRK2, CDG2_SDIRK3 or CDG2_SDIRK4 (Sec. 3.2 names DIRK of
+ *   order 2, 3 or 4 without tableaux; Reading: L-stable stiffly accurate
+ *   SDIRK methods of Alexander (orders 2, 3) and Hairer-Wanner (order 4)).
  * mixed: 0 = FP64 Krylov vectors and FP64 JVP; 1 = FP32 Krylov vectors, FP32
  *   JVP about an FP32 copy of the stage iterate, FP64 Newton residual and
  *   update (iterative refinement).
@@ -128,8 +136,8 @@ typedef struct cdg2_stats {
     int stages;           /* stages of the scheme */
     int newton_iters;     /* Newton corrections, all stages */
     int gmres_iters;      /* GMRES iterations (JVP launches in Arnoldi), all stages */
-    double residual0[4];  /* ||G(Y^0)||_2 per stage */
-    double residual[4];   /* final ||G||_2 per stage */
+    double residual0[5];  /* ||G(Y^0)||_2 per stage */
+    double residual[5];   /* final ||G||_2 per stage */
     double seconds;       /* host wall time of the call */
 } cdg2_stats;
 
@@ -189,7 +197,7 @@ int cdg2_step(const cdg2_mesh* mesh, const cdg2_params* params, double* U, doubl
 
 /* cdg2_step that also stores the converged stage values Y_1..Y_s, the
  * linearisation points of the step's discrete adjoint.
- * stages: device float64 [s][n_elem][6][n_basis] (s = 2 or 3 for the scheme). */
+ * stages: device float64 [s][n_elem][6][n_basis] (s = 2, 3, 5 for SDIRK2, 3, 4). */
 int cdg2_step_stages(const cdg2_mesh* mesh, const cdg2_params* params, double* U, double t, double dt,
                      const cdg2_solver_opts* opts, double* stages, cdg2_stats* stats, void* stream);
 

@@ -195,6 +195,15 @@ def chi(x, y, a, b):
     return a * x / (y + b)
 
 
+def reduced(p) -> bool:
+    """True for the reduced three-species model of Eq. (2) (Sec. 4.2): p["model"] == 1."""
+    return int(p.get("model", 0)) == 1
+
+
+# species that evolve in the reduced model of Eq. (2): n1, n3, c1
+REDUCED_ACTIVE = (1.0, 0.0, 1.0, 1.0, 0.0, 0.0)
+
+
 def velocity(u, g, p):
     """Chemotactic velocities v_1, v_2 with F_s = U_s v_s (s = n1, n2).
 
@@ -207,6 +216,9 @@ def velocity(u, g, p):
     """
     n1, c1, c3 = u[0], u[3], u[5]
     a, b = p["chi0"], p["chith"]
+    if reduced(p):
+        # Eq. (2): n1 follows c1 only; n2 is not part of the model
+        return (a[0] / (c1 + b[0])) * g[3], torch.zeros_like(g[0])
     v1 = (a[0] / (c1 + b[0])) * g[3] + (a[1] / (c3 + b[1])) * g[5]
     v2 = (a[2] / (c1 + b[2])) * g[3] - (a[3] / (n1 + b[3])) * g[0]
     return v1, v2
@@ -217,6 +229,10 @@ def flux_F(u, g, p):
     a, b = p["chi0"], p["chith"]
     n1, n2, c1, c3 = u[0], u[1], u[3], u[5]
     F = torch.zeros_like(g)
+    if reduced(p):
+        # Eq. (2): F_1 = chi(n1, c1; chi11) grad c1; the other rows are zero
+        F0 = chi(n1, c1, a[0], b[0]) * g[3]
+        return torch.stack([F0] + [torch.zeros_like(F0)] * 5)
     F0 = chi(n1, c1, a[0], b[0]) * g[3] + chi(n1, c3, a[1], b[1]) * g[5]
     F1 = chi(n2, c1, a[2], b[2]) * g[3] - chi(n2, n1, a[3], b[3]) * g[0]
     F = torch.stack([F0, F1] + [torch.zeros_like(F0)] * 4)
@@ -224,8 +240,11 @@ def flux_F(u, g, p):
 
 
 def diffusivity(p):
-    """A = diag(mu1, mu2, mu3, nu1, nu2, nu3) (Sec. 2)."""
-    return torch.stack([p["mu"][0], p["mu"][1], p["mu"][2], p["nu"][0], p["nu"][1], p["nu"][2]])
+    """A = diag(mu1, mu2, mu3, nu1, nu2, nu3) (Sec. 2); inactive species of Eq. (2) get 0."""
+    A = torch.stack([p["mu"][0], p["mu"][1], p["mu"][2], p["nu"][0], p["nu"][1], p["nu"][2]])
+    if reduced(p):
+        A = A * torch.tensor(REDUCED_ACTIVE, dtype=F64)
+    return A
 
 
 def source_S(u, p):
@@ -236,6 +255,12 @@ def source_S(u, p):
     constant; F(n3, c3) is the constant gamma < 0 of Sec. 2.
     """
     n1, n2, n3, c1, c2, c3 = u
+    if reduced(p):
+        # Eq. (2): n1 has no source; n3 gains d1 n1 + d2 n2 - gamma n1 (n2 absent, taken 0);
+        # c1 loses alpha1 n1 c1 and gains f1 n3; n2, c2, c3 do not evolve
+        z = torch.zeros_like(n1)
+        return torch.stack([z, z, p["d1"] * n1 + p["d2"] * n2 - p["gamma"] * n1,
+                            -p["alpha1"] * n1 * c1 + p["f1"] * n3, z, z])
     return torch.stack([
         -p["d1"] * n1,
         -p["d2"] * n2,
@@ -383,10 +408,14 @@ def boundary_residual(mesh: Mesh, U, p):
             inside = ((x[..., 0] >= mesh.gamma1_in[0]) & (x[..., 0] <= mesh.gamma1_in[1])).to(F64)
             g0 = p["bc_sign"] * p["mu"][0] * p["beta1"] * heaviside(u[3] - p["c1_star"])
             g4 = p["bc_sign"] * p["nu"][1] * p["sigma"] * inside
+            if reduced(p):
+                g4 = torch.zeros_like(g4)          # no LDL in Eq. (2)
             g = torch.stack([g0, torch.zeros_like(g0), torch.zeros_like(g0), torch.zeros_like(g0), g4,
                              torch.zeros_like(g0)])
         else:
             g1 = p["bc_sign"] * p["mu"][1] * p["beta2"] * heaviside(u[3] - p["c1_star2"])
+            if reduced(p):
+                g1 = torch.zeros_like(g1)          # no SMCs in Eq. (2)
             z = torch.zeros_like(g1)
             g = torch.stack([z, g1, z, z, z, z])
         R = R.index_add(0, el, torch.einsum("p,sfp,pi->fsi", area * wf, g, phi))
@@ -532,9 +561,10 @@ def mms_forcing(params: dict, phases, Ly):
 # Time stepping (Sec. 3.2): SDIRK + Newton + GMRES, matrix-free
 # ----------------------------------------------------------------------------
 def sdirk_tableau(name: str):
-    """Butcher tableau (A, b, c) of the L-stable SDIRK methods of Alexander (1977).
+    """Butcher tableau (A, b, c) of L-stable, stiffly accurate SDIRK methods.
 
     Reading: the paper names DIRK of order 2, 3 or 4 without tableaux.
+    sdirk2, sdirk3: Alexander (1977); sdirk4: Hairer and Wanner's 5-stage method.
     sdirk2: 2 stages, gamma = 1 - 1/sqrt(2), stiffly accurate.
     sdirk3: 3 stages, gamma the root in (1/6, 1/2) of 6 g^3 - 18 g^2 + 9 g - 1,
     c2 = (1 + gamma)/2, b1 = -(6 g^2 - 16 g + 1)/4, b2 = (6 g^2 - 20 g + 5)/4.
@@ -542,6 +572,13 @@ def sdirk_tableau(name: str):
     if name == "sdirk2":
         g = 1.0 - 1.0 / math.sqrt(2.0)
         A = np.array([[g, 0.0], [1.0 - g, g]])
+    elif name == "sdirk4":
+        # Hairer & Wanner, Solving ODEs II, Sec. IV.6: 5 stages, gamma = 1/4, order 4
+        A = np.array([[1 / 4, 0, 0, 0, 0],
+                      [1 / 2, 1 / 4, 0, 0, 0],
+                      [17 / 50, -1 / 25, 1 / 4, 0, 0],
+                      [371 / 1360, -137 / 2720, 15 / 544, 1 / 4, 0],
+                      [25 / 24, -49 / 48, 125 / 16, -85 / 12, 1 / 4]])
     elif name == "sdirk3":
         roots = np.roots([6.0, -18.0, 9.0, -1.0])
         g = float([r.real for r in roots if abs(r.imag) < 1e-14 and 1 / 6 < r.real < 0.5][0])
@@ -568,13 +605,23 @@ def _gmres(matvec, rhs, tol, restart=50, maxit=2000):
     return torch.from_numpy(x).reshape(rhs.shape)
 
 
+def _newton_correction(mesh: Mesh, Y, G, gdt: float, params: dict, gmres_tol: float):
+    """Solve (I - gdt J(Y)) d = -G: dense Jacobian and LU for tiny systems, else GMRES."""
+    n = Y.numel()
+    if n <= 3000:
+        J = torch.func.jacfwd(lambda V: apply(mesh, V, params))(Y).reshape(n, n)
+        return torch.linalg.solve(torch.eye(n, dtype=F64) - gdt * J, -G.reshape(-1)).reshape(Y.shape)
+    return _gmres(lambda v: v - gdt * jvp(mesh, Y, v, params), -G, gmres_tol)
+
+
 def step(mesh: Mesh, U, params: dict, t: float, dt: float, scheme="sdirk2", forcing=None,
          newton_tol=1e-13, gmres_tol=1e-13, max_newton=30):
     """One SDIRK step U_n -> U_{n+1} for U' = f(U, t) = M^{-1} L_h(U) (+ forcing).
 
     Stage i solves Y_i - dt a_ii f(Y_i, t + c_i dt) = U_n + dt sum_{j<i} a_ij K_j by
     Newton's method; each Newton correction solves (I - dt a_ii J(Y)) d = -G with
-    GMRES using J(Y) v from automatic differentiation (Jacobian-free Newton-Krylov).
+    GMRES using J(Y) v from automatic differentiation (Jacobian-free Newton-Krylov),
+    or, for systems of at most 3000 unknowns, with the dense Jacobian and LU.
     Newton stops when ||G||_2 <= newton_tol * max(1, ||rhs_i||_2).
     """
     A, b, c = sdirk_tableau(scheme)
@@ -593,12 +640,7 @@ def step(mesh: Mesh, U, params: dict, t: float, dt: float, scheme="sdirk2", forc
             G = Y - gdt * fY - rhs
             if float(torch.linalg.norm(G)) <= newton_tol * scale:
                 break
-            Yc = Y
-
-            def mv(v, Yc=Yc):
-                return v - gdt * jvp(mesh, Yc, v, params)
-
-            Y = Y + _gmres(mv, -G, gmres_tol)
+            Y = Y + _newton_correction(mesh, Y, G, gdt, params, gmres_tol)
         else:
             raise RuntimeError("oracle Newton did not converge")
         K.append(apply(mesh, Y, params, forcing, ti))
@@ -627,8 +669,7 @@ def step_stages(mesh: Mesh, U, params: dict, t: float, dt: float, scheme="sdirk2
             G = Y - gdt * fY - rhs
             if float(torch.linalg.norm(G)) <= kw.get("newton_tol", 1e-13) * scale:
                 break
-            Yc = Y
-            Y = Y + _gmres(lambda v, Yc=Yc: v - gdt * jvp(mesh, Yc, v, params), -G, kw.get("gmres_tol", 1e-13))
+            Y = Y + _newton_correction(mesh, Y, G, gdt, params, kw.get("gmres_tol", 1e-13))
         stages.append(Y.clone())
         K.append(apply(mesh, Y, params, kw.get("forcing"), ti))
     out = U.clone()

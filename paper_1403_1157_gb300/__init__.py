@@ -17,7 +17,7 @@ __all__ = [
     "CDG2_MINV", "CDG2_FORCING", "CDG2_FP32", "Cdg2Error", "Mesh", "load_library", "library_path",
     "make_params", "cdg2_mesh_create", "cdg2_mesh_destroy", "cdg2_mesh_info", "cdg2_apply", "cdg2_last_error",
     "cdg2_project_gaussians", "cdg2_project_mms", "cdg2_jvp", "cdg2_vjp", "cdg2_step",
-    "CDG2_SDIRK2", "CDG2_SDIRK3", "SolverOpts", "Stats", "make_opts", "cdg2_step_stages", "cdg2_step_adjoint",
+    "CDG2_SDIRK2", "CDG2_SDIRK3", "CDG2_SDIRK4", "SolverOpts", "Stats", "make_opts", "cdg2_step_stages", "cdg2_step_adjoint",
     "stages_of",
 ]
 
@@ -26,6 +26,7 @@ CDG2_FORCING = 2
 CDG2_FP32 = 4
 CDG2_SDIRK2 = 2
 CDG2_SDIRK3 = 3
+CDG2_SDIRK4 = 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
@@ -65,6 +66,7 @@ class Params(ctypes.Structure):
         ("c1_star", ctypes.c_double), ("c1_star2", ctypes.c_double),
         ("bc_sign", ctypes.c_double),
         ("mms_phase", ctypes.c_double * 6),
+        ("model", ctypes.c_int),
     ]
 
 
@@ -80,7 +82,7 @@ class SolverOpts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [
         ("stages", ctypes.c_int), ("newton_iters", ctypes.c_int), ("gmres_iters", ctypes.c_int),
-        ("residual0", ctypes.c_double * 4), ("residual", ctypes.c_double * 4), ("seconds", ctypes.c_double),
+        ("residual0", ctypes.c_double * 5), ("residual", ctypes.c_double * 5), ("seconds", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -160,6 +162,7 @@ def make_params(p: dict, mms_phase=None) -> Params:
     ph = mms_phase if mms_phase is not None else p.get("mms_phase", (0.0,) * 6)
     for j in range(6):
         out.mms_phase[j] = float(ph[j])
+    out.model = int(p.get("model", 0))
     return out
 
 
@@ -327,7 +330,7 @@ def cdg2_step(mesh: Mesh, params, U: torch.Tensor, t: float, dt: float, opts: So
 
 
 def stages_of(opts: SolverOpts) -> int:
-    return 2 if opts.scheme == CDG2_SDIRK2 else 3
+    return {CDG2_SDIRK2: 2, CDG2_SDIRK3: 3, CDG2_SDIRK4: 5}[opts.scheme]
 
 
 def cdg2_step_stages(mesh: Mesh, params, U: torch.Tensor, t: float, dt: float, stages: torch.Tensor,

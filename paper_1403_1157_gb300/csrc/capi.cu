@@ -45,6 +45,17 @@ Coef make_coef(const cdg2_params& p) {
     c.c1ss = p.c1_star2;
     c.bc_sign = p.bc_sign;
     for (int s = 0; s < NS; ++s) c.phase[s] = p.mms_phase[s];
+    c.model = p.model;
+    if (p.model == 1) {
+        // Reduced model of Eq. (2) (Sec. 4.2): only n1, n3, c1 evolve.  Species
+        // n2, c2, c3 are inactive (no diffusion, taxis, sources or inflow;
+        // their fields are expected to be zero), n1 loses its c3-taxis and its
+        // death term, c1 loses the alpha2 term; n3 keeps d1 n1 - gamma n1.
+        c.A[1] = c.A[4] = c.A[5] = 0.0;
+        c.chi0[1] = c.chi0[2] = c.chi0[3] = 0.0;
+        c.d2 = c.alpha2 = c.k_ox = 0.0;
+        c.beta2 = c.sigma = 0.0;
+    }
     return c;
 }
 

@@ -44,6 +44,7 @@ struct Coef {
     double d1, d2, gamma, alpha1, alpha2, f1, k_ox;
     double beta1, beta2, sigma, c1s, c1ss, bc_sign;
     double phase[NS];
+    int model;                     // 0: Eq. (1); 1: reduced model of Eq. (2)
 };
 
 Coef make_coef(const cdg2_params& p);

@@ -178,6 +178,7 @@ struct CoefT {
     T inv_vol;      // 1 / |K| (M^{-1} of the orthonormal basis)
     T invh[3];      // 1 / h_j
     T chi_e;        // CDG2 lifting factor
+    T death1;       // 1: Eq. (1); 0: the reduced model of Eq. (2) (no n1 death term)
 };
 
 // Host-side conversion (kernel parameters live in the constant bank, so the
@@ -211,6 +212,7 @@ inline CoefT<T> make_coefT(const Coef& c, const Geo& g, const double* dtheta) {
     d.inv_vol = T(1.0 / g.vol);
     for (int j = 0; j < 3; ++j) d.invh[j] = T(1.0 / g.h[j]);
     d.chi_e = T(g.chi_e);
+    d.death1 = T(c.model == 1 ? 0.0 : 1.0);
     return d;
 }
 
@@ -244,7 +246,7 @@ __device__ __forceinline__ void mms_forcing(T x, T y, T t, T Ly, const C& c, T g
     T divF[NS] = {div_chem(0, 3, 0) + div_chem(0, 5, 1), div_chem(1, 3, 2) - div_chem(1, 0, 3), 0, 0, 0, 0};
     const T n1 = u[0], n2 = u[1], n3 = u[2], c1 = u[3], c2 = u[4];
     T S[NS];
-    S[0] = -T(c.d1) * n1;
+    S[0] = -T(c.death1) * T(c.d1) * n1;
     S[1] = -T(c.d2) * n2;
     S[2] = T(c.d1) * n1 + T(c.d2) * n2 - T(c.gamma) * n1;
     S[3] = -T(c.alpha1) * n1 * c1 - T(c.alpha2) * n2 * c1 + T(c.f1) * n3;

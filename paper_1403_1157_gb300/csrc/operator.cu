@@ -91,7 +91,8 @@ constexpr int fields_of(int mode) { return mode == MODE_APPLY ? 1 : 2; }
 
 // Volume flux at one quadrature point (Eq. elementint): Phi_s = F_s(U, grad U)
 // - A_s grad U_s and S(U) (Reading: the c1 row of S follows Eq. (1),
-// -alpha1 n1 c1 - alpha2 n2 c1 + f1 n3).
+// -alpha1 n1 c1 - alpha2 n2 c1 + f1 n3).  death1 = 0 drops the n1 death term
+// (the reduced model of Eq. (2), which keeps d1 n1 in the n3 equation).
 template <int D, typename T>
 __device__ __forceinline__ void volume_point(const CoefT<T>& c, const T u[NS], const T g[NS][D], T Phi[NS][D],
                                              T S[NS]) {
@@ -109,7 +110,7 @@ __device__ __forceinline__ void volume_point(const CoefT<T>& c, const T u[NS], c
         for (int s = 2; s < NS; ++s) Phi[s][j] = -T(c.A[s]) * g[s][j];
     }
     const T n1 = u[0], n2 = u[1], n3 = u[2], c1 = u[3], c2 = u[4];
-    S[0] = -T(c.d1) * n1;
+    S[0] = -c.death1 * c.d1 * n1;
     S[1] = -T(c.d2) * n2;
     S[2] = T(c.d1) * n1 + T(c.d2) * n2 - T(c.gamma) * n1;
     S[3] = -T(c.alpha1) * n1 * c1 - T(c.alpha2) * n2 * c1 + T(c.f1) * n3;
@@ -144,7 +145,7 @@ __device__ __forceinline__ void volume_point_lin(const CoefT<T>& c, const T u[NS
 #pragma unroll
         for (int s = 2; s < NS; ++s) dPhi[s][j] = -T(c.A[s]) * dg[s][j];
     }
-    dS[0] = -T(c.d1) * du[0];
+    dS[0] = -c.death1 * c.d1 * du[0];
     dS[1] = -T(c.d2) * du[1];
     dS[2] = T(c.d1) * du[0] + T(c.d2) * du[1] - T(c.gamma) * du[0];
     dS[3] = -T(c.alpha1) * (du[0] * u[3] + u[0] * du[3]) - T(c.alpha2) * (du[1] * u[3] + u[1] * du[3]) +
@@ -153,7 +154,7 @@ __device__ __forceinline__ void volume_point_lin(const CoefT<T>& c, const T u[NS
     dS[5] = T(c.k_ox) * du[4];
     if (has_dth) {
         const T n1 = u[0], n2 = u[1], n3 = u[2], c1 = u[3], c2 = u[4];
-        dS[0] += -c.dth[0] * n1;
+        dS[0] += -c.death1 * c.dth[0] * n1;
         dS[1] += -c.dth[1] * n2;
         dS[2] += c.dth[0] * n1 + c.dth[1] * n2 - c.dth[2] * n1;
         dS[3] += -c.dth[3] * n1 * c1 - c.dth[4] * n2 * c1 + c.dth[5] * n3;
@@ -286,12 +287,12 @@ __device__ __forceinline__ void volume_point_adj(const CoefT<T>& c, const T u[NS
     ub[5] += -k13 * r13 * kb13;
     ub[0] += -k22 * r22 * kb22;
     // reaction source
-    ub[0] += -T(c.d1) * sb[0] + (T(c.d1) - T(c.gamma)) * sb[2] - T(c.alpha1) * u[3] * sb[3];
+    ub[0] += -c.death1 * c.d1 * sb[0] + (T(c.d1) - T(c.gamma)) * sb[2] - T(c.alpha1) * u[3] * sb[3];
     ub[1] += -T(c.d2) * sb[1] + T(c.d2) * sb[2] - T(c.alpha2) * u[3] * sb[3];
     ub[2] += T(c.f1) * sb[3];
     ub[3] += (-T(c.alpha1) * u[0] - T(c.alpha2) * u[1]) * sb[3];
     ub[4] += -T(c.k_ox) * sb[4] + T(c.k_ox) * sb[5];
-    th[0] += u[0] * (sb[2] - sb[0]);
+    th[0] += u[0] * (sb[2] - c.death1 * sb[0]);
     th[1] += u[1] * (sb[2] - sb[1]);
     th[2] += -u[0] * sb[2];
     th[3] += -u[0] * u[3] * sb[3];

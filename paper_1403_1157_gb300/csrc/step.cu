@@ -3,7 +3,8 @@
 // Jacobian-free Newton-Krylov method with GMRES (Sec. 3.2).
 //
 // Reading: the paper names DIRK methods of order 2, 3 or 4 without tableaux;
-// this uses Alexander's L-stable, stiffly accurate SDIRK2 and SDIRK3.
+// this uses Alexander's L-stable, stiffly accurate SDIRK2 and SDIRK3 and
+// Hairer and Wanner's 5-stage L-stable SDIRK4.
 //
 // Stage i solves G(Y) = Y - dt a_ii f(Y, t + c_i dt) - rhs_i = 0 with
 // rhs_i = U_n + dt sum_{j<i} a_ij K_j.  Newton: the residual G is always
@@ -28,11 +29,13 @@
 
 namespace cdg2 {
 
+constexpr int MAX_STAGES = 5;
+
 struct Tableau {
     int s;
-    double A[3][3];
-    double b[3];
-    double c[3];
+    double A[MAX_STAGES][MAX_STAGES];
+    double b[MAX_STAGES];
+    double c[MAX_STAGES];
 };
 
 // Alexander (1977): SDIRK2 with gamma = 1 - 1/sqrt(2); SDIRK3 with gamma the
@@ -47,6 +50,17 @@ static Tableau sdirk_tableau(int scheme) {
         T.A[0][0] = g;
         T.A[1][0] = 1.0 - g;
         T.A[1][1] = g;
+    } else if (scheme == CDG2_SDIRK4) {
+        // Hairer & Wanner (Solving ODEs II, Sec. IV.6): 5 stages, gamma = 1/4,
+        // stiffly accurate, L-stable, order 4.
+        static const double a[5][5] = {{1.0 / 4, 0, 0, 0, 0},
+                                       {1.0 / 2, 1.0 / 4, 0, 0, 0},
+                                       {17.0 / 50, -1.0 / 25, 1.0 / 4, 0, 0},
+                                       {371.0 / 1360, -137.0 / 2720, 15.0 / 544, 1.0 / 4, 0},
+                                       {25.0 / 24, -49.0 / 48, 125.0 / 16, -85.0 / 12, 1.0 / 4}};
+        T.s = 5;
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 5; ++j) T.A[i][j] = a[i][j];
     } else {
         double g = 0.43;
         for (int it = 0; it < 60; ++it) {
@@ -81,7 +95,7 @@ struct Work {
     double* fY;
     double* G;
     double* b64;
-    double* K[3];
+    double* K[MAX_STAGES];
     void* basis;      // (m + 2) vectors of the Krylov precision: V_0..V_m, w
     void* dx;         // the Krylov correction
     void* Yk;         // primal state in the Krylov precision (mixed) / unused
@@ -101,8 +115,8 @@ static int ensure_work(const cdg2_mesh& m, int kdim, bool mixed, Work& w) {
     const size_t red = align256(sizeof(double) * reduction_scratch_doubles(MAX_KRYLOV + 1));
     const size_t out = align256(sizeof(double) * (MAX_KRYLOV + 1));
     const size_t tab = align256(sizeof(double) * NS * m.nb);
-    // 8 FP64 vectors; basis (kdim + 2) + dx + Yk + bk in the Krylov precision
-    const size_t need = 8 * vec64 + (size_t)(kdim + 5) * veck + red + out + tab;
+    // 5 + MAX_STAGES FP64 vectors; basis (kdim + 2) + dx + Yk + bk in the Krylov precision
+    const size_t need = (5 + MAX_STAGES) * vec64 + (size_t)(kdim + 5) * veck + red + out + tab;
     if (m.step_ws_bytes < need) {
         if (m.step_ws) cudaFree(m.step_ws);
         m.step_ws = nullptr;
@@ -114,7 +128,7 @@ static int ensure_work(const cdg2_mesh& m, int kdim, bool mixed, Work& w) {
     char* p = static_cast<char*>(m.step_ws);
     w.n = n;
     w.m = kdim;
-    double** v64[8] = {&w.rhs, &w.Y, &w.fY, &w.G, &w.b64, &w.K[0], &w.K[1], &w.K[2]};
+    double** v64[5 + MAX_STAGES] = {&w.rhs, &w.Y, &w.fY, &w.G, &w.b64, &w.K[0], &w.K[1], &w.K[2], &w.K[3], &w.K[4]};
     for (auto* q : v64) {
         *q = reinterpret_cast<double*>(p);
         p += vec64;
@@ -301,10 +315,10 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
 using namespace cdg2;
 
 static int check_opts(const cdg2_solver_opts* o, double dt, const char* who) {
-    if ((o->scheme != CDG2_SDIRK2 && o->scheme != CDG2_SDIRK3) || o->gmres_restart < 1 ||
+    if ((o->scheme != CDG2_SDIRK2 && o->scheme != CDG2_SDIRK3 && o->scheme != CDG2_SDIRK4) || o->gmres_restart < 1 ||
         o->gmres_restart > MAX_KRYLOV || o->max_newton < 1 || o->max_gmres < 1 || !(dt > 0.0) ||
         (o->flags & ~CDG2_FORCING) || (o->precond != 0 && o->precond != 1)) {
-        set_error(std::string(who) + ": invalid options (scheme 2|3, 1 <= gmres_restart <= 64, max_newton, "
+        set_error(std::string(who) + ": invalid options (scheme 2|3|4, 1 <= gmres_restart <= 64, max_newton, "
                   "max_gmres >= 1, dt > 0, flags in {0, CDG2_FORCING}, precond in {0, 1})");
         return CDG2_ERR_INVALID_ARG;
     }

@@ -143,7 +143,7 @@ def test_step_iteration_cap_is_reported(G):
 def test_step_rejects_bad_options(G):
     om, gm = _pair(G, 2, (4, 2), 1)
     U = torch.zeros(gm.n_dof, dtype=torch.float64, device="cuda")
-    for bad in (dict(scheme=4), dict(gmres_restart=0), dict(gmres_restart=65), dict(max_newton=0)):
+    for bad in (dict(scheme=5), dict(gmres_restart=0), dict(gmres_restart=65), dict(max_newton=0), dict(precond=2)):
         rc, _ = G.cdg2_step(gm, I.default_params(), U, 0.0, 1e-3, G.make_opts(**bad), raise_on_error=False)
         assert rc == -1
     rc, _ = G.cdg2_step(gm, I.default_params(), U, 0.0, 0.0, G.make_opts(), raise_on_error=False)

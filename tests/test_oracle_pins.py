@@ -382,7 +382,7 @@ def test_table1_eoc_definition():
 # --------------------------------------------------------------------------
 def test_sdirk_tableaux():
     gold = dict(l.split() for l in open(os.path.join(GOLDEN, "sdirk_gamma.txt")) if l.strip() and not l.startswith("#"))
-    for name, order in (("sdirk2", 2), ("sdirk3", 3)):
+    for name, order in (("sdirk2", 2), ("sdirk3", 3), ("sdirk4", 4)):
         A, b, c = O.sdirk_tableau(name)
         assert abs(A[0, 0] - float(gold[name])) < 1e-10
         assert np.allclose(np.diag(A), A[0, 0])
@@ -391,11 +391,16 @@ def test_sdirk_tableaux():
             assert abs(b @ c ** 2 - 1 / 3) < 1e-14 and abs(b @ A @ c - 1 / 6) < 1e-14
         else:
             assert abs(b @ c ** 2 - 1 / 3) > 1e-3
+        if order >= 4:
+            assert abs(b @ c ** 3 - 1 / 4) < 1e-13 and abs(b @ (c * (A @ c)) - 1 / 8) < 1e-13
+            assert abs(b @ A @ c ** 2 - 1 / 12) < 1e-13 and abs(b @ A @ A @ c - 1 / 24) < 1e-13
+        elif order == 3:
+            assert abs(b @ c ** 3 - 1 / 4) > 1e-6
         # L-stable: R(inf) = 1 - b^T A^{-1} 1 = 0
         assert abs(1 - b @ np.linalg.solve(A, np.ones(len(b)))) < 1e-13
 
 
-@pytest.mark.parametrize("scheme,order", [("sdirk2", 2), ("sdirk3", 3)])
+@pytest.mark.parametrize("scheme,order", [("sdirk2", 2), ("sdirk3", 3), ("sdirk4", 4)])
 def test_step_temporal_order_against_matrix_exponential(scheme, order):
     from scipy.linalg import expm
     mesh = O.Mesh(2, (4, 2), (1.0, 0.2), (1, 0), 1)
@@ -448,3 +453,25 @@ def test_step_adjoint_matches_finite_differences_of_the_step(scheme):
         pm[name] -= h
         fdt = float((lam * (O.step(mesh, U, pp, 0.0, dt, scheme) - O.step(mesh, U, pm, 0.0, dt, scheme))).sum()) / (2 * h)
         assert abs(fdt - float(gth[i])) <= 1e-6 * max(1.0, abs(fdt)), name
+
+
+def test_reduced_model_eq2_for_constants_and_inactive_species():
+    """Eq. (2): for spatially constant n1, n3, c1 (n2 = c2 = c3 = 0), d n1/dt = 0,
+    d n3/dt = d1 n1 + d2 n2 - F n1 with F := gamma, d c1/dt = -alpha1 n1 c1 + f1 n3;
+    the species outside the reduced model do not evolve."""
+    mesh = O.Mesh(3, (3, 2, 2), (1.0, 0.2, 0.2), (1, 0, 1), 1)
+    p = I.default_params()
+    p["model"] = 1
+    p["beta1"] = 0.0
+    n1, n3, c1 = 0.7, 0.3, 0.9
+    U = torch.zeros(mesh.E, 6, mesh.nb, dtype=F64)
+    U[:, 0, 0], U[:, 2, 0], U[:, 3, 0] = n1, n3, c1
+    f = O.apply(mesh, U, p)
+    expect = [0.0, 0.0, p["d1"] * n1 - p["gamma"] * n1, -p["alpha1"] * n1 * c1 + p["f1"] * n3, 0.0, 0.0]
+    assert torch.allclose(f[:, :, 0], torch.tensor(expect, dtype=F64).expand(mesh.E, 6), atol=1e-14)
+    # with smooth active fields the inactive rows stay exactly zero and mass of n1 is conserved
+    V = smooth_state(mesh, seed=8)
+    V[:, [1, 4, 5], :] = 0.0
+    g = O.apply(mesh, V, p)
+    assert float(g[:, [1, 4, 5], :].abs().max()) == 0.0
+    assert abs(float(mesh.vol * g[:, 0, 0].sum())) < 1e-13 * float(mesh.vol * g.abs().sum())

@@ -47,6 +47,11 @@ extern "C" {
 #define CDG2_FORCING 2   /* add the manufactured-solution forcing at time t */
 #define CDG2_FP32 4      /* arrays are float32 and the kernel computes in FP32 */
 
+/* diffusion fluxes of cdg2_mesh_desc.flux */
+#define CDG2_FLUX_CDG2 0
+#define CDG2_FLUX_BR2 1
+#define CDG2_FLUX_SIPG 2
+
 /* time-stepping schemes of cdg2_step */
 #define CDG2_SDIRK2 2    /* Alexander's 2-stage L-stable SDIRK, order 2 */
 #define CDG2_SDIRK3 3    /* Alexander's 3-stage L-stable SDIRK, order 3 */
@@ -60,7 +65,14 @@ typedef struct cdg2_mesh cdg2_mesh;
  * q1: Gauss points per direction; 0 selects k+2 (the only supported value).
  * chi_e: CDG2 lifting factor (Sec. 3.1: half the faces per element);
  *   <= 0 selects dim (2 for quads, 3 for hexes).
- * gamma1_in: x-range [x0, x1] of the LDL inflow part Gamma_{1,in} of Gamma_1. */
+ * gamma1_in: x-range [x0, x1] of the LDL inflow part Gamma_{1,in} of Gamma_1.
+ * flux: diffusion flux A^ of Eq. (surfaceint): CDG2_FLUX_CDG2 (0, the paper's
+ *   choice), CDG2_FLUX_BR2 (1: eta {A r_e([U])}, liftings on both cells) or
+ *   CDG2_FLUX_SIPG (2: interior penalty -C (k+1)^2 A [U] / h) -- the schemes
+ *   compared in Fig. 2.  penalty: eta of BR2 (<= 0: 2 dim, the number of
+ *   faces) or C of SIPG (<= 0: 2 dim); unused for CDG2.  On these uniform
+ *   cells all three reduce to a penalty -c (k+1)^2 A Delta / h_a with
+ *   c = chi_e (CDG2), eta / 2 (BR2), C (SIPG). */
 typedef struct cdg2_mesh_desc {
     int dim;
     int cells[3];
@@ -70,6 +82,8 @@ typedef struct cdg2_mesh_desc {
     int q1;
     double chi_e;
     double gamma1_in[2];
+    int flux;
+    double penalty;
 } cdg2_mesh_desc;
 
 /* Model coefficients of Eq. (1) and Eq. (3) (Sec. 2).

@@ -109,7 +109,8 @@ class Mesh:
     k + 2 (Reading: the paper gives no quadrature for L_h).
     """
 
-    def __init__(self, dim, cells, extent, periodic, k, q1=None, chi_e=None, gamma1_in=(0.375, 0.625)):
+    def __init__(self, dim, cells, extent, periodic, k, q1=None, chi_e=None, gamma1_in=(0.375, 0.625),
+                 flux="cdg2", penalty=None):
         self.dim = dim
         self.cells = tuple(int(c) for c in cells[:dim])
         self.extent = tuple(float(x) for x in extent[:dim])
@@ -118,6 +119,9 @@ class Mesh:
         self.q1 = int(q1) if q1 else self.k + 2
         self.chi_e = float(chi_e) if chi_e is not None else float(dim)
         self.gamma1_in = tuple(gamma1_in)
+        # diffusion flux (Sec. 3.1 uses CDG2; Fig. 2 compares it with BR2 and IP)
+        self.flux = flux
+        self.penalty = float(penalty) if penalty else 2.0 * dim
         self.h = [self.extent[a] / self.cells[a] for a in range(dim)]
         self.vol = math.prod(self.h)
         self.E = math.prod(self.cells)
@@ -294,12 +298,13 @@ def volume_residual(mesh: Mesh, U, p):
 
 
 def lifting_normal(mesh: Mesh, phiM, Delta, nvec, area, wf):
-    """r_e([U]) . n^- on the face, r_e restricted to K^- (lifting identity of Sec. 3.1).
+    """r_e([U]) . n^- on the face, r_e restricted to one adjacent cell (lifting identity of Sec. 3.1).
 
     r_e is the element of [V_h]^d with int_Omega r_e : tau = -int_e [U] : {tau}
-    for all tau.  On K^- (with [U] = n^- (x) Delta, {tau} = tau^-/2 there):
-      M_{K^-} rho_{s,j} = -1/2 int_e n^-_j Delta_s phi_i^-,
+    for all tau.  On a cell K adjacent to e (with [U] = n^- (x) Delta, {tau} = tau_K/2 there):
+      M_K rho_{s,j} = -1/2 int_e n^-_j Delta_s phi_i^K,
     solved with the quadrature mass matrix, then evaluated at the face points.
+    phiM: that cell's basis tabulated at the face points (K^- for CDG2; both cells for BR2).
     Delta: (F, 6, P).  Returns (F, 6, P).
     """
     rhs = -0.5 * area * torch.einsum("p,j,fsp,pi->fsji", wf, nvec, Delta, phiM)
@@ -368,8 +373,18 @@ def face_residual(mesh: Mesh, U, p):
         lam = torch.stack(lam + [zero] * 4)
         Fhat_n = 0.5 * (FnM + FnP) + 0.5 * lam * Delta
 
-        rn = lifting_normal(mesh, phiM, Delta.permute(1, 0, 2), nvec, area, wf).permute(1, 0, 2)
-        Ahat_n = 2.0 * mesh.chi_e * A[:, None, None] * rn
+        if mesh.flux == "cdg2":
+            # A^ = 2 chi_e A r_e([U]) restricted to K^-
+            rn = lifting_normal(mesh, phiM, Delta.permute(1, 0, 2), nvec, area, wf).permute(1, 0, 2)
+            Ahat_n = 2.0 * mesh.chi_e * A[:, None, None] * rn
+        elif mesh.flux == "br2":
+            # A^ = eta A {r_e([U])}: the lifting on both cells, each evaluated on e from its side
+            rM = lifting_normal(mesh, phiM, Delta.permute(1, 0, 2), nvec, area, wf).permute(1, 0, 2)
+            rP = lifting_normal(mesh, phiP, Delta.permute(1, 0, 2), nvec, area, wf).permute(1, 0, 2)
+            Ahat_n = mesh.penalty * A[:, None, None] * 0.5 * (rM + rP)
+        else:
+            # interior penalty: A^ . n^- = -C (k+1)^2 A Delta |e| / |K|
+            Ahat_n = -mesh.penalty * (mesh.k + 1) ** 2 * (area / mesh.vol) * A[:, None, None] * Delta
 
         sigma = A[:, None, None] * avg_dn - Fhat_n + Ahat_n       # multiplies phi^- - phi^+
         tau = 0.5 * A[:, None, None] * Delta                       # multiplies dn phi^- + dn phi^+

@@ -50,6 +50,8 @@ class MeshDesc(ctypes.Structure):
         ("q1", ctypes.c_int),
         ("chi_e", ctypes.c_double),
         ("gamma1_in", ctypes.c_double * 2),
+        ("flux", ctypes.c_int),
+        ("penalty", ctypes.c_double),
     ]
 
 
@@ -194,7 +196,11 @@ class Mesh:
             pass
 
 
-def cdg2_mesh_create(dim, cells, extent, periodic, k, q1=0, chi_e=0.0, gamma1_in=(0.375, 0.625)) -> Mesh:
+CDG2_FLUX_CDG2, CDG2_FLUX_BR2, CDG2_FLUX_SIPG = 0, 1, 2
+
+
+def cdg2_mesh_create(dim, cells, extent, periodic, k, q1=0, chi_e=0.0, gamma1_in=(0.375, 0.625), flux=0,
+                     penalty=0.0) -> Mesh:
     desc = MeshDesc()
     desc.dim = int(dim)
     for a in range(3):
@@ -205,6 +211,8 @@ def cdg2_mesh_create(dim, cells, extent, periodic, k, q1=0, chi_e=0.0, gamma1_in
     desc.q1 = int(q1)
     desc.chi_e = float(chi_e)
     desc.gamma1_in[0], desc.gamma1_in[1] = float(gamma1_in[0]), float(gamma1_in[1])
+    desc.flux = int(flux)
+    desc.penalty = float(penalty)
     h = ctypes.c_void_p()
     _check(load_library().cdg2_mesh_create(ctypes.byref(desc), ctypes.byref(h)))
     return Mesh(h.value, desc)

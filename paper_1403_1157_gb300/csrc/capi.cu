@@ -169,6 +169,18 @@ int cdg2_mesh_create(const cdg2_mesh_desc* d, cdg2_mesh** out) {
         if (in) g.vol *= g.h[a];
     }
     g.chi_e = d->chi_e > 0.0 ? d->chi_e : (double)d->dim;
+    if (d->flux < CDG2_FLUX_CDG2 || d->flux > CDG2_FLUX_SIPG) {
+        delete m;
+        set_error("cdg2_mesh_create: flux must be CDG2_FLUX_CDG2, CDG2_FLUX_BR2 or CDG2_FLUX_SIPG");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    {
+        const double pdef = 2.0 * d->dim;
+        const double pp = d->penalty > 0.0 ? d->penalty : pdef;
+        // CDG2: 2 chi_e A r_e on K^-; BR2: eta A {r_e}; SIPG: the penalty itself.  With
+        // r_e . n^- = -(k+1)^2 |e| / (2 |K|) Delta on either cell of these uniform meshes:
+        g.pen_c = d->flux == CDG2_FLUX_CDG2 ? g.chi_e : (d->flux == CDG2_FLUX_BR2 ? 0.5 * pp : pp);
+    }
     g.g1in[0] = d->gamma1_in[0];
     g.g1in[1] = d->gamma1_in[1];
     g.E = E;

@@ -33,6 +33,7 @@ struct Geo {
     double L[3];
     double vol;        // |K|
     double chi_e;      // CDG2 lifting factor
+    double pen_c;      // face penalty constant c: -c (k+1)^2 A Delta / h (chi_e, eta/2 or C_IP)
     double g1in[2];    // Gamma_{1,in} x-range
     long long E;       // elements
 };

@@ -177,7 +177,7 @@ struct CoefT {
     T vol;          // |K|
     T inv_vol;      // 1 / |K| (M^{-1} of the orthonormal basis)
     T invh[3];      // 1 / h_j
-    T chi_e;        // CDG2 lifting factor
+    T pen_c;        // face penalty constant (chi_e for CDG2, eta/2 for BR2, C for SIPG)
     T death1;       // 1: Eq. (1); 0: the reduced model of Eq. (2) (no n1 death term)
 };
 
@@ -211,7 +211,7 @@ inline CoefT<T> make_coefT(const Coef& c, const Geo& g, const double* dtheta) {
     d.vol = T(g.vol);
     d.inv_vol = T(1.0 / g.vol);
     for (int j = 0; j < 3; ++j) d.invh[j] = T(1.0 / g.h[j]);
-    d.chi_e = T(g.chi_e);
+    d.pen_c = T(g.pen_c);
     d.death1 = T(c.model == 1 ? 0.0 : 1.0);
     return d;
 }

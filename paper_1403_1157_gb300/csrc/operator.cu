@@ -462,7 +462,7 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
     __syncthreads();
 
     // pointwise fluxes, weighted: W_p = w_p |e|, |e| = |K| / h_A
-    const T pen = c.chi_e * T((K + 1) * (K + 1)) * invh;
+    const T pen = c.pen_c * T((K + 1) * (K + 1)) * invh;
     for (int idx = threadIdx.x; idx < EPB * 2 * NQT; idx += blockDim.x) {
         const int p = idx % NQT;
         const int f = (idx / NQT) % 2;
@@ -782,7 +782,7 @@ __global__ void __launch_bounds__(128) face_kernel(const Geo g, const Tab1D tab,
     }
     __syncthreads();
 
-    const T pen = c.chi_e * T((K + 1) * (K + 1)) * invh;
+    const T pen = c.pen_c * T((K + 1) * (K + 1)) * invh;
     for (int idx = threadIdx.x; idx < FPB * NQT; idx += blockDim.x) {
         const int p = idx % NQT, j = idx / NQT;
         const int kd = kind[j];

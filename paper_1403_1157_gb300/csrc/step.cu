@@ -162,7 +162,7 @@ static void modal_pinv(const cdg2_mesh& m, const Coef& c, double gdt, std::vecto
         double vol = 0.0;
         for (int q = 0; q < k + 2; ++q) vol += t.w[q] * t.D[q][a] * t.D[q][a];
         const double face = t.d[1][a] * t.e[1][a] - t.d[0][a] * t.e[0][a];
-        const double pen = g.chi_e * (k + 1) * (k + 1) * (t.e[0][a] * t.e[0][a] + t.e[1][a] * t.e[1][a]);
+        const double pen = g.pen_c * (k + 1) * (k + 1) * (t.e[0][a] * t.e[0][a] + t.e[1][a] * t.e[1][a]);
         d1[a] = -vol + face - pen;
     }
     out.assign((size_t)NS * m.nb, 1.0);

@@ -49,6 +49,8 @@ def test_mesh_create_validates(lib):
         G.cdg2_mesh_create(2, (0, 2), (1, 1), (1, 0), 1)
     with pytest.raises(G.Cdg2Error):
         G.cdg2_mesh_create(2, (2, 2), (1, 1), (1, 0), 2, q1=5)
+    with pytest.raises(G.Cdg2Error):
+        G.cdg2_mesh_create(2, (2, 2), (1, 1), (1, 0), 2, flux=3)
     m = G.cdg2_mesh_create(3, (4, 3, 2), (1, 0.2, 0.2), (1, 0, 1), 2)
     assert (m.n_elem, m.n_basis, m.n_dof) == (24, 27, 24 * 27 * 6)
 

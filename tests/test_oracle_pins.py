@@ -475,3 +475,27 @@ def test_reduced_model_eq2_for_constants_and_inactive_species():
     g = O.apply(mesh, V, p)
     assert float(g[:, [1, 4, 5], :].abs().max()) == 0.0
     assert abs(float(mesh.vol * g[:, 0, 0].sum())) < 1e-13 * float(mesh.vol * g.abs().sum())
+
+
+def test_br2_and_ip_fluxes():
+    """On uniform cells BR2 with eta = 2 chi_e and SIPG with C = chi_e coincide with CDG2
+    (all three penalise -c (k+1)^2 A Delta / h); other penalties keep the diffusion form
+    symmetric and negative semi-definite with the constants as kernel."""
+    p = I.default_params()
+    for dim, k in ((2, 2), (3, 1)):
+        cdg = O.Mesh(dim, (4, 2, 2), (1.0, 0.2, 0.2), (1, 0, 1), k)
+        U = smooth_state(cdg, seed=6)
+        ref = O.apply(cdg, U, p)
+        br2 = O.Mesh(dim, (4, 2, 2), (1.0, 0.2, 0.2), (1, 0, 1), k, flux="br2", penalty=2 * cdg.chi_e)
+        ip = O.Mesh(dim, (4, 2, 2), (1.0, 0.2, 0.2), (1, 0, 1), k, flux="sipg", penalty=cdg.chi_e)
+        assert torch.allclose(O.apply(br2, U, p), ref, rtol=1e-12, atol=1e-12 * float(ref.abs().max()))
+        assert torch.allclose(O.apply(ip, U, p), ref, rtol=1e-12, atol=1e-12 * float(ref.abs().max()))
+    q = no_reaction_params(chemotaxis=False)
+    for flux, pen in (("br2", 5.0), ("sipg", 3.0)):
+        mesh = O.Mesh(2, (4, 3), (1.0, 0.2), (1, 0), 1, flux=flux, penalty=pen)
+        n = mesh.E * 6 * mesh.nb
+        B = mesh.vol * torch.func.jacfwd(lambda V: O.apply(mesh, V, q))(torch.zeros(mesh.E, 6, mesh.nb, dtype=F64)).reshape(n, n)
+        assert torch.allclose(B, B.T, atol=1e-12 * float(B.abs().max()))
+        ev = torch.linalg.eigvalsh(0.5 * (B + B.T))
+        assert float(ev.max()) < 1e-10 * float(ev.abs().max())
+        assert int((ev.abs() < 1e-9 * float(ev.abs().max())).sum()) == 6

@@ -185,6 +185,8 @@ int cdg2_mesh_create(const cdg2_mesh_desc* d, cdg2_mesh** out) {
     g.g1in[1] = d->gamma1_in[1];
     g.E = E;
     tabulate(d->k, d->k + 2, m->tab);
+    m->tp64 = make_tabp<double>(m->tab, g);
+    m->tp32 = make_tabp<float>(m->tab, g);
     m->nb = nb;
     m->ndof = E * NS * nb;
     *out = m;

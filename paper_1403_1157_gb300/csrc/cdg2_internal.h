@@ -24,6 +24,22 @@ struct Tab1D {
     double d[2][MAXK + 1];      // psi'_a(0), psi'_a(1)
 };
 
+// The 1D tables in a kernel's precision, with the mesh spacing and Gauss
+// weights folded in per axis j (derivatives divided by h_j; weighted test
+// tables).  Built once per mesh on the host, passed to the operator kernels
+// by value, so a kernel's set-up is a plain copy.
+template <typename T>
+struct TabP {
+    T B[MAXQ][MAXK + 1];          // psi_a(xi_q)
+    T Bw[MAXQ][MAXK + 1];         // w_q psi_a(xi_q)
+    T Dh[3][MAXQ][MAXK + 1];      // psi'_a(xi_q) / h_j
+    T Dwh[3][MAXQ][MAXK + 1];     // w_q psi'_a(xi_q) / h_j
+    T w[MAXQ];
+    T xi[MAXQ];
+    T e[2][MAXK + 1];             // psi_a(0), psi_a(1)
+    T dh[3][2][MAXK + 1];         // psi'_a(0) / h_j, psi'_a(1) / h_j
+};
+
 // Uniform Cartesian geometry (Sec. 3.1 tessellation, read as boxes).
 struct Geo {
     int dim, k;
@@ -50,11 +66,36 @@ struct Coef {
 
 Coef make_coef(const cdg2_params& p);
 
+template <typename T>
+TabP<T> make_tabp(const Tab1D& t, const Geo& g) {
+    TabP<T> p{};
+    for (int q = 0; q < MAXQ; ++q) {
+        for (int a = 0; a <= MAXK; ++a) {
+            p.B[q][a] = (T)t.B[q][a];
+            p.Bw[q][a] = (T)(t.w[q] * t.B[q][a]);
+            for (int j = 0; j < 3; ++j) {
+                p.Dh[j][q][a] = (T)(t.D[q][a] / g.h[j]);
+                p.Dwh[j][q][a] = (T)(t.w[q] * t.D[q][a] / g.h[j]);
+            }
+        }
+        p.w[q] = (T)t.w[q];
+        p.xi[q] = (T)t.xi[q];
+    }
+    for (int f = 0; f < 2; ++f)
+        for (int a = 0; a <= MAXK; ++a) {
+            p.e[f][a] = (T)t.e[f][a];
+            for (int j = 0; j < 3; ++j) p.dh[j][f][a] = (T)(t.d[f][a] / g.h[j]);
+        }
+    return p;
+}
+
 }  // namespace cdg2
 
 struct cdg2_mesh {
     cdg2::Geo geo;
     cdg2::Tab1D tab;
+    cdg2::TabP<double> tp64;   // tables of the FP64 and FP32 operator kernels
+    cdg2::TabP<float> tp32;
     int nb;            // basis per species per element
     long long ndof;
     // Face buffer of the face-once apply/JVP path (allocated by the first

@@ -21,32 +21,42 @@ struct Shape {
     static constexpr int NQT = ipow(NQ1, D - 1);      // face points
 };
 
-// 1D tables in shared memory in the kernel's precision.
+// 1D tables in shared memory in the kernel's precision, at the kernel's
+// degree: a copy of the kernel's TabP argument (1/h_j and the Gauss weights
+// already folded in, so the pointwise code does no scaling multiplications).
 template <int K, typename T>
 struct STab {
-    T B[K + 2][K + 1];   // psi_a(xi_q)
-    T D[K + 2][K + 1];   // psi'_a(xi_q)
+    T B[K + 2][K + 1];       // psi_a(xi_q)
+    T Bw[K + 2][K + 1];      // w_q psi_a(xi_q)
+    T Dh[3][K + 2][K + 1];   // psi'_a(xi_q) / h_j
+    T Dwh[3][K + 2][K + 1];  // w_q psi'_a(xi_q) / h_j
     T w[K + 2];
     T xi[K + 2];
-    T e[2][K + 1];       // psi_a(0), psi_a(1)
-    T d[2][K + 1];       // psi'_a(0), psi'_a(1)
+    T e[2][K + 1];           // psi_a(0), psi_a(1)
+    T dh[3][2][K + 1];       // psi'_a(0) / h_j, psi'_a(1) / h_j
 };
 
 template <int K, typename T>
-__device__ __forceinline__ void load_tab(STab<K, T>& s, const Tab1D& t) {
+__device__ __forceinline__ void load_tab(STab<K, T>& s, const TabP<T>& t) {
     for (int i = threadIdx.x; i < (K + 2) * (K + 1); i += blockDim.x) {
-        int q = i / (K + 1), a = i % (K + 1);
-        s.B[q][a] = (T)t.B[q][a];
-        s.D[q][a] = (T)t.D[q][a];
+        const int q = i / (K + 1), a = i % (K + 1);
+        s.B[q][a] = t.B[q][a];
+        s.Bw[q][a] = t.Bw[q][a];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            s.Dh[j][q][a] = t.Dh[j][q][a];
+            s.Dwh[j][q][a] = t.Dwh[j][q][a];
+        }
     }
     for (int i = threadIdx.x; i < K + 2; i += blockDim.x) {
-        s.w[i] = (T)t.w[i];
-        s.xi[i] = (T)t.xi[i];
+        s.w[i] = t.w[i];
+        s.xi[i] = t.xi[i];
     }
     for (int i = threadIdx.x; i < 2 * (K + 1); i += blockDim.x) {
-        int f = i / (K + 1), a = i % (K + 1);
-        s.e[f][a] = (T)t.e[f][a];
-        s.d[f][a] = (T)t.d[f][a];
+        const int f = i / (K + 1), a = i % (K + 1);
+        s.e[f][a] = t.e[f][a];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) s.dh[j][f][a] = t.dh[j][f][a];
     }
 }
 
@@ -61,35 +71,76 @@ __device__ __forceinline__ float qdiv<float>(float a, float b) {
     return __fdividef(a, b);
 }
 
+// Reciprocals r_i = 1 / x_i of N values.  FP64: simultaneous inversion
+// (Montgomery's trick: prefix products, one division, 3(N-1) multiplications
+// instead of N divisions, a few ulp), with the N divisions when the product of
+// all values is outside [1e-250, 1e250] or not finite.  FP32: qdiv per value.
+template <int N, typename T>
+__device__ __forceinline__ void recips(const T* x, T* r) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) r[i] = qdiv<T>(T(1), x[i]);
+    } else {
+        T p[N];
+        p[0] = x[0];
+#pragma unroll
+        for (int i = 1; i < N; ++i) p[i] = p[i - 1] * x[i];
+        const T a = fabs(p[N - 1]);
+        if (a > T(1e-250) && a < T(1e250)) {
+            T inv = T(1) / p[N - 1];
+#pragma unroll
+            for (int i = N - 1; i > 0; --i) {
+                r[i] = inv * p[i - 1];
+                inv = inv * x[i];
+            }
+            r[0] = inv;
+        } else {
+#pragma unroll
+            for (int i = 0; i < N; ++i) r[i] = T(1) / x[i];
+        }
+    }
+}
+
 template <typename T>
 struct Ident {
     using type = T;
 };
 
 // One sum-factorisation pass over nt tensors stored back to back.
-// Input tensors have extents (I0, I1, I2) (x fastest); axis AX (extent NI)
-// is replaced by NO in the output:
+// One 1D pass of sum factorisation.  Input tensors have extents (I0, I1, I2)
+// (x fastest); axis AX (extent NI) is replaced by NO in the output:
 //     out[t][..o..] = sum_i M1(o,i) in1[t][..i..]  (+ M2(o,i) in2[t][..i..])
-// M(o,i) = M[o][i] (TR = false) or M[i][o] (TR = true), row length LD.
-// One thread computes one whole line along AX: its index arithmetic is done
-// once per line, the 1D matrices are held in registers, and each input is
-// loaded once for NO outputs (shared-memory traffic, not FMA issue, limits
-// these passes).  The sums run over i in increasing order.
-template <int AX, int I0, int I1, int I2, int NO, bool TR, int LD, bool TWO, typename T>
-__device__ __forceinline__ void sf_pass(const T* __restrict__ in1, const T* __restrict__ M1,
-                                        const typename Ident<T>::type* __restrict__ in2,
-                                        const typename Ident<T>::type* __restrict__ M2, int in_stride,
-                                        T* __restrict__ out, int out_stride, int nt) {
+// with M(o,i) = M[o][i] (TR = false: points from modes) or M[i][o] (TR = true:
+// modes from points), M stored [point][mode] with row length LD.  One thread
+// computes one whole line along AX: its index arithmetic is done once per
+// line, the 1D matrices are held in registers, each input is loaded once.
+// The matrices have the mirror symmetry of Legendre modes at a symmetric
+// Gauss rule, M(NQ-1-q, a) = P (-1)^a M(q, a), P = +1 for values (B, Bw) and
+// -1 for derivatives (Dh, Dwh), and only rows q < ceil(NQ/2) are read.
+// Forward: out(q) and out(NQ-1-q) are E +- O with E, O the sums over the even
+// and odd modes.  Transposed: the inputs are paired as x(q) +- x(NQ-1-q) and
+// each mode takes the pair combination of its parity.  For k = 3 this is 14
+// operations per line and matrix instead of 20.
+template <int AX, int I0, int I1, int I2, int NO, bool TR, int LD, bool TWO, int P1, int P2, typename T>
+__device__ __forceinline__ void sf_sym(const T* __restrict__ in1, const T* __restrict__ M1,
+                                       const typename Ident<T>::type* __restrict__ in2,
+                                       const typename Ident<T>::type* __restrict__ M2, int in_stride,
+                                       T* __restrict__ out, int out_stride, int nt) {
     constexpr int NI = AX == 0 ? I0 : (AX == 1 ? I1 : I2);
-    constexpr int NL = I0 * I1 * I2 / NI;                       // lines per tensor
-    constexpr int ST = AX == 0 ? 1 : (AX == 1 ? I0 : I0 * I1);  // stride along AX (input and output)
-    T m1[NO][NI], m2[TWO ? NO : 1][TWO ? NI : 1];
+    constexpr int NQ = TR ? NI : NO;   // points
+    constexpr int NM = TR ? NO : NI;   // modes
+    constexpr int H = NQ / 2;          // mirrored pairs (q, NQ-1-q), q < H
+    constexpr int MID = NQ % 2;        // a middle point q = H
+    static_assert(TR || !TWO, "two-matrix passes are transposed");
+    constexpr int NL = I0 * I1 * I2 / NI;
+    constexpr int ST = AX == 0 ? 1 : (AX == 1 ? I0 : I0 * I1);
+    T m1[H + MID][NM], m2[TWO ? H + MID : 1][TWO ? NM : 1];
 #pragma unroll
-    for (int o = 0; o < NO; ++o)
+    for (int q = 0; q < H + MID; ++q)
 #pragma unroll
-        for (int i = 0; i < NI; ++i) {
-            m1[o][i] = TR ? M1[i * LD + o] : M1[o * LD + i];
-            if constexpr (TWO) m2[o][i] = TR ? M2[i * LD + o] : M2[o * LD + i];
+        for (int a = 0; a < NM; ++a) {
+            m1[q][a] = M1[q * LD + a];
+            if constexpr (TWO) m2[q][a] = M2[q * LD + a];
         }
     const int total = nt * NL;
     for (int line = threadIdx.x; line < total; line += blockDim.x) {
@@ -108,25 +159,63 @@ __device__ __forceinline__ void sf_pass(const T* __restrict__ in1, const T* __re
             ob = r;
         }
         const T* s1 = in1 + tt * in_stride + ib;
-        T v1[NI], v2[TWO ? NI : 1];
-#pragma unroll
-        for (int i = 0; i < NI; ++i) v1[i] = s1[i * ST];
-        if constexpr (TWO) {
-            const T* s2 = in2 + tt * in_stride + ib;
-#pragma unroll
-            for (int i = 0; i < NI; ++i) v2[i] = s2[i * ST];
-        }
         T* d = out + tt * out_stride + ob;
+        if constexpr (!TR) {
+            T v[NM];
 #pragma unroll
-        for (int o = 0; o < NO; ++o) {
-            T acc = T(0);
+            for (int a = 0; a < NM; ++a) v[a] = s1[a * ST];
 #pragma unroll
-            for (int i = 0; i < NI; ++i) acc = fma(m1[o][i], v1[i], acc);
-            if constexpr (TWO) {
+            for (int q = 0; q < H; ++q) {
+                T ev = T(0), od = T(0);
 #pragma unroll
-                for (int i = 0; i < NI; ++i) acc = fma(m2[o][i], v2[i], acc);
+                for (int a = 0; a < NM; a += 2) ev = fma(m1[q][a], v[a], ev);
+#pragma unroll
+                for (int a = 1; a < NM; a += 2) od = fma(m1[q][a], v[a], od);
+                d[q * ST] = ev + od;
+                d[(NQ - 1 - q) * ST] = P1 > 0 ? ev - od : od - ev;
             }
-            d[o * ST] = acc;
+            if constexpr (MID) {
+                // the modes of the other parity vanish at the middle point
+                T acc = T(0);
+#pragma unroll
+                for (int a = P1 > 0 ? 0 : 1; a < NM; a += 2) acc = fma(m1[H][a], v[a], acc);
+                d[H * ST] = acc;
+            }
+        } else {
+            T sp1[H], sm1[H], mid1 = T(0), sp2[TWO ? H : 1], sm2[TWO ? H : 1], mid2 = T(0);
+#pragma unroll
+            for (int q = 0; q < H; ++q) {
+                const T x = s1[q * ST], y = s1[(NQ - 1 - q) * ST];
+                sp1[q] = x + y;
+                sm1[q] = x - y;
+            }
+            if constexpr (MID) mid1 = s1[H * ST];
+            if constexpr (TWO) {
+                const T* s2 = in2 + tt * in_stride + ib;
+#pragma unroll
+                for (int q = 0; q < H; ++q) {
+                    const T x = s2[q * ST], y = s2[(NQ - 1 - q) * ST];
+                    sp2[q] = x + y;
+                    sm2[q] = x - y;
+                }
+                if constexpr (MID) mid2 = s2[H * ST];
+            }
+#pragma unroll
+            for (int a = 0; a < NM; ++a) {
+                // mode a pairs with the sums when P (-1)^a = +1, else with the differences
+                const bool even1 = (P1 > 0) == (a % 2 == 0);
+                T acc = T(0);
+#pragma unroll
+                for (int q = 0; q < H; ++q) acc = fma(m1[q][a], even1 ? sp1[q] : sm1[q], acc);
+                if (MID && even1) acc = fma(m1[MID ? H : 0][a], mid1, acc);
+                if constexpr (TWO) {
+                    const bool even2 = (P2 > 0) == (a % 2 == 0);
+#pragma unroll
+                    for (int q = 0; q < H; ++q) acc = fma(m2[q][a], even2 ? sp2[q] : sm2[q], acc);
+                    if (MID && even2) acc = fma(m2[MID ? H : 0][a], mid2, acc);
+                }
+                d[a * ST] = acc;
+            }
         }
     }
 }

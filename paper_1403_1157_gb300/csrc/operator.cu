@@ -30,6 +30,8 @@
 // times sum_m psi_m(1)^2 = (k+1)^2 in the normal direction.
 #include <cstdio>
 
+#include <type_traits>
+
 #include "elem_common.cuh"
 
 namespace cdg2 {
@@ -89,6 +91,16 @@ constexpr int fields_of(int mode) { return mode == MODE_APPLY ? 1 : 2; }
 // Pointwise physics (Sec. 2)
 // ---------------------------------------------------------------------------
 
+// Denominators of the chemotactic sensitivities (Sec. 2) at one point:
+// kappa11(c1), kappa13(c3), kappa21(c1), kappa22(n1) = chi0_i / den_i.
+template <typename T>
+__device__ __forceinline__ void kappa_den(const CoefT<T>& c, const T u[NS], T* den) {
+    den[0] = u[3] + T(c.chith[0]);
+    den[1] = u[5] + T(c.chith[1]);
+    den[2] = u[3] + T(c.chith[2]);
+    den[3] = u[0] + T(c.chith[3]);
+}
+
 // Volume flux at one quadrature point (Eq. elementint): Phi_s = F_s(U, grad U)
 // - A_s grad U_s and S(U) (Reading: the c1 row of S follows Eq. (1),
 // -alpha1 n1 c1 - alpha2 n2 c1 + f1 n3).  death1 = 0 drops the n1 death term
@@ -96,10 +108,11 @@ constexpr int fields_of(int mode) { return mode == MODE_APPLY ? 1 : 2; }
 template <int D, typename T>
 __device__ __forceinline__ void volume_point(const CoefT<T>& c, const T u[NS], const T g[NS][D], T Phi[NS][D],
                                              T S[NS]) {
-    const T k11 = qdiv<T>(T(c.chi0[0]), u[3] + T(c.chith[0]));
-    const T k13 = qdiv<T>(T(c.chi0[1]), u[5] + T(c.chith[1]));
-    const T k21 = qdiv<T>(T(c.chi0[2]), u[3] + T(c.chith[2]));
-    const T k22 = qdiv<T>(T(c.chi0[3]), u[0] + T(c.chith[3]));
+    T den[4], r[4];
+    kappa_den<T>(c, u, den);
+    recips<4, T>(den, r);
+    const T k11 = T(c.chi0[0]) * r[0], k13 = T(c.chi0[1]) * r[1];
+    const T k21 = T(c.chi0[2]) * r[2], k22 = T(c.chi0[3]) * r[3];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const T v1 = k11 * g[3][j] + k13 * g[5][j];
@@ -126,10 +139,10 @@ template <int D, typename T>
 __device__ __forceinline__ void volume_point_lin(const CoefT<T>& c, const T u[NS], const T g[NS][D], const T du[NS],
                                                  const T dg[NS][D], bool has_dth, T dPhi[NS][D],
                                                  T dS[NS]) {
-    const T r11 = qdiv<T>(T(1), u[3] + T(c.chith[0]));
-    const T r13 = qdiv<T>(T(1), u[5] + T(c.chith[1]));
-    const T r21 = qdiv<T>(T(1), u[3] + T(c.chith[2]));
-    const T r22 = qdiv<T>(T(1), u[0] + T(c.chith[3]));
+    T den[4], r[4];
+    kappa_den<T>(c, u, den);
+    recips<4, T>(den, r);
+    const T r11 = r[0], r13 = r[1], r21 = r[2], r22 = r[3];
     const T k11 = T(c.chi0[0]) * r11, k13 = T(c.chi0[1]) * r13;
     const T k21 = T(c.chi0[2]) * r21, k22 = T(c.chi0[3]) * r22;
     const T dk11 = -k11 * r11 * du[3], dk13 = -k13 * r13 * du[5];
@@ -173,15 +186,19 @@ template <typename T>
 __device__ __forceinline__ void face_point(const CoefT<T>& c, T pen, const T uM[NS], const T dM[NS], const T uP[NS],
                                            const T dP[NS], const T del[NS], T sig[NS], T tau[NS]) {
     T Fh[2];
+    T den[8], r[8];   // K^- side, then K^+ side
+    kappa_den<T>(c, uM, den);
+    kappa_den<T>(c, uP, den + 4);
+    recips<8, T>(den, r);
     {
-        const T vM = qdiv<T>(T(c.chi0[0]), uM[3] + T(c.chith[0])) * dM[3] + qdiv<T>(T(c.chi0[1]), uM[5] + T(c.chith[1])) * dM[5];
-        const T vP = qdiv<T>(T(c.chi0[0]), uP[3] + T(c.chith[0])) * dP[3] + qdiv<T>(T(c.chi0[1]), uP[5] + T(c.chith[1])) * dP[5];
+        const T vM = T(c.chi0[0]) * r[0] * dM[3] + T(c.chi0[1]) * r[1] * dM[5];
+        const T vP = T(c.chi0[0]) * r[4] * dP[3] + T(c.chi0[1]) * r[5] * dP[5];
         const T lam = fmax(fabs(vM), fabs(vP));
         Fh[0] = T(0.5) * (uM[0] * vM + uP[0] * vP) + T(0.5) * lam * del[0];
     }
     {
-        const T vM = qdiv<T>(T(c.chi0[2]), uM[3] + T(c.chith[2])) * dM[3] - qdiv<T>(T(c.chi0[3]), uM[0] + T(c.chith[3])) * dM[0];
-        const T vP = qdiv<T>(T(c.chi0[2]), uP[3] + T(c.chith[2])) * dP[3] - qdiv<T>(T(c.chi0[3]), uP[0] + T(c.chith[3])) * dP[0];
+        const T vM = T(c.chi0[2]) * r[2] * dM[3] - T(c.chi0[3]) * r[3] * dM[0];
+        const T vP = T(c.chi0[2]) * r[6] * dP[3] - T(c.chi0[3]) * r[7] * dP[0];
         const T lam = fmax(fabs(vM), fabs(vP));
         Fh[1] = T(0.5) * (uM[1] * vM + uP[1] * vP) + T(0.5) * lam * del[1];
     }
@@ -201,17 +218,18 @@ __device__ __forceinline__ T sgn0(T x) {
 }
 
 // One side's chemotactic normal velocity of species 0 or 1 and its derivative:
-// v_0 = kappa11(c1) d_n c1 + kappa13(c3) d_n c3,  v_1 = kappa21(c1) d_n c1 - kappa22(n1) d_n n1.
+// v_0 = kappa11(c1) d_n c1 + kappa13(c3) d_n c3,  v_1 = kappa21(c1) d_n c1 - kappa22(n1) d_n n1,
+// with rk the reciprocals of that side's kappa_den.
 template <typename T>
-__device__ __forceinline__ void velocity_lin(const CoefT<T>& c, int sp, const T u[NS], const T dn[NS], const T du[NS],
+__device__ __forceinline__ void velocity_lin(const CoefT<T>& c, int sp, const T* rk, const T dn[NS], const T du[NS],
                                              const T ddn[NS], T& v, T& dv) {
     if (sp == 0) {
-        const T r1 = qdiv<T>(T(1), u[3] + T(c.chith[0])), r3 = qdiv<T>(T(1), u[5] + T(c.chith[1]));
+        const T r1 = rk[0], r3 = rk[1];
         const T k1 = T(c.chi0[0]) * r1, k3 = T(c.chi0[1]) * r3;
         v = k1 * dn[3] + k3 * dn[5];
         dv = -k1 * r1 * du[3] * dn[3] + k1 * ddn[3] - k3 * r3 * du[5] * dn[5] + k3 * ddn[5];
     } else {
-        const T r1 = qdiv<T>(T(1), u[3] + T(c.chith[2])), r0 = qdiv<T>(T(1), u[0] + T(c.chith[3]));
+        const T r1 = rk[2], r0 = rk[3];
         const T k1 = T(c.chi0[2]) * r1, k0 = T(c.chi0[3]) * r0;
         v = k1 * dn[3] - k0 * dn[0];
         dv = -k1 * r1 * du[3] * dn[3] + k1 * ddn[3] + k0 * r0 * du[0] * dn[0] - k0 * ddn[0];
@@ -226,11 +244,15 @@ __device__ __forceinline__ void face_point_lin(const CoefT<T>& c, T pen, const T
                                                const T duP[NS], const T ddP[NS], const T ddel[NS], T dsig[NS],
                                                T dtau[NS]) {
     T dFh[2];
+    T den[8], r[8];   // K^- side, then K^+ side
+    kappa_den<T>(c, uM, den);
+    kappa_den<T>(c, uP, den + 4);
+    recips<8, T>(den, r);
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
         T vM, dvM, vP, dvP;
-        velocity_lin<T>(c, sp, uM, dM, duM, ddM, vM, dvM);
-        velocity_lin<T>(c, sp, uP, dP, duP, ddP, vP, dvP);
+        velocity_lin<T>(c, sp, r, dM, duM, ddM, vM, dvM);
+        velocity_lin<T>(c, sp, r + 4, dP, duP, ddP, vP, dvP);
         const T aM = fabs(vM), aP = fabs(vP);
         const bool takeM = aM >= aP;
         const T lam = takeM ? aM : aP;
@@ -256,10 +278,10 @@ __device__ __forceinline__ void face_point_lin(const CoefT<T>& c, T pen, const T
 template <int D, typename T>
 __device__ __forceinline__ void volume_point_adj(const CoefT<T>& c, const T u[NS], const T g[NS][D], const T sb[NS],
                                                  const T gb[NS][D], T ub[NS], T Gb[NS][D], T th[8]) {
-    const T r11 = qdiv<T>(T(1), u[3] + T(c.chith[0]));
-    const T r13 = qdiv<T>(T(1), u[5] + T(c.chith[1]));
-    const T r21 = qdiv<T>(T(1), u[3] + T(c.chith[2]));
-    const T r22 = qdiv<T>(T(1), u[0] + T(c.chith[3]));
+    T den[4], r[4];
+    kappa_den<T>(c, u, den);
+    recips<4, T>(den, r);
+    const T r11 = r[0], r13 = r[1], r21 = r[2], r22 = r[3];
     const T k11 = T(c.chi0[0]) * r11, k13 = T(c.chi0[1]) * r13;
     const T k21 = T(c.chi0[2]) * r21, k22 = T(c.chi0[3]) * r22;
 #pragma unroll
@@ -319,12 +341,17 @@ __device__ __forceinline__ void face_point_adj(const CoefT<T>& c, T pen, bool ow
         ub[s] = sX * T(c.A[s]) * (T(0.5) * tb[s] - pen * sb[s]);
         db[s] = T(0.5) * T(c.A[s]) * sb[s];
     }
+    T den[8], r[8];   // K^- side, then K^+ side
+    kappa_den<T>(c, uM, den);
+    kappa_den<T>(c, uP, den + 4);
+    recips<8, T>(den, r);
+    const T* rX = ownM ? r : r + 4;
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
         T vM, vP, dummy;
         const T zero[NS] = {0, 0, 0, 0, 0, 0};
-        velocity_lin<T>(c, sp, uM, dM, zero, zero, vM, dummy);
-        velocity_lin<T>(c, sp, uP, dP, zero, zero, vP, dummy);
+        velocity_lin<T>(c, sp, r, dM, zero, zero, vM, dummy);
+        velocity_lin<T>(c, sp, r + 4, dP, zero, zero, vP, dummy);
         const bool takeM = fabs(vM) >= fabs(vP);
         const T lam = takeM ? fabs(vM) : fabs(vP);
         const T vX = ownM ? vM : vP;
@@ -333,14 +360,14 @@ __device__ __forceinline__ void face_point_adj(const CoefT<T>& c, T pen, bool ow
         ub[sp] += Fb * (T(0.5) * vX + T(0.5) * lam * sX);
         const T vb = Fb * (T(0.5) * uX[sp] + (fromX ? T(0.5) * del[sp] * sgn0(vX) : T(0)));
         if (sp == 0) {
-            const T r1 = qdiv<T>(T(1), uX[3] + T(c.chith[0])), r3 = qdiv<T>(T(1), uX[5] + T(c.chith[1]));
+            const T r1 = rX[0], r3 = rX[1];
             const T k1 = T(c.chi0[0]) * r1, k3 = T(c.chi0[1]) * r3;
             ub[3] += vb * (-k1 * r1 * dX[3]);
             ub[5] += vb * (-k3 * r3 * dX[5]);
             db[3] += vb * k1;
             db[5] += vb * k3;
         } else {
-            const T r1 = qdiv<T>(T(1), uX[3] + T(c.chith[2])), r0 = qdiv<T>(T(1), uX[0] + T(c.chith[3]));
+            const T r1 = rX[2], r0 = rX[3];
             const T k1 = T(c.chi0[2]) * r1, k0 = T(c.chi0[3]) * r0;
             ub[3] += vb * (-k1 * r1 * dX[3]);
             ub[0] += vb * (k0 * r0 * dX[0]);
@@ -414,7 +441,7 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
         for (int m = 0; m < NB1; ++m) {
             const T v = own[coef_index<D, K, A>(m, b0, b1)];
             uo = fma(tb.e[f][m], v, uo);
-            dO = fma(tb.d[f][m], v, dO);
+            dO = fma(tb.dh[A][f][m], v, dO);
         }
         const long long nb = nbr[e][f];
         if (nb >= 0) {
@@ -438,25 +465,25 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
                 del = fma(-tb.e[0][m], up[m], del);
             }
 #pragma unroll
-            for (int m = 0; m < NB1; ++m) dn = fma(tb.d[1 - f][m], nbv[m], dn);
+            for (int m = 0; m < NB1; ++m) dn = fma(tb.dh[A][1 - f][m], nbv[m], dn);
         }
         T* o = FC + (((fi * EPB + e) * 2 + f) * 4) * NS * NBT + s * NBT + t;
         o[0 * NS * NBT] = uo;
         o[1 * NS * NBT] = del;
-        o[2 * NS * NBT] = dO * invh;
-        o[3 * NS * NBT] = dn * invh;
+        o[2 * NS * NBT] = dO;
+        o[3 * NS * NBT] = dn;
     }
     __syncthreads();
 
     // tangential interpolation to the face points
     if constexpr (D == 2) {
-        sf_pass<0, NB1, 1, 1, NQ1, false, K + 1, false>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FP, NQT,
+        sf_sym<0, NB1, 1, 1, NQ1, false, K + 1, false, 1, 1>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FP, NQT,
                                                          F * EPB * 2 * 4 * NS);
     } else {
-        sf_pass<0, NB1, NB1, 1, NQ1, false, K + 1, false>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT, NQ1 * NB1,
+        sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT, NQ1 * NB1,
                                                            F * EPB * 2 * 4 * NS);
         __syncthreads();
-        sf_pass<1, NQ1, NB1, 1, NQ1, false, K + 1, false>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, FP, NQT,
+        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, FP, NQT,
                                                            F * EPB * 2 * 4 * NS);
     }
     __syncthreads();
@@ -481,7 +508,8 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
         const int p0 = p % NQ1, p1 = p / NQ1;
         T wp = tb.w[p0];
         if constexpr (D == 3) wp *= tb.w[p1];
-        const T Wp = wp * c.vol * invh;
+        // forward modes: the residual is accumulated divided by |K| (see the kernel's store)
+        const T Wp = MODE == MODE_VJP ? wp * c.vol * invh : wp * invh;
         const long long nb = nbr[e][f];
         if (nb >= 0) {
             T uN[NS];   // neighbour trace recovered from the jump
@@ -568,13 +596,13 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
 
     // tangential test against the own basis
     if constexpr (D == 2) {
-        sf_pass<0, NQ1, 1, 1, NB1, true, K + 1, false>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS, NBT,
+        sf_sym<0, NQ1, 1, 1, NB1, true, K + 1, false, 1, 1>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS, NBT,
                                                         EPB * 2 * 2 * NS);
     } else {
-        sf_pass<0, NQ1, NQ1, 1, NB1, true, K + 1, false>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1, NB1 * NQ1,
+        sf_sym<0, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1, NB1 * NQ1,
                                                           EPB * 2 * 2 * NS);
         __syncthreads();
-        sf_pass<1, NB1, NQ1, 1, NB1, true, K + 1, false>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1, TS, NBT,
+        sf_sym<1, NB1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1, TS, NBT,
                                                           EPB * 2 * 2 * NS);
     }
     __syncthreads();
@@ -605,7 +633,7 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
         for (int f = 0; f < 2; ++f) {
             const T* ts = TS + ((e * 2 + f) * 2) * NS * NBT + s * NBT + t;
             acc = fma(tb.e[f][m], ts[0], acc);
-            acc = fma(tb.d[f][m] * invh, ts[NS * NBT], acc);
+            acc = fma(tb.dh[A][f][m], ts[NS * NBT], acc);
         }
         sR[idx] = acc;
     }
@@ -659,7 +687,7 @@ __device__ __forceinline__ long long low_layer_index(const Geo& g, long long e, 
 }
 
 template <int D, int K, int MODE, int A, typename T>
-__global__ void __launch_bounds__(128) face_kernel(const Geo g, const Tab1D tab, const OpArgs<T> args) {
+__global__ void __launch_bounds__(128) face_kernel(const Geo g, const TabP<T> tab, const OpArgs<T> args) {
     constexpr int F = fields_of(MODE);
     using P = FacePlan<D, K, F>;
     using S = Shape<D, K>;
@@ -759,25 +787,25 @@ __global__ void __launch_bounds__(128) face_kernel(const Geo g, const Tab1D tab,
             }
 #pragma unroll
             for (int m = 0; m < NB1; ++m) {
-                dm = fma(tb.d[1][m], vm[m], dm);
-                dp = fma(tb.d[0][m], vp[m], dp);
+                dm = fma(tb.dh[A][1][m], vm[m], dm);
+                dp = fma(tb.dh[A][0][m], vp[m], dp);
             }
         }
         T* o = FC + ((fi * FPB + j) * 4) * NS * NBT + s * NBT + t;
         o[0 * NS * NBT] = uo;
         o[1 * NS * NBT] = del;
-        o[2 * NS * NBT] = dm * invh;
-        o[3 * NS * NBT] = dp * invh;
+        o[2 * NS * NBT] = dm;
+        o[3 * NS * NBT] = dp;
     }
     __syncthreads();
     if constexpr (D == 2) {
-        sf_pass<0, NB1, 1, 1, NQ1, false, K + 1, false>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FPt, NQT,
+        sf_sym<0, NB1, 1, 1, NQ1, false, K + 1, false, 1, 1>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FPt, NQT,
                                                          F * FPB * 4 * NS);
     } else {
-        sf_pass<0, NB1, NB1, 1, NQ1, false, K + 1, false>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT, NQ1 * NB1,
+        sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT, NQ1 * NB1,
                                                            F * FPB * 4 * NS);
         __syncthreads();
-        sf_pass<1, NQ1, NB1, 1, NQ1, false, K + 1, false>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, FPt, NQT,
+        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, FPt, NQT,
                                                            F * FPB * 4 * NS);
     }
     __syncthreads();
@@ -790,7 +818,7 @@ __global__ void __launch_bounds__(128) face_kernel(const Geo g, const Tab1D tab,
         const int p0 = p % NQ1, p1 = p / NQ1;
         T wp = tb.w[p0];
         if constexpr (D == 3) wp *= tb.w[p1];
-        const T Wp = wp * c.vol * invh;
+        const T Wp = wp * invh;   // the element kernel accumulates the residual divided by |K|
         T uo[NS], del[NS], dm[NS], dp[NS];
         {
             const T* base = FPt + (j * 4) * NS * NQT + p;
@@ -854,13 +882,13 @@ __global__ void __launch_bounds__(128) face_kernel(const Geo g, const Tab1D tab,
     }
     __syncthreads();
     if constexpr (D == 2) {
-        sf_pass<0, NQ1, 1, 1, NB1, true, K + 1, false>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS, NBT,
+        sf_sym<0, NQ1, 1, 1, NB1, true, K + 1, false, 1, 1>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS, NBT,
                                                         FPB * 2 * NS);
     } else {
-        sf_pass<0, NQ1, NQ1, 1, NB1, true, K + 1, false>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1, NB1 * NQ1,
+        sf_sym<0, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1, NB1 * NQ1,
                                                           FPB * 2 * NS);
         __syncthreads();
-        sf_pass<1, NB1, NQ1, 1, NB1, true, K + 1, false>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1, TS, NBT,
+        sf_sym<1, NB1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1, TS, NBT,
                                                           FPB * 2 * NS);
     }
     __syncthreads();
@@ -892,7 +920,6 @@ __device__ __forceinline__ void faces_expand(const Geo& g, const STab<K, T>& tb,
         fid[threadIdx.x][1] = hi;
     }
     __syncthreads();
-    const T invh = c.invh[A];
     for (int idx = threadIdx.x; idx < epb * NS * NB; idx += blockDim.x) {
         const int i = idx % NB;
         const int es = idx / NB;
@@ -918,16 +945,16 @@ __device__ __forceinline__ void faces_expand(const Geo& g, const STab<K, T>& tb,
         const T* hi = fb + fid[e][1] * 2 * NS * NBT + s * NBT + t;
         T acc = sR[idx];
         acc = fma(-tb.e[0][m], lo[0], acc);
-        acc = fma(tb.d[0][m] * invh, lo[NS * NBT], acc);
+        acc = fma(tb.dh[A][0][m], lo[NS * NBT], acc);
         acc = fma(tb.e[1][m], hi[0], acc);
-        acc = fma(tb.d[1][m] * invh, hi[NS * NBT], acc);
+        acc = fma(tb.dh[A][1][m], hi[NS * NBT], acc);
         sR[idx] = acc;
     }
     __syncthreads();
 }
 
 template <int D, int K, int MODE, typename T>
-__global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, const OpArgs<T> args) {
+__global__ void __launch_bounds__(128) op_kernel(const Geo g, const TabP<T> tab, const OpArgs<T> args) {
     constexpr int F = fields_of(MODE);
     using P = OpPlan<D, K, F>;
     using S = Shape<D, K>;
@@ -968,38 +995,37 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
     T* Q = Y + 3 * P::YSZ;   // D + 1 slots of F*EPB*NS tensors: u, g_0, .., g_{D-1}
     const int nt = F * EPB * NS;
     if constexpr (D == 2) {
-        sf_pass<0, NB1, NB1, 1, NQ1, false, K + 1, false>(sU, &tb.B[0][0], nullptr, nullptr, NB, X0, NQ1 * NB1, nt);
-        sf_pass<0, NB1, NB1, 1, NQ1, false, K + 1, false>(sU, &tb.D[0][0], nullptr, nullptr, NB, X1, NQ1 * NB1, nt);
+        sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(sU, &tb.B[0][0], nullptr, nullptr, NB, X0, NQ1 * NB1, nt);
+        sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, -1, 1>(sU, &tb.Dh[0][0][0], nullptr, nullptr, NB, X1, NQ1 * NB1, nt);
         __syncthreads();
-        sf_pass<1, NQ1, NB1, 1, NQ1, false, K + 1, false>(X0, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, Q, NQ, nt);
-        sf_pass<1, NQ1, NB1, 1, NQ1, false, K + 1, false>(X1, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1,
+        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(X0, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, Q, NQ, nt);
+        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(X1, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1,
                                                            Q + P::QSZ, NQ, nt);
-        sf_pass<1, NQ1, NB1, 1, NQ1, false, K + 1, false>(X0, &tb.D[0][0], nullptr, nullptr, NQ1 * NB1,
+        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, -1, 1>(X0, &tb.Dh[1][0][0], nullptr, nullptr, NQ1 * NB1,
                                                            Q + 2 * P::QSZ, NQ, nt);
     } else {
         constexpr int XS = NQ1 * NB1 * NB1, YS = NQ1 * NQ1 * NB1;
-        sf_pass<0, NB1, NB1, NB1, NQ1, false, K + 1, false>(sU, &tb.B[0][0], nullptr, nullptr, NB, X0, XS, nt);
-        sf_pass<0, NB1, NB1, NB1, NQ1, false, K + 1, false>(sU, &tb.D[0][0], nullptr, nullptr, NB, X1, XS, nt);
+        sf_sym<0, NB1, NB1, NB1, NQ1, false, K + 1, false, 1, 1>(sU, &tb.B[0][0], nullptr, nullptr, NB, X0, XS, nt);
+        sf_sym<0, NB1, NB1, NB1, NQ1, false, K + 1, false, -1, 1>(sU, &tb.Dh[0][0][0], nullptr, nullptr, NB, X1, XS, nt);
         __syncthreads();
-        sf_pass<1, NQ1, NB1, NB1, NQ1, false, K + 1, false>(X0, &tb.B[0][0], nullptr, nullptr, XS, Y, YS, nt);
-        sf_pass<1, NQ1, NB1, NB1, NQ1, false, K + 1, false>(X1, &tb.B[0][0], nullptr, nullptr, XS, Y + P::YSZ, YS,
+        sf_sym<1, NQ1, NB1, NB1, NQ1, false, K + 1, false, 1, 1>(X0, &tb.B[0][0], nullptr, nullptr, XS, Y, YS, nt);
+        sf_sym<1, NQ1, NB1, NB1, NQ1, false, K + 1, false, 1, 1>(X1, &tb.B[0][0], nullptr, nullptr, XS, Y + P::YSZ, YS,
                                                              nt);
-        sf_pass<1, NQ1, NB1, NB1, NQ1, false, K + 1, false>(X0, &tb.D[0][0], nullptr, nullptr, XS,
+        sf_sym<1, NQ1, NB1, NB1, NQ1, false, K + 1, false, -1, 1>(X0, &tb.Dh[1][0][0], nullptr, nullptr, XS,
                                                              Y + 2 * P::YSZ, YS, nt);
         __syncthreads();
-        sf_pass<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false>(Y, &tb.B[0][0], nullptr, nullptr, YS, Q, NQ, nt);
-        sf_pass<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false>(Y + P::YSZ, &tb.B[0][0], nullptr, nullptr, YS,
+        sf_sym<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false, 1, 1>(Y, &tb.B[0][0], nullptr, nullptr, YS, Q, NQ, nt);
+        sf_sym<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false, 1, 1>(Y + P::YSZ, &tb.B[0][0], nullptr, nullptr, YS,
                                                              Q + P::QSZ, NQ, nt);
-        sf_pass<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false>(Y + 2 * P::YSZ, &tb.B[0][0], nullptr, nullptr, YS,
+        sf_sym<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false, 1, 1>(Y + 2 * P::YSZ, &tb.B[0][0], nullptr, nullptr, YS,
                                                              Q + 2 * P::QSZ, NQ, nt);
-        sf_pass<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false>(Y, &tb.D[0][0], nullptr, nullptr, YS, Q + 3 * P::QSZ,
+        sf_sym<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false, -1, 1>(Y, &tb.Dh[2][0][0], nullptr, nullptr, YS, Q + 3 * P::QSZ,
                                                              NQ, nt);
     }
     __syncthreads();
 
-    // ---- volume: pointwise fluxes, weighted by w_q |K| (and 1/h_j for gradients) ----
+    // ---- volume: pointwise fluxes (gradients are physical: 1/h_j is in the tables) ----
     // The result goes to the slots of the last input field (the only one tested).
-    const T invh[3] = {c.invh[0], c.invh[1], c.invh[2]};
     constexpr int OFF = (F - 1) * EPB * NS * NQ;
     for (int idx = threadIdx.x; idx < EPB * NQ; idx += blockDim.x) {
         const int q = idx % NQ, e = idx / NQ;
@@ -1008,7 +1034,7 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
         for (int s = 0; s < NS; ++s) {
             u[s] = Q[(e * NS + s) * NQ + q];
 #pragma unroll
-            for (int j = 0; j < D; ++j) gr[s][j] = Q[(j + 1) * P::QSZ + (e * NS + s) * NQ + q] * invh[j];
+            for (int j = 0; j < D; ++j) gr[s][j] = Q[(j + 1) * P::QSZ + (e * NS + s) * NQ + q];
         }
         const int q0 = q % NQ1, q1 = (q / NQ1) % NQ1, q2 = q / (NQ1 * NQ1);
         T wq = tb.w[q0] * tb.w[q1];
@@ -1022,7 +1048,7 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
             for (int s = 0; s < NS; ++s) {
                 du[s] = Q[OFF + (e * NS + s) * NQ + q];
 #pragma unroll
-                for (int j = 0; j < D; ++j) dg[s][j] = Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q] * invh[j];
+                for (int j = 0; j < D; ++j) dg[s][j] = Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q];
             }
             if constexpr (MODE == MODE_JVP) {
                 volume_point_lin<D, T>(c, u, gr, du, dg, args.has_dtheta != 0, Phi, Sr);
@@ -1041,7 +1067,7 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
                 for (int s = 0; s < NS; ++s) {
                     Q[OFF + (e * NS + s) * NQ + q] = Sr[s];
 #pragma unroll
-                    for (int j = 0; j < D; ++j) Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q] = Phi[s][j] * invh[j];
+                    for (int j = 0; j < D; ++j) Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q] = Phi[s][j];
                 }
                 continue;
             }
@@ -1060,9 +1086,9 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
         }
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            Q[OFF + (e * NS + s) * NQ + q] = Wq * Sr[s];
+            Q[OFF + (e * NS + s) * NQ + q] = Sr[s];   // weights and 1/h live in the test tables
 #pragma unroll
-            for (int j = 0; j < D; ++j) Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q] = Wq * Phi[s][j] * invh[j];
+            for (int j = 0; j < D; ++j) Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q] = Phi[s][j];
         }
     }
     __syncthreads();
@@ -1070,34 +1096,40 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
     // ---- volume: test with phi and grad phi (transposed sum factorisation) ----
     const int nto = EPB * NS;
     T* Qo = Q + OFF;
+    // forward modes: Gauss-weighted tables (the residual is accumulated divided by
+    // |K|); VJP: its cotangents already carry the weights, plain tables
+    const T* TB = MODE == MODE_VJP ? &tb.B[0][0] : &tb.Bw[0][0];
+    const T* TD0 = MODE == MODE_VJP ? &tb.Dh[0][0][0] : &tb.Dwh[0][0][0];
+    const T* TD1 = MODE == MODE_VJP ? &tb.Dh[1][0][0] : &tb.Dwh[1][0][0];
+    const T* TD2 = MODE == MODE_VJP ? &tb.Dh[2][0][0] : &tb.Dwh[2][0][0];
     if constexpr (D == 2) {
         // Y0 = B^T_y S' + D^T_y Phi_y',  Y1 = B^T_y Phi_x'
         T* Y0 = X0;
         T* Y1 = X1;
-        sf_pass<1, NQ1, NQ1, 1, NB1, true, K + 1, true>(Qo, &tb.B[0][0], Qo + 2 * P::QSZ, &tb.D[0][0], NQ, Y0,
+        sf_sym<1, NQ1, NQ1, 1, NB1, true, K + 1, true, 1, -1>(Qo, TB, Qo + 2 * P::QSZ, TD1, NQ, Y0,
                                                          NQ1 * NB1, nto);
-        sf_pass<1, NQ1, NQ1, 1, NB1, true, K + 1, false>(Qo + P::QSZ, &tb.B[0][0], nullptr, nullptr, NQ, Y1,
+        sf_sym<1, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(Qo + P::QSZ, TB, nullptr, nullptr, NQ, Y1,
                                                           NQ1 * NB1, nto);
         __syncthreads();
-        sf_pass<0, NQ1, NB1, 1, NB1, true, K + 1, true>(Y0, &tb.B[0][0], Y1, &tb.D[0][0], NQ1 * NB1, sR, NB, nto);
+        sf_sym<0, NQ1, NB1, 1, NB1, true, K + 1, true, 1, -1>(Y0, TB, Y1, TD0, NQ1 * NB1, sR, NB, nto);
     } else {
         constexpr int ZS = NQ1 * NQ1 * NB1, XS = NQ1 * NB1 * NB1;
         T* Z0 = Y;
         T* Z1 = Y + P::YSZ;
         T* Z2 = Y + 2 * P::YSZ;
-        sf_pass<2, NQ1, NQ1, NQ1, NB1, true, K + 1, true>(Qo, &tb.B[0][0], Qo + 3 * P::QSZ, &tb.D[0][0], NQ, Z0, ZS,
+        sf_sym<2, NQ1, NQ1, NQ1, NB1, true, K + 1, true, 1, -1>(Qo, TB, Qo + 3 * P::QSZ, TD2, NQ, Z0, ZS,
                                                            nto);
-        sf_pass<2, NQ1, NQ1, NQ1, NB1, true, K + 1, false>(Qo + 2 * P::QSZ, &tb.B[0][0], nullptr, nullptr, NQ, Z1,
+        sf_sym<2, NQ1, NQ1, NQ1, NB1, true, K + 1, false, 1, 1>(Qo + 2 * P::QSZ, TB, nullptr, nullptr, NQ, Z1,
                                                             ZS, nto);
-        sf_pass<2, NQ1, NQ1, NQ1, NB1, true, K + 1, false>(Qo + P::QSZ, &tb.B[0][0], nullptr, nullptr, NQ, Z2, ZS,
+        sf_sym<2, NQ1, NQ1, NQ1, NB1, true, K + 1, false, 1, 1>(Qo + P::QSZ, TB, nullptr, nullptr, NQ, Z2, ZS,
                                                             nto);
         __syncthreads();
         T* Y0 = X0;
         T* Y1 = X1;
-        sf_pass<1, NQ1, NQ1, NB1, NB1, true, K + 1, true>(Z0, &tb.B[0][0], Z1, &tb.D[0][0], ZS, Y0, XS, nto);
-        sf_pass<1, NQ1, NQ1, NB1, NB1, true, K + 1, false>(Z2, &tb.B[0][0], nullptr, nullptr, ZS, Y1, XS, nto);
+        sf_sym<1, NQ1, NQ1, NB1, NB1, true, K + 1, true, 1, -1>(Z0, TB, Z1, TD1, ZS, Y0, XS, nto);
+        sf_sym<1, NQ1, NQ1, NB1, NB1, true, K + 1, false, 1, 1>(Z2, TB, nullptr, nullptr, ZS, Y1, XS, nto);
         __syncthreads();
-        sf_pass<0, NQ1, NB1, NB1, NB1, true, K + 1, true>(Y0, &tb.B[0][0], Y1, &tb.D[0][0], XS, sR, NB, nto);
+        sf_sym<0, NQ1, NB1, NB1, NB1, true, K + 1, true, 1, -1>(Y0, TB, Y1, TD0, XS, sR, NB, nto);
     }
     __syncthreads();
 
@@ -1113,7 +1145,9 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const Tab1D tab, c
     }
 
     // ---- M^{-1} = I / |K| for the orthonormal basis; coalesced store ----
-    const T scale = (args.flags & CDG2_MINV) ? c.inv_vol : T(1);
+    // forward modes accumulate R / |K|; the VJP accumulates R itself
+    const T scale = MODE == MODE_VJP ? ((args.flags & CDG2_MINV) ? c.inv_vol : T(1))
+                                     : ((args.flags & CDG2_MINV) ? T(1) : c.vol);
     const T alphaT = T(args.alpha), betaT = T(args.beta);
     for (int i = threadIdx.x; i < P::UR; i += blockDim.x) {
         const long long ge = e0 + i / (NS * NB);
@@ -1158,6 +1192,12 @@ __global__ void __launch_bounds__(256) theta_reduce_kernel(const double* __restr
         __syncthreads();
     }
     if (threadIdx.x < 8) gtheta[threadIdx.x] = red[threadIdx.x][0];
+}
+
+template <typename T>
+static const TabP<T>& tab_of(const cdg2_mesh& m) {
+    if constexpr (std::is_same<T, double>::value) return m.tp64;
+    else return m.tp32;
 }
 
 template <int MODE>
@@ -1226,12 +1266,12 @@ static cudaError_t launch_one(const cdg2_mesh& m, const Coef& c, OpArgs<T> a, cu
                 if (ax < D) off += faces_of_axis(m.geo, ax) * per_face;
             }
             auto fgrid = [&](int ax) { return (unsigned)((faces_of_axis(m.geo, ax) + FPl::FPB - 1) / FPl::FPB); };
-            face_kernel<D, K, MODE, 0, T><<<fgrid(0), FPl::NT, fsmem, st>>>(m.geo, m.tab, a);
-            face_kernel<D, K, MODE, 1, T><<<fgrid(1), FPl::NT, fsmem, st>>>(m.geo, m.tab, a);
-            if constexpr (D == 3) face_kernel<D, K, MODE, 2, T><<<fgrid(2), FPl::NT, fsmem, st>>>(m.geo, m.tab, a);
+            face_kernel<D, K, MODE, 0, T><<<fgrid(0), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
+            face_kernel<D, K, MODE, 1, T><<<fgrid(1), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
+            if constexpr (D == 3) face_kernel<D, K, MODE, 2, T><<<fgrid(2), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
         }
     }
-    op_kernel<D, K, MODE, T><<<(unsigned)blocks, P::NT, smem, st>>>(m.geo, m.tab, a);
+    op_kernel<D, K, MODE, T><<<(unsigned)blocks, P::NT, smem, st>>>(m.geo, tab_of<T>(m), a);
     return cudaGetLastError();
 }
 

@@ -29,35 +29,51 @@ METRIC = "L_h apply GDOF/s FP64 vs mixed at stated error; VJP GDOF/s; % HBM roof
 def apply_flops_per_element(dim: int, k: int) -> int:
     """Floating-point operations per element of one FP64 apply (face-once path).
 
-    Counted from the kernels' loops (an FMA is 2 flops, a divide 1).  Element
-    kernel: sum-factorised interpolation of U and grad U to the (k+2)^d Gauss
-    points, the pointwise volume flux (33 + 34 d per point), the transposed
-    test passes, and per axis the normal expansion of its two faces' tested
-    fluxes.  Face kernel, one face per element and axis: normal contraction
-    (owning trace, jump, both normal derivatives), tangential interpolation
-    of 4 fields, the pointwise face flux (112 per point), tangential test of
-    2 fields.
+    Counted from the kernels' loops (an FMA is 2 flops; an add, multiply or
+    divide 1).  The 1D passes split even and odd modes (mirror symmetry of
+    the Legendre modes at the symmetric Gauss rule): a forward line (k+1
+    modes to k+2 points) costs H (2b + 2) + 2 m flops with H = q // 2 point
+    pairs and m the modes of the matrix's parity at the middle point; a
+    transposed line 2H + 2Hb + 2m, a two-matrix transposed line 4H + 4Hb + 2b.
+    Element kernel: interpolation of U and grad U, the pointwise volume flux
+    (43 + 34 d per point, the four sensitivities inverted together), the
+    transposed test passes, and per axis the normal expansion of its two
+    faces' tested fluxes.  Face kernel, one face per element and axis: normal
+    contraction (owning trace, jump, both normal derivatives), tangential
+    interpolation of 4 fields, the pointwise face flux (126 per point, eight
+    sensitivities inverted together), tangential test of 2 fields.
     """
     b, q, d, s = k + 1, k + 2, dim, 6
+    H, mid = q // 2, q % 2
+    npar = {1: (b + 1) // 2, -1: b // 2}   # modes of each parity
+
+    def fwd(par):
+        return H * (2 * b + 2) + mid * 2 * npar[par]
+
+    def tr(par):
+        return 2 * H + 2 * H * b + mid * 2 * npar[par]
+
+    tr2 = 4 * H + 4 * H * b + mid * 2 * b
     if d == 2:
-        interp = 2 * q * b * b + 3 * q * q * b
-        test = 3 * q * q * b + 2 * q * b * b
-        face = 4 * b ** 2 + 4 * q * b + 2 * q * b
+        interp = b * (fwd(1) + fwd(-1)) + q * (2 * fwd(1) + fwd(-1))
+        test = q * (tr2 + tr(1)) + b * tr2
+        tang = 4 * fwd(1) + 2 * tr(1)
     else:
-        interp = 2 * q * b ** 3 + 3 * q * q * b * b + 4 * q ** 3 * b
-        test = 4 * q ** 3 * b + 3 * q * q * b * b + 2 * q * b ** 3
-        face = 4 * b ** 3 + 4 * (q * b * b + q * q * b) + 2 * (b * q * q + b * b * q)
-    expand = 4 * b ** d
-    fma = s * (interp + test + d * (face + expand))
-    pointwise = q ** d * (33 + 34 * d) + d * q ** (d - 1) * 112
-    return 2 * fma + pointwise
+        interp = b * b * (fwd(1) + fwd(-1)) + q * b * (2 * fwd(1) + fwd(-1)) + q * q * (3 * fwd(1) + fwd(-1))
+        test = q * q * (tr2 + 2 * tr(1)) + q * b * (tr2 + tr(1)) + b * b * tr2
+        tang = 4 * (b * fwd(1) + q * fwd(1)) + 2 * (q * tr(1) + b * tr(1))
+    normal = b ** (d - 1) * (2 * (5 * b - 2) + 1)
+    expand = 8 * b ** d
+    per_species = interp + test + d * (normal + tang + expand)
+    pointwise = q ** d * (43 + 34 * d) + d * q ** (d - 1) * 126
+    return s * per_species + pointwise
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP64 apply (its face and
 # element kernels), from one ncu capture (profiles/), keyed by workload and
 # valid only for the kernel sources the counters were taken with (first 16 hex
 # of their sha256).
-NCU_TRAFFIC = {("2D 256x64 Q3 manufactured solution", "double"): (50657792, "ef09e5ba5f7f13d7")}
+NCU_TRAFFIC = {("2D 256x64 Q3 manufactured solution", "double"): (50643211, "10d8deda10165d5d")}
 KERNEL_SOURCES = ("paper_1403_1157_gb300/csrc/operator.cu", "paper_1403_1157_gb300/csrc/elem_common.cuh")
 
 
@@ -198,7 +214,7 @@ def measure_derivatives(G, torch, w, mesh, p, U, flush, steps):
     return out
 
 
-def measure_solve(G, torch, cfg: int, steps: int):
+def measure_solve(G, torch, cfg: int, steps: int, precond: int):
     """Implicit SDIRK steps to Newton relative residual 1e-10: FP64 Krylov vs FP32 Krylov + FP64 refinement."""
     import cdg2_inputs as I
     w = I.workload(cfg)
@@ -206,20 +222,20 @@ def measure_solve(G, torch, cfg: int, steps: int):
     U0, p = make_inputs(G, w, I, mesh)
     scheme = G.CDG2_SDIRK2 if w.k == 1 else G.CDG2_SDIRK3
     result = {"workload": w.name, "n_dof": w.n_dof, "dt": w.dt, "steps": steps, "scheme": f"SDIRK{scheme}",
-              "newton_rtol": 1e-10}
+              "newton_rtol": 1e-10, "precond": {1: "modal diagonal", 2: "element-block Jacobi"}.get(precond, "none")}
     finals = {}
     for mode, mixed, eta in (("fp64", False, 1e-3), ("mixed", True, 1e-4)):
         U = U0.clone()
         # one untimed step warms up the kernels and allocates the workspace
         G.cdg2_step(mesh, p, U.clone(), 0.0, w.dt, G.make_opts(scheme=scheme, mixed=mixed, newton_rtol=1e-10,
-                                                                 gmres_rtol=eta))
+                                                                 gmres_rtol=eta, precond=precond))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         newton = gm = 0
         worst = 0.0
         for i in range(steps):
             rc, st = G.cdg2_step(mesh, p, U, i * w.dt, w.dt, G.make_opts(scheme=scheme, mixed=mixed, newton_rtol=1e-10,
-                                                                          gmres_rtol=eta))
+                                                                          gmres_rtol=eta, precond=precond))
             newton += st["newton_iters"]
             gm += st["gmres_iters"]
             worst = max([worst] + [r / r0 for r, r0 in zip(st["residual"], st["residual0"]) if r0 > 0])
@@ -235,7 +251,7 @@ def measure_solve(G, torch, cfg: int, steps: int):
     return result
 
 
-def measure_gradient(G, torch, cfg: int, steps: int | None, mixed: bool):
+def measure_gradient(G, torch, cfg: int, steps: int | None, mixed: bool, precond: int):
     """Forward + checkpointed discrete-adjoint backward of J = int n3(T) w.r.t. (U0, theta)."""
     import numpy as np
 
@@ -248,7 +264,8 @@ def measure_gradient(G, torch, cfg: int, steps: int | None, mixed: bool):
     U0, p = make_inputs(G, w, I, mesh)
     theta = torch.tensor([p[n] for n in Adj.THETA_NAMES], dtype=torch.float64, device="cuda")
     scheme = G.CDG2_SDIRK2 if w.k == 1 else G.CDG2_SDIRK3
-    opts = G.make_opts(scheme=scheme, mixed=mixed, newton_rtol=1e-10, gmres_rtol=1e-4 if mixed else 1e-3)
+    opts = G.make_opts(scheme=scheme, mixed=mixed, newton_rtol=1e-10, gmres_rtol=1e-4 if mixed else 1e-3,
+                       precond=precond)
     vol = float(np.prod([e / c for e, c in zip(w.extent[: w.dim], w.cells[: w.dim])]))
     U = U0.clone().requires_grad_(True)
     th = theta.clone().requires_grad_(True)
@@ -262,7 +279,9 @@ def measure_gradient(G, torch, cfg: int, steps: int | None, mixed: bool):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     return {"workload": w.name, "n_dof": w.n_dof, "steps": nsteps, "checkpoint": cp, "dt": w.dt,
-            "precision": "mixed" if mixed else "fp64", "forward_s": t1 - t0, "backward_s": t2 - t1,
+            "precision": "mixed" if mixed else "fp64",
+            "precond": {1: "modal diagonal", 2: "element-block Jacobi"}.get(precond, "none"),
+            "forward_s": t1 - t0, "backward_s": t2 - t1,
             "functional": "int n3(T)", "dJ_dtheta": [float(v) for v in th.grad],
             "dJ_dU0_norm": float(U.grad.norm())}
 
@@ -345,6 +364,11 @@ def main():
     ap.add_argument("--grad-config", type=int, default=2, help="workload of the gradient-through-steps timing")
     ap.add_argument("--profile-solve", choices=["mixed", "fp64"], default=None,
                     help="run one implicit step of the solve workload and exit (for ncu launch lists)")
+    ap.add_argument("--precond", type=int, default=2, choices=[0, 1, 2],
+                    help="GMRES preconditioner of the solve timing (1: modal diagonal, 2: element blocks)")
+    ap.add_argument("--grad-precond", type=int, default=1, choices=[0, 1, 2],
+                    help="GMRES preconditioner of the gradient timing (its adjoint solves have smooth right-hand "
+                         "sides, where the modal diagonal needs fewer iterations)")
     ap.add_argument("--grad-steps", type=int, default=-1, help="steps of the gradient timing (-1: the workload's; 0: skip)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -363,8 +387,10 @@ def main():
         mixed = args.profile_solve == "mixed"
         scheme = G.CDG2_SDIRK2 if w.k == 1 else G.CDG2_SDIRK3
         rc, st = G.cdg2_step(mesh, p, U, 0.0, w.dt, G.make_opts(scheme=scheme, mixed=mixed, newton_rtol=1e-10,
-                                                                 gmres_rtol=1e-4 if mixed else 1e-3))
-        print(json.dumps({"profile_solve": args.profile_solve, "workload": w.name, "stats": st}))
+                                                                 gmres_rtol=1e-4 if mixed else 1e-3,
+                                                                 precond=args.precond))
+        print(json.dumps({"profile_solve": args.profile_solve, "precond": args.precond, "workload": w.name,
+                          "stats": st}))
         return
 
     import torch
@@ -455,10 +481,11 @@ def main():
            "d2h_bytes_per_step": nbytes}
 
     derivs = measure_derivatives(G, torch, w, mesh, p, U, flush, max(10, args.steps // 8))
-    solve = measure_solve(G, torch, args.solve_config, args.solve_steps) if args.solve_steps > 0 else None
+    solve = measure_solve(G, torch, args.solve_config, args.solve_steps, args.precond) if args.solve_steps > 0 else None
     grad = None
     if args.grad_steps != 0:
-        grad = measure_gradient(G, torch, args.grad_config, None if args.grad_steps < 0 else args.grad_steps, True)
+        grad = measure_gradient(G, torch, args.grad_config, None if args.grad_steps < 0 else args.grad_steps, True,
+                                args.grad_precond)
 
     if rank != 0:
         if world > 1:

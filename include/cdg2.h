@@ -131,7 +131,13 @@ typedef struct cdg2_params {
  *   P = 1 - dt a_ii A_s d_i of the diffusion part (for an orthonormal mode on
  *   a Cartesian cell the volume and consistency terms cancel on the
  *   diagonal, leaving the CDG2 penalty: d_i = -chi_e (k+1)^2 sum_j
- *   (psi_{a_j}(0)^2 + psi_{a_j}(1)^2) / h_j^2), applied inside the JVP. */
+ *   (psi_{a_j}(0)^2 + psi_{a_j}(1)^2) / h_j^2), applied inside the JVP;
+ *   2 = element-block Jacobi: P = the (element, species) diagonal blocks
+ *   I - dt a_ii A_s K_e of the diffusion part (cdg2_element_block), inverted
+ *   on the host once per call (a few distinct blocks per mesh) and applied
+ *   by a kernel before every JVP/VJP.  The preconditioner changes the
+ *   iteration count, not the converged result.  The adjoint uses the same
+ *   P (K_e is symmetric). */
 typedef struct cdg2_solver_opts {
     int scheme;
     int mixed;
@@ -283,6 +289,20 @@ int cdg2_project_mms(const cdg2_mesh* mesh, const cdg2_params* params, double t,
                      void* stream);
 
 /* Human-readable description of the last error on this thread. */
+/* The block that precond = 2 inverts, for element `elem` and species
+ * `species`: I - gdt A_s K_e (row-major n_basis x n_basis, host memory
+ * `out`), where K_e is the diagonal block of the diffusion part of
+ * M^{-1} L_h (Sec. 3.1 Eq. convDiscr with only the A terms: the volume
+ * stiffness and the element's own terms of the consistency, symmetry and
+ * penalty (CDG2: chi_e (k+1)^2 / h; BR2, SIPG: their constants) parts of
+ * its interior faces; boundary faces add nothing).  The paper defers
+ * assembled operators and preconditioners (Sec. 3.2); this block is the
+ * one piece of the assembled operator the solver uses.  Host-only (no
+ * device work); gdt may be any finite value.  Errors: INVALID_ARG (NULL,
+ * elem or species out of range). */
+int cdg2_element_block(const cdg2_mesh* mesh, const cdg2_params* params, double gdt, long long elem, int species,
+                       double* out);
+
 const char* cdg2_last_error(void);
 
 #ifdef __cplusplus

@@ -134,6 +134,8 @@ def load_library():
     lib.cdg2_project_gaussians.restype = i
     lib.cdg2_project_mms.argtypes = [vp, ctypes.POINTER(Params), d, vp, i, vp]
     lib.cdg2_project_mms.restype = i
+    lib.cdg2_element_block.argtypes = [vp, ctypes.POINTER(Params), d, ctypes.c_longlong, i, dp]
+    lib.cdg2_element_block.restype = i
     lib.cdg2_last_error.argtypes = []
     lib.cdg2_last_error.restype = ctypes.c_char_p
     _LIB = lib
@@ -277,6 +279,16 @@ def cdg2_project_mms(mesh: Mesh, params, t: float, out: torch.Tensor, flags: int
     _check(load_library().cdg2_project_mms(mesh.handle, ctypes.byref(p), float(t), _dev(out, mesh, dt, "out"),
                                            int(flags), _stream_ptr(stream)))
     return out
+
+
+def cdg2_element_block(mesh: Mesh, params, gdt: float, elem: int, species: int) -> torch.Tensor:
+    """The block I - gdt A_s K_e that precond = 2 inverts (host call), as an
+    (n_basis, n_basis) float64 CPU tensor."""
+    nb = mesh.n_basis
+    out = (ctypes.c_double * (nb * nb))()
+    p = _params(params)
+    _check(load_library().cdg2_element_block(mesh.handle, ctypes.byref(p), float(gdt), int(elem), int(species), out))
+    return torch.tensor(list(out), dtype=torch.float64).reshape(nb, nb)
 
 
 def _theta_ptr(dtheta):

@@ -1,0 +1,320 @@
+// Element-block-Jacobi preconditioner of the stage systems (I - gdt J) d = r
+// of the DIRK stages (Sec. 3.2 solves them by Newton-GMRES and leaves the
+// preconditioner open).  The block of element K and species s is the
+// diagonal block of I - gdt J for the diffusion part of M^{-1} L_h:
+//     P_Ks = I - gdt A_s K_K,   K_K = sum_j h_j^{-2} S_j^{tau_j} (x) I,
+// the Kronecker sum over the axes of a 1D matrix S^tau on [0,1] built from
+// the Legendre tables: the volume stiffness and the element's own terms of
+// the interior-face diffusion flux of Sec. 3.1 (Eq. convDiscr: consistency,
+// symmetry and the CDG2 penalty chi_e (k+1)^2 / h on the jump; BR2 and SIPG
+// use their own penalty constant).  Along axis j the element has both faces
+// (tau = 0), no low face (1, Gamma_1 or a no-flow wall), no high face (2),
+// neither (3), or one face with itself (4, a periodic axis of one cell).
+// On the orthonormal basis the tangential mass is the identity, so K_K
+// separates by axis.  Boundary faces add nothing: their data do not depend
+// on U (Eq. (3), H' = 0).  The chemotaxis and reaction parts are left out:
+// with them the blocks change per element and Newton iterate, without them
+// there are a few distinct blocks per mesh, and GMRES needs as many
+// iterations with either (both measured on small 2D meshes at dt = 1e-3, 1e-2).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "precond.h"
+
+namespace cdg2 {
+
+namespace {
+
+constexpr int NTAU = 5;
+
+int tau_of(const Geo& g, int j, long long i) {
+    if (g.periodic[j]) return g.n[j] == 1 ? 4 : 0;
+    if (g.n[j] == 1) return 3;
+    if (i == 0) return 1;
+    if (i == g.n[j] - 1) return 2;
+    return 0;
+}
+
+// S^tau[a][b] on the reference interval (multiply by h^-2): row a is the
+// test mode, column b the trial mode.
+void oned_matrix(const Tab1D& t, int k, double pc, int tau, double* S) {
+    const int nb1 = k + 1, nq = k + 2;
+    const bool low = tau == 0 || tau == 2, high = tau == 0 || tau == 1, self = tau == 4;
+    for (int a = 0; a < nb1; ++a)
+        for (int b = 0; b < nb1; ++b) {
+            double v = 0.0;
+            for (int q = 0; q < nq; ++q) v -= t.w[q] * t.D[q][a] * t.D[q][b];
+            const double e0a = t.e[0][a], e1a = t.e[1][a], d0a = t.d[0][a], d1a = t.d[1][a];
+            const double e0b = t.e[0][b], e1b = t.e[1][b], d0b = t.d[0][b], d1b = t.d[1][b];
+            if (high)   // K is K^-: sigma (phi^-) + tau (d_n phi^-), U^- = U_K
+                v += 0.5 * (e1a * d1b + d1a * e1b) - pc * e1a * e1b;
+            if (low)    // K is K^+: -sigma (phi^+) + tau (d_n phi^+), U^+ = U_K
+                v += -0.5 * (e0a * d0b + d0a * e0b) - pc * e0a * e0b;
+            if (self) { // one face with K on both sides: U^- = U^+ = U_K
+                const double sig = 0.5 * (d1b + d0b) - pc * (e1b - e0b);
+                const double tau_b = 0.5 * (e1b - e0b);
+                v += (e1a - e0a) * sig + (d1a + d0a) * tau_b;
+            }
+            S[a * nb1 + b] = v;
+        }
+}
+
+// Present tau values per axis and the type numbering.
+void type_layout(const Geo& g, BlockTable& bt, std::vector<int> taus[3]) {
+    int stride = 1;
+    for (int j = 0; j < 3; ++j) {
+        taus[j].clear();
+        for (int u = 0; u < NTAU; ++u) bt.slot[j][u] = 0;
+        if (j >= g.dim) {
+            taus[j].push_back(0);
+            bt.stride[j] = 0;
+            continue;
+        }
+        bool seen[NTAU] = {false, false, false, false, false};
+        for (long long i = 0; i < g.n[j]; ++i) seen[tau_of(g, j, i)] = true;
+        for (int u = 0; u < NTAU; ++u)
+            if (seen[u]) {
+                bt.slot[j][u] = (int)taus[j].size();
+                taus[j].push_back(u);
+            }
+        bt.stride[j] = stride;
+        stride *= (int)taus[j].size();
+    }
+    bt.n_types = stride;
+}
+
+// P = I - gdt A_s sum_j h_j^-2 S_j^{tau_j} (x) I on the element basis
+// (index a_0 + (k+1) (a_1 + (k+1) a_2)), row-major nb x nb.
+void element_block(const cdg2_mesh& m, double As, double gdt, const int tau[3], double* P) {
+    const Geo& g = m.geo;
+    const int k = g.k, nb1 = k + 1, nb = m.nb;
+    const double pc = g.pen_c * (k + 1) * (k + 1);
+    std::vector<double> S[3];
+    for (int j = 0; j < g.dim; ++j) {
+        S[j].resize((size_t)nb1 * nb1);
+        oned_matrix(m.tab, k, pc, tau[j], S[j].data());
+    }
+    for (int r = 0; r < nb; ++r)
+        for (int c = 0; c < nb; ++c) {
+            int ar[3] = {r % nb1, (r / nb1) % nb1, r / (nb1 * nb1)};
+            int ac[3] = {c % nb1, (c / nb1) % nb1, c / (nb1 * nb1)};
+            double kv = 0.0;
+            for (int j = 0; j < g.dim; ++j) {
+                bool other_equal = true;
+                for (int l = 0; l < g.dim; ++l)
+                    if (l != j && ar[l] != ac[l]) other_equal = false;
+                if (other_equal) kv += S[j][(size_t)ar[j] * nb1 + ac[j]] / (g.h[j] * g.h[j]);
+            }
+            P[(size_t)r * nb + c] = (r == c ? 1.0 : 0.0) - gdt * As * kv;
+        }
+}
+
+// Gauss-Jordan inverse with partial pivoting; false if singular.
+bool invert(int n, std::vector<double>& A, std::vector<double>& X) {
+    X.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) X[(size_t)i * n + i] = 1.0;
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (std::fabs(A[(size_t)r * n + col]) > std::fabs(A[(size_t)piv * n + col])) piv = r;
+        if (!(std::fabs(A[(size_t)piv * n + col]) > 0.0)) return false;
+        if (piv != col)
+            for (int c = 0; c < n; ++c) {
+                std::swap(A[(size_t)piv * n + c], A[(size_t)col * n + c]);
+                std::swap(X[(size_t)piv * n + c], X[(size_t)col * n + c]);
+            }
+        const double inv = 1.0 / A[(size_t)col * n + col];
+        for (int c = 0; c < n; ++c) {
+            A[(size_t)col * n + c] *= inv;
+            X[(size_t)col * n + c] *= inv;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            const double f = A[(size_t)r * n + col];
+            if (f == 0.0) continue;
+            for (int c = 0; c < n; ++c) {
+                A[(size_t)r * n + c] -= f * A[(size_t)col * n + c];
+                X[(size_t)r * n + c] -= f * X[(size_t)col * n + c];
+            }
+        }
+    }
+    return true;
+}
+
+struct ApplyArgs {
+    long long E;
+    int nb, dim;
+    int n[3], periodic[3];
+    int stride[3];
+    int slot[3][NTAU];
+};
+
+__device__ __forceinline__ int dev_tau(const ApplyArgs& a, int j, long long i) {
+    if (a.periodic[j]) return a.n[j] == 1 ? 4 : 0;
+    if (a.n[j] == 1) return 3;
+    if (i == 0) return 1;
+    if (i == a.n[j] - 1) return 2;
+    return 0;
+}
+
+// z = P^{-1} v for one species and a run of CH consecutive elements per CTA.
+// Thread (g, i), g < G = 128 / NB, owns output mode i of every G-th element
+// of the run and keeps row i of its element type's inverse block in
+// registers (reloaded only when the type changes along the run: at boundary
+// layers); the run's input slices are staged in shared memory.
+template <int NB, typename T>
+__global__ void __launch_bounds__(128) k_block_apply(const ApplyArgs a, const T* __restrict__ M,
+                                                     const T* __restrict__ v, T* __restrict__ z) {
+    constexpr int G = 128 / NB;
+    constexpr int CH = 8 * G;
+    __shared__ T sv[CH][NB];
+    __shared__ int stype[CH];
+    const int s = blockIdx.y;
+    const long long e0 = (long long)blockIdx.x * CH;
+    const int ne = (int)min((long long)CH, a.E - e0);
+    for (int idx = threadIdx.x; idx < ne * NB; idx += 128) {
+        const int e = idx / NB, j = idx % NB;
+        sv[e][j] = v[((e0 + e) * NS + s) * NB + j];
+    }
+    // the element types of the run, once per element (index arithmetic in
+    // 64-bit and indexed argument loads are slow per thread)
+    for (int e = threadIdx.x; e < ne; e += 128) {
+        long long rest = e0 + e;
+        int type = 0;
+        for (int j = 0; j < a.dim; ++j) {
+            const long long ij = rest % a.n[j];
+            rest /= a.n[j];
+            type += a.slot[j][dev_tau(a, j, ij)] * a.stride[j];
+        }
+        stype[e] = type;
+    }
+    __syncthreads();
+    const int g = threadIdx.x / NB, i = threadIdx.x % NB;
+    if (g >= G) return;
+    T m[NB];
+    int cur = -1;
+    for (int e = g; e < ne; e += G) {
+        const int type = stype[e];
+        if (type != cur) {
+            const T* Mts = M + ((size_t)type * NS + s) * NB * NB;
+#pragma unroll
+            for (int j = 0; j < NB; ++j) m[j] = Mts[j * NB + i];
+            cur = type;
+        }
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < NB; ++j) acc = fma(m[j], sv[e][j], acc);
+        z[((e0 + e) * NS + s) * NB + i] = acc;
+    }
+}
+
+template <int NB, typename T>
+static void launch_nb(const ApplyArgs& a, const T* M, const T* v, T* z, cudaStream_t st) {
+    constexpr int CH = 8 * (128 / NB);
+    const dim3 grid((unsigned)((a.E + CH - 1) / CH), NS);
+    k_block_apply<NB, T><<<grid, 128, 0, st>>>(a, M, v, z);
+}
+
+int max_types(const Geo& g) {
+    int t = 1;
+    for (int j = 0; j < g.dim; ++j) t *= 3;   // at most three tau values on one axis
+    return t;
+}
+
+}  // namespace
+
+size_t block_table_bytes(const cdg2_mesh& m) {
+    const size_t per = (size_t)max_types(m.geo) * NS * m.nb * m.nb;
+    return (per * sizeof(double) + 255) / 256 * 256 + (per * sizeof(float) + 255) / 256 * 256;
+}
+
+int build_block_table(const cdg2_mesh& m, const Coef& c, double gdt, void* dev, BlockTable& bt) {
+    std::vector<int> taus[3];
+    type_layout(m.geo, bt, taus);
+    const int nb = m.nb;
+    const size_t per_block = (size_t)nb * nb;
+    std::vector<double> h64((size_t)bt.n_types * NS * per_block);
+    std::vector<float> h32(h64.size());
+    std::vector<double> P(per_block), X;
+    for (int t = 0; t < bt.n_types; ++t) {
+        int tau[3] = {0, 0, 0};
+        for (int j = 0; j < m.geo.dim; ++j) tau[j] = taus[j][(t / bt.stride[j]) % (int)taus[j].size()];
+        for (int s = 0; s < NS; ++s) {
+            element_block(m, c.A[s], gdt, tau, P.data());
+            if (!invert(nb, P, X)) {
+                set_error("cdg2_step: singular preconditioner block (dt * A too large for I - dt a_ii A K)");
+                return CDG2_ERR_INVALID_ARG;
+            }
+            double* dst = h64.data() + ((size_t)t * NS + s) * per_block;
+            for (int i = 0; i < nb; ++i)
+                for (int j = 0; j < nb; ++j) dst[(size_t)j * nb + i] = X[(size_t)i * nb + j];
+        }
+    }
+    for (size_t i = 0; i < h64.size(); ++i) h32[i] = (float)h64[i];
+    const size_t per = (size_t)max_types(m.geo) * NS * per_block;
+    char* base = static_cast<char*>(dev);
+    double* d64 = reinterpret_cast<double*>(base);
+    float* d32 = reinterpret_cast<float*>(base + (per * sizeof(double) + 255) / 256 * 256);
+    cudaError_t e = cudaMemcpy(d64, h64.data(), sizeof(double) * h64.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d32, h32.data(), sizeof(float) * h32.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cdg2_step: preconditioner blocks");
+    bt.m64 = d64;
+    bt.m32 = d32;
+    return CDG2_OK;
+}
+
+template <typename T>
+cudaError_t block_apply(const cdg2_mesh& m, const BlockTable& bt, const T* v, T* z, cudaStream_t st) {
+    ApplyArgs a;
+    a.E = m.geo.E;
+    a.nb = m.nb;
+    a.dim = m.geo.dim;
+    for (int j = 0; j < 3; ++j) {
+        a.n[j] = m.geo.n[j];
+        a.periodic[j] = m.geo.periodic[j];
+        a.stride[j] = bt.stride[j];
+        for (int u = 0; u < NTAU; ++u) a.slot[j][u] = bt.slot[j][u];
+    }
+    const T* M;
+    if constexpr (sizeof(T) == 8) M = bt.m64;
+    else M = bt.m32;
+    switch (a.nb) {
+        case 4: launch_nb<4, T>(a, M, v, z, st); break;
+        case 8: launch_nb<8, T>(a, M, v, z, st); break;
+        case 9: launch_nb<9, T>(a, M, v, z, st); break;
+        case 16: launch_nb<16, T>(a, M, v, z, st); break;
+        case 27: launch_nb<27, T>(a, M, v, z, st); break;
+        case 64: launch_nb<64, T>(a, M, v, z, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t block_apply<double>(const cdg2_mesh&, const BlockTable&, const double*, double*, cudaStream_t);
+template cudaError_t block_apply<float>(const cdg2_mesh&, const BlockTable&, const float*, float*, cudaStream_t);
+
+}  // namespace cdg2
+
+using namespace cdg2;
+
+extern "C" int cdg2_element_block(const cdg2_mesh* m, const cdg2_params* p, double gdt, long long elem, int species,
+                                  double* out) {
+    if (!m || !p || !out) {
+        set_error("cdg2_element_block: NULL argument");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (elem < 0 || elem >= m->geo.E || species < 0 || species >= NS || !std::isfinite(gdt)) {
+        set_error("cdg2_element_block: element, species or gdt out of range");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    const Coef c = make_coef(*p);
+    int tau[3] = {0, 0, 0};
+    long long rest = elem;
+    for (int j = 0; j < m->geo.dim; ++j) {
+        tau[j] = tau_of(m->geo, j, rest % m->geo.n[j]);
+        rest /= m->geo.n[j];
+    }
+    element_block(*m, c.A[species], gdt, tau, out);
+    return CDG2_OK;
+}

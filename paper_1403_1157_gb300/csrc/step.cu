@@ -26,6 +26,7 @@
 
 #include "cdg2_internal.h"
 #include "krylov.h"
+#include "precond.h"
 
 namespace cdg2 {
 
@@ -103,6 +104,15 @@ struct Work {
     double* red;      // reduction partials
     double* red_out;  // reduction results (MAX_KRYLOV + 1)
     double* pinv;     // [6][n_basis] right preconditioner P^{-1}
+    void* blk;        // element-block table (precond.cu)
+    void* ptmp;       // P^{-1} v in the Krylov precision
+};
+
+// Right preconditioner of GMRES: the modal diagonal (applied inside the
+// JVP/VJP kernel) or the element-block-Jacobi table (its own kernel).
+struct Precond {
+    const double* pinv = nullptr;
+    const BlockTable* bt = nullptr;
 };
 
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -115,8 +125,9 @@ static int ensure_work(const cdg2_mesh& m, int kdim, bool mixed, Work& w) {
     const size_t red = align256(sizeof(double) * reduction_scratch_doubles(MAX_KRYLOV + 1));
     const size_t out = align256(sizeof(double) * (MAX_KRYLOV + 1));
     const size_t tab = align256(sizeof(double) * NS * m.nb);
-    // 5 + MAX_STAGES FP64 vectors; basis (kdim + 2) + dx + Yk + bk in the Krylov precision
-    const size_t need = (5 + MAX_STAGES) * vec64 + (size_t)(kdim + 5) * veck + red + out + tab;
+    const size_t blk = align256(block_table_bytes(m));
+    // 5 + MAX_STAGES FP64 vectors; basis (kdim + 2) + dx + Yk + bk + ptmp in the Krylov precision
+    const size_t need = (5 + MAX_STAGES) * vec64 + (size_t)(kdim + 6) * veck + red + out + tab + blk;
     if (m.step_ws_bytes < need) {
         if (m.step_ws) cudaFree(m.step_ws);
         m.step_ws = nullptr;
@@ -146,6 +157,10 @@ static int ensure_work(const cdg2_mesh& m, int kdim, bool mixed, Work& w) {
     w.red_out = reinterpret_cast<double*>(p);
     p += out;
     w.pinv = reinterpret_cast<double*>(p);
+    p += tab;
+    w.blk = p;
+    p += blk;
+    w.ptmp = p;
     return CDG2_OK;
 }
 
@@ -179,6 +194,23 @@ static void modal_pinv(const cdg2_mesh& m, const Coef& c, double gdt, std::vecto
         }
 }
 
+// The preconditioner of one step (SDIRK: one diagonal coefficient a_ii for
+// all stages, so one set of blocks per call).
+static int setup_precond(const cdg2_mesh& m, const Coef& c, double gdt, int kind, Work& w, Precond& pc,
+                         BlockTable& bt) {
+    if (kind == 1) {
+        std::vector<double> ptab;
+        modal_pinv(m, c, gdt, ptab);
+        cudaError_t e = cudaMemcpy(w.pinv, ptab.data(), sizeof(double) * ptab.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cdg2_step: preconditioner");
+        pc.pinv = w.pinv;
+    } else if (kind == 2) {
+        if (int rc = build_block_table(m, c, gdt, w.blk, bt)) return rc;
+        pc.bt = &bt;
+    }
+    return CDG2_OK;
+}
+
 #define CDG2_TRY(...)                                              \
     do {                                                           \
         cudaError_t e_ = (__VA_ARGS__);                            \
@@ -206,19 +238,25 @@ static bool done_cycle_needs_restart(bool done, int jlast, int kdim) { return !d
 // The operator's matvec: w = (I - gdt J) P^{-1} v, or with J^T (adjoint).
 template <typename T>
 static cudaError_t matvec(bool adjoint, const cdg2_mesh& m, const Coef& c, const T* Yop, const T* v, double gdt,
-                          const double* pinv, T* out, int flags, cudaStream_t st) {
-    if (adjoint) return launch_vjp_axpby(m, c, Yop, v, 1.0, -gdt, pinv, out, flags, st);
-    return launch_jvp_axpby(m, c, Yop, v, 1.0, -gdt, pinv, out, flags, st);
+                          const Precond& pc, T* tmp, T* out, int flags, cudaStream_t st) {
+    if (pc.bt) {   // v <- P^{-1} v by blocks, then the plain operator
+        cudaError_t e = block_apply<T>(m, *pc.bt, v, tmp, st);
+        if (e != cudaSuccess) return e;
+        v = tmp;
+    }
+    if (adjoint) return launch_vjp_axpby(m, c, Yop, v, 1.0, -gdt, pc.pinv, out, flags, st);
+    return launch_jvp_axpby(m, c, Yop, v, 1.0, -gdt, pc.pinv, out, flags, st);
 }
 
 template <typename T>
 static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, const T* b, T* x, double rtol,
-                 int maxit, const Work& w, cudaStream_t st, int flags, const double* pinv, int* iters,
+                 int maxit, const Work& w, cudaStream_t st, int flags, const Precond& pc, int* iters,
                  double* relres, bool adjoint = false) {
     const long long n = w.n;
     const int kdim = w.m;
     T* V = static_cast<T*>(w.basis);
     T* wv = V + (size_t)(kdim + 1) * n;
+    T* tmp = static_cast<T*>(w.ptmp);
     const int jflags = CDG2_MINV | ((sizeof(T) == 4) ? CDG2_FP32 : 0) | (flags & CDG2_FORCING);
     CDG2_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
     double beta0 = 0.0;
@@ -242,7 +280,7 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
         bool done = false;
         for (int j = 0; j < kdim; ++j) {
             T* vj = V + (size_t)j * n;
-            CDG2_TRY(matvec<T>(adjoint, m, c, Yop, vj, gdt, pinv, wv, jflags, st));   // w = (I - gdt J) P^-1 v_j
+            CDG2_TRY(matvec<T>(adjoint, m, c, Yop, vj, gdt, pc, tmp, wv, jflags, st));   // w = (I - gdt J) P^-1 v_j
             std::fill(hcol.begin(), hcol.end(), 0.0);
             for (int pass = 0; pass < 2; ++pass) {                                // CGS2
                 CDG2_TRY(vec_mdot<T>(n, j + 1, V, n, wv, w.red, w.red_out, st));
@@ -293,7 +331,7 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
         CDG2_TRY(vec_basis_combine<T>(n, jlast + 1, V, n, yc, x, st));
         if (resid <= rtol * beta0 || total >= maxit || !done_cycle_needs_restart(done, jlast, kdim)) break;
         // restart: r = b - A x into V_0
-        CDG2_TRY(matvec<T>(adjoint, m, c, Yop, x, gdt, pinv, wv, jflags, st));
+        CDG2_TRY(matvec<T>(adjoint, m, c, Yop, x, gdt, pc, tmp, wv, jflags, st));
         CDG2_TRY(vec_convert<T, T>(n, b, 1.0, V, st));
         CDG2_TRY(vec_axpby<T>(n, -1.0, wv, 1.0, V, st));
         if (int rc = norm2<T>(w, V, st, &beta)) return rc;
@@ -304,7 +342,11 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
         CDG2_TRY(vec_convert<T, T>(n, V, 1.0 / beta, V, st));
     }
     // right preconditioning: the Krylov iterate lives in P-space, x = P^{-1} y
-    if (pinv) CDG2_TRY(vec_scale_modes<T>(n, pinv, NS * m.nb, x, st));
+    if (pc.pinv) CDG2_TRY(vec_scale_modes<T>(n, pc.pinv, NS * m.nb, x, st));
+    if (pc.bt) {
+        CDG2_TRY(block_apply<T>(m, *pc.bt, x, tmp, st));
+        CDG2_TRY(cudaMemcpyAsync(x, tmp, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+    }
     *iters = total;
     *relres = resid / beta0;
     return CDG2_OK;
@@ -317,9 +359,9 @@ using namespace cdg2;
 static int check_opts(const cdg2_solver_opts* o, double dt, const char* who) {
     if ((o->scheme != CDG2_SDIRK2 && o->scheme != CDG2_SDIRK3 && o->scheme != CDG2_SDIRK4) || o->gmres_restart < 1 ||
         o->gmres_restart > MAX_KRYLOV || o->max_newton < 1 || o->max_gmres < 1 || !(dt > 0.0) ||
-        (o->flags & ~CDG2_FORCING) || (o->precond != 0 && o->precond != 1)) {
+        (o->flags & ~CDG2_FORCING) || (o->precond < 0 || o->precond > 2)) {
         set_error(std::string(who) + ": invalid options (scheme 2|3|4, 1 <= gmres_restart <= 64, max_newton, "
-                  "max_gmres >= 1, dt > 0, flags in {0, CDG2_FORCING}, precond in {0, 1})");
+                  "max_gmres >= 1, dt > 0, flags in {0, CDG2_FORCING}, precond in {0, 1, 2})");
         return CDG2_ERR_INVALID_ARG;
     }
     return CDG2_OK;
@@ -340,13 +382,9 @@ static int run_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double 
     const Coef c = make_coef(*p);
     const Tableau T = sdirk_tableau(o->scheme);
     const long long n = w.n;
-    const double* pinv = nullptr;
-    std::vector<double> ptab;
-    if (o->precond == 1) {   // SDIRK: one diagonal coefficient for all stages
-        modal_pinv(*m, c, dt * T.A[0][0], ptab);
-        CDG2_TRY(cudaMemcpy(w.pinv, ptab.data(), sizeof(double) * ptab.size(), cudaMemcpyHostToDevice));
-        pinv = w.pinv;
-    }
+    Precond pc;
+    BlockTable bt;
+    if (int rc = setup_precond(*m, c, dt * T.A[0][0], o->precond, w, pc, bt)) return rc;
     cdg2_stats S;
     std::memset(&S, 0, sizeof(S));
     S.stages = T.s;
@@ -387,13 +425,13 @@ static int run_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double 
             if (!mixed) {
                 CDG2_TRY(vec_convert<double, double>(n, w.G, -1.0, w.b64, st));
                 rc = gmres<double>(*m, c, w.Y, gdt, w.b64, static_cast<double*>(w.dx), o->gmres_rtol, o->max_gmres, w,
-                                   st, o->flags, pinv, &its, &rr);
+                                   st, o->flags, pc, &its, &rr);
                 if (rc == CDG2_OK) CDG2_TRY(vec_add_into<double>(n, static_cast<double*>(w.dx), w.Y, st));
             } else {
                 CDG2_TRY(vec_convert<double, float>(n, w.Y, 1.0, static_cast<float*>(w.Yk), st));
                 CDG2_TRY(vec_convert<double, float>(n, w.G, -1.0, static_cast<float*>(w.bk), st));
                 rc = gmres<float>(*m, c, static_cast<float*>(w.Yk), gdt, static_cast<float*>(w.bk),
-                                  static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, o->flags, pinv, &its, &rr);
+                                  static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, o->flags, pc, &its, &rr);
                 if (rc == CDG2_OK) CDG2_TRY(vec_add_into<float>(n, static_cast<float*>(w.dx), w.Y, st));
             }
             S.gmres_iters += its;
@@ -481,13 +519,9 @@ extern "C" int cdg2_step_adjoint(const cdg2_mesh* m, const cdg2_params* p, const
         }
         part = m->theta_part;
     }
-    const double* pinv = nullptr;
-    std::vector<double> ptab;
-    if (o->precond == 1) {
-        modal_pinv(*m, c, dt * T.A[0][0], ptab);
-        CDG2_TRY(cudaMemcpy(w.pinv, ptab.data(), sizeof(double) * ptab.size(), cudaMemcpyHostToDevice));
-        pinv = w.pinv;
-    }
+    Precond pc;
+    BlockTable bt;
+    if (int rc = setup_precond(*m, c, dt * T.A[0][0], o->precond, w, pc, bt)) return rc;
     cdg2_stats S;
     std::memset(&S, 0, sizeof(S));
     S.stages = T.s;
@@ -524,13 +558,13 @@ extern "C" int cdg2_step_adjoint(const cdg2_mesh* m, const cdg2_params* p, const
             double rr = 0.0;
             if (!mixed) {
                 rc = gmres<double>(*m, c, Yi, gdt, w.G, static_cast<double*>(w.dx), o->gmres_rtol, o->max_gmres, w, st,
-                                   0, pinv, &its, &rr, true);
+                                   0, pc, &its, &rr, true);
                 if (rc == CDG2_OK) CDG2_TRY(vec_add_into<double>(n, static_cast<double*>(w.dx), w.Y, st));
             } else {
                 CDG2_TRY(vec_convert<double, float>(n, Yi, 1.0, static_cast<float*>(w.Yk), st));
                 CDG2_TRY(vec_convert<double, float>(n, w.G, 1.0, static_cast<float*>(w.bk), st));
                 rc = gmres<float>(*m, c, static_cast<float*>(w.Yk), gdt, static_cast<float*>(w.bk),
-                                  static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, 0, pinv, &its, &rr,
+                                  static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, 0, pc, &its, &rr,
                                   true);
                 if (rc == CDG2_OK) CDG2_TRY(vec_add_into<float>(n, static_cast<float*>(w.dx), w.Y, st));
             }

@@ -39,7 +39,8 @@ def _tight(G, scheme, mixed=False):
 
 
 @pytest.mark.parametrize("scheme,name", [(2, "sdirk2"), (3, "sdirk3")])
-def test_step_adjoint_matches_oracle_dense_adjoint(G, scheme, name):
+@pytest.mark.parametrize("precond", [1, 2])
+def test_step_adjoint_matches_oracle_dense_adjoint(G, scheme, name, precond):
     om = O.Mesh(2, (4, 2), (1.0, 0.2), (1, 0), 1)
     gm = G.cdg2_mesh_create(2, (4, 2), (1.0, 0.2), (1, 0), 1)
     p = _params()
@@ -50,6 +51,7 @@ def test_step_adjoint_matches_oracle_dense_adjoint(G, scheme, name):
     lam = torch.from_numpy(np.random.default_rng(3).standard_normal(U.shape))
     lam_ref, gth_ref = O.step_adjoint(om, stages, p, dt, name, lam, I.THETA_NAMES)
     o = _tight(G, scheme)
+    o.precond = precond
     st = torch.empty(len(stages) * gm.n_dof, dtype=torch.float64, device="cuda")
     Ud = U.clone().cuda()
     G.cdg2_step_stages(gm, p, Ud, 0.0, dt, st, o)

@@ -143,7 +143,8 @@ def test_step_iteration_cap_is_reported(G):
 def test_step_rejects_bad_options(G):
     om, gm = _pair(G, 2, (4, 2), 1)
     U = torch.zeros(gm.n_dof, dtype=torch.float64, device="cuda")
-    for bad in (dict(scheme=5), dict(gmres_restart=0), dict(gmres_restart=65), dict(max_newton=0), dict(precond=2)):
+    for bad in (dict(scheme=5), dict(gmres_restart=0), dict(gmres_restart=65), dict(max_newton=0), dict(precond=3),
+                dict(precond=-1)):
         rc, _ = G.cdg2_step(gm, I.default_params(), U, 0.0, 1e-3, G.make_opts(**bad), raise_on_error=False)
         assert rc == -1
     rc, _ = G.cdg2_step(gm, I.default_params(), U, 0.0, 0.0, G.make_opts(), raise_on_error=False)
@@ -156,11 +157,30 @@ def test_preconditioner_changes_iterations_not_the_solution(G, mixed):
     p = I.default_params()
     U0 = gaussian_state(om, n_gauss=8, sigma=0.04, seed=1160).cuda()
     out, its = {}, {}
-    for pc in (0, 1):
+    for pc in (0, 1, 2):
         U = U0.clone()
         rc, st = G.cdg2_step(gm, p, U, 0.0, 1e-3, G.make_opts(scheme=3, mixed=mixed, precond=pc, newton_rtol=1e-11,
                                                                gmres_rtol=1e-4))
         assert rc == 0
         out[pc], its[pc] = U, st["gmres_iters"]
     assert float((out[1] - out[0]).norm() / out[0].norm()) <= 1e-10
+    assert float((out[2] - out[0]).norm() / out[0].norm()) <= 1e-10
     assert its[1] < its[0]
+    assert its[2] < its[1]   # the element blocks hold the modal diagonal and its couplings
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_block_preconditioned_step_matches_oracle(G, mixed):
+    om, gm = _pair(G, 2, (8, 4), 2)
+    p = I.default_params()
+    U0 = gaussian_state(om, sigma=0.08, seed=31)
+    ref = U0.clone()
+    for i in range(2):
+        ref = O.step(om, ref, p, i * 1e-3, 1e-3, "sdirk3")
+    U = U0.clone().cuda()
+    o = _tight(G, 3, mixed)
+    o.precond = 2
+    for i in range(2):
+        rc, st = G.cdg2_step(gm, p, U, i * 1e-3, 1e-3, o)
+        assert rc == 0
+    assert _rel(U, ref) <= 1e-10

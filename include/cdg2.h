@@ -125,7 +125,9 @@ typedef struct cdg2_params {
  * Newton stops when ||G||_2 <= max(newton_rtol ||G(Y^0)||_2, newton_atol),
  *   G(Y) = Y - dt a_ii f(Y) - rhs_i, Y^0 the previous stage value (U_n first);
  *   at most max_newton corrections per stage.
- * GMRES(gmres_restart) with CGS2 stops at ||r||_2 <= gmres_rtol ||G||_2 or
+ * GMRES(gmres_restart) (Arnoldi by classical Gram-Schmidt, a second pass
+ *   when the DGKS criterion |w'| < |w|/sqrt(2) flags cancellation) stops at
+ *   ||r||_2 <= gmres_rtol ||G||_2 or
  *   after max_gmres iterations per Newton correction; 1 <= gmres_restart <= 64.
  * precond: 0 = none; 1 = right preconditioning by the modal diagonal
  *   P = 1 - dt a_ii A_s d_i of the diffusion part (for an orthonormal mode on
@@ -159,6 +161,7 @@ typedef struct cdg2_stats {
     double residual0[5];  /* ||G(Y^0)||_2 per stage */
     double residual[5];   /* final ||G||_2 per stage */
     double seconds;       /* host wall time of the call */
+    int gmres_reorth;     /* Arnoldi steps that needed a second Gram-Schmidt pass */
 } cdg2_stats;
 
 /* Build a mesh (host call, synchronous).  Tabulates the 1D basis and Gauss

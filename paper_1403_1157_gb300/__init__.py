@@ -85,12 +85,13 @@ class Stats(ctypes.Structure):
     _fields_ = [
         ("stages", ctypes.c_int), ("newton_iters", ctypes.c_int), ("gmres_iters", ctypes.c_int),
         ("residual0", ctypes.c_double * 5), ("residual", ctypes.c_double * 5), ("seconds", ctypes.c_double),
+        ("gmres_reorth", ctypes.c_int),
     ]
 
     def as_dict(self):
         return {"stages": self.stages, "newton_iters": self.newton_iters, "gmres_iters": self.gmres_iters,
                 "residual0": list(self.residual0)[: self.stages], "residual": list(self.residual)[: self.stages],
-                "seconds": self.seconds}
+                "seconds": self.seconds, "gmres_reorth": self.gmres_reorth}
 
 
 def library_path() -> str:

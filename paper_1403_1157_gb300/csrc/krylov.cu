@@ -75,13 +75,18 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // chunk blockIdx.y (j = NVC * blockIdx.y + jj): w is read once per chunk and
 // the NVC independent loads per element keep enough bytes in flight.
 constexpr int NVC = 8;
+// With self_dot, chunk 0 also forms w . w as row nv (one pass gives the
+// projections and the norm before projection).
 template <typename T>
 __global__ void __launch_bounds__(VT) k_mdot_partial(long long n, int nv, const T* __restrict__ V, long long ldv,
-                                                      const T* __restrict__ w, double* __restrict__ part) {
+                                                      const T* __restrict__ w, double* __restrict__ part,
+                                                      int self_dot) {
     __shared__ double sh[VT];
     const int j0 = blockIdx.y * NVC;
     const int nj = nv - j0 < NVC ? nv - j0 : NVC;
+    const bool with_self = self_dot && blockIdx.y == 0;
     T acc[NVC];
+    T accw = T(0);
 #pragma unroll
     for (int jj = 0; jj < NVC; ++jj) acc[jj] = T(0);
     const long long stride = (long long)gridDim.x * VT;
@@ -92,11 +97,16 @@ __global__ void __launch_bounds__(VT) k_mdot_partial(long long n, int nv, const 
         for (int jj = 0; jj < NVC; ++jj) v[jj] = jj < nj ? V[(j0 + jj) * ldv + i] : T(0);
 #pragma unroll
         for (int jj = 0; jj < NVC; ++jj) acc[jj] = fma(v[jj], wi, acc[jj]);
+        if (with_self) accw = fma(wi, wi, accw);
     }
     for (int jj = 0; jj < nj; ++jj) {
         const double s = block_sum(double(acc[jj]), sh);
         if (threadIdx.x == 0) part[(long long)(j0 + jj) * gridDim.x + blockIdx.x] = s;
         __syncthreads();
+    }
+    if (with_self) {
+        const double s = block_sum(double(accw), sh);
+        if (threadIdx.x == 0) part[(long long)nv * gridDim.x + blockIdx.x] = s;
     }
 }
 
@@ -110,13 +120,17 @@ __global__ void __launch_bounds__(VT) k_rows_sum(const double* __restrict__ part
     if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
-// w -= sum_j h_j V_j  (h on the device): NVC independent loads per step
+// w -= sum_j h_j V_j and part[blockIdx.x] = this block's slice of |w|^2 after
+// the update (fixed grid of RED_BLOCKS blocks: a deterministic partition)
 template <typename T>
-__global__ void __launch_bounds__(VT) k_mgs_update(long long n, int nv, const T* __restrict__ V, long long ldv,
-                                                   const double* __restrict__ h, T* __restrict__ w) {
+__global__ void __launch_bounds__(VT) k_update_norm(long long n, int nv, const T* __restrict__ V, long long ldv,
+                                                    const double* __restrict__ h, T* __restrict__ w,
+                                                    double* __restrict__ part) {
     __shared__ T hs[MAX_KRYLOV + 1];
+    __shared__ double sh[VT];
     for (int j = threadIdx.x; j < nv; j += VT) hs[j] = T(-h[j]);
     __syncthreads();
+    T nrm = T(0);
     for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) {
         T acc = w[i];
         int j = 0;
@@ -129,7 +143,10 @@ __global__ void __launch_bounds__(VT) k_mgs_update(long long n, int nv, const T*
         }
         for (; j < nv; ++j) acc = fma(hs[j], V[j * ldv + i], acc);
         w[i] = acc;
+        nrm = fma(acc, acc, nrm);
     }
+    const double s = block_sum(double(nrm), sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 // x += sum_j y_j V_j  (y passed by value)
@@ -205,14 +222,25 @@ template <typename T>
 cudaError_t vec_mdot(long long n, int nv, const T* V, long long ldv, const T* w, double* part, double* out,
                      cudaStream_t st) {
     dim3 grid(RED_BLOCKS, (nv + NVC - 1) / NVC);
-    k_mdot_partial<T><<<grid, VT, 0, st>>>(n, nv, V, ldv, w, part);
+    k_mdot_partial<T><<<grid, VT, 0, st>>>(n, nv, V, ldv, w, part, 0);
     k_rows_sum<<<nv, VT, 0, st>>>(part, RED_BLOCKS, out);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t vec_mgs_update(long long n, int nv, const T* V, long long ldv, const double* h, T* w, cudaStream_t st) {
-    k_mgs_update<T><<<grid_for(n), VT, 0, st>>>(n, nv, V, ldv, h, w);
+cudaError_t vec_mdot_self(long long n, int nv, const T* V, long long ldv, const T* w, double* part, double* out,
+                          cudaStream_t st) {
+    dim3 grid(RED_BLOCKS, (nv + NVC - 1) / NVC);
+    k_mdot_partial<T><<<grid, VT, 0, st>>>(n, nv, V, ldv, w, part, 1);
+    k_rows_sum<<<nv + 1, VT, 0, st>>>(part, RED_BLOCKS, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t vec_update_norm(long long n, int nv, const T* V, long long ldv, const double* h, T* w, double* part,
+                            double* norm2_out, cudaStream_t st) {
+    k_update_norm<T><<<RED_BLOCKS, VT, 0, st>>>(n, nv, V, ldv, h, w, part);
+    k_rows_sum<<<1, VT, 0, st>>>(part, RED_BLOCKS, norm2_out);
     return cudaGetLastError();
 }
 
@@ -241,14 +269,18 @@ template cudaError_t vec_convert<double, double>(long long, const double*, doubl
 template cudaError_t vec_convert<float, float>(long long, const float*, double, float*, cudaStream_t);
 template cudaError_t vec_add_into<double>(long long, const double*, double*, cudaStream_t);
 template cudaError_t vec_add_into<float>(long long, const float*, double*, cudaStream_t);
+template cudaError_t vec_mdot_self<double>(long long, int, const double*, long long, const double*, double*,
+                                           double*, cudaStream_t);
+template cudaError_t vec_mdot_self<float>(long long, int, const float*, long long, const float*, double*, double*,
+                                          cudaStream_t);
+template cudaError_t vec_update_norm<double>(long long, int, const double*, long long, const double*, double*,
+                                             double*, double*, cudaStream_t);
+template cudaError_t vec_update_norm<float>(long long, int, const float*, long long, const double*, float*,
+                                            double*, double*, cudaStream_t);
 template cudaError_t vec_mdot<double>(long long, int, const double*, long long, const double*, double*, double*,
                                       cudaStream_t);
 template cudaError_t vec_mdot<float>(long long, int, const float*, long long, const float*, double*, double*,
                                      cudaStream_t);
-template cudaError_t vec_mgs_update<double>(long long, int, const double*, long long, const double*, double*,
-                                            cudaStream_t);
-template cudaError_t vec_mgs_update<float>(long long, int, const float*, long long, const double*, float*,
-                                           cudaStream_t);
 template cudaError_t vec_basis_combine<double>(long long, int, const double*, long long, const Coeffs&, double*,
                                                cudaStream_t);
 template cudaError_t vec_basis_combine<float>(long long, int, const float*, long long, const Coeffs&, float*,

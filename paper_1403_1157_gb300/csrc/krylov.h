@@ -26,8 +26,14 @@ cudaError_t vec_add_into(long long n, const T* x, double* y, cudaStream_t st);
 template <typename T>
 cudaError_t vec_mdot(long long n, int nv, const T* V, long long ldv, const T* w, double* part, double* out,
                      cudaStream_t st);
+// as vec_mdot, and out[nv] = w . w (the norm before projection) in the same pass
 template <typename T>
-cudaError_t vec_mgs_update(long long n, int nv, const T* V, long long ldv, const double* h, T* w, cudaStream_t st);
+cudaError_t vec_mdot_self(long long n, int nv, const T* V, long long ldv, const T* w, double* part, double* out,
+                          cudaStream_t st);
+// w -= sum_j h_j V_j and *norm2_out = |w|^2 after the update, in one pass
+template <typename T>
+cudaError_t vec_update_norm(long long n, int nv, const T* V, long long ldv, const double* h, T* w, double* part,
+                            double* norm2_out, cudaStream_t st);
 template <typename T>
 cudaError_t vec_basis_combine(long long n, int nv, const T* V, long long ldv, const Coeffs& y, T* x,
                               cudaStream_t st);

@@ -9,9 +9,10 @@
 // Stage i solves G(Y) = Y - dt a_ii f(Y, t + c_i dt) - rhs_i = 0 with
 // rhs_i = U_n + dt sum_{j<i} a_ij K_j.  Newton: the residual G is always
 // formed in FP64; the correction solves (I - dt a_ii J(Y)) d = -G by
-// restarted GMRES with classical Gram-Schmidt applied twice (CGS2), whose
-// matrix-vector product is one JVP launch (J from the kernel, not a finite
-// difference).  In the mixed mode the Krylov vectors, the JVP and the
+// restarted GMRES whose Arnoldi step is classical Gram-Schmidt with the
+// Daniel-Gragg-Kaufman-Stewart criterion (a second projection pass only when
+// the first removed more than half of |w|^2), and whose matrix-vector product
+// is one JVP launch (J from the kernel, not a finite difference).  In the mixed mode the Krylov vectors, the JVP and the
 // primal state it linearises about are FP32 while G, Y and the convergence
 // test stay FP64: iterative refinement, so the converged stage agrees with
 // the FP64 solve to the Newton tolerance.
@@ -123,7 +124,7 @@ static int ensure_work(const cdg2_mesh& m, int kdim, bool mixed, Work& w) {
     const size_t vec64 = align256(sizeof(double) * n);
     const size_t veck = align256(ks * n);
     const size_t red = align256(sizeof(double) * reduction_scratch_doubles(MAX_KRYLOV + 1));
-    const size_t out = align256(sizeof(double) * (MAX_KRYLOV + 1));
+    const size_t out = align256(sizeof(double) * (MAX_KRYLOV + 2));   // projections, then one norm slot
     const size_t tab = align256(sizeof(double) * NS * m.nb);
     const size_t blk = align256(block_table_bytes(m));
     // 5 + MAX_STAGES FP64 vectors; basis (kdim + 2) + dx + Yk + bk + ptmp in the Krylov precision
@@ -232,7 +233,8 @@ static int norm2(const Work& w, const T* x, cudaStream_t st, double* out) {
 // otherwise it used all kdim vectors and GMRES restarts from the true residual.
 static bool done_cycle_needs_restart(bool done, int jlast, int kdim) { return !done && jlast == kdim - 1; }
 
-// Restarted GMRES(m) with CGS2 for (I - gdt J(Yop)) x = b, x0 = 0.
+// Restarted GMRES(m) for (I - gdt J(Yop)) x = b, x0 = 0, Arnoldi by classical
+// Gram-Schmidt with DGKS reorthogonalisation (*reorth counts second passes).
 // Stops when ||b - A x||_2 <= rtol ||b||_2 (the Arnoldi estimate) or after
 // maxit inner iterations.  T is the Krylov precision.
 // The operator's matvec: w = (I - gdt J) P^{-1} v, or with J^T (adjoint).
@@ -251,7 +253,7 @@ static cudaError_t matvec(bool adjoint, const cdg2_mesh& m, const Coef& c, const
 template <typename T>
 static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, const T* b, T* x, double rtol,
                  int maxit, const Work& w, cudaStream_t st, int flags, const Precond& pc, int* iters,
-                 double* relres, bool adjoint = false) {
+                 int* reorth, double* relres, bool adjoint = false) {
     const long long n = w.n;
     const int kdim = w.m;
     T* V = static_cast<T*>(w.basis);
@@ -282,16 +284,24 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
             T* vj = V + (size_t)j * n;
             CDG2_TRY(matvec<T>(adjoint, m, c, Yop, vj, gdt, pc, tmp, wv, jflags, st));   // w = (I - gdt J) P^-1 v_j
             std::fill(hcol.begin(), hcol.end(), 0.0);
-            for (int pass = 0; pass < 2; ++pass) {                                // CGS2
-                CDG2_TRY(vec_mdot<T>(n, j + 1, V, n, wv, w.red, w.red_out, st));
-                CDG2_TRY(vec_mgs_update<T>(n, j + 1, V, n, w.red_out, wv, st));
-                std::vector<double> hp(j + 1);
-                CDG2_TRY(cudaMemcpyAsync(hp.data(), w.red_out, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
+            // Classical Gram-Schmidt with the DGKS criterion: one projection
+            // pass (its multi-dot also gives |w| before, the update |w| after);
+            // a second pass only when |w'| < |w| / sqrt(2) (cancellation).
+            double* nslot = w.red_out + (MAX_KRYLOV + 1);
+            double hn = 0.0;
+            for (int pass = 0; pass < 2; ++pass) {
+                if (pass == 0) CDG2_TRY(vec_mdot_self<T>(n, j + 1, V, n, wv, w.red, w.red_out, st));
+                else CDG2_TRY(vec_mdot<T>(n, j + 1, V, n, wv, w.red, w.red_out, st));
+                CDG2_TRY(vec_update_norm<T>(n, j + 1, V, n, w.red_out, wv, w.red, nslot, st));
+                std::vector<double> hp(MAX_KRYLOV + 2);
+                CDG2_TRY(cudaMemcpyAsync(hp.data(), w.red_out, sizeof(double) * (MAX_KRYLOV + 2),
+                                         cudaMemcpyDeviceToHost, st));
                 CDG2_TRY(cudaStreamSynchronize(st));
                 for (int i = 0; i <= j; ++i) hcol[i] += hp[i];
+                hn = std::sqrt(std::max(hp[MAX_KRYLOV + 1], 0.0));
+                if (pass == 1) ++*reorth;
+                if (pass == 1 || !(hn < 0.7071067811865476 * std::sqrt(std::max(hp[j + 1], 0.0)))) break;
             }
-            double hn = 0.0;
-            if (int rc = norm2<T>(w, wv, st, &hn)) return rc;
             hcol[j + 1] = hn;
             // previous Givens rotations, then a new one zeroing hcol[j + 1]
             for (int i = 0; i < j; ++i) {
@@ -425,13 +435,13 @@ static int run_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double 
             if (!mixed) {
                 CDG2_TRY(vec_convert<double, double>(n, w.G, -1.0, w.b64, st));
                 rc = gmres<double>(*m, c, w.Y, gdt, w.b64, static_cast<double*>(w.dx), o->gmres_rtol, o->max_gmres, w,
-                                   st, o->flags, pc, &its, &rr);
+                                   st, o->flags, pc, &its, &S.gmres_reorth, &rr);
                 if (rc == CDG2_OK) CDG2_TRY(vec_add_into<double>(n, static_cast<double*>(w.dx), w.Y, st));
             } else {
                 CDG2_TRY(vec_convert<double, float>(n, w.Y, 1.0, static_cast<float*>(w.Yk), st));
                 CDG2_TRY(vec_convert<double, float>(n, w.G, -1.0, static_cast<float*>(w.bk), st));
                 rc = gmres<float>(*m, c, static_cast<float*>(w.Yk), gdt, static_cast<float*>(w.bk),
-                                  static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, o->flags, pc, &its, &rr);
+                                  static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, o->flags, pc, &its, &S.gmres_reorth, &rr);
                 if (rc == CDG2_OK) CDG2_TRY(vec_add_into<float>(n, static_cast<float*>(w.dx), w.Y, st));
             }
             S.gmres_iters += its;
@@ -558,13 +568,13 @@ extern "C" int cdg2_step_adjoint(const cdg2_mesh* m, const cdg2_params* p, const
             double rr = 0.0;
             if (!mixed) {
                 rc = gmres<double>(*m, c, Yi, gdt, w.G, static_cast<double*>(w.dx), o->gmres_rtol, o->max_gmres, w, st,
-                                   0, pc, &its, &rr, true);
+                                   0, pc, &its, &S.gmres_reorth, &rr, true);
                 if (rc == CDG2_OK) CDG2_TRY(vec_add_into<double>(n, static_cast<double*>(w.dx), w.Y, st));
             } else {
                 CDG2_TRY(vec_convert<double, float>(n, Yi, 1.0, static_cast<float*>(w.Yk), st));
                 CDG2_TRY(vec_convert<double, float>(n, w.G, 1.0, static_cast<float*>(w.bk), st));
                 rc = gmres<float>(*m, c, static_cast<float*>(w.Yk), gdt, static_cast<float*>(w.bk),
-                                  static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, 0, pc, &its, &rr,
+                                  static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, 0, pc, &its, &S.gmres_reorth, &rr,
                                   true);
                 if (rc == CDG2_OK) CDG2_TRY(vec_add_into<float>(n, static_cast<float*>(w.dx), w.Y, st));
             }

@@ -187,3 +187,72 @@ def random_coefficients(n_elem: int, n_basis: int, seed: int, scale: float = 0.1
     out = scale * (2.0 * u - 1.0) / (1.0 + i)
     out[:, :, 0] = 0.5 + u[:, :, 0]
     return out
+
+
+def tri_mesh(nx: int, ny: int, lx: float = 1.0, ly: float = 0.2, jitter: float = 0.0, seed: int = 0):
+    """A triangulation of [0, lx] x [0, ly]: an nx x ny grid of vertices moved
+    by seeded jitter, each quad cut into two triangles.
+
+    Vertices (i, j), i fastest, sit at (i lx / nx, j ly / ny); interior
+    vertices are shifted by jitter * h * (2u - 1) per coordinate (u from
+    SplitMix64(seed), x then y per vertex in index order), boundary vertices
+    stay.  Quad (i, j) (i fastest) with corners a = (i, j), b = (i+1, j),
+    c = (i+1, j+1), d = (i, j+1) gives the triangles (a, b, c), (a, c, d)
+    when i + j is even and (a, b, d), (b, c, d) when odd, all counter-
+    clockwise.  Returns (xy [n_vert][2] float64, tri [n_tri][3] int64) numpy
+    arrays.  jitter < 0.25 keeps every triangle valid.
+    """
+    import numpy as np
+    hx, hy = lx / nx, ly / ny
+    nv = (nx + 1) * (ny + 1)
+    u = splitmix64_uniform_array(seed, 2 * nv).reshape(nv, 2)
+    xy = np.zeros((nv, 2))
+    for j in range(ny + 1):
+        for i in range(nx + 1):
+            v = j * (nx + 1) + i
+            xy[v] = (i * hx, j * hy)
+            if 0 < i < nx and 0 < j < ny:
+                xy[v, 0] += jitter * hx * (2.0 * u[v, 0] - 1.0)
+                xy[v, 1] += jitter * hy * (2.0 * u[v, 1] - 1.0)
+    tri = []
+    for j in range(ny):
+        for i in range(nx):
+            a = j * (nx + 1) + i
+            b, c, d = a + 1, a + nx + 2, a + nx + 1
+            tri += [(a, b, c), (a, c, d)] if (i + j) % 2 == 0 else [(a, b, d), (b, c, d)]
+    return xy, np.array(tri, dtype=np.int64)
+
+
+@dataclass
+class TriWorkload:
+    name: str
+    nx: int
+    ny: int
+    k: int
+    jitter: float
+    seed: int
+    extent: tuple = (1.0, 0.2)
+
+    @property
+    def n_elem(self) -> int:
+        return 2 * self.nx * self.ny
+
+    @property
+    def n_basis(self) -> int:
+        return (self.k + 1) * (self.k + 2) // 2
+
+    @property
+    def n_dof(self) -> int:
+        return N_SPECIES * self.n_elem * self.n_basis
+
+
+def tri_workload(which: int, k: int | None = None) -> TriWorkload:
+    """Triangle workloads (the paper's 2D runs use triangles, P_k, chi_e = 1.5):
+    0: 16x4 quads (128 triangles) P2, jitter 0.2, seed 1170 (oracle sized);
+    1: 256x64 quads (32,768 triangles) P3, jitter 0.2, seed 1171
+    (983,040 DOF; the same domain and vertex spacing as the 256x64 Q3 mesh)."""
+    if which == 0:
+        return TriWorkload("2D triangles 16x4x2 P2 (jittered)", 16, 4, 2 if k is None else k, 0.2, 1170)
+    if which == 1:
+        return TriWorkload("2D triangles 256x64x2 P3 (jittered)", 256, 64, 3 if k is None else k, 0.2, 1171)
+    raise ValueError(f"unknown triangle workload {which}")

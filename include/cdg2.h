@@ -306,6 +306,51 @@ int cdg2_project_mms(const cdg2_mesh* mesh, const cdg2_params* params, double t,
 int cdg2_element_block(const cdg2_mesh* mesh, const cdg2_params* params, double gdt, long long elem, int species,
                        double* out);
 
+/* ---- Triangle meshes (Sec. 3.1: P_k on triangles, chi_e = 1.5) ----------
+ * The operator f(U) = M^{-1} L_h(U) of cdg2_apply on an affine triangle
+ * mesh, FP64.  Readings (the paper fixes none of them): on the reference
+ * triangle {xi, eta >= 0, xi + eta <= 1} the orthonormal Dubiner basis
+ * psi_pq = sqrt(2 (2p+1) (p+q+1)) (1-eta)^p P_p(2 xi/(1-eta) - 1)
+ * P_q^{(2p+1,0)}(2 eta - 1), modes ordered by p + q then q, mapped by
+ * x = x_0 + [x_1 - x_0, x_2 - x_0] (xi, eta) (so M_K = 2 |K| I); the
+ * collapsed Gauss rule with (k+2)^2 volume points and k+2 points per edge;
+ * K^-_e the smaller adjacent triangle (Sec. 3.1; areas within a relative
+ * 1e-12 tie, a tie goes to the lower triangle index); boundary edges on
+ * y = 0 are Gamma_1 and on y = max y Gamma_2 (Eq. (3)), every other boundary
+ * edge is a no-flow wall.  Layout of U and out: [n_tri][6][n_basis],
+ * n_basis = (k+1)(k+2)/2. */
+typedef struct cdg2_tri_mesh cdg2_tri_mesh;
+
+typedef struct cdg2_tri_desc {
+    long long n_vert;
+    const double* xy;        /* host [n_vert][2] vertex coordinates */
+    long long n_tri;
+    const long long* tri;    /* host [n_tri][3] vertex indices, counter-clockwise */
+    int k;                   /* 1..3 */
+    double chi_e;            /* CDG2 lifting factor; <= 0 selects 1.5 (Sec. 3.1, triangles) */
+    double gamma1_in[2];     /* x-range of Gamma_{1,in} on y = 0 */
+} cdg2_tri_desc;
+
+/* Build a triangle mesh (host call; the arrays are copied).  Errors:
+ * INVALID_ARG for k outside 1..3, an index out of range, a degenerate or
+ * clockwise triangle, neighbours with inconsistent orientation, or an edge
+ * shared by more than two triangles.  Device memory is allocated by the first
+ * cdg2_tri_apply and freed by cdg2_tri_mesh_destroy (calls sharing a mesh
+ * must be ordered on one stream). */
+int cdg2_tri_mesh_create(const cdg2_tri_desc* desc, cdg2_tri_mesh** out);
+void cdg2_tri_mesh_destroy(cdg2_tri_mesh* mesh);
+int cdg2_tri_mesh_info(const cdg2_tri_mesh* mesh, long long* n_elem, int* n_basis, long long* n_dof,
+                       long long* n_faces);
+
+/* out = M^{-1} L_h(U) (flags = CDG2_MINV) or <phi, L_h(U)> (flags = 0) on a
+ * triangle mesh; U, out: device float64 [n_tri][6][n_basis], not
+ * overlapping.  Two kernels: every interior edge once (traces, the CDG2
+ * lifting on K^-, the face flux, its test against both sides) into a face
+ * buffer, then every element (volume terms, its edges, boundary data,
+ * M^{-1}).  Errors: INVALID_ARG (NULL, overlap, other flags), CUDA. */
+int cdg2_tri_apply(const cdg2_tri_mesh* mesh, const cdg2_params* params, const double* U, double* out, int flags,
+                   void* stream);
+
 const char* cdg2_last_error(void);
 
 #ifdef __cplusplus

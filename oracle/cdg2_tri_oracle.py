@@ -126,6 +126,7 @@ class TriMesh:
         self.tri = torch.as_tensor(np.asarray(tri), dtype=torch.long)
         self.k = int(k)
         self.dim = 2
+        self.periodic = (False, False)       # Reading: triangle meshes are not periodic here
         self.chi_e = float(chi_e)
         self.gamma1_in = tuple(gamma1_in)
         self.E = self.tri.shape[0]

@@ -81,6 +81,18 @@ class SolverOpts(ctypes.Structure):
     ]
 
 
+class TriDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_vert", ctypes.c_longlong),
+        ("xy", ctypes.POINTER(ctypes.c_double)),
+        ("n_tri", ctypes.c_longlong),
+        ("tri", ctypes.POINTER(ctypes.c_longlong)),
+        ("k", ctypes.c_int),
+        ("chi_e", ctypes.c_double),
+        ("gamma1_in", ctypes.c_double * 2),
+    ]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [
         ("stages", ctypes.c_int), ("newton_iters", ctypes.c_int), ("gmres_iters", ctypes.c_int),
@@ -135,6 +147,15 @@ def load_library():
     lib.cdg2_project_gaussians.restype = i
     lib.cdg2_project_mms.argtypes = [vp, ctypes.POINTER(Params), d, vp, i, vp]
     lib.cdg2_project_mms.restype = i
+    lib.cdg2_tri_mesh_create.argtypes = [ctypes.POINTER(TriDesc), ctypes.POINTER(vp)]
+    lib.cdg2_tri_mesh_create.restype = i
+    lib.cdg2_tri_mesh_destroy.argtypes = [vp]
+    lib.cdg2_tri_mesh_destroy.restype = None
+    lib.cdg2_tri_mesh_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i),
+                                       ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.cdg2_tri_mesh_info.restype = i
+    lib.cdg2_tri_apply.argtypes = [vp, ctypes.POINTER(Params), vp, vp, i, vp]
+    lib.cdg2_tri_apply.restype = i
     lib.cdg2_element_block.argtypes = [vp, ctypes.POINTER(Params), d, ctypes.c_longlong, i, dp]
     lib.cdg2_element_block.restype = i
     lib.cdg2_last_error.argtypes = []
@@ -290,6 +311,53 @@ def cdg2_element_block(mesh: Mesh, params, gdt: float, elem: int, species: int) 
     p = _params(params)
     _check(load_library().cdg2_element_block(mesh.handle, ctypes.byref(p), float(gdt), int(elem), int(species), out))
     return torch.tensor(list(out), dtype=torch.float64).reshape(nb, nb)
+
+
+class TriMesh:
+    """Owning handle of a cdg2_tri_mesh."""
+
+    def __init__(self, handle: int, k: int):
+        self.handle = handle
+        self.k = k
+        ne, nb, nd, nf = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load_library().cdg2_tri_mesh_info(handle, ctypes.byref(ne), ctypes.byref(nb), ctypes.byref(nd),
+                                                 ctypes.byref(nf)))
+        self.n_elem, self.n_basis, self.n_dof, self.n_faces = ne.value, nb.value, nd.value, nf.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.cdg2_tri_mesh_destroy(self.handle)
+            self.handle = None
+
+
+def cdg2_tri_mesh_create(xy, tri, k: int, chi_e: float = 0.0, gamma1_in=(0.375, 0.625)) -> TriMesh:
+    """Triangle mesh from vertex coordinates xy [n_v][2] and counter-clockwise triples tri [n_t][3]."""
+    import numpy as np
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int64)
+    d = TriDesc()
+    d.n_vert = xy.shape[0]
+    d.xy = xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.n_tri = tri.shape[0]
+    d.tri = tri.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
+    d.k = int(k)
+    d.chi_e = float(chi_e)
+    d.gamma1_in[0], d.gamma1_in[1] = float(gamma1_in[0]), float(gamma1_in[1])
+    h = ctypes.c_void_p()
+    _check(load_library().cdg2_tri_mesh_create(ctypes.byref(d), ctypes.byref(h)))
+    return TriMesh(h.value, int(k))
+
+
+def cdg2_tri_apply(mesh: TriMesh, params, U: torch.Tensor, out: torch.Tensor, flags: int = CDG2_MINV,
+                   stream=None) -> torch.Tensor:
+    """out = M^{-1} L_h(U) on a triangle mesh (float64 CUDA tensors of n_dof values)."""
+    for name, t in (("U", U), ("out", out)):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == mesh.n_dof):
+            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of {mesh.n_dof} values")
+    p = _params(params)
+    _check(load_library().cdg2_tri_apply(mesh.handle, ctypes.byref(p), ctypes.c_void_p(U.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), int(flags), _stream_ptr(stream)))
+    return out
 
 
 def _theta_ptr(dtheta):

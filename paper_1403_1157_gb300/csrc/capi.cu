@@ -74,7 +74,7 @@ static void legendre(int n, double t, double* P, double* dP) {
 
 // n-point Gauss-Legendre rule on [0,1]: Newton iteration on P_n from the
 // Chebyshev-like initial guesses cos(pi (i + 3/4) / (n + 1/2)).
-static void gauss01(int n, double* x, double* w) {
+void gauss01(int n, double* x, double* w) {
     double P[16], dP[16];
     for (int i = 0; i < n; ++i) {
         double t = std::cos(M_PI * (i + 0.75) / (n + 0.5));

@@ -66,6 +66,9 @@ struct Coef {
 
 Coef make_coef(const cdg2_params& p);
 
+// Gauss-Legendre rule with n points on [0,1] (ascending points, weights sum 1).
+void gauss01(int n, double* x, double* w);
+
 template <typename T>
 TabP<T> make_tabp(const Tab1D& t, const Geo& g) {
     TabP<T> p{};

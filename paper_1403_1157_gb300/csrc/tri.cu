@@ -1,0 +1,630 @@
+// The CDG2 operator on triangle meshes (Sec. 3.1: P_k on triangles, chi_e =
+// 1.5): f(U) = M^{-1} L_h(U) in FP64, face-once.
+//
+// Readings (shared with the oracle; the paper fixes none of them):
+//  * basis: on the reference triangle T = {xi, eta >= 0, xi + eta <= 1} the
+//    orthonormal Dubiner basis psi_pq = c_pq L_p(xi, eta) P_q^{(2p+1,0)}(2 eta
+//    - 1), L_p = (1 - eta)^p P_p(2 xi / (1 - eta) - 1), c_pq = sqrt(2 (2p+1)
+//    (p+q+1)), modes ordered by p + q then q; element e uses psi o F_e^{-1}
+//    with F_e(xi) = x_0 + J_e xi, so M_K = det J_e I;
+//  * quadrature: the collapsed Gauss rule, xi = u (1 - v), eta = v with k+2
+//    Gauss points per direction (u fastest), weight w_u w_v (1 - v); k+2
+//    Gauss points per edge;
+//  * K^-_e: the adjacent element with the smaller area (Sec. 3.1), areas
+//    within a relative 1e-12 tie and a tie goes to the lower index;
+//  * boundary edges on y = 0 are Gamma_1, on y = max y Gamma_2 (Eq. (3));
+//    every other boundary edge is a no-flow wall.
+// The CDG2 flux needs r_e([U]) . n^- on K^-: with M_{K^-} = det I the
+// lifting identity gives r . n (x_p) = -(|e| / (2 det_-)) sum_p' L[p][p']
+// Delta(x_p'), L[p][p'] = sum_i psi_i(x_p) psi_i(x_p') w_p', tabulated per
+// local edge of K^-.  Face points are listed in K^-'s orientation of the
+// edge; K^+ runs the edge the other way (both counter-clockwise), so its
+// point p is its own edge point k+1-p (the Gauss rule is symmetric).
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "physics.cuh"
+
+namespace cdg2 {
+
+constexpr int TMAXB = 10;   // basis functions for k = 3
+constexpr int TMAXQ = 25;   // volume points for k = 3
+constexpr int TMAXP = 5;    // edge points for k = 3
+
+// Tables in FP64 (device copy staged into shared memory by the kernels).
+struct TriTab {
+    double VB[TMAXQ][TMAXB];          // psi_i at the volume points
+    double VD[2][TMAXQ][TMAXB];       // d psi_i / d xi, d eta
+    double VW[TMAXQ];
+    double VX[TMAXQ][2];              // reference volume points
+    double EB[3][TMAXP][TMAXB];       // psi_i at edge l's points (t ascending from vertex l)
+    double ED[2][3][TMAXP][TMAXB];
+    double EW[TMAXP];
+    double ET[TMAXP];
+    double LF[3][TMAXP][TMAXP];       // lifting kernel of K^-'s edge l
+};
+
+// Element geometry: x0, y0, J (row-major), J^{-1} (row-major), det J.
+constexpr int GEO = 11;
+
+}  // namespace cdg2
+
+struct cdg2_tri_mesh {
+    int k = 0, nb = 0, nq = 0, np = 0;
+    long long E = 0, NF = 0;
+    double chi_e = 1.5, ly = 0.0;
+    double g1in[2] = {0.375, 0.625};
+    std::vector<double> geo;     // [E][GEO]
+    std::vector<int> emap;       // [E][3]: 2 face + side (0: K^-, 1: K^+), or -1 - tag (0 wall, 1 Gamma_1, 2 Gamma_2)
+    std::vector<int> face;       // [NF][4]: eM, eP, lM, lP
+    std::vector<double> fgeo;    // [NF][4]: n_x, n_y, |e|, det J of K^-
+    cdg2::TriTab tab;
+    // device copies, uploaded by the first apply (calls on one mesh must be ordered on one stream)
+    mutable double* d_geo = nullptr;
+    mutable int* d_emap = nullptr;
+    mutable int* d_face = nullptr;
+    mutable double* d_fgeo = nullptr;
+    mutable cdg2::TriTab* d_tab = nullptr;
+    mutable double* d_fbuf = nullptr;   // [NF][2][6][nb] tested face fluxes
+};
+
+namespace cdg2 {
+
+namespace {
+
+// Jacobi P_n^{(a,0)} and its derivative at x (three-term recurrence, DLMF
+// 18.9.1 with beta = 0, and its derivative).
+void jacobi_d(int n, double a, double x, double& P, double& dP) {
+    double p0 = 1.0, d0 = 0.0;
+    if (n == 0) {
+        P = p0;
+        dP = d0;
+        return;
+    }
+    double p1 = (a + 1.0) + (a + 2.0) * (x - 1.0) / 2.0, d1 = (a + 2.0) / 2.0;
+    for (int m = 2; m <= n; ++m) {
+        const double c = 2.0 * m + a;
+        const double a1 = 2.0 * m * (m + a) * (c - 2.0);
+        const double a2 = (c - 1.0) * c * (c - 2.0);
+        const double a3 = (c - 1.0) * a * a;
+        const double a4 = 2.0 * (m + a - 1.0) * (m - 1.0) * c;
+        const double p2 = ((a2 * x + a3) * p1 - a4 * p0) / a1;
+        const double d2 = ((a2 * x + a3) * d1 + a2 * p1 - a4 * d0) / a1;
+        p0 = p1;
+        d0 = d1;
+        p1 = p2;
+        d1 = d2;
+    }
+    P = p1;
+    dP = d1;
+}
+
+// psi_i and its reference gradient at (xi, eta).
+void dubiner(int k, double xi, double eta, double* psi, double* dxi, double* deta) {
+    const double s = 1.0 - eta, xt = 2.0 * xi - s;
+    double L[4], Lx[4], Ly[4];
+    L[0] = 1.0;
+    Lx[0] = 0.0;
+    Ly[0] = 0.0;
+    if (k >= 1) {
+        L[1] = xt;
+        Lx[1] = 2.0;
+        Ly[1] = 1.0;
+    }
+    for (int p = 2; p <= k; ++p) {
+        L[p] = ((2 * p - 1) * xt * L[p - 1] - (p - 1) * s * s * L[p - 2]) / p;
+        Lx[p] = ((2 * p - 1) * (2.0 * L[p - 1] + xt * Lx[p - 1]) - (p - 1) * s * s * Lx[p - 2]) / p;
+        Ly[p] = ((2 * p - 1) * (L[p - 1] + xt * Ly[p - 1]) - (p - 1) * (-2.0 * s * L[p - 2] + s * s * Ly[p - 2])) / p;
+    }
+    int i = 0;
+    for (int d = 0; d <= k; ++d)
+        for (int q = 0; q <= d; ++q, ++i) {
+            const int p = d - q;
+            const double c = std::sqrt(2.0 * (2 * p + 1) * (p + q + 1));
+            double J, dJ;
+            jacobi_d(q, 2.0 * p + 1.0, 2.0 * eta - 1.0, J, dJ);
+            psi[i] = c * L[p] * J;
+            dxi[i] = c * Lx[p] * J;
+            deta[i] = c * (Ly[p] * J + L[p] * 2.0 * dJ);
+        }
+}
+
+void ref_edge_point(int l, double t, double& xi, double& eta) {
+    if (l == 0) {
+        xi = t;
+        eta = 0.0;
+    } else if (l == 1) {
+        xi = 1.0 - t;
+        eta = t;
+    } else {
+        xi = 0.0;
+        eta = 1.0 - t;
+    }
+}
+
+void build_tables(int k, TriTab& T) {
+    std::memset(&T, 0, sizeof(T));
+    const int n = k + 2;
+    double g[16], w[16];
+    gauss01(n, g, w);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            const int q = i + n * j;
+            const double xi = g[i] * (1.0 - g[j]), eta = g[j];
+            T.VX[q][0] = xi;
+            T.VX[q][1] = eta;
+            T.VW[q] = w[i] * w[j] * (1.0 - g[j]);
+            dubiner(k, xi, eta, T.VB[q], T.VD[0][q], T.VD[1][q]);
+        }
+    for (int p = 0; p < n; ++p) {
+        T.EW[p] = w[p];
+        T.ET[p] = g[p];
+    }
+    const int nb = (k + 1) * (k + 2) / 2;
+    for (int l = 0; l < 3; ++l) {
+        for (int p = 0; p < n; ++p) {
+            double xi, eta;
+            ref_edge_point(l, g[p], xi, eta);
+            dubiner(k, xi, eta, T.EB[l][p], T.ED[0][l][p], T.ED[1][l][p]);
+        }
+        for (int p = 0; p < n; ++p)
+            for (int pp = 0; pp < n; ++pp) {
+                double acc = 0.0;
+                for (int i = 0; i < nb; ++i) acc += T.EB[l][p][i] * T.EB[l][pp][i];
+                T.LF[l][p][pp] = acc * w[pp];
+            }
+    }
+}
+
+}  // namespace
+
+}  // namespace cdg2
+
+namespace cdg2 {
+
+template <int K>
+struct TriShape {
+    static constexpr int NB = (K + 1) * (K + 2) / 2;
+    static constexpr int NQ = (K + 2) * (K + 2);
+    static constexpr int NP = K + 2;
+};
+
+struct TriArgs {
+    const double* U;
+    double* out;
+    int flags;
+    double chi_e;
+    long long E, NF;
+    const double* geo;
+    const int* emap;
+    const int* face;
+    const double* fgeo;
+    const TriTab* tab;
+    double* fbuf;
+    Geo g;               // only g1in is read (Gamma_{1,in})
+    CoefT<double> c;
+};
+
+__device__ __forceinline__ void load_tritab(TriTab& s, const TriTab* t) {
+    const double* src = reinterpret_cast<const double*>(t);
+    double* dst = reinterpret_cast<double*>(&s);
+    for (int i = threadIdx.x; i < (int)(sizeof(TriTab) / sizeof(double)); i += blockDim.x) dst[i] = src[i];
+}
+
+// One CTA: FPB interior edges.  Traces of both sides, the K^- lifting, the
+// face flux of Eq. surfaceint per point, and its test against both sides'
+// basis; the tested fluxes go to the face buffer ([face][side][6][nb]).
+template <int K, int FPB>
+__global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
+    using S = TriShape<K>;
+    constexpr int NB = S::NB, NP = S::NP;
+    __shared__ TriTab tb;
+    __shared__ double sU[FPB][2][NS][NB];
+    __shared__ double sG[FPB][2][4];         // J^{-1} of each side
+    __shared__ double sF[FPB][4];            // n_x, n_y, |e|, det_-
+    __shared__ int sI[FPB][4];               // eM, eP, lM, lP
+    __shared__ double sT[FPB][2][2][NS][NP];  // [side][value, normal derivative][s][p]
+    __shared__ double sS[FPB][2][NS][NP];     // sigma, tau
+    load_tritab(tb, a.tab);
+    const long long f0 = (long long)blockIdx.x * FPB;
+    const int nf = (int)min((long long)FPB, a.NF - f0);
+    for (int i = threadIdx.x; i < nf * 4; i += blockDim.x) {
+        const int j = i / 4, c = i % 4;
+        sI[j][c] = a.face[(f0 + j) * 4 + c];
+        sF[j][c] = a.fgeo[(f0 + j) * 4 + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf * 2 * 4; i += blockDim.x) {
+        const int j = i / 8, side = (i / 4) % 2, c = i % 4;
+        sG[j][side][c] = a.geo[(long long)sI[j][side] * GEO + 6 + c];
+    }
+    for (int i = threadIdx.x; i < nf * 2 * NS * NB; i += blockDim.x) {
+        const int j = i / (2 * NS * NB), side = (i / (NS * NB)) % 2, r = i % (NS * NB);
+        sU[j][side][r / NB][r % NB] = a.U[(long long)sI[j][side] * NS * NB + r];
+    }
+    __syncthreads();
+    // traces at the face points (K^-'s order; K^+ reads its own edge reversed)
+    for (int i = threadIdx.x; i < nf * 2 * NS * NP; i += blockDim.x) {
+        const int j = i / (2 * NS * NP), side = (i / (NS * NP)) % 2, s = (i / NP) % NS, p = i % NP;
+        const int l = sI[j][2 + side];
+        const int pp = side ? NP - 1 - p : p;
+        double v = 0.0, gx = 0.0, gy = 0.0;
+#pragma unroll
+        for (int m = 0; m < NB; ++m) {
+            const double u = sU[j][side][s][m];
+            v = fma(tb.EB[l][pp][m], u, v);
+            gx = fma(tb.ED[0][l][pp][m], u, gx);
+            gy = fma(tb.ED[1][l][pp][m], u, gy);
+        }
+        const double* Ji = sG[j][side];
+        const double dx = Ji[0] * gx + Ji[2] * gy, dy = Ji[1] * gx + Ji[3] * gy;
+        sT[j][side][0][s][p] = v;
+        sT[j][side][1][s][p] = sF[j][0] * dx + sF[j][1] * dy;
+    }
+    __syncthreads();
+    // pointwise flux with the lifted jump
+    for (int i = threadIdx.x; i < nf * NP; i += blockDim.x) {
+        const int j = i / NP, p = i % NP;
+        const int lM = sI[j][2];
+        const double lift = -sF[j][2] / (2.0 * sF[j][3]);
+        double uM[NS], dM[NS], uP[NS], dP[NS], del[NS], sig[NS], tau[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            uM[s] = sT[j][0][0][s][p];
+            dM[s] = sT[j][0][1][s][p];
+            uP[s] = sT[j][1][0][s][p];
+            dP[s] = sT[j][1][1][s][p];
+            del[s] = uM[s] - uP[s];
+        }
+        face_point<double>(a.c, 0.0, uM, dM, uP, dP, del, sig, tau);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            double rn = 0.0;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) rn = fma(tb.LF[lM][p][q], sT[j][0][0][s][q] - sT[j][1][0][s][q], rn);
+            sS[j][0][s][p] = sig[s] + 2.0 * a.chi_e * a.c.A[s] * lift * rn;
+            sS[j][1][s][p] = tau[s];
+        }
+    }
+    __syncthreads();
+    // test: K^- gets sigma phi^- + tau d_n phi^-, K^+ gets -sigma phi^+ + tau d_n phi^+
+    for (int i = threadIdx.x; i < nf * 2 * NS * NB; i += blockDim.x) {
+        const int j = i / (2 * NS * NB), side = (i / (NS * NB)) % 2, s = (i / NB) % NS, m = i % NB;
+        const int l = sI[j][2 + side];
+        const double* Ji = sG[j][side];
+        const double nx = sF[j][0], ny = sF[j][1];
+        double acc = 0.0;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const int pp = side ? NP - 1 - p : p;
+            const double gx = tb.ED[0][l][pp][m], gy = tb.ED[1][l][pp][m];
+            const double dn = nx * (Ji[0] * gx + Ji[2] * gy) + ny * (Ji[1] * gx + Ji[3] * gy);
+            const double ph = side ? -tb.EB[l][pp][m] : tb.EB[l][pp][m];
+            acc = fma(tb.EW[p], sS[j][0][s][p] * ph + sS[j][1][s][p] * dn, acc);
+        }
+        a.fbuf[((f0 + j) * 2 + side) * NS * NB + s * NB + m] = sF[j][2] * acc;
+    }
+}
+
+// One CTA: EPB elements.  Volume terms at the collapsed Gauss points, the
+// tested fluxes of the element's interior edges from the face buffer, the
+// boundary data of Eq. (3) on its boundary edges, M^{-1} = 1 / det J.
+template <int K, int EPB>
+__global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
+    using S = TriShape<K>;
+    constexpr int NB = S::NB, NQ = S::NQ, NP = S::NP;
+    __shared__ TriTab tb;
+    __shared__ double sU[EPB][NS][NB];
+    __shared__ double sG[EPB][GEO];
+    __shared__ double sPhi[EPB][NQ][NS][3];   // Phi_x, Phi_y, S
+    load_tritab(tb, a.tab);
+    const long long e0 = (long long)blockIdx.x * EPB;
+    const int ne = (int)min((long long)EPB, a.E - e0);
+    for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) sG[i / GEO][i % GEO] = a.geo[e0 * GEO + i];
+    for (int i = threadIdx.x; i < ne * NS * NB; i += blockDim.x) {
+        const int e = i / (NS * NB), r = i % (NS * NB);
+        sU[e][r / NB][r % NB] = a.U[e0 * NS * NB + i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ne * NQ; i += blockDim.x) {
+        const int e = i / NQ, q = i % NQ;
+        const double* Ji = sG[e] + 6;
+        double u[NS], g[NS][2], Phi[NS][2], Sr[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            double v = 0.0, gx = 0.0, gy = 0.0;
+#pragma unroll
+            for (int m = 0; m < NB; ++m) {
+                v = fma(tb.VB[q][m], sU[e][s][m], v);
+                gx = fma(tb.VD[0][q][m], sU[e][s][m], gx);
+                gy = fma(tb.VD[1][q][m], sU[e][s][m], gy);
+            }
+            u[s] = v;
+            g[s][0] = Ji[0] * gx + Ji[2] * gy;
+            g[s][1] = Ji[1] * gx + Ji[3] * gy;
+        }
+        volume_point<2, double>(a.c, u, g, Phi, Sr);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            sPhi[e][q][s][0] = Phi[s][0];
+            sPhi[e][q][s][1] = Phi[s][1];
+            sPhi[e][q][s][2] = Sr[s];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ne * NS * NB; i += blockDim.x) {
+        const int e = i / (NS * NB), s = (i / NB) % NS, m = i % NB;
+        const double* G = sG[e];
+        const double* Ji = G + 6;
+        const double det = G[10];
+        double acc = 0.0;
+#pragma unroll 5
+        for (int q = 0; q < NQ; ++q) {
+            const double gx = tb.VD[0][q][m], gy = tb.VD[1][q][m];
+            const double px = Ji[0] * gx + Ji[2] * gy, py = Ji[1] * gx + Ji[3] * gy;
+            acc = fma(tb.VW[q], sPhi[e][q][s][0] * px + sPhi[e][q][s][1] * py + sPhi[e][q][s][2] * tb.VB[q][m], acc);
+        }
+        double R = det * acc;
+        const long long ge = e0 + e;
+        for (int l = 0; l < 3; ++l) {
+            const int code = a.emap[ge * 3 + l];
+            if (code >= 0) {
+                R += a.fbuf[(long long)code * NS * NB + s * NB + m];
+            } else if (code != -1) {
+                // boundary edge l on Gamma_1 (code -2) or Gamma_2 (code -3)
+                const int f = -code - 2;
+                const double r0x = l == 1 ? 1.0 : 0.0, r0y = l == 2 ? 1.0 : 0.0;   // reference vertex l
+                const double r1x = l == 0 ? 1.0 : 0.0, r1y = l == 1 ? 1.0 : 0.0;   // reference vertex l + 1
+                const double Ax = G[0] + G[2] * r0x + G[3] * r0y, Ay = G[1] + G[4] * r0x + G[5] * r0y;
+                const double Bx = G[0] + G[2] * r1x + G[3] * r1y, By = G[1] + G[4] * r1x + G[5] * r1y;
+                const double len = sqrt((Bx - Ax) * (Bx - Ax) + (By - Ay) * (By - Ay));
+                double bacc = 0.0;
+                for (int p = 0; p < NP; ++p) {
+                    double uo[NS] = {0, 0, 0, 0, 0, 0}, sig[NS];
+                    double c1 = 0.0;
+#pragma unroll
+                    for (int mm = 0; mm < NB; ++mm) c1 = fma(tb.EB[l][p][mm], sU[e][3][mm], c1);
+                    uo[3] = c1;
+                    const double x = Ax + tb.ET[p] * (Bx - Ax);
+                    boundary_point<double>(a.c, f, x, a.g, uo, sig, a.c.beta1, true);
+                    bacc = fma(tb.EW[p], sig[s] * tb.EB[l][p][m], bacc);
+                }
+                R += len * bacc;
+            }
+        }
+        a.out[ge * NS * NB + s * NB + m] = (a.flags & CDG2_MINV) ? R / det : R;
+    }
+}
+
+}  // namespace cdg2
+
+namespace cdg2 {
+
+constexpr int TRI_FPB = 8;   // faces per CTA
+constexpr int TRI_EPB = 4;   // elements per CTA
+
+template <int K>
+static cudaError_t tri_launch(const TriArgs& a, cudaStream_t st) {
+    if (a.NF > 0) {
+        const unsigned fb = (unsigned)((a.NF + TRI_FPB - 1) / TRI_FPB);
+        tri_face_kernel<K, TRI_FPB><<<fb, 128, 0, st>>>(a);
+    }
+    const unsigned eb = (unsigned)((a.E + TRI_EPB - 1) / TRI_EPB);
+    tri_elem_kernel<K, TRI_EPB><<<eb, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+static int tri_upload(const cdg2_tri_mesh& m) {
+    if (m.d_tab) return CDG2_OK;
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void** dst, const void* src, size_t bytes) {
+        if (e != cudaSuccess) return;
+        e = cudaMalloc(dst, bytes > 0 ? bytes : 8);
+        if (e == cudaSuccess && src && bytes > 0) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up((void**)&m.d_geo, m.geo.data(), sizeof(double) * m.geo.size());
+    up((void**)&m.d_emap, m.emap.data(), sizeof(int) * m.emap.size());
+    up((void**)&m.d_face, m.face.data(), sizeof(int) * m.face.size());
+    up((void**)&m.d_fgeo, m.fgeo.data(), sizeof(double) * m.fgeo.size());
+    up((void**)&m.d_fbuf, nullptr, sizeof(double) * (size_t)m.NF * 2 * NS * m.nb);
+    up((void**)&m.d_tab, &m.tab, sizeof(TriTab));
+    if (e != cudaSuccess) return cuda_fail(e, "cdg2_tri_apply: mesh upload");
+    return CDG2_OK;
+}
+
+}  // namespace cdg2
+
+using namespace cdg2;
+
+extern "C" int cdg2_tri_mesh_create(const cdg2_tri_desc* d, cdg2_tri_mesh** out) {
+    if (!d || !out || !d->xy || !d->tri) {
+        set_error("cdg2_tri_mesh_create: NULL argument");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (d->k < 1 || d->k > 3 || d->n_vert < 3 || d->n_tri < 1 || d->n_tri > (1LL << 29)) {
+        set_error("cdg2_tri_mesh_create: need 1 <= k <= 3, n_vert >= 3, 1 <= n_tri < 2^29");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    auto* m = new (std::nothrow) cdg2_tri_mesh;
+    if (!m) {
+        set_error("cdg2_tri_mesh_create: out of host memory");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    m->k = d->k;
+    m->nb = (d->k + 1) * (d->k + 2) / 2;
+    m->nq = (d->k + 2) * (d->k + 2);
+    m->np = d->k + 2;
+    m->E = d->n_tri;
+    m->chi_e = d->chi_e > 0.0 ? d->chi_e : 1.5;
+    m->g1in[0] = d->gamma1_in[0];
+    m->g1in[1] = d->gamma1_in[1];
+    const double* xy = d->xy;
+    double ly = xy[1];
+    for (long long v = 0; v < d->n_vert; ++v) ly = std::max(ly, xy[2 * v + 1]);
+    m->ly = ly;
+    m->geo.assign((size_t)m->E * GEO, 0.0);
+    for (long long e = 0; e < m->E; ++e) {
+        long long v[3];
+        for (int j = 0; j < 3; ++j) {
+            v[j] = d->tri[3 * e + j];
+            if (v[j] < 0 || v[j] >= d->n_vert) {
+                delete m;
+                set_error("cdg2_tri_mesh_create: vertex index out of range");
+                return CDG2_ERR_INVALID_ARG;
+            }
+        }
+        const double x0 = xy[2 * v[0]], y0 = xy[2 * v[0] + 1];
+        const double J00 = xy[2 * v[1]] - x0, J01 = xy[2 * v[2]] - x0;
+        const double J10 = xy[2 * v[1] + 1] - y0, J11 = xy[2 * v[2] + 1] - y0;
+        const double det = J00 * J11 - J01 * J10;
+        if (!(det > 0.0)) {
+            delete m;
+            set_error("cdg2_tri_mesh_create: triangle " + std::to_string(e) +
+                      " is degenerate or clockwise (vertices must be counter-clockwise)");
+            return CDG2_ERR_INVALID_ARG;
+        }
+        double* G = &m->geo[(size_t)e * GEO];
+        G[0] = x0;
+        G[1] = y0;
+        G[2] = J00;
+        G[3] = J01;
+        G[4] = J10;
+        G[5] = J11;
+        G[6] = J11 / det;
+        G[7] = -J01 / det;
+        G[8] = -J10 / det;
+        G[9] = J00 / det;
+        G[10] = det;
+    }
+    // edges: sorted vertex pair -> owners (element, local edge)
+    std::map<std::pair<long long, long long>, std::vector<std::pair<long long, int>>> edges;
+    for (long long e = 0; e < m->E; ++e)
+        for (int l = 0; l < 3; ++l) {
+            const long long a = d->tri[3 * e + l], b = d->tri[3 * e + (l + 1) % 3];
+            edges[{std::min(a, b), std::max(a, b)}].push_back({e, l});
+        }
+    m->emap.assign((size_t)m->E * 3, -1);
+    const double tol = 1e-12 * std::max(1.0, ly);
+    for (const auto& kv : edges) {
+        const auto& own = kv.second;
+        if (own.size() == 2) {
+            long long e1 = own[0].first, e2 = own[1].first;
+            int l1 = own[0].second, l2 = own[1].second;
+            const long long a1 = d->tri[3 * e1 + l1], a2 = d->tri[3 * e2 + l2];
+            if (a1 == a2) {
+                delete m;
+                set_error("cdg2_tri_mesh_create: neighbouring triangles with inconsistent orientation");
+                return CDG2_ERR_INVALID_ARG;
+            }
+            const double ar1 = m->geo[(size_t)e1 * GEO + 10], ar2 = m->geo[(size_t)e2 * GEO + 10];
+            const bool tie = std::fabs(ar1 - ar2) <= 1e-12 * std::max(ar1, ar2);
+            if (!((!tie && ar1 < ar2) || (tie && e1 < e2))) {
+                std::swap(e1, e2);
+                std::swap(l1, l2);
+            }
+            const long long f = (long long)m->face.size() / 4;
+            m->face.insert(m->face.end(), {(int)e1, (int)e2, l1, l2});
+            const long long va = d->tri[3 * e1 + l1], vb = d->tri[3 * e1 + (l1 + 1) % 3];
+            const double dx = xy[2 * vb] - xy[2 * va], dy = xy[2 * vb + 1] - xy[2 * va + 1];
+            const double len = std::sqrt(dx * dx + dy * dy);
+            m->fgeo.insert(m->fgeo.end(), {dy / len, -dx / len, len, m->geo[(size_t)e1 * GEO + 10]});
+            m->emap[(size_t)e1 * 3 + l1] = (int)(2 * f);
+            m->emap[(size_t)e2 * 3 + l2] = (int)(2 * f + 1);
+        } else if (own.size() == 1) {
+            const double ya = xy[2 * kv.first.first + 1], yb = xy[2 * kv.first.second + 1];
+            int tag = 0;
+            if (std::fabs(ya) <= tol && std::fabs(yb) <= tol) tag = 1;
+            else if (std::fabs(ya - ly) <= tol && std::fabs(yb - ly) <= tol) tag = 2;
+            m->emap[(size_t)own[0].first * 3 + own[0].second] = -1 - tag;
+        } else {
+            delete m;
+            set_error("cdg2_tri_mesh_create: an edge is shared by more than two triangles");
+            return CDG2_ERR_INVALID_ARG;
+        }
+    }
+    m->NF = (long long)m->face.size() / 4;
+    build_tables(m->k, m->tab);
+    *out = m;
+    return CDG2_OK;
+}
+
+extern "C" void cdg2_tri_mesh_destroy(cdg2_tri_mesh* m) {
+    if (!m) return;
+    cudaFree(m->d_geo);
+    cudaFree(m->d_emap);
+    cudaFree(m->d_face);
+    cudaFree(m->d_fgeo);
+    cudaFree(m->d_fbuf);
+    cudaFree(m->d_tab);
+    delete m;
+}
+
+extern "C" int cdg2_tri_mesh_info(const cdg2_tri_mesh* m, long long* n_elem, int* n_basis, long long* n_dof,
+                                  long long* n_faces) {
+    if (!m) {
+        set_error("cdg2_tri_mesh_info: NULL mesh");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (n_elem) *n_elem = m->E;
+    if (n_basis) *n_basis = m->nb;
+    if (n_dof) *n_dof = m->E * NS * m->nb;
+    if (n_faces) *n_faces = m->NF;
+    return CDG2_OK;
+}
+
+extern "C" int cdg2_tri_apply(const cdg2_tri_mesh* m, const cdg2_params* p, const double* U, double* out, int flags,
+                              void* stream) {
+    if (!m || !p || !U || !out) {
+        set_error("cdg2_tri_apply: NULL argument");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (U == out) {
+        set_error("cdg2_tri_apply: U and out must not overlap");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (flags & ~CDG2_MINV) {
+        set_error("cdg2_tri_apply: only CDG2_MINV is supported on triangle meshes");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (int rc = tri_upload(*m)) return rc;
+    TriArgs a;
+    a.U = U;
+    a.out = out;
+    a.flags = flags;
+    a.chi_e = m->chi_e;
+    a.E = m->E;
+    a.NF = m->NF;
+    a.geo = m->d_geo;
+    a.emap = m->d_emap;
+    a.face = m->d_face;
+    a.fgeo = m->d_fgeo;
+    a.tab = m->d_tab;
+    a.fbuf = m->d_fbuf;
+    Geo g;
+    std::memset(&g, 0, sizeof(g));
+    g.dim = 2;
+    g.k = m->k;
+    g.vol = 1.0;
+    for (int j = 0; j < 3; ++j) {
+        g.h[j] = 1.0;
+        g.n[j] = 1;
+    }
+    g.g1in[0] = m->g1in[0];
+    g.g1in[1] = m->g1in[1];
+    a.g = g;
+    a.c = make_coefT<double>(make_coef(*p), g, nullptr);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    switch (m->k) {
+        case 1: e = tri_launch<1>(a, st); break;
+        case 2: e = tri_launch<2>(a, st); break;
+        default: e = tri_launch<3>(a, st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cdg2_tri_apply");
+    return CDG2_OK;
+}

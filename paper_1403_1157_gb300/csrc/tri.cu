@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
     __shared__ double sF[FPB][4];            // n_x, n_y, |e|, det_-
     __shared__ int sI[FPB][4];               // eM, eP, lM, lP
     __shared__ double sT[FPB][2][2][NS][NP];  // [side][value, normal derivative][s][p]
+    __shared__ double sDN[FPB][2][NP][NB];    // n^- . grad phi_m of each side at the face points
     __shared__ double sS[FPB][2][NS][NP];     // sigma, tau
     load_tritab(tb, a.tab);
     const long long f0 = (long long)blockIdx.x * FPB;
@@ -246,24 +247,30 @@ __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
         const int j = i / (2 * NS * NB), side = (i / (NS * NB)) % 2, r = i % (NS * NB);
         sU[j][side][r / NB][r % NB] = a.U[(long long)sI[j][side] * NS * NB + r];
     }
+    // normal derivatives of the basis at the face points (K^-'s order; K^+ reads its edge reversed)
+    for (int i = threadIdx.x; i < nf * 2 * NP * NB; i += blockDim.x) {
+        const int j = i / (2 * NP * NB), side = (i / (NP * NB)) % 2, p = (i / NB) % NP, m = i % NB;
+        const int l = sI[j][2 + side];
+        const int pp = side ? NP - 1 - p : p;
+        const double* Ji = sG[j][side];
+        const double gx = tb.ED[0][l][pp][m], gy = tb.ED[1][l][pp][m];
+        sDN[j][side][p][m] = sF[j][0] * (Ji[0] * gx + Ji[2] * gy) + sF[j][1] * (Ji[1] * gx + Ji[3] * gy);
+    }
     __syncthreads();
-    // traces at the face points (K^-'s order; K^+ reads its own edge reversed)
+    // traces at the face points
     for (int i = threadIdx.x; i < nf * 2 * NS * NP; i += blockDim.x) {
         const int j = i / (2 * NS * NP), side = (i / (NS * NP)) % 2, s = (i / NP) % NS, p = i % NP;
         const int l = sI[j][2 + side];
         const int pp = side ? NP - 1 - p : p;
-        double v = 0.0, gx = 0.0, gy = 0.0;
+        double v = 0.0, dn = 0.0;
 #pragma unroll
         for (int m = 0; m < NB; ++m) {
             const double u = sU[j][side][s][m];
             v = fma(tb.EB[l][pp][m], u, v);
-            gx = fma(tb.ED[0][l][pp][m], u, gx);
-            gy = fma(tb.ED[1][l][pp][m], u, gy);
+            dn = fma(sDN[j][side][p][m], u, dn);
         }
-        const double* Ji = sG[j][side];
-        const double dx = Ji[0] * gx + Ji[2] * gy, dy = Ji[1] * gx + Ji[3] * gy;
         sT[j][side][0][s][p] = v;
-        sT[j][side][1][s][p] = sF[j][0] * dx + sF[j][1] * dy;
+        sT[j][side][1][s][p] = dn;
     }
     __syncthreads();
     // pointwise flux with the lifted jump
@@ -295,16 +302,12 @@ __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
     for (int i = threadIdx.x; i < nf * 2 * NS * NB; i += blockDim.x) {
         const int j = i / (2 * NS * NB), side = (i / (NS * NB)) % 2, s = (i / NB) % NS, m = i % NB;
         const int l = sI[j][2 + side];
-        const double* Ji = sG[j][side];
-        const double nx = sF[j][0], ny = sF[j][1];
         double acc = 0.0;
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             const int pp = side ? NP - 1 - p : p;
-            const double gx = tb.ED[0][l][pp][m], gy = tb.ED[1][l][pp][m];
-            const double dn = nx * (Ji[0] * gx + Ji[2] * gy) + ny * (Ji[1] * gx + Ji[3] * gy);
             const double ph = side ? -tb.EB[l][pp][m] : tb.EB[l][pp][m];
-            acc = fma(tb.EW[p], sS[j][0][s][p] * ph + sS[j][1][s][p] * dn, acc);
+            acc = fma(tb.EW[p], fma(sS[j][0][s][p], ph, sS[j][1][s][p] * sDN[j][side][p][m]), acc);
         }
         a.fbuf[((f0 + j) * 2 + side) * NS * NB + s * NB + m] = sF[j][2] * acc;
     }
@@ -321,6 +324,7 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
     __shared__ double sU[EPB][NS][NB];
     __shared__ double sG[EPB][GEO];
     __shared__ double sPhi[EPB][NQ][NS][3];   // Phi_x, Phi_y, S
+    __shared__ double sGP[EPB][NQ][NB][2];    // physical gradients of the basis at the points
     load_tritab(tb, a.tab);
     const long long e0 = (long long)blockIdx.x * EPB;
     const int ne = (int)min((long long)EPB, a.E - e0);
@@ -330,9 +334,16 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
         sU[e][r / NB][r % NB] = a.U[e0 * NS * NB + i];
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < ne * NQ * NB; i += blockDim.x) {
+        const int e = i / (NQ * NB), q = (i / NB) % NQ, m = i % NB;
+        const double* Ji = sG[e] + 6;
+        const double gx = tb.VD[0][q][m], gy = tb.VD[1][q][m];
+        sGP[e][q][m][0] = Ji[0] * gx + Ji[2] * gy;
+        sGP[e][q][m][1] = Ji[1] * gx + Ji[3] * gy;
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < ne * NQ; i += blockDim.x) {
         const int e = i / NQ, q = i % NQ;
-        const double* Ji = sG[e] + 6;
         double u[NS], g[NS][2], Phi[NS][2], Sr[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
@@ -340,12 +351,12 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
 #pragma unroll
             for (int m = 0; m < NB; ++m) {
                 v = fma(tb.VB[q][m], sU[e][s][m], v);
-                gx = fma(tb.VD[0][q][m], sU[e][s][m], gx);
-                gy = fma(tb.VD[1][q][m], sU[e][s][m], gy);
+                gx = fma(sGP[e][q][m][0], sU[e][s][m], gx);
+                gy = fma(sGP[e][q][m][1], sU[e][s][m], gy);
             }
             u[s] = v;
-            g[s][0] = Ji[0] * gx + Ji[2] * gy;
-            g[s][1] = Ji[1] * gx + Ji[3] * gy;
+            g[s][0] = gx;
+            g[s][1] = gy;
         }
         volume_point<2, double>(a.c, u, g, Phi, Sr);
 #pragma unroll
@@ -359,14 +370,13 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
     for (int i = threadIdx.x; i < ne * NS * NB; i += blockDim.x) {
         const int e = i / (NS * NB), s = (i / NB) % NS, m = i % NB;
         const double* G = sG[e];
-        const double* Ji = G + 6;
         const double det = G[10];
         double acc = 0.0;
 #pragma unroll 5
         for (int q = 0; q < NQ; ++q) {
-            const double gx = tb.VD[0][q][m], gy = tb.VD[1][q][m];
-            const double px = Ji[0] * gx + Ji[2] * gy, py = Ji[1] * gx + Ji[3] * gy;
-            acc = fma(tb.VW[q], sPhi[e][q][s][0] * px + sPhi[e][q][s][1] * py + sPhi[e][q][s][2] * tb.VB[q][m], acc);
+            const double t = fma(sPhi[e][q][s][0], sGP[e][q][m][0],
+                                 fma(sPhi[e][q][s][1], sGP[e][q][m][1], sPhi[e][q][s][2] * tb.VB[q][m]));
+            acc = fma(tb.VW[q], t, acc);
         }
         double R = det * acc;
         const long long ge = e0 + e;

@@ -29,19 +29,22 @@ METRIC = "L_h apply GDOF/s FP64 vs mixed at stated error; VJP GDOF/s; % HBM roof
 def apply_flops_per_element(dim: int, k: int) -> int:
     """Floating-point operations per element of one FP64 apply (face-once path).
 
-    Counted from the kernels' loops (an FMA is 2 flops; an add, multiply or
-    divide 1).  The 1D passes split even and odd modes (mirror symmetry of
-    the Legendre modes at the symmetric Gauss rule): a forward line (k+1
-    modes to k+2 points) costs H (2b + 2) + 2 m flops with H = q // 2 point
+    Counted from the kernels' loops as they run (an FMA is 2 flops; an add,
+    multiply or divide 1).  The 1D passes split even and odd modes (mirror
+    symmetry of the Legendre modes at the symmetric Gauss rule): a forward line
+    (k+1 modes to k+2 points) costs H (2b + 2) + 2 m flops with H = q // 2 point
     pairs and m the modes of the matrix's parity at the middle point; a
     transposed line 2H + 2Hb + 2m, a two-matrix transposed line 4H + 4Hb + 2b.
-    Element kernel: interpolation of U and grad U, the pointwise volume flux
-    (43 + 34 d per point, the four sensitivities inverted together), the
-    transposed test passes, and per axis the normal expansion of its two
-    faces' tested fluxes.  Face kernel, one face per element and axis: normal
-    contraction (owning trace, jump, both normal derivatives), tangential
-    interpolation of 4 fields, the pointwise face flux (126 per point, eight
-    sensitivities inverted together), tangential test of 2 fields.
+    Element kernel: values of all six species at the Gauss points, gradients
+    of n1, c1, c3 only; the pointwise flux (43 + 28 d per point: the four
+    sensitivities inverted together, Phi formed for n1 and n2 only); the test
+    with grad phi for n1, n2 and with phi alone for n3..c3; the diffusion of
+    n2..c3 in modal form (the nonzero entries of the 1D stiffness: same parity,
+    both modes > 0); per axis the normal expansion of its two faces' tested
+    fluxes.  Face kernel, one face per element and axis: normal contraction
+    (owning trace, jump, both normal derivatives), tangential interpolation of
+    4 fields, the pointwise face flux (126 per point, eight sensitivities
+    inverted together), tangential test of 2 fields.
     """
     b, q, d, s = k + 1, k + 2, dim, 6
     H, mid = q // 2, q % 2
@@ -55,18 +58,25 @@ def apply_flops_per_element(dim: int, k: int) -> int:
 
     tr2 = 4 * H + 4 * H * b + mid * 2 * b
     if d == 2:
-        interp = b * (fwd(1) + fwd(-1)) + q * (2 * fwd(1) + fwd(-1))
-        test = q * (tr2 + tr(1)) + b * tr2
+        values = b * fwd(1) + q * fwd(1)
+        grads = b * fwd(-1) + q * (fwd(1) + fwd(-1))
+        test_grad = q * (tr2 + tr(1)) + b * tr2
+        test_val = q * tr(1) + b * tr(1)
         tang = 4 * fwd(1) + 2 * tr(1)
     else:
-        interp = b * b * (fwd(1) + fwd(-1)) + q * b * (2 * fwd(1) + fwd(-1)) + q * q * (3 * fwd(1) + fwd(-1))
-        test = q * q * (tr2 + 2 * tr(1)) + q * b * (tr2 + tr(1)) + b * b * tr2
+        values = b * b * fwd(1) + q * b * fwd(1) + q * q * fwd(1)
+        grads = b * b * fwd(-1) + q * b * (fwd(1) + fwd(-1)) + q * q * (2 * fwd(1) + fwd(-1))
+        test_grad = q * q * (tr2 + 2 * tr(1)) + q * b * (tr2 + tr(1)) + b * b * tr2
+        test_val = q * q * tr(1) + q * b * tr(1) + b * b * tr(1)
         tang = 4 * (b * fwd(1) + q * fwd(1)) + 2 * (q * tr(1) + b * tr(1))
+    nz = [0] + [len(range(1 if a % 2 else 2, b, 2)) for a in range(1, b)]   # stiffness entries per row
+    modal = sum(2 * nz[a] for a in range(b)) * d * b ** (d - 1) + 2 * b ** d
     normal = b ** (d - 1) * (2 * (5 * b - 2) + 1)
     expand = 8 * b ** d
-    per_species = interp + test + d * (normal + tang + expand)
-    pointwise = q ** d * (43 + 34 * d) + d * q ** (d - 1) * 126
-    return s * per_species + pointwise
+    volume = 6 * values + 3 * grads + 2 * test_grad + 4 * test_val + 5 * modal
+    faces = s * d * (normal + tang + expand)
+    pointwise = q ** d * (43 + 28 * d) + d * q ** (d - 1) * 126
+    return volume + faces + pointwise
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP64 apply (its face and
@@ -74,7 +84,8 @@ def apply_flops_per_element(dim: int, k: int) -> int:
 # valid only for the kernel sources the counters were taken with (first 16 hex
 # of their sha256).
 NCU_TRAFFIC = {("2D 256x64 Q3 manufactured solution", "double"): (50643211, "10d8deda10165d5d")}
-KERNEL_SOURCES = ("paper_1403_1157_gb300/csrc/operator.cu", "paper_1403_1157_gb300/csrc/elem_common.cuh")
+KERNEL_SOURCES = ("paper_1403_1157_gb300/csrc/operator.cu", "paper_1403_1157_gb300/csrc/elem_common.cuh",
+                  "paper_1403_1157_gb300/csrc/physics.cuh")
 
 
 def kernel_source_hash() -> str:

@@ -38,6 +38,7 @@ struct TabP {
     T xi[MAXQ];
     T e[2][MAXK + 1];             // psi_a(0), psi_a(1)
     T dh[3][2][MAXK + 1];         // psi'_a(0) / h_j, psi'_a(1) / h_j
+    T K1h[3][MAXK + 1][MAXK + 1]; // sum_q w_q psi'_a psi'_b / h_j^2 (exact 1D stiffness)
 };
 
 // Uniform Cartesian geometry (Sec. 3.1 tessellation, read as boxes).
@@ -88,6 +89,12 @@ TabP<T> make_tabp(const Tab1D& t, const Geo& g) {
         for (int a = 0; a <= MAXK; ++a) {
             p.e[f][a] = (T)t.e[f][a];
             for (int j = 0; j < 3; ++j) p.dh[j][f][a] = (T)(t.d[f][a] / g.h[j]);
+        }
+    for (int a = 0; a <= MAXK; ++a)
+        for (int b = 0; b <= MAXK; ++b) {
+            double k1 = 0.0;
+            for (int q = 0; q < MAXQ; ++q) k1 += t.w[q] * t.D[q][a] * t.D[q][b];
+            for (int j = 0; j < 3; ++j) p.K1h[j][a][b] = (T)(k1 / (g.h[j] * g.h[j]));
         }
     return p;
 }

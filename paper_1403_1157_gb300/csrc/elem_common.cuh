@@ -34,6 +34,7 @@ struct STab {
     T xi[K + 2];
     T e[2][K + 1];           // psi_a(0), psi_a(1)
     T dh[3][2][K + 1];       // psi'_a(0) / h_j, psi'_a(1) / h_j
+    T K1h[3][K + 1][K + 1];  // int_0^1 psi'_a psi'_b / h_j^2 (1D stiffness, exact)
 };
 
 template <int K, typename T>
@@ -57,6 +58,10 @@ __device__ __forceinline__ void load_tab(STab<K, T>& s, const TabP<T>& t) {
         s.e[f][a] = t.e[f][a];
 #pragma unroll
         for (int j = 0; j < 3; ++j) s.dh[j][f][a] = t.dh[j][f][a];
+    }
+    for (int i = threadIdx.x; i < 3 * (K + 1) * (K + 1); i += blockDim.x) {
+        const int j = i / ((K + 1) * (K + 1)), a = (i / (K + 1)) % (K + 1), b = i % (K + 1);
+        s.K1h[j][a][b] = t.K1h[j][a][b];
     }
 }
 
@@ -107,6 +112,38 @@ struct Ident {
 };
 
 // One sum-factorisation pass over nt tensors stored back to back.
+// Species subsets of the forward volume terms (the diffusion of n2..c3 is
+// applied in modal form, see op_kernel): 0 all six; 1 {n1, c1, c3}, whose
+// gradients the fluxes need at the points; 2 {n1, n2}, the fluxes tested with
+// grad phi; 3 {n3, c1, c2, c3}, tested with phi only; 4 {n2, .., c3}.
+template <int SEL>
+struct SpeciesSet;
+template <>
+struct SpeciesSet<0> {
+    static constexpr int N = NS;
+    __device__ static constexpr int s(int k) { return k; }
+};
+template <>
+struct SpeciesSet<1> {
+    static constexpr int N = 3;
+    __device__ static constexpr int s(int k) { return k == 0 ? 0 : (k == 1 ? 3 : 5); }
+};
+template <>
+struct SpeciesSet<2> {
+    static constexpr int N = 2;
+    __device__ static constexpr int s(int k) { return k; }
+};
+template <>
+struct SpeciesSet<3> {
+    static constexpr int N = 4;
+    __device__ static constexpr int s(int k) { return k + 2; }
+};
+template <>
+struct SpeciesSet<4> {
+    static constexpr int N = 5;
+    __device__ static constexpr int s(int k) { return k + 1; }
+};
+
 // One 1D pass of sum factorisation.  Input tensors have extents (I0, I1, I2)
 // (x fastest); axis AX (extent NI) is replaced by NO in the output:
 //     out[t][..o..] = sum_i M1(o,i) in1[t][..i..]  (+ M2(o,i) in2[t][..i..])
@@ -120,8 +157,10 @@ struct Ident {
 // Forward: out(q) and out(NQ-1-q) are E +- O with E, O the sums over the even
 // and odd modes.  Transposed: the inputs are paired as x(q) +- x(NQ-1-q) and
 // each mode takes the pair combination of its parity.  For k = 3 this is 14
-// operations per line and matrix instead of 20.
-template <int AX, int I0, int I1, int I2, int NO, bool TR, int LD, bool TWO, int P1, int P2, typename T>
+// operations per line and matrix instead of 20.  SEL restricts the pass to
+// the species of SpeciesSet<SEL>: tensor t is then (t / N, species s(t % N))
+// of an element-major [..][6] layout, and nt counts only those tensors.
+template <int AX, int I0, int I1, int I2, int NO, bool TR, int LD, bool TWO, int P1, int P2, typename T, int SEL = 0>
 __device__ __forceinline__ void sf_sym(const T* __restrict__ in1, const T* __restrict__ M1,
                                        const typename Ident<T>::type* __restrict__ in2,
                                        const typename Ident<T>::type* __restrict__ M2, int in_stride,
@@ -158,8 +197,10 @@ __device__ __forceinline__ void sf_sym(const T* __restrict__ in1, const T* __res
             ib = r;
             ob = r;
         }
-        const T* s1 = in1 + tt * in_stride + ib;
-        T* d = out + tt * out_stride + ob;
+        using SS = SpeciesSet<SEL>;
+        const int tm = SEL == 0 ? tt : (tt / SS::N) * NS + SS::s(tt % SS::N);
+        const T* s1 = in1 + tm * in_stride + ib;
+        T* d = out + tm * out_stride + ob;
         if constexpr (!TR) {
             T v[NM];
 #pragma unroll
@@ -191,7 +232,7 @@ __device__ __forceinline__ void sf_sym(const T* __restrict__ in1, const T* __res
             }
             if constexpr (MID) mid1 = s1[H * ST];
             if constexpr (TWO) {
-                const T* s2 = in2 + tt * in_stride + ib;
+                const T* s2 = in2 + tm * in_stride + ib;
 #pragma unroll
                 for (int q = 0; q < H; ++q) {
                     const T x = s2[q * ST], y = s2[(NQ - 1 - q) * ST];

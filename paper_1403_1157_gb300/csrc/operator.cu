@@ -684,34 +684,43 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const TabP<T> tab,
     T* X1 = X0 + P::XSZ;
     T* Y = X1 + P::XSZ;
     T* Q = Y + 3 * P::YSZ;   // D + 1 slots of F*EPB*NS tensors: u, g_0, .., g_{D-1}
+    // FP64 forward modes apply the diffusion of n2..c3 in modal form (after the
+    // test): gradients are interpolated for n1, c1, c3 only (GS), values for
+    // all.  (It saves FP64 pipe work; the FP32 kernels are bound by issue and
+    // shared-memory traffic instead, and its extra loop made them slower.)
+    constexpr bool MODAL = MODE != MODE_VJP && sizeof(T) == 8;
+    constexpr int GS = MODAL ? 1 : 0;
     const int nt = F * EPB * NS;
+    const int ng = F * EPB * SpeciesSet<GS>::N;
     if constexpr (D == 2) {
         sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(sU, &tb.B[0][0], nullptr, nullptr, NB, X0, NQ1 * NB1, nt);
-        sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, -1, 1>(sU, &tb.Dh[0][0][0], nullptr, nullptr, NB, X1, NQ1 * NB1, nt);
+        sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, -1, 1, T, GS>(sU, &tb.Dh[0][0][0], nullptr, nullptr, NB, X1,
+                                                                      NQ1 * NB1, ng);
         __syncthreads();
         sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(X0, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, Q, NQ, nt);
-        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(X1, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1,
-                                                           Q + P::QSZ, NQ, nt);
-        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, -1, 1>(X0, &tb.Dh[1][0][0], nullptr, nullptr, NQ1 * NB1,
-                                                           Q + 2 * P::QSZ, NQ, nt);
+        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1, T, GS>(X1, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1,
+                                                                     Q + P::QSZ, NQ, ng);
+        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, -1, 1, T, GS>(X0, &tb.Dh[1][0][0], nullptr, nullptr, NQ1 * NB1,
+                                                                      Q + 2 * P::QSZ, NQ, ng);
     } else {
         constexpr int XS = NQ1 * NB1 * NB1, YS = NQ1 * NQ1 * NB1;
         sf_sym<0, NB1, NB1, NB1, NQ1, false, K + 1, false, 1, 1>(sU, &tb.B[0][0], nullptr, nullptr, NB, X0, XS, nt);
-        sf_sym<0, NB1, NB1, NB1, NQ1, false, K + 1, false, -1, 1>(sU, &tb.Dh[0][0][0], nullptr, nullptr, NB, X1, XS, nt);
+        sf_sym<0, NB1, NB1, NB1, NQ1, false, K + 1, false, -1, 1, T, GS>(sU, &tb.Dh[0][0][0], nullptr, nullptr, NB, X1,
+                                                                        XS, ng);
         __syncthreads();
         sf_sym<1, NQ1, NB1, NB1, NQ1, false, K + 1, false, 1, 1>(X0, &tb.B[0][0], nullptr, nullptr, XS, Y, YS, nt);
-        sf_sym<1, NQ1, NB1, NB1, NQ1, false, K + 1, false, 1, 1>(X1, &tb.B[0][0], nullptr, nullptr, XS, Y + P::YSZ, YS,
-                                                             nt);
-        sf_sym<1, NQ1, NB1, NB1, NQ1, false, K + 1, false, -1, 1>(X0, &tb.Dh[1][0][0], nullptr, nullptr, XS,
-                                                             Y + 2 * P::YSZ, YS, nt);
+        sf_sym<1, NQ1, NB1, NB1, NQ1, false, K + 1, false, 1, 1, T, GS>(X1, &tb.B[0][0], nullptr, nullptr, XS,
+                                                                       Y + P::YSZ, YS, ng);
+        sf_sym<1, NQ1, NB1, NB1, NQ1, false, K + 1, false, -1, 1, T, GS>(X0, &tb.Dh[1][0][0], nullptr, nullptr, XS,
+                                                                        Y + 2 * P::YSZ, YS, ng);
         __syncthreads();
         sf_sym<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false, 1, 1>(Y, &tb.B[0][0], nullptr, nullptr, YS, Q, NQ, nt);
-        sf_sym<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false, 1, 1>(Y + P::YSZ, &tb.B[0][0], nullptr, nullptr, YS,
-                                                             Q + P::QSZ, NQ, nt);
-        sf_sym<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false, 1, 1>(Y + 2 * P::YSZ, &tb.B[0][0], nullptr, nullptr, YS,
-                                                             Q + 2 * P::QSZ, NQ, nt);
-        sf_sym<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false, -1, 1>(Y, &tb.Dh[2][0][0], nullptr, nullptr, YS, Q + 3 * P::QSZ,
-                                                             NQ, nt);
+        sf_sym<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false, 1, 1, T, GS>(Y + P::YSZ, &tb.B[0][0], nullptr, nullptr, YS,
+                                                                       Q + P::QSZ, NQ, ng);
+        sf_sym<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false, 1, 1, T, GS>(Y + 2 * P::YSZ, &tb.B[0][0], nullptr, nullptr,
+                                                                       YS, Q + 2 * P::QSZ, NQ, ng);
+        sf_sym<2, NQ1, NQ1, NB1, NQ1, false, K + 1, false, -1, 1, T, GS>(Y, &tb.Dh[2][0][0], nullptr, nullptr, YS,
+                                                                        Q + 3 * P::QSZ, NQ, ng);
     }
     __syncthreads();
 
@@ -724,25 +733,27 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const TabP<T> tab,
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             u[s] = Q[(e * NS + s) * NQ + q];
+            const bool have = !MODAL || s == 0 || s == 3 || s == 5;   // interpolated gradients
 #pragma unroll
-            for (int j = 0; j < D; ++j) gr[s][j] = Q[(j + 1) * P::QSZ + (e * NS + s) * NQ + q];
+            for (int j = 0; j < D; ++j) gr[s][j] = have ? Q[(j + 1) * P::QSZ + (e * NS + s) * NQ + q] : T(0);
         }
         const int q0 = q % NQ1, q1 = (q / NQ1) % NQ1, q2 = q / (NQ1 * NQ1);
         T wq = tb.w[q0] * tb.w[q1];
         if constexpr (D == 3) wq *= tb.w[q2];
         const T Wq = wq * c.vol;
         if constexpr (MODE == MODE_APPLY) {
-            volume_point<D, T>(c, u, gr, Phi, Sr);
+            volume_point<D, T, MODAL>(c, u, gr, Phi, Sr);
         } else {
             T du[NS], dg[NS][D];
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 du[s] = Q[OFF + (e * NS + s) * NQ + q];
+                const bool have = !MODAL || s == 0 || s == 3 || s == 5;
 #pragma unroll
-                for (int j = 0; j < D; ++j) dg[s][j] = Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q];
+                for (int j = 0; j < D; ++j) dg[s][j] = have ? Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q] : T(0);
             }
             if constexpr (MODE == MODE_JVP) {
-                volume_point_lin<D, T>(c, u, gr, du, dg, args.has_dtheta != 0, Phi, Sr);
+                volume_point_lin<D, T, MODAL>(c, u, gr, du, dg, args.has_dtheta != 0, Phi, Sr);
             } else {
                 // du, dg are mu and grad mu here; weighted they are the cotangents of S and Phi
 #pragma unroll
@@ -778,8 +789,10 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const TabP<T> tab,
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             Q[OFF + (e * NS + s) * NQ + q] = Sr[s];   // weights and 1/h live in the test tables
+            if (s < 2 || !MODAL) {                      // (modal: only n1, n2 are tested with grad phi)
 #pragma unroll
-            for (int j = 0; j < D; ++j) Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q] = Phi[s][j];
+                for (int j = 0; j < D; ++j) Q[(j + 1) * P::QSZ + OFF + (e * NS + s) * NQ + q] = Phi[s][j];
+            }
         }
     }
     __syncthreads();
@@ -793,34 +806,99 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const TabP<T> tab,
     const T* TD0 = MODE == MODE_VJP ? &tb.Dh[0][0][0] : &tb.Dwh[0][0][0];
     const T* TD1 = MODE == MODE_VJP ? &tb.Dh[1][0][0] : &tb.Dwh[1][0][0];
     const T* TD2 = MODE == MODE_VJP ? &tb.Dh[2][0][0] : &tb.Dwh[2][0][0];
-    if constexpr (D == 2) {
-        // Y0 = B^T_y S' + D^T_y Phi_y',  Y1 = B^T_y Phi_x'
-        T* Y0 = X0;
-        T* Y1 = X1;
-        sf_sym<1, NQ1, NQ1, 1, NB1, true, K + 1, true, 1, -1>(Qo, TB, Qo + 2 * P::QSZ, TD1, NQ, Y0,
-                                                         NQ1 * NB1, nto);
-        sf_sym<1, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(Qo + P::QSZ, TB, nullptr, nullptr, NQ, Y1,
-                                                          NQ1 * NB1, nto);
+    if constexpr (MODAL) {
+        // n1, n2 (set 2): phi and grad phi; n3..c3 (set 3): phi only
+        constexpr int N2 = SpeciesSet<2>::N, N3 = SpeciesSet<3>::N;
+        if constexpr (D == 2) {
+            T* Y0 = X0;
+            T* Y1 = X1;
+            sf_sym<1, NQ1, NQ1, 1, NB1, true, K + 1, true, 1, -1, T, 2>(Qo, TB, Qo + 2 * P::QSZ, TD1, NQ, Y0,
+                                                                       NQ1 * NB1, EPB * N2);
+            sf_sym<1, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1, T, 2>(Qo + P::QSZ, TB, nullptr, nullptr, NQ, Y1,
+                                                                       NQ1 * NB1, EPB * N2);
+            sf_sym<1, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1, T, 3>(Qo, TB, nullptr, nullptr, NQ, Y0, NQ1 * NB1,
+                                                                       EPB * N3);
+            __syncthreads();
+            sf_sym<0, NQ1, NB1, 1, NB1, true, K + 1, true, 1, -1, T, 2>(Y0, TB, Y1, TD0, NQ1 * NB1, sR, NB, EPB * N2);
+            sf_sym<0, NQ1, NB1, 1, NB1, true, K + 1, false, 1, 1, T, 3>(Y0, TB, nullptr, nullptr, NQ1 * NB1, sR, NB,
+                                                                       EPB * N3);
+        } else {
+            constexpr int ZS = NQ1 * NQ1 * NB1, XS = NQ1 * NB1 * NB1;
+            T* Z0 = Y;
+            T* Z1 = Y + P::YSZ;
+            T* Z2 = Y + 2 * P::YSZ;
+            sf_sym<2, NQ1, NQ1, NQ1, NB1, true, K + 1, true, 1, -1, T, 2>(Qo, TB, Qo + 3 * P::QSZ, TD2, NQ, Z0, ZS,
+                                                                         EPB * N2);
+            sf_sym<2, NQ1, NQ1, NQ1, NB1, true, K + 1, false, 1, 1, T, 2>(Qo + 2 * P::QSZ, TB, nullptr, nullptr, NQ, Z1,
+                                                                         ZS, EPB * N2);
+            sf_sym<2, NQ1, NQ1, NQ1, NB1, true, K + 1, false, 1, 1, T, 2>(Qo + P::QSZ, TB, nullptr, nullptr, NQ, Z2, ZS,
+                                                                         EPB * N2);
+            sf_sym<2, NQ1, NQ1, NQ1, NB1, true, K + 1, false, 1, 1, T, 3>(Qo, TB, nullptr, nullptr, NQ, Z0, ZS,
+                                                                         EPB * N3);
+            __syncthreads();
+            T* Y0 = X0;
+            T* Y1 = X1;
+            sf_sym<1, NQ1, NQ1, NB1, NB1, true, K + 1, true, 1, -1, T, 2>(Z0, TB, Z1, TD1, ZS, Y0, XS, EPB * N2);
+            sf_sym<1, NQ1, NQ1, NB1, NB1, true, K + 1, false, 1, 1, T, 2>(Z2, TB, nullptr, nullptr, ZS, Y1, XS, EPB * N2);
+            sf_sym<1, NQ1, NQ1, NB1, NB1, true, K + 1, false, 1, 1, T, 3>(Z0, TB, nullptr, nullptr, ZS, Y0, XS, EPB * N3);
+            __syncthreads();
+            sf_sym<0, NQ1, NB1, NB1, NB1, true, K + 1, true, 1, -1, T, 2>(Y0, TB, Y1, TD0, XS, sR, NB, EPB * N2);
+            sf_sym<0, NQ1, NB1, NB1, NB1, true, K + 1, false, 1, 1, T, 3>(Y0, TB, nullptr, nullptr, XS, sR, NB,
+                                                                         EPB * N3);
+        }
         __syncthreads();
-        sf_sym<0, NQ1, NB1, 1, NB1, true, K + 1, true, 1, -1>(Y0, TB, Y1, TD0, NQ1 * NB1, sR, NB, nto);
+        // Diffusion of n2..c3 in modal form: their flux -A_s grad U_s tested with
+        // grad phi is, by exact quadrature on the orthonormal tensor basis,
+        // -A_s sum_j (K1_j (x) I) U_s with K1_j[a][b] = int psi'_a psi'_b / h_j^2
+        // (zero unless a = b mod 2 and a, b > 0).
+        const T* Uf = sU + (F - 1) * P::UR;
+        for (int idx = threadIdx.x; idx < EPB * SpeciesSet<4>::N * NB; idx += blockDim.x) {
+            const int i = idx % NB, es = idx / NB;
+            const int e = es / SpeciesSet<4>::N, s = SpeciesSet<4>::s(es % SpeciesSet<4>::N);
+            const T* u = Uf + (e * NS + s) * NB;
+            T acc = T(0);
+            int stride = 1, rest = i;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const int a = rest % NB1;
+                rest /= NB1;
+                const int base = i - a * stride;
+                for (int bb = (a & 1) ? 1 : 2; a > 0 && bb <= K; bb += 2) acc = fma(tb.K1h[j][a][bb], u[base + bb * stride], acc);
+                stride *= NB1;
+            }
+            sR[(e * NS + s) * NB + i] = fma(-T(c.A[s]), acc, sR[(e * NS + s) * NB + i]);
+        }
     } else {
-        constexpr int ZS = NQ1 * NQ1 * NB1, XS = NQ1 * NB1 * NB1;
-        T* Z0 = Y;
-        T* Z1 = Y + P::YSZ;
-        T* Z2 = Y + 2 * P::YSZ;
-        sf_sym<2, NQ1, NQ1, NQ1, NB1, true, K + 1, true, 1, -1>(Qo, TB, Qo + 3 * P::QSZ, TD2, NQ, Z0, ZS,
-                                                           nto);
-        sf_sym<2, NQ1, NQ1, NQ1, NB1, true, K + 1, false, 1, 1>(Qo + 2 * P::QSZ, TB, nullptr, nullptr, NQ, Z1,
-                                                            ZS, nto);
-        sf_sym<2, NQ1, NQ1, NQ1, NB1, true, K + 1, false, 1, 1>(Qo + P::QSZ, TB, nullptr, nullptr, NQ, Z2, ZS,
-                                                            nto);
+        if constexpr (D == 2) {
+            // Y0 = B^T_y S' + D^T_y Phi_y',  Y1 = B^T_y Phi_x'
+            T* Y0 = X0;
+            T* Y1 = X1;
+            sf_sym<1, NQ1, NQ1, 1, NB1, true, K + 1, true, 1, -1>(Qo, TB, Qo + 2 * P::QSZ, TD1, NQ, Y0,
+                                                             NQ1 * NB1, nto);
+            sf_sym<1, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(Qo + P::QSZ, TB, nullptr, nullptr, NQ, Y1,
+                                                              NQ1 * NB1, nto);
+            __syncthreads();
+            sf_sym<0, NQ1, NB1, 1, NB1, true, K + 1, true, 1, -1>(Y0, TB, Y1, TD0, NQ1 * NB1, sR, NB, nto);
+        } else {
+            constexpr int ZS = NQ1 * NQ1 * NB1, XS = NQ1 * NB1 * NB1;
+            T* Z0 = Y;
+            T* Z1 = Y + P::YSZ;
+            T* Z2 = Y + 2 * P::YSZ;
+            sf_sym<2, NQ1, NQ1, NQ1, NB1, true, K + 1, true, 1, -1>(Qo, TB, Qo + 3 * P::QSZ, TD2, NQ, Z0, ZS,
+                                                               nto);
+            sf_sym<2, NQ1, NQ1, NQ1, NB1, true, K + 1, false, 1, 1>(Qo + 2 * P::QSZ, TB, nullptr, nullptr, NQ, Z1,
+                                                                ZS, nto);
+            sf_sym<2, NQ1, NQ1, NQ1, NB1, true, K + 1, false, 1, 1>(Qo + P::QSZ, TB, nullptr, nullptr, NQ, Z2, ZS,
+                                                                nto);
+            __syncthreads();
+            T* Y0 = X0;
+            T* Y1 = X1;
+            sf_sym<1, NQ1, NQ1, NB1, NB1, true, K + 1, true, 1, -1>(Z0, TB, Z1, TD1, ZS, Y0, XS, nto);
+            sf_sym<1, NQ1, NQ1, NB1, NB1, true, K + 1, false, 1, 1>(Z2, TB, nullptr, nullptr, ZS, Y1, XS, nto);
+            __syncthreads();
+            sf_sym<0, NQ1, NB1, NB1, NB1, true, K + 1, true, 1, -1>(Y0, TB, Y1, TD0, XS, sR, NB, nto);
+        }
         __syncthreads();
-        T* Y0 = X0;
-        T* Y1 = X1;
-        sf_sym<1, NQ1, NQ1, NB1, NB1, true, K + 1, true, 1, -1>(Z0, TB, Z1, TD1, ZS, Y0, XS, nto);
-        sf_sym<1, NQ1, NQ1, NB1, NB1, true, K + 1, false, 1, 1>(Z2, TB, nullptr, nullptr, ZS, Y1, XS, nto);
-        __syncthreads();
-        sf_sym<0, NQ1, NB1, NB1, NB1, true, K + 1, true, 1, -1>(Y0, TB, Y1, TD0, XS, sR, NB, nto);
     }
     __syncthreads();
 

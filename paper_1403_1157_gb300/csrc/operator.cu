@@ -47,7 +47,8 @@ struct OpPlan {
     static constexpr int XSZ = F * EPB * NS * NQ1 * ipow(NB1, D - 1);
     static constexpr int YSZ = D == 3 ? F * EPB * NS * NQ1 * NQ1 * NB1 : 0;
     static constexpr int QSZ = F * EPB * NS * S::NQ;
-    static constexpr int VOL = (D + 1) * QSZ + 2 * XSZ + 3 * YSZ;
+    // 3D: the point values Q overlay X (dead once Y is formed): Y | X / Q
+    static constexpr int VOL = D == 3 ? 3 * YSZ + cmax(2 * XSZ, (D + 1) * QSZ) : (D + 1) * QSZ + 2 * XSZ;
     // face phase (the two faces normal to one axis)
     static constexpr int FC = F * EPB * 2 * 4 * NS * S::NBT;
     static constexpr int FT = D == 3 ? F * EPB * 2 * 4 * NS * NQ1 * NB1 : 0;
@@ -680,10 +681,12 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const TabP<T> tab,
     __syncthreads();
 
     // ---- volume: U, grad U (of every input field) at the Gauss points ----
-    T* X0 = W;
+    // 2D: X0 | X1 | Q.  3D: Y | X0 X1, with Q over X (X is dead once Y is
+    // formed, and Q once the test's first pass has read it).
+    T* Y = D == 3 ? W : W + 2 * P::XSZ;
+    T* X0 = D == 3 ? W + 3 * P::YSZ : W;
     T* X1 = X0 + P::XSZ;
-    T* Y = X1 + P::XSZ;
-    T* Q = Y + 3 * P::YSZ;   // D + 1 slots of F*EPB*NS tensors: u, g_0, .., g_{D-1}
+    T* Q = D == 3 ? X0 : W + 2 * P::XSZ;   // D + 1 slots of F*EPB*NS tensors: u, g_0, .., g_{D-1}
     // FP64 forward modes apply the diffusion of n2..c3 in modal form (after the
     // test): gradients are interpolated for n1, c1, c3 only (GS), values for
     // all.  (It saves FP64 pipe work; the FP32 kernels are bound by issue and

@@ -83,7 +83,7 @@ def apply_flops_per_element(dim: int, k: int) -> int:
 # element kernels), from one ncu capture (profiles/), keyed by workload and
 # valid only for the kernel sources the counters were taken with (first 16 hex
 # of their sha256).
-NCU_TRAFFIC = {("2D 256x64 Q3 manufactured solution", "double"): (50643211, "10d8deda10165d5d")}
+NCU_TRAFFIC = {("2D 256x64 Q3 manufactured solution", "double"): (50636477, "6d354302f83ea1ce")}
 KERNEL_SOURCES = ("paper_1403_1157_gb300/csrc/operator.cu", "paper_1403_1157_gb300/csrc/elem_common.cuh",
                   "paper_1403_1157_gb300/csrc/physics.cuh")
 

@@ -195,6 +195,7 @@ struct TriShape {
 
 struct TriArgs {
     const double* U;
+    const double* dU;    // JVP: the tangent
     double* out;
     int flags;
     double chi_e;
@@ -215,21 +216,30 @@ __device__ __forceinline__ void load_tritab(TriTab& s, const TriTab* t) {
     for (int i = threadIdx.x; i < (int)(sizeof(TriTab) / sizeof(double)); i += blockDim.x) dst[i] = src[i];
 }
 
+constexpr int TRI_APPLY = 0, TRI_JVP = 1, TRI_VJP = 2;
+
 // One CTA: FPB interior edges.  Traces of both sides, the K^- lifting, the
-// face flux of Eq. surfaceint per point, and its test against both sides'
-// basis; the tested fluxes go to the face buffer ([face][side][6][nb]).
-template <int K, int FPB>
+// face flux of Eq. surfaceint per point (JVP: its linearisation along the
+// tangent; the lifting is linear), and its test against both sides' basis;
+// the tested fluxes go to the face buffer ([face][side][6][nb]).  VJP: with
+// mu = M^{-1} lambda (or lambda) the cotangents of sigma and tau at point p
+// are |e| w_p (mu^- - mu^+) and |e| w_p (d_n mu^- + d_n mu^+); they go back
+// through face_point (face_point_adj, per side) and the lifting (its
+// transpose), and each side's trace cotangents are tested into the buffer.
+template <int K, int FPB, int MODE>
 __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
     using S = TriShape<K>;
-    constexpr int NB = S::NB, NP = S::NP;
+    constexpr int NB = S::NB, NP = S::NP, F = MODE == TRI_APPLY ? 1 : 2;
     __shared__ TriTab tb;
-    __shared__ double sU[FPB][2][NS][NB];
+    __shared__ double sU[FPB][2][F][NS][NB];
     __shared__ double sG[FPB][2][4];         // J^{-1} of each side
     __shared__ double sF[FPB][4];            // n_x, n_y, |e|, det_-
     __shared__ int sI[FPB][4];               // eM, eP, lM, lP
-    __shared__ double sT[FPB][2][2][NS][NP];  // [side][value, normal derivative][s][p]
+    __shared__ double sT[FPB][2][F][2][NS][NP];  // [side][field][value, normal derivative][s][p]
     __shared__ double sDN[FPB][2][NP][NB];    // n^- . grad phi_m of each side at the face points
-    __shared__ double sS[FPB][2][NS][NP];     // sigma, tau
+    __shared__ double sS[FPB][2][NS][NP];     // sigma, tau (VJP: their cotangents)
+    __shared__ double sA[MODE == TRI_VJP ? FPB : 1][2][2][NS][NP];   // VJP: [side][value, d_n] trace cotangents
+    __shared__ double sDet[FPB][2];
     load_tritab(tb, a.tab);
     const long long f0 = (long long)blockIdx.x * FPB;
     const int nf = (int)min((long long)FPB, a.NF - f0);
@@ -242,11 +252,14 @@ __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
     for (int i = threadIdx.x; i < nf * 2 * 4; i += blockDim.x) {
         const int j = i / 8, side = (i / 4) % 2, c = i % 4;
         sG[j][side][c] = a.geo[(long long)sI[j][side] * GEO + 6 + c];
+        if (c == 0) sDet[j][side] = a.geo[(long long)sI[j][side] * GEO + 10];
     }
-    for (int i = threadIdx.x; i < nf * 2 * NS * NB; i += blockDim.x) {
-        const int j = i / (2 * NS * NB), side = (i / (NS * NB)) % 2, r = i % (NS * NB);
-        sU[j][side][r / NB][r % NB] = a.U[(long long)sI[j][side] * NS * NB + r];
+    for (int i = threadIdx.x; i < nf * 2 * F * NS * NB; i += blockDim.x) {
+        const int j = i / (2 * F * NS * NB), side = (i / (F * NS * NB)) % 2, fi = (i / (NS * NB)) % F;
+        const int r = i % (NS * NB);
+        sU[j][side][fi][r / NB][r % NB] = (fi ? a.dU : a.U)[(long long)sI[j][side] * NS * NB + r];
     }
+    __syncthreads();   // sG, sDet and sU are read by other threads below
     // normal derivatives of the basis at the face points (K^-'s order; K^+ reads its edge reversed)
     for (int i = threadIdx.x; i < nf * 2 * NP * NB; i += blockDim.x) {
         const int j = i / (2 * NP * NB), side = (i / (NP * NB)) % 2, p = (i / NB) % NP, m = i % NB;
@@ -258,21 +271,80 @@ __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
     }
     __syncthreads();
     // traces at the face points
-    for (int i = threadIdx.x; i < nf * 2 * NS * NP; i += blockDim.x) {
-        const int j = i / (2 * NS * NP), side = (i / (NS * NP)) % 2, s = (i / NP) % NS, p = i % NP;
+    for (int i = threadIdx.x; i < nf * 2 * F * NS * NP; i += blockDim.x) {
+        const int j = i / (2 * F * NS * NP), side = (i / (F * NS * NP)) % 2, fi = (i / (NS * NP)) % F;
+        const int s = (i / NP) % NS, p = i % NP;
         const int l = sI[j][2 + side];
         const int pp = side ? NP - 1 - p : p;
         double v = 0.0, dn = 0.0;
 #pragma unroll
         for (int m = 0; m < NB; ++m) {
-            const double u = sU[j][side][s][m];
+            const double u = sU[j][side][fi][s][m];
             v = fma(tb.EB[l][pp][m], u, v);
             dn = fma(sDN[j][side][p][m], u, dn);
         }
-        sT[j][side][0][s][p] = v;
-        sT[j][side][1][s][p] = dn;
+        // VJP: the cotangent field enters as mu = M^{-1} lambda = lambda / det J (with CDG2_MINV)
+        const double sc = (MODE == TRI_VJP && fi == 1 && (a.flags & CDG2_MINV)) ? 1.0 / sDet[j][side] : 1.0;
+        sT[j][side][fi][0][s][p] = v * sc;
+        sT[j][side][fi][1][s][p] = dn * sc;
     }
     __syncthreads();
+    if constexpr (MODE == TRI_VJP) {
+        // cotangents of sigma and tau at every face point
+        for (int i = threadIdx.x; i < nf * NS * NP; i += blockDim.x) {
+            const int j = i / (NS * NP), s = (i / NP) % NS, p = i % NP;
+            const double W = sF[j][2] * tb.EW[p];
+            sS[j][0][s][p] = W * (sT[j][0][1][0][s][p] - sT[j][1][1][0][s][p]);
+            sS[j][1][s][p] = W * (sT[j][0][1][1][s][p] + sT[j][1][1][1][s][p]);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nf * NP; i += blockDim.x) {
+            const int j = i / NP, q = i % NP;
+            const int lM = sI[j][2];
+            const double lift = -sF[j][2] / (2.0 * sF[j][3]);
+            double uM[NS], dM[NS], uP[NS], dP[NS], del[NS], sb[NS], tbb[NS], ub[NS], db[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                uM[s] = sT[j][0][0][0][s][q];
+                dM[s] = sT[j][0][0][1][s][q];
+                uP[s] = sT[j][1][0][0][s][q];
+                dP[s] = sT[j][1][0][1][s][q];
+                del[s] = uM[s] - uP[s];
+                sb[s] = sS[j][0][s][q];
+                tbb[s] = sS[j][1][s][q];
+            }
+            // the lifting's transpose: Delta(q) feeds sigma(p) through lift LF[p][q]
+            double lb[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                double acc = 0.0;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) acc = fma(sS[j][0][s][p], tb.LF[lM][p][q], acc);
+                lb[s] = 2.0 * a.chi_e * a.c.A[s] * lift * acc;
+            }
+            for (int side = 0; side < 2; ++side) {
+                face_point_adj<double>(a.c, 0.0, side == 0, uM, dM, uP, dP, del, sb, tbb, ub, db);
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    sA[j][side][0][s][q] = ub[s] + (side == 0 ? lb[s] : -lb[s]);
+                    sA[j][side][1][s][q] = db[s];
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nf * 2 * NS * NB; i += blockDim.x) {
+            const int j = i / (2 * NS * NB), side = (i / (NS * NB)) % 2, s = (i / NB) % NS, m = i % NB;
+            const int l = sI[j][2 + side];
+            double acc = 0.0;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int pp = side ? NP - 1 - p : p;
+                acc = fma(sA[j][side][0][s][p], tb.EB[l][pp][m], fma(sA[j][side][1][s][p], sDN[j][side][p][m], acc));
+            }
+            a.fbuf[((f0 + j) * 2 + side) * NS * NB + s * NB + m] = acc;
+        }
+        return;
+    }
     // pointwise flux with the lifted jump
     for (int i = threadIdx.x; i < nf * NP; i += blockDim.x) {
         const int j = i / NP, p = i % NP;
@@ -281,18 +353,33 @@ __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
         double uM[NS], dM[NS], uP[NS], dP[NS], del[NS], sig[NS], tau[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            uM[s] = sT[j][0][0][s][p];
-            dM[s] = sT[j][0][1][s][p];
-            uP[s] = sT[j][1][0][s][p];
-            dP[s] = sT[j][1][1][s][p];
+            uM[s] = sT[j][0][0][0][s][p];
+            dM[s] = sT[j][0][0][1][s][p];
+            uP[s] = sT[j][1][0][0][s][p];
+            dP[s] = sT[j][1][0][1][s][p];
             del[s] = uM[s] - uP[s];
         }
-        face_point<double>(a.c, 0.0, uM, dM, uP, dP, del, sig, tau);
+        if constexpr (MODE == TRI_APPLY) {
+            face_point<double>(a.c, 0.0, uM, dM, uP, dP, del, sig, tau);
+        } else {
+            double duM[NS], ddM[NS], duP[NS], ddP[NS], ddel[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                duM[s] = sT[j][0][F - 1][0][s][p];
+                ddM[s] = sT[j][0][F - 1][1][s][p];
+                duP[s] = sT[j][1][F - 1][0][s][p];
+                ddP[s] = sT[j][1][F - 1][1][s][p];
+                ddel[s] = duM[s] - duP[s];
+            }
+            face_point_lin<double>(a.c, 0.0, uM, dM, uP, dP, del, duM, ddM, duP, ddP, ddel, sig, tau);
+        }
+        // the lifting of the (tangent) jump of the last field
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             double rn = 0.0;
 #pragma unroll
-            for (int q = 0; q < NP; ++q) rn = fma(tb.LF[lM][p][q], sT[j][0][0][s][q] - sT[j][1][0][s][q], rn);
+            for (int q = 0; q < NP; ++q)
+                rn = fma(tb.LF[lM][p][q], sT[j][0][F - 1][0][s][q] - sT[j][1][F - 1][0][s][q], rn);
             sS[j][0][s][p] = sig[s] + 2.0 * a.chi_e * a.c.A[s] * lift * rn;
             sS[j][1][s][p] = tau[s];
         }
@@ -313,15 +400,16 @@ __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
     }
 }
 
-// One CTA: EPB elements.  Volume terms at the collapsed Gauss points, the
-// tested fluxes of the element's interior edges from the face buffer, the
-// boundary data of Eq. (3) on its boundary edges, M^{-1} = 1 / det J.
-template <int K, int EPB>
+// One CTA: EPB elements.  Volume terms at the collapsed Gauss points (JVP:
+// linearised), the tested fluxes of the element's interior edges from the
+// face buffer, the boundary data of Eq. (3) on its boundary edges (JVP: none,
+// H' = 0), M^{-1} = 1 / det J.
+template <int K, int EPB, int MODE>
 __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
     using S = TriShape<K>;
-    constexpr int NB = S::NB, NQ = S::NQ, NP = S::NP;
+    constexpr int NB = S::NB, NQ = S::NQ, NP = S::NP, F = MODE == TRI_APPLY ? 1 : 2;
     __shared__ TriTab tb;
-    __shared__ double sU[EPB][NS][NB];
+    __shared__ double sU[EPB][F][NS][NB];
     __shared__ double sG[EPB][GEO];
     __shared__ double sPhi[EPB][NQ][NS][3];   // Phi_x, Phi_y, S
     __shared__ double sGP[EPB][NQ][NB][2];    // physical gradients of the basis at the points
@@ -329,9 +417,10 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
     const long long e0 = (long long)blockIdx.x * EPB;
     const int ne = (int)min((long long)EPB, a.E - e0);
     for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) sG[i / GEO][i % GEO] = a.geo[e0 * GEO + i];
-    for (int i = threadIdx.x; i < ne * NS * NB; i += blockDim.x) {
-        const int e = i / (NS * NB), r = i % (NS * NB);
-        sU[e][r / NB][r % NB] = a.U[e0 * NS * NB + i];
+    for (int i = threadIdx.x; i < F * ne * NS * NB; i += blockDim.x) {
+        const int fi = i / (ne * NS * NB), r0 = i % (ne * NS * NB);
+        const int e = r0 / (NS * NB), r = r0 % (NS * NB);
+        sU[e][fi][r / NB][r % NB] = (fi ? a.dU : a.U)[e0 * NS * NB + r0];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ne * NQ * NB; i += blockDim.x) {
@@ -344,21 +433,41 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
     __syncthreads();
     for (int i = threadIdx.x; i < ne * NQ; i += blockDim.x) {
         const int e = i / NQ, q = i % NQ;
-        double u[NS], g[NS][2], Phi[NS][2], Sr[NS];
+        double u[F][NS], g[F][NS][2], Phi[NS][2], Sr[NS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            double v = 0.0, gx = 0.0, gy = 0.0;
+        for (int fi = 0; fi < F; ++fi)
 #pragma unroll
-            for (int m = 0; m < NB; ++m) {
-                v = fma(tb.VB[q][m], sU[e][s][m], v);
-                gx = fma(sGP[e][q][m][0], sU[e][s][m], gx);
-                gy = fma(sGP[e][q][m][1], sU[e][s][m], gy);
+            for (int s = 0; s < NS; ++s) {
+                double v = 0.0, gx = 0.0, gy = 0.0;
+#pragma unroll
+                for (int m = 0; m < NB; ++m) {
+                    v = fma(tb.VB[q][m], sU[e][fi][s][m], v);
+                    gx = fma(sGP[e][q][m][0], sU[e][fi][s][m], gx);
+                    gy = fma(sGP[e][q][m][1], sU[e][fi][s][m], gy);
+                }
+                u[fi][s] = v;
+                g[fi][s][0] = gx;
+                g[fi][s][1] = gy;
             }
-            u[s] = v;
-            g[s][0] = gx;
-            g[s][1] = gy;
+        if constexpr (MODE == TRI_APPLY) {
+            volume_point<2, double>(a.c, u[0], g[0], Phi, Sr);
+        } else if constexpr (MODE == TRI_JVP) {
+            volume_point_lin<2, double>(a.c, u[0], g[0], u[F - 1], g[F - 1], false, Phi, Sr);
+        } else {
+            // cotangents of S and Phi at the point: det w_q mu and det w_q grad mu,
+            // mu = M^{-1} lambda = lambda / det (with CDG2_MINV); back through the
+            // flux (w_q is applied by the test loop below)
+            const double det = sG[e][10];
+            const double W = (a.flags & CDG2_MINV) ? 1.0 : det;
+            double sb[NS], gb[NS][2], th[8];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                sb[s] = W * u[F - 1][s];
+                gb[s][0] = W * g[F - 1][s][0];
+                gb[s][1] = W * g[F - 1][s][1];
+            }
+            volume_point_adj<2, double>(a.c, u[0], g[0], sb, gb, Sr, Phi, th);   // Sr <- ub, Phi <- Gb
         }
-        volume_point<2, double>(a.c, u, g, Phi, Sr);
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             sPhi[e][q][s][0] = Phi[s][0];
@@ -378,13 +487,14 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
                                  fma(sPhi[e][q][s][1], sGP[e][q][m][1], sPhi[e][q][s][2] * tb.VB[q][m]));
             acc = fma(tb.VW[q], t, acc);
         }
-        double R = det * acc;
+        // forward: R = det sum_q w_q (Phi . grad phi + S phi); VJP: the cotangents carry det
+        double R = MODE == TRI_VJP ? acc : det * acc;
         const long long ge = e0 + e;
         for (int l = 0; l < 3; ++l) {
             const int code = a.emap[ge * 3 + l];
             if (code >= 0) {
                 R += a.fbuf[(long long)code * NS * NB + s * NB + m];
-            } else if (code != -1) {
+            } else if (MODE == TRI_APPLY && code != -1) {
                 // boundary edge l on Gamma_1 (code -2) or Gamma_2 (code -3)
                 const int f = -code - 2;
                 const double r0x = l == 1 ? 1.0 : 0.0, r0y = l == 2 ? 1.0 : 0.0;   // reference vertex l
@@ -397,7 +507,7 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
                     double uo[NS] = {0, 0, 0, 0, 0, 0}, sig[NS];
                     double c1 = 0.0;
 #pragma unroll
-                    for (int mm = 0; mm < NB; ++mm) c1 = fma(tb.EB[l][p][mm], sU[e][3][mm], c1);
+                    for (int mm = 0; mm < NB; ++mm) c1 = fma(tb.EB[l][p][mm], sU[e][0][3][mm], c1);
                     uo[3] = c1;
                     const double x = Ax + tb.ET[p] * (Bx - Ax);
                     boundary_point<double>(a.c, f, x, a.g, uo, sig, a.c.beta1, true);
@@ -406,7 +516,7 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
                 R += len * bacc;
             }
         }
-        a.out[ge * NS * NB + s * NB + m] = (a.flags & CDG2_MINV) ? R / det : R;
+        a.out[ge * NS * NB + s * NB + m] = (MODE != TRI_VJP && (a.flags & CDG2_MINV)) ? R / det : R;
     }
 }
 
@@ -414,17 +524,17 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
 
 namespace cdg2 {
 
-constexpr int TRI_FPB = 8;   // faces per CTA
 constexpr int TRI_EPB = 4;   // elements per CTA
 
-template <int K>
+template <int K, int MODE>
 static cudaError_t tri_launch(const TriArgs& a, cudaStream_t st) {
+    constexpr int FPB = MODE == TRI_APPLY ? 8 : 4;   // faces per CTA (static shared memory <= 48 KB)
     if (a.NF > 0) {
-        const unsigned fb = (unsigned)((a.NF + TRI_FPB - 1) / TRI_FPB);
-        tri_face_kernel<K, TRI_FPB><<<fb, 128, 0, st>>>(a);
+        const unsigned fb = (unsigned)((a.NF + FPB - 1) / FPB);
+        tri_face_kernel<K, FPB, MODE><<<fb, 128, 0, st>>>(a);
     }
     const unsigned eb = (unsigned)((a.E + TRI_EPB - 1) / TRI_EPB);
-    tri_elem_kernel<K, TRI_EPB><<<eb, 128, 0, st>>>(a);
+    tri_elem_kernel<K, TRI_EPB, MODE><<<eb, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -587,23 +697,24 @@ extern "C" int cdg2_tri_mesh_info(const cdg2_tri_mesh* m, long long* n_elem, int
     return CDG2_OK;
 }
 
-extern "C" int cdg2_tri_apply(const cdg2_tri_mesh* m, const cdg2_params* p, const double* U, double* out, int flags,
-                              void* stream) {
-    if (!m || !p || !U || !out) {
-        set_error("cdg2_tri_apply: NULL argument");
+static int tri_run(const char* who, const cdg2_tri_mesh* m, const cdg2_params* p, const double* U, const double* dU,
+                   double* out, int flags, int mode, void* stream) {
+    if (!m || !p || !U || !out || (mode != TRI_APPLY && !dU)) {
+        set_error(std::string(who) + ": NULL argument");
         return CDG2_ERR_INVALID_ARG;
     }
-    if (U == out) {
-        set_error("cdg2_tri_apply: U and out must not overlap");
+    if (U == out || dU == out) {
+        set_error(std::string(who) + ": the inputs and out must not overlap");
         return CDG2_ERR_INVALID_ARG;
     }
     if (flags & ~CDG2_MINV) {
-        set_error("cdg2_tri_apply: only CDG2_MINV is supported on triangle meshes");
+        set_error(std::string(who) + ": only CDG2_MINV is supported on triangle meshes");
         return CDG2_ERR_INVALID_ARG;
     }
     if (int rc = tri_upload(*m)) return rc;
     TriArgs a;
     a.U = U;
+    a.dU = dU;
     a.out = out;
     a.flags = flags;
     a.chi_e = m->chi_e;
@@ -630,11 +741,40 @@ extern "C" int cdg2_tri_apply(const cdg2_tri_mesh* m, const cdg2_params* p, cons
     a.c = make_coefT<double>(make_coef(*p), g, nullptr);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
-    switch (m->k) {
-        case 1: e = tri_launch<1>(a, st); break;
-        case 2: e = tri_launch<2>(a, st); break;
-        default: e = tri_launch<3>(a, st); break;
+    if (mode == TRI_APPLY) {
+        switch (m->k) {
+            case 1: e = tri_launch<1, TRI_APPLY>(a, st); break;
+            case 2: e = tri_launch<2, TRI_APPLY>(a, st); break;
+            default: e = tri_launch<3, TRI_APPLY>(a, st); break;
+        }
+    } else if (mode == TRI_JVP) {
+        switch (m->k) {
+            case 1: e = tri_launch<1, TRI_JVP>(a, st); break;
+            case 2: e = tri_launch<2, TRI_JVP>(a, st); break;
+            default: e = tri_launch<3, TRI_JVP>(a, st); break;
+        }
+    } else {
+        switch (m->k) {
+            case 1: e = tri_launch<1, TRI_VJP>(a, st); break;
+            case 2: e = tri_launch<2, TRI_VJP>(a, st); break;
+            default: e = tri_launch<3, TRI_VJP>(a, st); break;
+        }
     }
-    if (e != cudaSuccess) return cuda_fail(e, "cdg2_tri_apply");
+    if (e != cudaSuccess) return cuda_fail(e, who);
     return CDG2_OK;
+}
+
+extern "C" int cdg2_tri_apply(const cdg2_tri_mesh* m, const cdg2_params* p, const double* U, double* out, int flags,
+                              void* stream) {
+    return tri_run("cdg2_tri_apply", m, p, U, nullptr, out, flags, TRI_APPLY, stream);
+}
+
+extern "C" int cdg2_tri_jvp(const cdg2_tri_mesh* m, const cdg2_params* p, const double* U, const double* dU,
+                            double* out, int flags, void* stream) {
+    return tri_run("cdg2_tri_jvp", m, p, U, dU, out, flags, TRI_JVP, stream);
+}
+
+extern "C" int cdg2_tri_vjp(const cdg2_tri_mesh* m, const cdg2_params* p, const double* U, const double* lam,
+                            double* gU, int flags, void* stream) {
+    return tri_run("cdg2_tri_vjp", m, p, U, lam, gU, flags, TRI_VJP, stream);
 }

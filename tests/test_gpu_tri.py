@@ -126,3 +126,58 @@ def test_tri_apply_full_size_sampled_rows(G):
         ref = T.apply(om, U[cells], p)[c]
         err = float((got[int(e)] - ref).norm() / ref.norm())
         assert err <= 1e-12, (int(e), err)
+
+
+@pytest.mark.parametrize("nx,ny,k", [(6, 3, 1), (9, 4, 2), (7, 3, 3)])
+def test_tri_jvp_matches_oracle(G, nx, ny, k):
+    xy, tri = I.tri_mesh(nx, ny, 1.0, 0.2, 0.2, 200 + k)
+    om = T.TriMesh(xy, tri, k)
+    p = _params()
+    U = _state(om, 17 + k)
+    U[:, 3, 0] += 0.05
+    dU = torch.from_numpy(np.random.default_rng(k).standard_normal(U.shape))
+    gm = G.cdg2_tri_mesh_create(xy, tri, k)
+    out = torch.empty(gm.n_dof, dtype=torch.float64, device="cuda")
+    G.cdg2_tri_jvp(gm, p, U.reshape(-1).cuda(), dU.reshape(-1).contiguous().cuda(), out, G.CDG2_MINV)
+    got = out.cpu().reshape(U.shape)
+    assert rel_l2_per_species(got, T.jvp(om, U, dU, p)) <= 1e-12
+    # the JVP is the derivative of the GPU apply itself (central differences through the C ABI)
+    h = 1e-6
+    fp = _run(G, xy, tri, k, p, U + h * dU, G.CDG2_MINV)
+    fm = _run(G, xy, tri, k, p, U - h * dU, G.CDG2_MINV)
+    fd = (fp - fm) / (2 * h)
+    # (the LLF max and the signs of the normal velocities have kinks: 1e-4, as for the Cartesian JVP)
+    assert float((fd - got).norm() / got.norm()) <= 1e-4
+
+
+@pytest.mark.parametrize("nx,ny,k", [(6, 3, 1), (9, 4, 2), (7, 3, 3)])
+@pytest.mark.parametrize("minv", [True, False])
+def test_tri_vjp_matches_oracle_and_transposes_the_jvp(G, nx, ny, k, minv):
+    xy, tri = I.tri_mesh(nx, ny, 1.0, 0.2, 0.2, 300 + k)
+    om = T.TriMesh(xy, tri, k)
+    p = _params()
+    U = _state(om, 27 + k)
+    U[:, 3, 0] += 0.05
+    rng = np.random.default_rng(10 + k)
+    lam = torch.from_numpy(rng.standard_normal(U.shape))
+    dU = torch.from_numpy(rng.standard_normal(U.shape))
+    gm = G.cdg2_tri_mesh_create(xy, tri, k)
+    flags = G.CDG2_MINV if minv else 0
+    gU = torch.empty(gm.n_dof, dtype=torch.float64, device="cuda")
+    G.cdg2_tri_vjp(gm, p, U.reshape(-1).cuda(), lam.reshape(-1).contiguous().cuda(), gU, flags)
+    got = gU.cpu().reshape(U.shape)
+    if minv:
+        ref = T.vjp(om, U, lam, p)
+    else:
+        _, fn = torch.func.vjp(lambda V: T.apply_residual(om, V, O.param_vector(p)), U)
+        ref = fn(lam)[0]
+    assert rel_l2_per_species(got, ref) <= 1e-12
+    jv = torch.empty_like(gU)
+    G.cdg2_tri_jvp(gm, p, U.reshape(-1).cuda(), dU.reshape(-1).contiguous().cuda(), jv, flags)
+    lhs = float((lam.reshape(-1) * jv.cpu()).sum())
+    rhs = float((got.reshape(-1) * dU.reshape(-1)).sum())
+    assert abs(lhs - rhs) <= 1e-11 * max(abs(lhs), 1.0) * 10
+    # bitwise reproducible (no atomics)
+    gU2 = torch.empty_like(gU)
+    G.cdg2_tri_vjp(gm, p, U.reshape(-1).cuda(), lam.reshape(-1).contiguous().cuda(), gU2, flags)
+    assert torch.equal(gU, gU2)

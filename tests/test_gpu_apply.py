@@ -4,6 +4,9 @@ Bars: FP64 relative L2 error per species <= 1e-12; the FP32 path <= 1e-5.
 Meshes span several CTAs and leave a ragged last CTA; the full-size
 workloads are compared element by element as well.
 """
+import itertools
+
+import numpy as np
 import pytest
 import torch
 
@@ -141,3 +144,66 @@ def test_project_mms_parity(G, dim, cells, k):
     out = torch.empty(gm.n_dof, dtype=torch.float64, device="cuda")
     G.cdg2_project_mms(gm, G.make_params(I.default_params(), ph), 0.25, out)
     assert rel_l2_per_species(out, ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("cfg", [2, 4])
+def test_apply_full_size_sampled_rows(G, cfg):
+    """2D 128x32 Q2 and the largest workload, 3D 128x32x32 Q2 (21.2M DOF): apply
+    and JVP rows of sampled elements against the oracle on the box of the element and its face
+    neighbours (which fixes the element's row of M^{-1} L_h): three cells along
+    each axis, two at a Gamma_1 / Gamma_2 side, Gamma_{1,in} shifted into the
+    box's coordinates.  A periodic wrap keeps its K^- (the last cell) in the
+    box's order."""
+    w = I.workload(cfg)
+    gm = G.cdg2_mesh_create(w.dim, w.cells, w.extent, w.periodic, w.k)
+    p = I.default_params()
+    p["chi0"] = (0.05, 0.02, 0.03, 0.02)
+    U = torch.from_numpy(I.random_coefficients(gm.n_elem, gm.n_basis, w.seed, 0.1))
+    out = torch.empty(gm.n_dof, dtype=torch.float64, device="cuda")
+    G.cdg2_apply(gm, p, U.reshape(-1).cuda(), out, G.CDG2_MINV)
+    got = out.cpu().reshape(U.shape)
+    dU = torch.from_numpy(I.random_coefficients(gm.n_elem, gm.n_basis, w.seed + 1, 0.3))
+    G.cdg2_jvp(gm, p, U.reshape(-1).cuda(), dU.reshape(-1).cuda(), out, G.CDG2_MINV)
+    got_jvp = out.cpu().reshape(U.shape)
+    n = list(w.cells[: w.dim])
+    h = [w.extent[a] / n[a] for a in range(w.dim)]
+    rng = np.random.default_rng(cfg)
+    picks = [tuple(int(rng.integers(0, n[a])) for a in range(w.dim)) for _ in range(24)]
+    picks += [tuple([0, 0] + [0] * (w.dim - 2)), tuple([n[0] - 1, n[1] - 1] + [n[a] - 1 for a in range(2, w.dim)]),
+              tuple([5, 0] + [3] * (w.dim - 2)), tuple([7, n[1] - 1] + [0] * (w.dim - 2))]
+    for idx in picks:
+        ranges, local = [], []
+        for a in range(w.dim):
+            if w.periodic[a] or 0 < idx[a] < n[a] - 1:
+                ranges.append([(idx[a] + d) % n[a] for d in (-1, 0, 1)])
+                local.append(1)
+            elif idx[a] == 0:
+                ranges.append([0, 1])
+                local.append(0)
+            else:
+                ranges.append([n[a] - 2, n[a] - 1])
+                local.append(1)
+        cells = tuple(len(r) for r in ranges)
+        ext = tuple(cells[a] * h[a] for a in range(w.dim))
+        shift = (idx[0] - local[0]) * h[0]
+        om = O.Mesh(w.dim, cells, ext, (0,) * w.dim, w.k,
+                    gamma1_in=(0.375 - shift, 0.625 - shift))
+        gids = []
+        for t in itertools.product(*reversed(ranges)):
+            g = list(reversed(t))
+            gid, stride = 0, 1
+            for a in range(w.dim):
+                gid += g[a] * stride
+                stride *= n[a]
+            gids.append(gid)
+        lid, stride = 0, 1
+        for a in range(w.dim):
+            lid += local[a] * stride
+            stride *= cells[a]
+        ref = O.apply(om, U[gids], p)[lid]
+        e = gids[lid]
+        err = float((got[e] - ref).norm() / ref.norm())
+        assert err <= 1e-12, (idx, err)
+        ref = O.jvp(om, U[gids], dU[gids], p)[lid]
+        err = float((got_jvp[e] - ref).norm() / ref.norm())
+        assert err <= 1e-12, ("jvp", idx, err)

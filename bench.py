@@ -159,6 +159,20 @@ def workload_setup(cfg: int, k: int | None):
     return w, I
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest value over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, n_dof: int, steps: int, total_ms: float) -> float:
+    """Whole-job GDOF/s: every rank applies the operator to its own replica of the
+    workload (weak scaling), timed by the slowest rank."""
+    return world * n_dof * steps / (total_ms * 1e-3) / 1e9
+
+
 def make_inputs(G, w, I, mesh, dtype_flag=0):
     import torch
     dt = torch.float32 if dtype_flag else torch.float64
@@ -456,12 +470,10 @@ def main():
     clk = clocks.stop()
     total_ms = sum(ms)
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, "cuda")
         dist.barrier()
     ms_step = total_ms / args.steps
-    value = world * w.n_dof * args.steps / (total_ms * 1e-3) / 1e9
+    value = job_throughput(world, w.n_dof, args.steps, total_ms)
 
     # ---- roofline of the dominant kernel (the fused FP64 apply kernel) ----
     fl = apply_flops_per_element(w.dim, w.k) * w.n_elem

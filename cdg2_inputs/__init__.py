@@ -256,3 +256,51 @@ def tri_workload(which: int, k: int | None = None) -> TriWorkload:
     if which == 1:
         return TriWorkload("2D triangles 256x64x2 P3 (jittered)", 256, 64, 3 if k is None else k, 0.2, 1171)
     raise ValueError(f"unknown triangle workload {which}")
+
+
+def tet_mesh(nx: int, ny: int, nz: int, lx: float = 1.0, ly: float = 0.2, lz: float = 0.2, jitter: float = 0.0,
+             seed: int = 0):
+    """A tetrahedral mesh of [0, lx] x [0, ly] x [0, lz]: an (nx+1)(ny+1)(nz+1)
+    vertex grid, interior vertices moved by jitter * h * (2u - 1) per coordinate
+    (SplitMix64(seed); x, y, z per vertex in index order, i fastest), each cell
+    cut into the six tetrahedra of Kuhn's subdivision: for every ordering
+    (a, b, c) of the axes, (v, v + e_a, v + e_a + e_b, v + e_a + e_b + e_c)
+    from the cell's lower corner v, axis orderings in lexicographic order; for
+    an odd ordering the last two vertices are swapped, so every tetrahedron is
+    positively oriented.  The subdivision is conforming across cells.
+    Returns (xyz [n_vert][3] float64, tet [n_tet][4] int64) numpy arrays.
+    """
+    import itertools
+    import numpy as np
+    h = (lx / nx, ly / ny, lz / nz)
+    n = (nx + 1, ny + 1, nz + 1)
+    nv = n[0] * n[1] * n[2]
+    u = splitmix64_uniform_array(seed, 3 * nv).reshape(nv, 3)
+    xyz = np.zeros((nv, 3))
+    for k in range(n[2]):
+        for j in range(n[1]):
+            for i in range(n[0]):
+                v = (k * n[1] + j) * n[0] + i
+                xyz[v] = (i * h[0], j * h[1], k * h[2])
+                if 0 < i < nx and 0 < j < ny and 0 < k < nz:
+                    for a in range(3):
+                        xyz[v, a] += jitter * h[a] * (2.0 * u[v, a] - 1.0)
+
+    def vid(i, j, k):
+        return (k * n[1] + j) * n[0] + i
+
+    tets = []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                for perm in itertools.permutations(range(3)):
+                    p = [i, j, k]
+                    verts = [vid(*p)]
+                    for a in perm:
+                        p[a] += 1
+                        verts.append(vid(*p))
+                    inversions = sum(1 for x in range(3) for y in range(x + 1, 3) if perm[x] > perm[y])
+                    if inversions % 2:
+                        verts[2], verts[3] = verts[3], verts[2]
+                    tets.append(verts)
+    return xyz, np.array(tets, dtype=np.int64)

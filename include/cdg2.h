@@ -368,6 +368,50 @@ int cdg2_tri_jvp(const cdg2_tri_mesh* mesh, const cdg2_params* params, const dou
 int cdg2_tri_vjp(const cdg2_tri_mesh* mesh, const cdg2_params* params, const double* U, const double* lam,
                  double* gU, int flags, void* stream);
 
+/* ---- Tetrahedral meshes (Sec. 3.1: P_k on tetrahedra, chi_e = 2) ----------
+ * The operator of cdg2_apply on an affine tetrahedral mesh, FP64.  Readings:
+ * on the reference tetrahedron the orthonormal Dubiner basis psi_pqr =
+ * c_pqr L_p J_q R_r (L_p = s^p P_p((2 xi - s)/s), s = 1 - eta - zeta; J_q =
+ * t^q P_q^{(2p+1,0)}((2 eta - t)/t), t = 1 - zeta; R_r = P_r^{(2p+2q+2,0)}
+ * (2 zeta - 1); c_pqr = sqrt((2p+1)(2p+2q+2)(2p+2q+2r+3)); modes by total
+ * degree, then r, then q), so M_K = 6 |K| I; the collapsed Gauss rule with
+ * (k+2)^3 volume points and the collapsed triangle rule with (k+2)^2 points
+ * per face in K^-'s parametrisation (local face l: the vertices other than l
+ * in increasing local order); K^-_e the smaller tetrahedron (volumes within a
+ * relative 1e-12 tie, a tie goes to the lower index); boundary faces on
+ * y = 0 are Gamma_1, on y = max y Gamma_2, other boundary faces are walls.
+ * U and out: [n_tet][6][n_basis], n_basis = (k+1)(k+2)(k+3)/6. */
+typedef struct cdg2_tet_mesh cdg2_tet_mesh;
+
+typedef struct cdg2_tet_desc {
+    long long n_vert;
+    const double* xyz;       /* host [n_vert][3] vertex coordinates */
+    long long n_tet;
+    const long long* tet;    /* host [n_tet][4] vertex indices, positively oriented */
+    int k;                   /* 1..3 */
+    double chi_e;            /* CDG2 lifting factor; <= 0 selects 2 (Sec. 3.1, tetrahedra) */
+    double gamma1_in[2];     /* x-range of Gamma_{1,in} on y = 0 */
+} cdg2_tet_desc;
+
+/* Build a tetrahedral mesh (host call; the arrays are copied).  Errors:
+ * INVALID_ARG for k outside 1..3, an index out of range, a degenerate or
+ * negatively oriented tetrahedron, an inconsistent shared face, or a face of
+ * more than two tetrahedra.  Device memory is allocated by the first
+ * cdg2_tet_apply and freed by cdg2_tet_mesh_destroy. */
+int cdg2_tet_mesh_create(const cdg2_tet_desc* desc, cdg2_tet_mesh** out);
+void cdg2_tet_mesh_destroy(cdg2_tet_mesh* mesh);
+int cdg2_tet_mesh_info(const cdg2_tet_mesh* mesh, long long* n_elem, int* n_basis, long long* n_dof,
+                       long long* n_faces);
+
+/* out = M^{-1} L_h(U) (flags = CDG2_MINV) or <phi, L_h(U)> (flags = 0) on a
+ * tetrahedral mesh; U, out: device float64, not overlapping.  A face kernel
+ * (every interior face once: traces of both sides at K^-'s face points, the
+ * CDG2 lifting on K^-, the face flux, its test against both sides into a face
+ * buffer) and an element kernel (volume terms, its faces, boundary data,
+ * M^{-1}).  Errors: INVALID_ARG (NULL, overlap, other flags), CUDA. */
+int cdg2_tet_apply(const cdg2_tet_mesh* mesh, const cdg2_params* params, const double* U, double* out, int flags,
+                   void* stream);
+
 const char* cdg2_last_error(void);
 
 #ifdef __cplusplus

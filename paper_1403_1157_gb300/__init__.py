@@ -93,6 +93,18 @@ class TriDesc(ctypes.Structure):
     ]
 
 
+class TetDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_vert", ctypes.c_longlong),
+        ("xyz", ctypes.POINTER(ctypes.c_double)),
+        ("n_tet", ctypes.c_longlong),
+        ("tet", ctypes.POINTER(ctypes.c_longlong)),
+        ("k", ctypes.c_int),
+        ("chi_e", ctypes.c_double),
+        ("gamma1_in", ctypes.c_double * 2),
+    ]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [
         ("stages", ctypes.c_int), ("newton_iters", ctypes.c_int), ("gmres_iters", ctypes.c_int),
@@ -160,6 +172,15 @@ def load_library():
     lib.cdg2_tri_jvp.restype = i
     lib.cdg2_tri_vjp.argtypes = [vp, ctypes.POINTER(Params), vp, vp, vp, i, vp]
     lib.cdg2_tri_vjp.restype = i
+    lib.cdg2_tet_mesh_create.argtypes = [ctypes.POINTER(TetDesc), ctypes.POINTER(vp)]
+    lib.cdg2_tet_mesh_create.restype = i
+    lib.cdg2_tet_mesh_destroy.argtypes = [vp]
+    lib.cdg2_tet_mesh_destroy.restype = None
+    lib.cdg2_tet_mesh_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i),
+                                       ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.cdg2_tet_mesh_info.restype = i
+    lib.cdg2_tet_apply.argtypes = [vp, ctypes.POINTER(Params), vp, vp, i, vp]
+    lib.cdg2_tet_apply.restype = i
     lib.cdg2_element_block.argtypes = [vp, ctypes.POINTER(Params), d, ctypes.c_longlong, i, dp]
     lib.cdg2_element_block.restype = i
     lib.cdg2_last_error.argtypes = []
@@ -388,6 +409,53 @@ def cdg2_tri_vjp(mesh: TriMesh, params, U: torch.Tensor, lam: torch.Tensor, gU: 
                                        ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(gU.data_ptr()), int(flags),
                                        _stream_ptr(stream)))
     return gU
+
+
+class TetMesh:
+    """Owning handle of a cdg2_tet_mesh."""
+
+    def __init__(self, handle: int, k: int):
+        self.handle = handle
+        self.k = k
+        ne, nb, nd, nf = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load_library().cdg2_tet_mesh_info(handle, ctypes.byref(ne), ctypes.byref(nb), ctypes.byref(nd),
+                                                 ctypes.byref(nf)))
+        self.n_elem, self.n_basis, self.n_dof, self.n_faces = ne.value, nb.value, nd.value, nf.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.cdg2_tet_mesh_destroy(self.handle)
+            self.handle = None
+
+
+def cdg2_tet_mesh_create(xyz, tet, k: int, chi_e: float = 0.0, gamma1_in=(0.375, 0.625)) -> TetMesh:
+    """Tetrahedral mesh from vertex coordinates xyz [n_v][3] and positively oriented quadruples tet [n_t][4]."""
+    import numpy as np
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tet = np.ascontiguousarray(tet, dtype=np.int64)
+    d = TetDesc()
+    d.n_vert = xyz.shape[0]
+    d.xyz = xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.n_tet = tet.shape[0]
+    d.tet = tet.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
+    d.k = int(k)
+    d.chi_e = float(chi_e)
+    d.gamma1_in[0], d.gamma1_in[1] = float(gamma1_in[0]), float(gamma1_in[1])
+    h = ctypes.c_void_p()
+    _check(load_library().cdg2_tet_mesh_create(ctypes.byref(d), ctypes.byref(h)))
+    return TetMesh(h.value, int(k))
+
+
+def cdg2_tet_apply(mesh: TetMesh, params, U: torch.Tensor, out: torch.Tensor, flags: int = CDG2_MINV,
+                   stream=None) -> torch.Tensor:
+    """out = M^{-1} L_h(U) on a tetrahedral mesh (float64 CUDA tensors of n_dof values)."""
+    for name, t in (("U", U), ("out", out)):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == mesh.n_dof):
+            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of {mesh.n_dof} values")
+    p = _params(params)
+    _check(load_library().cdg2_tet_apply(mesh.handle, ctypes.byref(p), ctypes.c_void_p(U.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), int(flags), _stream_ptr(stream)))
+    return out
 
 
 def _theta_ptr(dtheta):

@@ -1,0 +1,652 @@
+// The CDG2 operator on tetrahedral meshes (Sec. 3.1: P_k on tetrahedra,
+// chi_e = 2): f(U) = M^{-1} L_h(U) in FP64, face-once.
+//
+// Readings (shared with the oracle; the paper fixes none of them):
+//  * basis: on the reference tetrahedron T = {xi, eta, zeta >= 0, xi + eta +
+//    zeta <= 1} the orthonormal Dubiner basis psi_pqr = c_pqr L_p J_q R_r with
+//    L_p = s^p P_p((2 xi - s)/s), s = 1 - eta - zeta; J_q = t^q P_q^{(2p+1,0)}
+//    ((2 eta - t)/t), t = 1 - zeta; R_r = P_r^{(2p+2q+2,0)}(2 zeta - 1);
+//    c_pqr = sqrt((2p+1)(2p+2q+2)(2p+2q+2r+3)); modes by total degree, then r,
+//    then q; mapped affinely by x = x_0 + J_e xi, so M_K = det J_e I;
+//  * volume quadrature: the collapsed Gauss rule with (k+2)^3 points (xi =
+//    u (1-v)(1-w), eta = v (1-w), zeta = w, weight w_u w_v w_w (1-v)(1-w)^2,
+//    u fastest); face quadrature: the collapsed triangle rule with (k+2)^2
+//    points (s = u (1-v), t = v, weight w_u w_v (1-v)) in K^-'s parametrisation
+//    A + s (B - A) + t (C - A) of the face, local face l being the vertices
+//    other than l in increasing local order;
+//  * K^-_e: the smaller adjacent tetrahedron (Sec. 3.1); volumes within a
+//    relative 1e-12 tie, a tie goes to the lower index;
+//  * boundary faces on y = 0 are Gamma_1, on y = max y Gamma_2 (Eq. (3)); other
+//    boundary faces are no-flow walls.
+// A face point with barycentric coordinates (lambda_a, lambda_b, lambda_c) on
+// the face's global vertices sits at sum lambda_i r_{l_i} in an element whose
+// local indices of those vertices are (l_a, l_b, l_c): the basis tables are
+// kept for each of the 24 ordered triples of local vertices ("frames"); K^-
+// reads its own face's frame, K^+ the frame of the same three global
+// vertices in its own numbering.  With M_{K^-} = det I, the lifting identity
+// gives r . n (x_p) = -(E / (2 det_-)) sum_p' L[p][p'] Delta(x_p'), E =
+// |(B - A) x (C - A)|, L[p][p'] = sum_i psi_i(x_p) psi_i(x_p') w_p'.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "physics.cuh"
+#include "simplex_host.h"
+
+namespace cdg2 {
+
+constexpr int TTMAXB = 20;    // basis functions for k = 3
+constexpr int TTMAXQ = 125;   // volume points for k = 3
+constexpr int TTMAXP = 25;    // face points for k = 3
+constexpr int NFRAME = 64;    // frame code a * 16 + b * 4 + c (24 of them used)
+constexpr int TGEO = 22;      // x0 (3), J (9, row-major), J^{-1} (9, row-major), det J
+
+__host__ __device__ constexpr int frame_code(int a, int b, int c) { return a * 16 + b * 4 + c; }
+
+struct TetTab {
+    double VB[TTMAXQ][TTMAXB];            // psi_i at the volume points
+    double VD[3][TTMAXQ][TTMAXB];         // reference gradient
+    double VW[TTMAXQ];
+    double FB[NFRAME][TTMAXP][TTMAXB];    // psi_i at the face points of each frame
+    double FD[3][NFRAME][TTMAXP][TTMAXB];
+    double LF[NFRAME][TTMAXP][TTMAXP];    // lifting kernel of each frame (read for K^-'s)
+    double FW[TTMAXP];                    // face rule weights (sum 1/2)
+    double FX[TTMAXP][2];                 // face rule points (s, t)
+};
+
+}  // namespace cdg2
+
+struct cdg2_tet_mesh {
+    int k = 0, nb = 0;
+    long long E = 0, NF = 0;
+    double chi_e = 2.0, ly = 0.0;
+    double g1in[2] = {0.375, 0.625};
+    std::vector<double> geo;     // [E][TGEO]
+    std::vector<int> emap;       // [E][4]: 2 face + side, or -1 - tag (0 wall, 1 Gamma_1, 2 Gamma_2)
+    std::vector<int> face;       // [NF][4]: eM, eP, frame of K^-, frame of K^+
+    std::vector<double> fgeo;    // [NF][5]: n (3), E = |(B - A) x (C - A)|, det J of K^-
+    std::vector<cdg2::TetTab> tab;   // one (large) table, host copy
+    mutable double* d_geo = nullptr;
+    mutable int* d_emap = nullptr;
+    mutable int* d_face = nullptr;
+    mutable double* d_fgeo = nullptr;
+    mutable cdg2::TetTab* d_tab = nullptr;
+    mutable double* d_fbuf = nullptr;   // [NF][2][6][nb]
+};
+
+namespace cdg2 {
+
+namespace {
+
+const int FACE_VERTS[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+const double REF_VERT[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+// psi_i and its reference gradient at (xi, eta, zeta).
+void dubiner3(int k, double xi, double eta, double zeta, double* psi, double* d0, double* d1, double* d2) {
+    const double s = 1.0 - eta - zeta, xt = 2.0 * xi - s;       // d xt = (2, 1, 1), d s = (0, -1, -1)
+    const double t = 1.0 - zeta, y = 2.0 * eta - t;             // d y = (0, 2, 1), d t = (0, 0, -1)
+    double L[4], dL[3][4];
+    L[0] = 1.0;
+    for (int j = 0; j < 3; ++j) dL[j][0] = 0.0;
+    const double dxt[3] = {2.0, 1.0, 1.0}, ds[3] = {0.0, -1.0, -1.0};
+    if (k >= 1) {
+        L[1] = xt;
+        for (int j = 0; j < 3; ++j) dL[j][1] = dxt[j];
+    }
+    for (int p = 2; p <= k; ++p) {
+        L[p] = ((2 * p - 1) * xt * L[p - 1] - (p - 1) * s * s * L[p - 2]) / p;
+        for (int j = 0; j < 3; ++j)
+            dL[j][p] = ((2 * p - 1) * (dxt[j] * L[p - 1] + xt * dL[j][p - 1]) -
+                        (p - 1) * (2.0 * s * ds[j] * L[p - 2] + s * s * dL[j][p - 2])) / p;
+    }
+    const double dy[3] = {0.0, 2.0, 1.0}, dt[3] = {0.0, 0.0, -1.0};
+    int i = 0;
+    for (int d = 0; d <= k; ++d)
+        for (int r = 0; r <= d; ++r)
+            for (int q = 0; q <= d - r; ++q, ++i) {
+                const int p = d - q - r;
+                const double al = 2.0 * p + 1.0;
+                // J_q = t^q P_q^{(al,0)}(y / t) by the scaled recurrence, with its gradient
+                double J0 = 1.0, J1 = 0.0, dJ0[3] = {0, 0, 0}, dJ1[3] = {0, 0, 0};
+                double Jq = 1.0, dJq[3] = {0, 0, 0};
+                if (q >= 1) {
+                    J1 = (al + 1.0) * t + (al + 2.0) * (y - t) / 2.0;
+                    for (int j = 0; j < 3; ++j) dJ1[j] = (al + 1.0) * dt[j] + (al + 2.0) * (dy[j] - dt[j]) / 2.0;
+                    for (int m = 2; m <= q; ++m) {
+                        const double c = 2.0 * m + al;
+                        const double a1 = 2.0 * m * (m + al) * (c - 2.0);
+                        const double a2 = (c - 1.0) * c * (c - 2.0);
+                        const double a3 = (c - 1.0) * al * al;
+                        const double a4 = 2.0 * (m + al - 1.0) * (m - 1.0) * c;
+                        const double J2 = ((a2 * y + a3 * t) * J1 - a4 * t * t * J0) / a1;
+                        double dJ2[3];
+                        for (int j = 0; j < 3; ++j)
+                            dJ2[j] = ((a2 * dy[j] + a3 * dt[j]) * J1 + (a2 * y + a3 * t) * dJ1[j] -
+                                      a4 * (2.0 * t * dt[j] * J0 + t * t * dJ0[j])) / a1;
+                        J0 = J1;
+                        J1 = J2;
+                        for (int j = 0; j < 3; ++j) {
+                            dJ0[j] = dJ1[j];
+                            dJ1[j] = dJ2[j];
+                        }
+                    }
+                    Jq = J1;
+                    for (int j = 0; j < 3; ++j) dJq[j] = dJ1[j];
+                }
+                double R, dR;
+                jacobi_d(r, 2.0 * p + 2.0 * q + 2.0, 2.0 * zeta - 1.0, R, dR);
+                const double cst = std::sqrt((2.0 * p + 1) * (2.0 * p + 2 * q + 2) * (2.0 * p + 2 * q + 2 * r + 3));
+                psi[i] = cst * L[p] * Jq * R;
+                double g[3];
+                for (int j = 0; j < 3; ++j) g[j] = cst * (dL[j][p] * Jq * R + L[p] * dJq[j] * R);
+                g[2] += cst * L[p] * Jq * 2.0 * dR;
+                d0[i] = g[0];
+                d1[i] = g[1];
+                d2[i] = g[2];
+            }
+}
+
+void build_tet_tables(int k, TetTab& T) {
+    std::memset(&T, 0, sizeof(T));
+    const int n = k + 2;
+    const int nb = (k + 1) * (k + 2) * (k + 3) / 6;
+    double g[16], w[16];
+    gauss01(n, g, w);
+    for (int c = 0; c < n; ++c)
+        for (int b = 0; b < n; ++b)
+            for (int a = 0; a < n; ++a) {
+                const int q = a + n * (b + n * c);
+                const double xi = g[a] * (1.0 - g[b]) * (1.0 - g[c]), eta = g[b] * (1.0 - g[c]), zeta = g[c];
+                T.VW[q] = w[a] * w[b] * w[c] * (1.0 - g[b]) * (1.0 - g[c]) * (1.0 - g[c]);
+                dubiner3(k, xi, eta, zeta, T.VB[q], T.VD[0][q], T.VD[1][q], T.VD[2][q]);
+            }
+    for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a) {
+            const int p = a + n * b;
+            T.FX[p][0] = g[a] * (1.0 - g[b]);
+            T.FX[p][1] = g[b];
+            T.FW[p] = w[a] * w[b] * (1.0 - g[b]);
+        }
+    const int np = n * n;
+    for (int la = 0; la < 4; ++la)
+        for (int lb = 0; lb < 4; ++lb)
+            for (int lc = 0; lc < 4; ++lc) {
+                if (la == lb || lb == lc || la == lc) continue;
+                const int f = frame_code(la, lb, lc);
+                for (int p = 0; p < np; ++p) {
+                    const double s = T.FX[p][0], t = T.FX[p][1], l0 = 1.0 - s - t;
+                    double x[3];
+                    for (int j = 0; j < 3; ++j) x[j] = l0 * REF_VERT[la][j] + s * REF_VERT[lb][j] + t * REF_VERT[lc][j];
+                    dubiner3(k, x[0], x[1], x[2], T.FB[f][p], T.FD[0][f][p], T.FD[1][f][p], T.FD[2][f][p]);
+                }
+                for (int p = 0; p < np; ++p)
+                    for (int pp = 0; pp < np; ++pp) {
+                        double acc = 0.0;
+                        for (int i = 0; i < nb; ++i) acc += T.FB[f][p][i] * T.FB[f][pp][i];
+                        T.LF[f][p][pp] = acc * T.FW[pp];
+                    }
+            }
+}
+
+}  // namespace
+
+}  // namespace cdg2
+
+namespace cdg2 {
+
+template <int K>
+struct TetShape {
+    static constexpr int NB = (K + 1) * (K + 2) * (K + 3) / 6;
+    static constexpr int NQ = (K + 2) * (K + 2) * (K + 2);
+    static constexpr int NP = (K + 2) * (K + 2);
+};
+
+struct TetArgs {
+    const double* U;
+    double* out;
+    int flags;
+    double chi_e;
+    long long E, NF;
+    const double* geo;
+    const int* emap;
+    const int* face;
+    const double* fgeo;
+    const TetTab* tab;
+    double* fbuf;
+    Geo g;               // only g1in is read (Gamma_{1,in})
+    CoefT<double> c;
+};
+
+// One CTA: FPB interior faces.  Traces of both sides at K^-'s face points
+// (each side through its frame), the K^- lifting, the face flux, and its test
+// against both sides' basis into the face buffer ([face][side][6][nb]).
+template <int K, int FPB>
+__global__ void __launch_bounds__(128) tet_face_kernel(const TetArgs a) {
+    using S = TetShape<K>;
+    constexpr int NB = S::NB, NP = S::NP;
+    const TetTab& tb = *a.tab;
+    __shared__ double sU[FPB][2][NS][NB];
+    __shared__ double sJ[FPB][2][9];          // J^{-1} of each side (row-major)
+    __shared__ double sF[FPB][5];             // n (3), E, det_-
+    __shared__ int sI[FPB][4];                // eM, eP, frame of K^-, frame of K^+
+    __shared__ double sDN[FPB][2][NP][NB];    // n^- . grad phi_m of each side at the face points
+    __shared__ double sT[FPB][2][2][NS][NP];  // [side][value, normal derivative][s][p]
+    __shared__ double sS[FPB][2][NS][NP];     // sigma, tau
+    const long long f0 = (long long)blockIdx.x * FPB;
+    const int nf = (int)min((long long)FPB, a.NF - f0);
+    for (int i = threadIdx.x; i < nf * 5; i += blockDim.x) {
+        const int j = i / 5, c = i % 5;
+        if (c < 4) sI[j][c] = a.face[(f0 + j) * 4 + c];
+        sF[j][c] = a.fgeo[(f0 + j) * 5 + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf * 2 * 9; i += blockDim.x) {
+        const int j = i / 18, side = (i / 9) % 2, c = i % 9;
+        sJ[j][side][c] = a.geo[(long long)sI[j][side] * TGEO + 12 + c];
+    }
+    for (int i = threadIdx.x; i < nf * 2 * NS * NB; i += blockDim.x) {
+        const int j = i / (2 * NS * NB), side = (i / (NS * NB)) % 2, r = i % (NS * NB);
+        sU[j][side][r / NB][r % NB] = a.U[(long long)sI[j][side] * NS * NB + r];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf * 2 * NP * NB; i += blockDim.x) {
+        const int j = i / (2 * NP * NB), side = (i / (NP * NB)) % 2, p = (i / NB) % NP, m = i % NB;
+        const int fr = sI[j][2 + side];
+        const double* Ji = sJ[j][side];
+        const double g0 = tb.FD[0][fr][p][m], g1 = tb.FD[1][fr][p][m], g2 = tb.FD[2][fr][p][m];
+        double dn = 0.0;
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) dn = fma(sF[j][jj], Ji[jj] * g0 + Ji[3 + jj] * g1 + Ji[6 + jj] * g2, dn);
+        sDN[j][side][p][m] = dn;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf * 2 * NS * NP; i += blockDim.x) {
+        const int j = i / (2 * NS * NP), side = (i / (NS * NP)) % 2, s = (i / NP) % NS, p = i % NP;
+        const int fr = sI[j][2 + side];
+        double v = 0.0, dn = 0.0;
+#pragma unroll 4
+        for (int m = 0; m < NB; ++m) {
+            const double u = sU[j][side][s][m];
+            v = fma(tb.FB[fr][p][m], u, v);
+            dn = fma(sDN[j][side][p][m], u, dn);
+        }
+        sT[j][side][0][s][p] = v;
+        sT[j][side][1][s][p] = dn;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf * NP; i += blockDim.x) {
+        const int j = i / NP, p = i % NP;
+        const int frM = sI[j][2];
+        const double lift = -sF[j][3] / (2.0 * sF[j][4]);
+        double uM[NS], dM[NS], uP[NS], dP[NS], del[NS], sig[NS], tau[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            uM[s] = sT[j][0][0][s][p];
+            dM[s] = sT[j][0][1][s][p];
+            uP[s] = sT[j][1][0][s][p];
+            dP[s] = sT[j][1][1][s][p];
+            del[s] = uM[s] - uP[s];
+        }
+        face_point<double>(a.c, 0.0, uM, dM, uP, dP, del, sig, tau);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            double rn = 0.0;
+            for (int q = 0; q < NP; ++q) rn = fma(tb.LF[frM][p][q], sT[j][0][0][s][q] - sT[j][1][0][s][q], rn);
+            sS[j][0][s][p] = sig[s] + 2.0 * a.chi_e * a.c.A[s] * lift * rn;
+            sS[j][1][s][p] = tau[s];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf * 2 * NS * NB; i += blockDim.x) {
+        const int j = i / (2 * NS * NB), side = (i / (NS * NB)) % 2, s = (i / NB) % NS, m = i % NB;
+        const int fr = sI[j][2 + side];
+        const double sg = side ? -1.0 : 1.0;
+        double acc = 0.0;
+        for (int p = 0; p < NP; ++p)
+            acc = fma(tb.FW[p], fma(sS[j][0][s][p], sg * tb.FB[fr][p][m], sS[j][1][s][p] * sDN[j][side][p][m]), acc);
+        a.fbuf[((f0 + j) * 2 + side) * NS * NB + s * NB + m] = sF[j][3] * acc;
+    }
+}
+
+// One CTA: one element.  Volume terms at the collapsed Gauss points (Phi is
+// mapped back by J^{-1}, so the test uses the reference gradients), the tested
+// fluxes of its interior faces, the boundary data of Eq. (3) on its boundary
+// faces, M^{-1} = 1 / det J.
+template <int K>
+__global__ void __launch_bounds__(128) tet_elem_kernel(const TetArgs a) {
+    using S = TetShape<K>;
+    constexpr int NB = S::NB, NQ = S::NQ, NP = S::NP;
+    const TetTab& tb = *a.tab;
+    __shared__ double sU[NS][NB];
+    __shared__ double sG[TGEO];
+    __shared__ double sPhi[NQ][NS][4];   // J^{-1} Phi (3), S
+    const long long e = blockIdx.x;
+    for (int i = threadIdx.x; i < TGEO; i += blockDim.x) sG[i] = a.geo[e * TGEO + i];
+    for (int i = threadIdx.x; i < NS * NB; i += blockDim.x) sU[i / NB][i % NB] = a.U[e * NS * NB + i];
+    __syncthreads();
+    const double* J = sG + 3;
+    const double* Ji = sG + 12;
+    for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
+        double u[NS], g[NS][3], Phi[NS][3], Sr[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            double v = 0.0, r0 = 0.0, r1 = 0.0, r2 = 0.0;
+            for (int m = 0; m < NB; ++m) {
+                const double c = sU[s][m];
+                v = fma(tb.VB[q][m], c, v);
+                r0 = fma(tb.VD[0][q][m], c, r0);
+                r1 = fma(tb.VD[1][q][m], c, r1);
+                r2 = fma(tb.VD[2][q][m], c, r2);
+            }
+            u[s] = v;
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj) g[s][jj] = Ji[jj] * r0 + Ji[3 + jj] * r1 + Ji[6 + jj] * r2;   // J^{-T} grad_ref
+        }
+        volume_point<3, double>(a.c, u, g, Phi, Sr);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+                sPhi[q][s][m] = Ji[3 * m] * Phi[s][0] + Ji[3 * m + 1] * Phi[s][1] + Ji[3 * m + 2] * Phi[s][2];
+            sPhi[q][s][3] = Sr[s];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NS * NB; i += blockDim.x) {
+        const int s = i / NB, m = i % NB;
+        const double det = sG[21];
+        double acc = 0.0;
+        for (int q = 0; q < NQ; ++q) {
+            const double t = fma(sPhi[q][s][0], tb.VD[0][q][m],
+                                 fma(sPhi[q][s][1], tb.VD[1][q][m],
+                                     fma(sPhi[q][s][2], tb.VD[2][q][m], sPhi[q][s][3] * tb.VB[q][m])));
+            acc = fma(tb.VW[q], t, acc);
+        }
+        double R = det * acc;
+        for (int l = 0; l < 4; ++l) {
+            const int code = a.emap[e * 4 + l];
+            if (code >= 0) {
+                R += a.fbuf[(long long)code * NS * NB + s * NB + m];
+            } else if (code != -1) {
+                // boundary face l on Gamma_1 (code -2) or Gamma_2 (code -3), in e's own frame
+                const int f = -code - 2;
+                const int va = l == 0 ? 1 : 0, vb = l <= 1 ? 2 : 1, vc = l <= 2 ? 3 : 2;   // the vertices other than l
+                const int fr = frame_code(va, vb, vc);
+                double X[3][3];   // the face's vertices
+                const int vv[3] = {va, vb, vc};
+                for (int t = 0; t < 3; ++t) {
+                    const double r0 = vv[t] == 1 ? 1.0 : 0.0, r1 = vv[t] == 2 ? 1.0 : 0.0, r2 = vv[t] == 3 ? 1.0 : 0.0;
+                    for (int jj = 0; jj < 3; ++jj) X[t][jj] = sG[jj] + J[3 * jj] * r0 + J[3 * jj + 1] * r1 + J[3 * jj + 2] * r2;
+                }
+                double e1[3], e2[3];
+                for (int jj = 0; jj < 3; ++jj) {
+                    e1[jj] = X[1][jj] - X[0][jj];
+                    e2[jj] = X[2][jj] - X[0][jj];
+                }
+                const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+                             cz = e1[0] * e2[1] - e1[1] * e2[0];
+                const double E2 = sqrt(cx * cx + cy * cy + cz * cz);
+                double bacc = 0.0;
+                for (int p = 0; p < NP; ++p) {
+                    double uo[NS] = {0, 0, 0, 0, 0, 0}, sig[NS];
+                    double c1 = 0.0;
+                    for (int mm = 0; mm < NB; ++mm) c1 = fma(tb.FB[fr][p][mm], sU[3][mm], c1);
+                    uo[3] = c1;
+                    const double x = X[0][0] + tb.FX[p][0] * e1[0] + tb.FX[p][1] * e2[0];
+                    boundary_point<double>(a.c, f, x, a.g, uo, sig, a.c.beta1, true);
+                    bacc = fma(tb.FW[p], sig[s] * tb.FB[fr][p][m], bacc);
+                }
+                R += E2 * bacc;
+            }
+        }
+        a.out[e * NS * NB + s * NB + m] = (a.flags & CDG2_MINV) ? R / det : R;
+    }
+}
+
+}  // namespace cdg2
+
+namespace cdg2 {
+
+template <int K>
+static cudaError_t tet_launch(const TetArgs& a, cudaStream_t st) {
+    constexpr int FPB = 2;
+    if (a.NF > 0) tet_face_kernel<K, FPB><<<(unsigned)((a.NF + FPB - 1) / FPB), 128, 0, st>>>(a);
+    tet_elem_kernel<K><<<(unsigned)a.E, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+static int tet_upload(const cdg2_tet_mesh& m) {
+    if (m.d_tab) return CDG2_OK;
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void** dst, const void* src, size_t bytes) {
+        if (e != cudaSuccess) return;
+        e = cudaMalloc(dst, bytes > 0 ? bytes : 8);
+        if (e == cudaSuccess && src && bytes > 0) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up((void**)&m.d_geo, m.geo.data(), sizeof(double) * m.geo.size());
+    up((void**)&m.d_emap, m.emap.data(), sizeof(int) * m.emap.size());
+    up((void**)&m.d_face, m.face.data(), sizeof(int) * m.face.size());
+    up((void**)&m.d_fgeo, m.fgeo.data(), sizeof(double) * m.fgeo.size());
+    up((void**)&m.d_fbuf, nullptr, sizeof(double) * (size_t)m.NF * 2 * NS * m.nb);
+    up((void**)&m.d_tab, m.tab.data(), sizeof(TetTab));
+    if (e != cudaSuccess) return cuda_fail(e, "cdg2_tet_apply: mesh upload");
+    return CDG2_OK;
+}
+
+}  // namespace cdg2
+
+using namespace cdg2;
+
+extern "C" int cdg2_tet_mesh_create(const cdg2_tet_desc* d, cdg2_tet_mesh** out) {
+    if (!d || !out || !d->xyz || !d->tet) {
+        set_error("cdg2_tet_mesh_create: NULL argument");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (d->k < 1 || d->k > 3 || d->n_vert < 4 || d->n_tet < 1 || d->n_tet > (1LL << 28)) {
+        set_error("cdg2_tet_mesh_create: need 1 <= k <= 3, n_vert >= 4, 1 <= n_tet < 2^28");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    auto* m = new (std::nothrow) cdg2_tet_mesh;
+    if (!m) {
+        set_error("cdg2_tet_mesh_create: out of host memory");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    auto fail = [&](const std::string& msg) {
+        delete m;
+        set_error("cdg2_tet_mesh_create: " + msg);
+        return CDG2_ERR_INVALID_ARG;
+    };
+    m->k = d->k;
+    m->nb = (d->k + 1) * (d->k + 2) * (d->k + 3) / 6;
+    m->E = d->n_tet;
+    m->chi_e = d->chi_e > 0.0 ? d->chi_e : 2.0;
+    m->g1in[0] = d->gamma1_in[0];
+    m->g1in[1] = d->gamma1_in[1];
+    const double* X = d->xyz;
+    double ly = X[1];
+    for (long long v = 0; v < d->n_vert; ++v) ly = std::max(ly, X[3 * v + 1]);
+    m->ly = ly;
+    m->geo.assign((size_t)m->E * TGEO, 0.0);
+    for (long long e = 0; e < m->E; ++e) {
+        long long v[4];
+        for (int j = 0; j < 4; ++j) {
+            v[j] = d->tet[4 * e + j];
+            if (v[j] < 0 || v[j] >= d->n_vert) return fail("vertex index out of range");
+        }
+        double J[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) J[r][c] = X[3 * v[c + 1] + r] - X[3 * v[0] + r];
+        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        if (!(det > 0.0))
+            return fail("tetrahedron " + std::to_string(e) + " is degenerate or negatively oriented");
+        double* G = &m->geo[(size_t)e * TGEO];
+        for (int r = 0; r < 3; ++r) G[r] = X[3 * v[0] + r];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) G[3 + 3 * r + c] = J[r][c];
+        // inverse by cofactors
+        G[12] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+        G[13] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+        G[14] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+        G[15] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+        G[16] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+        G[17] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+        G[18] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+        G[19] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+        G[20] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+        G[21] = det;
+    }
+    std::map<std::vector<long long>, std::vector<std::pair<long long, int>>> faces;
+    for (long long e = 0; e < m->E; ++e)
+        for (int l = 0; l < 4; ++l) {
+            std::vector<long long> key;
+            for (int t = 0; t < 3; ++t) key.push_back(d->tet[4 * e + FACE_VERTS[l][t]]);
+            std::sort(key.begin(), key.end());
+            faces[key].push_back({e, l});
+        }
+    m->emap.assign((size_t)m->E * 4, -1);
+    const double tol = 1e-12 * std::max(1.0, ly);
+    for (const auto& kv : faces) {
+        const auto& own = kv.second;
+        if (own.size() == 2) {
+            long long e1 = own[0].first, e2 = own[1].first;
+            int l1 = own[0].second, l2 = own[1].second;
+            const double v1 = m->geo[(size_t)e1 * TGEO + 21], v2 = m->geo[(size_t)e2 * TGEO + 21];
+            const bool tie = std::fabs(v1 - v2) <= 1e-12 * std::max(v1, v2);
+            if (!((!tie && v1 < v2) || (tie && e1 < e2))) {
+                std::swap(e1, e2);
+                std::swap(l1, l2);
+            }
+            // K^-'s face vertices in its order, and their local indices in K^+
+            long long gv[3];
+            int lp[3];
+            for (int t = 0; t < 3; ++t) {
+                gv[t] = d->tet[4 * e1 + FACE_VERTS[l1][t]];
+                lp[t] = -1;
+                for (int c = 0; c < 4; ++c)
+                    if (d->tet[4 * e2 + c] == gv[t]) lp[t] = c;
+                if (lp[t] < 0 || lp[t] == l2) return fail("inconsistent face between tetrahedra");
+            }
+            const int frM = frame_code(FACE_VERTS[l1][0], FACE_VERTS[l1][1], FACE_VERTS[l1][2]);
+            const int frP = frame_code(lp[0], lp[1], lp[2]);
+            const long long f = (long long)m->face.size() / 4;
+            m->face.insert(m->face.end(), {(int)e1, (int)e2, frM, frP});
+            double A[3], B[3], C[3], opp[3];
+            for (int r = 0; r < 3; ++r) {
+                A[r] = X[3 * gv[0] + r];
+                B[r] = X[3 * gv[1] + r];
+                C[r] = X[3 * gv[2] + r];
+                opp[r] = X[3 * d->tet[4 * e1 + l1] + r];
+            }
+            const double u[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+            const double w[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+            double cr[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+            const double E2 = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+            double side = 0.0;
+            for (int r = 0; r < 3; ++r) side += cr[r] * (opp[r] - A[r]);
+            const double sg = side > 0.0 ? -1.0 : 1.0;   // the normal points away from K^-'s opposite vertex
+            m->fgeo.insert(m->fgeo.end(), {sg * cr[0] / E2, sg * cr[1] / E2, sg * cr[2] / E2, E2,
+                                           m->geo[(size_t)e1 * TGEO + 21]});
+            m->emap[(size_t)e1 * 4 + l1] = (int)(2 * f);
+            m->emap[(size_t)e2 * 4 + l2] = (int)(2 * f + 1);
+        } else if (own.size() == 1) {
+            bool g1 = true, g2 = true;
+            for (long long v : kv.first) {
+                const double y = X[3 * v + 1];
+                g1 = g1 && std::fabs(y) <= tol;
+                g2 = g2 && std::fabs(y - ly) <= tol;
+            }
+            const int tag = g1 ? 1 : (g2 ? 2 : 0);
+            m->emap[(size_t)own[0].first * 4 + own[0].second] = -1 - tag;
+        } else {
+            return fail("a face is shared by more than two tetrahedra");
+        }
+    }
+    m->NF = (long long)m->face.size() / 4;
+    m->tab.resize(1);
+    build_tet_tables(m->k, m->tab[0]);
+    *out = m;
+    return CDG2_OK;
+}
+
+extern "C" void cdg2_tet_mesh_destroy(cdg2_tet_mesh* m) {
+    if (!m) return;
+    cudaFree(m->d_geo);
+    cudaFree(m->d_emap);
+    cudaFree(m->d_face);
+    cudaFree(m->d_fgeo);
+    cudaFree(m->d_fbuf);
+    cudaFree(m->d_tab);
+    delete m;
+}
+
+extern "C" int cdg2_tet_mesh_info(const cdg2_tet_mesh* m, long long* n_elem, int* n_basis, long long* n_dof,
+                                  long long* n_faces) {
+    if (!m) {
+        set_error("cdg2_tet_mesh_info: NULL mesh");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (n_elem) *n_elem = m->E;
+    if (n_basis) *n_basis = m->nb;
+    if (n_dof) *n_dof = m->E * NS * m->nb;
+    if (n_faces) *n_faces = m->NF;
+    return CDG2_OK;
+}
+
+extern "C" int cdg2_tet_apply(const cdg2_tet_mesh* m, const cdg2_params* p, const double* U, double* out, int flags,
+                              void* stream) {
+    if (!m || !p || !U || !out) {
+        set_error("cdg2_tet_apply: NULL argument");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (U == out) {
+        set_error("cdg2_tet_apply: U and out must not overlap");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (flags & ~CDG2_MINV) {
+        set_error("cdg2_tet_apply: only CDG2_MINV is supported on tetrahedral meshes");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (int rc = tet_upload(*m)) return rc;
+    TetArgs a;
+    a.U = U;
+    a.out = out;
+    a.flags = flags;
+    a.chi_e = m->chi_e;
+    a.E = m->E;
+    a.NF = m->NF;
+    a.geo = m->d_geo;
+    a.emap = m->d_emap;
+    a.face = m->d_face;
+    a.fgeo = m->d_fgeo;
+    a.tab = m->d_tab;
+    a.fbuf = m->d_fbuf;
+    Geo g;
+    std::memset(&g, 0, sizeof(g));
+    g.dim = 3;
+    g.k = m->k;
+    g.vol = 1.0;
+    for (int j = 0; j < 3; ++j) {
+        g.h[j] = 1.0;
+        g.n[j] = 1;
+    }
+    g.g1in[0] = m->g1in[0];
+    g.g1in[1] = m->g1in[1];
+    a.g = g;
+    a.c = make_coefT<double>(make_coef(*p), g, nullptr);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    switch (m->k) {
+        case 1: e = tet_launch<1>(a, st); break;
+        case 2: e = tet_launch<2>(a, st); break;
+        default: e = tet_launch<3>(a, st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cdg2_tet_apply");
+    return CDG2_OK;
+}

@@ -255,6 +255,22 @@ def measure_tri(G, torch, flush, steps):
             "kernels": "tri_face_kernel<3> + tri_elem_kernel<3> (one apply)"}
 
 
+def measure_tet(G, torch, flush, steps):
+    """FP64 cdg2_tet_apply on the 32x8x8x6 P3 tetrahedral mesh (seeded jitter,
+    seeded positive coefficients), L2 flushed before every timed apply."""
+    import cdg2_inputs as I
+    w = I.tet_workload(1)
+    xyz, tet = I.tet_mesh(*w.cells, *w.extent, w.jitter, w.seed)
+    mesh = G.cdg2_tet_mesh_create(xyz, tet, w.k)
+    p = I.default_params()
+    U = torch.from_numpy(I.random_coefficients(mesh.n_elem, mesh.n_basis, w.seed, 0.1)).reshape(-1).cuda()
+    out = torch.empty_like(U)
+    ms = time_op(G, torch, lambda: G.cdg2_tet_apply(mesh, p, U, out, G.CDG2_MINV), steps, 3, flush)
+    return {"workload": w.name, "n_dof": mesh.n_dof, "n_elem": mesh.n_elem, "n_faces": mesh.n_faces,
+            "ms": ms, "value": mesh.n_dof / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "dtype": "f64",
+            "kernels": "tet_face_kernel<3> + tet_elem_kernel<3> (one apply)"}
+
+
 def measure_solve(G, torch, cfg: int, steps: int, precond: int):
     """Implicit SDIRK steps to Newton relative residual 1e-10: FP64 Krylov vs FP32 Krylov + FP64 refinement."""
     import cdg2_inputs as I
@@ -400,7 +416,7 @@ def main():
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-tri", action="store_true", help="skip the triangle-mesh apply timing")
+    ap.add_argument("--no-tri", action="store_true", help="skip the triangle- and tetrahedral-mesh apply timings")
     ap.add_argument("--solve-config", type=int, default=3, help="workload of the implicit-solve comparison")
     ap.add_argument("--solve-steps", type=int, default=2, help="timed implicit steps per precision (0: skip)")
     ap.add_argument("--grad-config", type=int, default=2, help="workload of the gradient-through-steps timing")
@@ -522,6 +538,7 @@ def main():
 
     derivs = measure_derivatives(G, torch, w, mesh, p, U, flush, max(10, args.steps // 8))
     tri = measure_tri(G, torch, flush, max(10, args.steps // 8)) if not args.no_tri else None
+    tet = measure_tet(G, torch, flush, max(10, args.steps // 8)) if not args.no_tri else None
     solve = measure_solve(G, torch, args.solve_config, args.solve_steps, args.precond) if args.solve_steps > 0 else None
     grad = None
     if args.grad_steps != 0:
@@ -550,6 +567,7 @@ def main():
         "fp32": fp32,
         "derivatives": derivs,
         "triangles": tri,
+        "tetrahedra": tet,
         "solve": solve,
         "gradient": grad,
         "e2e": e2e,

@@ -304,3 +304,37 @@ def tet_mesh(nx: int, ny: int, nz: int, lx: float = 1.0, ly: float = 0.2, lz: fl
                         verts[2], verts[3] = verts[3], verts[2]
                     tets.append(verts)
     return xyz, np.array(tets, dtype=np.int64)
+
+
+@dataclass
+class TetWorkload:
+    name: str
+    cells: tuple
+    k: int
+    jitter: float
+    seed: int
+    extent: tuple = (1.0, 0.2, 0.2)
+
+    @property
+    def n_elem(self) -> int:
+        return 6 * self.cells[0] * self.cells[1] * self.cells[2]
+
+    @property
+    def n_basis(self) -> int:
+        return (self.k + 1) * (self.k + 2) * (self.k + 3) // 6
+
+    @property
+    def n_dof(self) -> int:
+        return N_SPECIES * self.n_elem * self.n_basis
+
+
+def tet_workload(which: int, k: int | None = None) -> TetWorkload:
+    """Tetrahedral workloads (the paper's 3D runs use tetrahedra, P_k, chi_e = 2):
+    0: 3x2x2 cells (72 tetrahedra) P2, jitter 0.15, seed 1180 (oracle sized);
+    1: 32x8x8 cells (12,288 tetrahedra) P3, jitter 0.15, seed 1181 (1,474,560
+    DOF on the box of the 3D workloads)."""
+    if which == 0:
+        return TetWorkload("3D tetrahedra 3x2x2x6 P2 (jittered)", (3, 2, 2), 2 if k is None else k, 0.15, 1180)
+    if which == 1:
+        return TetWorkload("3D tetrahedra 32x8x8x6 P3 (jittered)", (32, 8, 8), 3 if k is None else k, 0.15, 1181)
+    raise ValueError(f"unknown tetrahedral workload {which}")

@@ -323,30 +323,38 @@ __global__ void __launch_bounds__(128) tet_elem_kernel(const TetArgs a) {
     const TetTab& tb = *a.tab;
     __shared__ double sU[NS][NB];
     __shared__ double sG[TGEO];
-    __shared__ double sPhi[NQ][NS][4];   // J^{-1} Phi (3), S
+    __shared__ double sPhi[NQ][NS][4];   // grad U (3), U at the points; then J^{-1} Phi (3), S
     const long long e = blockIdx.x;
     for (int i = threadIdx.x; i < TGEO; i += blockDim.x) sG[i] = a.geo[e * TGEO + i];
     for (int i = threadIdx.x; i < NS * NB; i += blockDim.x) sU[i / NB][i % NB] = a.U[e * NS * NB + i];
     __syncthreads();
     const double* J = sG + 3;
     const double* Ji = sG + 12;
+    // values and physical gradients at the points, one (point, species) per thread
+    for (int i = threadIdx.x; i < NQ * NS; i += blockDim.x) {
+        const int q = i / NS, s = i % NS;
+        double v = 0.0, r0 = 0.0, r1 = 0.0, r2 = 0.0;
+        for (int m = 0; m < NB; ++m) {
+            const double c = sU[s][m];
+            v = fma(tb.VB[q][m], c, v);
+            r0 = fma(tb.VD[0][q][m], c, r0);
+            r1 = fma(tb.VD[1][q][m], c, r1);
+            r2 = fma(tb.VD[2][q][m], c, r2);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) sPhi[q][s][jj] = Ji[jj] * r0 + Ji[3 + jj] * r1 + Ji[6 + jj] * r2;   // J^{-T} grad_ref
+        sPhi[q][s][3] = v;
+    }
+    __syncthreads();
     for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
         double u[NS], g[NS][3], Phi[NS][3], Sr[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            double v = 0.0, r0 = 0.0, r1 = 0.0, r2 = 0.0;
-            for (int m = 0; m < NB; ++m) {
-                const double c = sU[s][m];
-                v = fma(tb.VB[q][m], c, v);
-                r0 = fma(tb.VD[0][q][m], c, r0);
-                r1 = fma(tb.VD[1][q][m], c, r1);
-                r2 = fma(tb.VD[2][q][m], c, r2);
-            }
-            u[s] = v;
+            u[s] = sPhi[q][s][3];
 #pragma unroll
-            for (int jj = 0; jj < 3; ++jj) g[s][jj] = Ji[jj] * r0 + Ji[3 + jj] * r1 + Ji[6 + jj] * r2;   // J^{-T} grad_ref
+            for (int jj = 0; jj < 3; ++jj) g[s][jj] = sPhi[q][s][jj];
         }
-        volume_point<3, double>(a.c, u, g, Phi, Sr);
+        volume_point<3, double>(a.c, u, g, Phi, Sr);   // (in place: this thread alone owns point q)
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
 #pragma unroll

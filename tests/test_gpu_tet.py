@@ -84,3 +84,38 @@ def test_tet_apply_reduced_model_and_outward_sign(G):
             V[:, [1, 4, 5], :] = 0.0
         got = _run(G, xyz, tet, k, p, V, G.CDG2_MINV)
         assert rel_l2_per_species(got, TT.apply(om, V, p)) <= 1e-12
+
+
+def test_tet_apply_full_size_sampled_rows(G):
+    """32x8x8x6 P3 (1.47M DOF): sampled tetrahedra against the oracle on the patch
+    of each tetrahedron and its face neighbours (ascending global index, so the
+    tie rule picks the same K^-), which fixes its row of M^{-1} L_h."""
+    w = I.tet_workload(1)
+    xyz, tet = I.tet_mesh(*w.cells, *w.extent, w.jitter, w.seed)
+    gm = G.cdg2_tet_mesh_create(xyz, tet, w.k)
+    p = _params()
+    U = torch.from_numpy(I.random_coefficients(gm.n_elem, gm.n_basis, w.seed, 0.1))
+    out = torch.empty(gm.n_dof, dtype=torch.float64, device="cuda")
+    G.cdg2_tet_apply(gm, p, U.reshape(-1).cuda(), out, G.CDG2_MINV)
+    got = out.cpu().reshape(U.shape)
+    owner = {}
+    for t in range(len(tet)):
+        for l in range(4):
+            key = tuple(sorted(int(v) for j, v in enumerate(tet[t]) if j != l))
+            owner.setdefault(key, []).append(t)
+    nbrs = {t: [] for t in range(len(tet))}
+    for ts in owner.values():
+        if len(ts) == 2:
+            nbrs[ts[0]].append(ts[1])
+            nbrs[ts[1]].append(ts[0])
+    rng = np.random.default_rng(5)
+    sample = list(rng.choice(len(tet), 30, replace=False)) + [0, len(tet) - 1]
+    for e in sample:
+        cells = sorted({int(e)} | set(nbrs[int(e)]))
+        verts = sorted({int(v) for c in cells for v in tet[c]})
+        vmap = {v: i for i, v in enumerate(verts)}
+        sub = np.array([[vmap[int(v)] for v in tet[c]] for c in cells], dtype=np.int64)
+        om = TT.TetMesh(xyz[verts], sub, w.k)
+        ref = TT.apply(om, U[cells], p)[cells.index(int(e))]
+        err = float((got[int(e)] - ref).norm() / ref.norm())
+        assert err <= 1e-12, (int(e), err)

@@ -412,6 +412,23 @@ int cdg2_tet_mesh_info(const cdg2_tet_mesh* mesh, long long* n_elem, int* n_basi
 int cdg2_tet_apply(const cdg2_tet_mesh* mesh, const cdg2_params* params, const double* U, double* out, int flags,
                    void* stream);
 
+/* out = J(U) dU, the derivative of cdg2_tet_apply along dU (the linearised
+ * element and face terms; the lifting is linear; H' = 0, so the boundary data
+ * drop out), same layout and flags.  U, dU, out: device float64, out must
+ * not overlap U or dU.  Errors as cdg2_tet_apply. */
+int cdg2_tet_jvp(const cdg2_tet_mesh* mesh, const cdg2_params* params, const double* U, const double* dU, double* out,
+                 int flags, void* stream);
+
+/* gU = J(U)^T lambda for cdg2_tet_apply with the same flags (CDG2_MINV: the
+ * transpose of M^{-1} L_h), as a gather: every interior face once (the
+ * cotangents of its flux back through the flux and the K^- lifting, tested
+ * against both sides into the face buffer), then every element (its volume
+ * terms and its faces); no atomics, bitwise reproducible.  H' = 0: the
+ * boundary data add nothing.  U, lam, gU: device float64, gU must not
+ * overlap U or lam.  Errors as cdg2_tet_apply. */
+int cdg2_tet_vjp(const cdg2_tet_mesh* mesh, const cdg2_params* params, const double* U, const double* lam,
+                 double* gU, int flags, void* stream);
+
 const char* cdg2_last_error(void);
 
 #ifdef __cplusplus

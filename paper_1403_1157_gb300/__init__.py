@@ -181,6 +181,9 @@ def load_library():
     lib.cdg2_tet_mesh_info.restype = i
     lib.cdg2_tet_apply.argtypes = [vp, ctypes.POINTER(Params), vp, vp, i, vp]
     lib.cdg2_tet_apply.restype = i
+    for name in ("cdg2_tet_jvp", "cdg2_tet_vjp"):
+        getattr(lib, name).argtypes = [vp, ctypes.POINTER(Params), vp, vp, vp, i, vp]
+        getattr(lib, name).restype = i
     lib.cdg2_element_block.argtypes = [vp, ctypes.POINTER(Params), d, ctypes.c_longlong, i, dp]
     lib.cdg2_element_block.restype = i
     lib.cdg2_last_error.argtypes = []
@@ -456,6 +459,32 @@ def cdg2_tet_apply(mesh: TetMesh, params, U: torch.Tensor, out: torch.Tensor, fl
     _check(load_library().cdg2_tet_apply(mesh.handle, ctypes.byref(p), ctypes.c_void_p(U.data_ptr()),
                                          ctypes.c_void_p(out.data_ptr()), int(flags), _stream_ptr(stream)))
     return out
+
+
+def cdg2_tet_jvp(mesh: TetMesh, params, U: torch.Tensor, dU: torch.Tensor, out: torch.Tensor,
+                 flags: int = CDG2_MINV, stream=None) -> torch.Tensor:
+    """out = J(U) dU on a tetrahedral mesh (float64 CUDA tensors of n_dof values)."""
+    for name, t in (("U", U), ("dU", dU), ("out", out)):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == mesh.n_dof):
+            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of {mesh.n_dof} values")
+    p = _params(params)
+    _check(load_library().cdg2_tet_jvp(mesh.handle, ctypes.byref(p), ctypes.c_void_p(U.data_ptr()),
+                                       ctypes.c_void_p(dU.data_ptr()), ctypes.c_void_p(out.data_ptr()), int(flags),
+                                       _stream_ptr(stream)))
+    return out
+
+
+def cdg2_tet_vjp(mesh: TetMesh, params, U: torch.Tensor, lam: torch.Tensor, gU: torch.Tensor,
+                 flags: int = CDG2_MINV, stream=None) -> torch.Tensor:
+    """gU = J(U)^T lam on a tetrahedral mesh (float64 CUDA tensors of n_dof values)."""
+    for name, t in (("U", U), ("lam", lam), ("gU", gU)):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == mesh.n_dof):
+            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of {mesh.n_dof} values")
+    p = _params(params)
+    _check(load_library().cdg2_tet_vjp(mesh.handle, ctypes.byref(p), ctypes.c_void_p(U.data_ptr()),
+                                       ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(gU.data_ptr()), int(flags),
+                                       _stream_ptr(stream)))
+    return gU
 
 
 def _theta_ptr(dtheta):

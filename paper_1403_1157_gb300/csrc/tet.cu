@@ -207,6 +207,7 @@ struct TetShape {
 
 struct TetArgs {
     const double* U;
+    const double* dU;    // JVP: the tangent; VJP: lambda
     double* out;
     int flags;
     double chi_e;
@@ -221,21 +222,28 @@ struct TetArgs {
     CoefT<double> c;
 };
 
+constexpr int TET_APPLY = 0, TET_JVP = 1, TET_VJP = 2;
+
 // One CTA: FPB interior faces.  Traces of both sides at K^-'s face points
-// (each side through its frame), the K^- lifting, the face flux, and its test
-// against both sides' basis into the face buffer ([face][side][6][nb]).
-template <int K, int FPB>
+// (each side through its frame), the K^- lifting, the face flux (JVP: its
+// linearisation; VJP: the cotangents E w_p (mu^- - mu^+) of sigma and
+// E w_p (d_n mu^- + d_n mu^+) of tau back through face_point_adj per side and
+// the transposed lifting, mu = M^{-1} lambda), and the test against both
+// sides' basis into the face buffer ([face][side][6][nb]).
+template <int K, int FPB, int MODE>
 __global__ void __launch_bounds__(128) tet_face_kernel(const TetArgs a) {
     using S = TetShape<K>;
-    constexpr int NB = S::NB, NP = S::NP;
+    constexpr int NB = S::NB, NP = S::NP, F = MODE == TET_APPLY ? 1 : 2;
     const TetTab& tb = *a.tab;
-    __shared__ double sU[FPB][2][NS][NB];
+    __shared__ double sU[FPB][2][F][NS][NB];
     __shared__ double sJ[FPB][2][9];          // J^{-1} of each side (row-major)
+    __shared__ double sDet[FPB][2];
     __shared__ double sF[FPB][5];             // n (3), E, det_-
     __shared__ int sI[FPB][4];                // eM, eP, frame of K^-, frame of K^+
     __shared__ double sDN[FPB][2][NP][NB];    // n^- . grad phi_m of each side at the face points
-    __shared__ double sT[FPB][2][2][NS][NP];  // [side][value, normal derivative][s][p]
-    __shared__ double sS[FPB][2][NS][NP];     // sigma, tau
+    __shared__ double sT[FPB][2][F][2][NS][NP];  // [side][field][value, normal derivative][s][p]
+    __shared__ double sS[FPB][2][NS][NP];     // sigma, tau (VJP: their cotangents)
+    __shared__ double sA[MODE == TET_VJP ? FPB : 1][2][2][NS][NP];   // VJP: trace cotangents
     const long long f0 = (long long)blockIdx.x * FPB;
     const int nf = (int)min((long long)FPB, a.NF - f0);
     for (int i = threadIdx.x; i < nf * 5; i += blockDim.x) {
@@ -247,10 +255,12 @@ __global__ void __launch_bounds__(128) tet_face_kernel(const TetArgs a) {
     for (int i = threadIdx.x; i < nf * 2 * 9; i += blockDim.x) {
         const int j = i / 18, side = (i / 9) % 2, c = i % 9;
         sJ[j][side][c] = a.geo[(long long)sI[j][side] * TGEO + 12 + c];
+        if (c == 0) sDet[j][side] = a.geo[(long long)sI[j][side] * TGEO + 21];
     }
-    for (int i = threadIdx.x; i < nf * 2 * NS * NB; i += blockDim.x) {
-        const int j = i / (2 * NS * NB), side = (i / (NS * NB)) % 2, r = i % (NS * NB);
-        sU[j][side][r / NB][r % NB] = a.U[(long long)sI[j][side] * NS * NB + r];
+    for (int i = threadIdx.x; i < nf * 2 * F * NS * NB; i += blockDim.x) {
+        const int j = i / (2 * F * NS * NB), side = (i / (F * NS * NB)) % 2, fi = (i / (NS * NB)) % F;
+        const int r = i % (NS * NB);
+        sU[j][side][fi][r / NB][r % NB] = (fi ? a.dU : a.U)[(long long)sI[j][side] * NS * NB + r];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nf * 2 * NP * NB; i += blockDim.x) {
@@ -264,20 +274,69 @@ __global__ void __launch_bounds__(128) tet_face_kernel(const TetArgs a) {
         sDN[j][side][p][m] = dn;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nf * 2 * NS * NP; i += blockDim.x) {
-        const int j = i / (2 * NS * NP), side = (i / (NS * NP)) % 2, s = (i / NP) % NS, p = i % NP;
+    for (int i = threadIdx.x; i < nf * 2 * F * NS * NP; i += blockDim.x) {
+        const int j = i / (2 * F * NS * NP), side = (i / (F * NS * NP)) % 2, fi = (i / (NS * NP)) % F;
+        const int s = (i / NP) % NS, p = i % NP;
         const int fr = sI[j][2 + side];
         double v = 0.0, dn = 0.0;
 #pragma unroll 4
         for (int m = 0; m < NB; ++m) {
-            const double u = sU[j][side][s][m];
+            const double u = sU[j][side][fi][s][m];
             v = fma(tb.FB[fr][p][m], u, v);
             dn = fma(sDN[j][side][p][m], u, dn);
         }
-        sT[j][side][0][s][p] = v;
-        sT[j][side][1][s][p] = dn;
+        // VJP: the cotangent field enters as mu = M^{-1} lambda = lambda / det J (with CDG2_MINV)
+        const double sc = (MODE == TET_VJP && fi == 1 && (a.flags & CDG2_MINV)) ? 1.0 / sDet[j][side] : 1.0;
+        sT[j][side][fi][0][s][p] = v * sc;
+        sT[j][side][fi][1][s][p] = dn * sc;
     }
     __syncthreads();
+    if constexpr (MODE == TET_VJP) {
+        for (int i = threadIdx.x; i < nf * NS * NP; i += blockDim.x) {
+            const int j = i / (NS * NP), s = (i / NP) % NS, p = i % NP;
+            const double W = sF[j][3] * tb.FW[p];
+            sS[j][0][s][p] = W * (sT[j][0][1][0][s][p] - sT[j][1][1][0][s][p]);
+            sS[j][1][s][p] = W * (sT[j][0][1][1][s][p] + sT[j][1][1][1][s][p]);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nf * NP; i += blockDim.x) {
+            const int j = i / NP, q = i % NP;
+            const int frM = sI[j][2];
+            const double lift = -sF[j][3] / (2.0 * sF[j][4]);
+            double uM[NS], dM[NS], uP[NS], dP[NS], del[NS], sb[NS], tbb[NS], ub[NS], db[NS], lb[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                uM[s] = sT[j][0][0][0][s][q];
+                dM[s] = sT[j][0][0][1][s][q];
+                uP[s] = sT[j][1][0][0][s][q];
+                dP[s] = sT[j][1][0][1][s][q];
+                del[s] = uM[s] - uP[s];
+                sb[s] = sS[j][0][s][q];
+                tbb[s] = sS[j][1][s][q];
+                double acc = 0.0;
+                for (int p = 0; p < NP; ++p) acc = fma(sS[j][0][s][p], tb.LF[frM][p][q], acc);
+                lb[s] = 2.0 * a.chi_e * a.c.A[s] * lift * acc;
+            }
+            for (int side = 0; side < 2; ++side) {
+                face_point_adj<double>(a.c, 0.0, side == 0, uM, dM, uP, dP, del, sb, tbb, ub, db);
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    sA[j][side][0][s][q] = ub[s] + (side == 0 ? lb[s] : -lb[s]);
+                    sA[j][side][1][s][q] = db[s];
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nf * 2 * NS * NB; i += blockDim.x) {
+            const int j = i / (2 * NS * NB), side = (i / (NS * NB)) % 2, s = (i / NB) % NS, m = i % NB;
+            const int fr = sI[j][2 + side];
+            double acc = 0.0;
+            for (int p = 0; p < NP; ++p)
+                acc = fma(sA[j][side][0][s][p], tb.FB[fr][p][m], fma(sA[j][side][1][s][p], sDN[j][side][p][m], acc));
+            a.fbuf[((f0 + j) * 2 + side) * NS * NB + s * NB + m] = acc;
+        }
+        return;
+    }
     for (int i = threadIdx.x; i < nf * NP; i += blockDim.x) {
         const int j = i / NP, p = i % NP;
         const int frM = sI[j][2];
@@ -285,17 +344,31 @@ __global__ void __launch_bounds__(128) tet_face_kernel(const TetArgs a) {
         double uM[NS], dM[NS], uP[NS], dP[NS], del[NS], sig[NS], tau[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            uM[s] = sT[j][0][0][s][p];
-            dM[s] = sT[j][0][1][s][p];
-            uP[s] = sT[j][1][0][s][p];
-            dP[s] = sT[j][1][1][s][p];
+            uM[s] = sT[j][0][0][0][s][p];
+            dM[s] = sT[j][0][0][1][s][p];
+            uP[s] = sT[j][1][0][0][s][p];
+            dP[s] = sT[j][1][0][1][s][p];
             del[s] = uM[s] - uP[s];
         }
-        face_point<double>(a.c, 0.0, uM, dM, uP, dP, del, sig, tau);
+        if constexpr (MODE == TET_APPLY) {
+            face_point<double>(a.c, 0.0, uM, dM, uP, dP, del, sig, tau);
+        } else {
+            double duM[NS], ddM[NS], duP[NS], ddP[NS], ddel[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                duM[s] = sT[j][0][F - 1][0][s][p];
+                ddM[s] = sT[j][0][F - 1][1][s][p];
+                duP[s] = sT[j][1][F - 1][0][s][p];
+                ddP[s] = sT[j][1][F - 1][1][s][p];
+                ddel[s] = duM[s] - duP[s];
+            }
+            face_point_lin<double>(a.c, 0.0, uM, dM, uP, dP, del, duM, ddM, duP, ddP, ddel, sig, tau);
+        }
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             double rn = 0.0;
-            for (int q = 0; q < NP; ++q) rn = fma(tb.LF[frM][p][q], sT[j][0][0][s][q] - sT[j][1][0][s][q], rn);
+            for (int q = 0; q < NP; ++q)
+                rn = fma(tb.LF[frM][p][q], sT[j][0][F - 1][0][s][q] - sT[j][1][F - 1][0][s][q], rn);
             sS[j][0][s][p] = sig[s] + 2.0 * a.chi_e * a.c.A[s] * lift * rn;
             sS[j][1][s][p] = tau[s];
         }
@@ -312,74 +385,104 @@ __global__ void __launch_bounds__(128) tet_face_kernel(const TetArgs a) {
     }
 }
 
-// One CTA: one element.  Volume terms at the collapsed Gauss points (Phi is
-// mapped back by J^{-1}, so the test uses the reference gradients), the tested
-// fluxes of its interior faces, the boundary data of Eq. (3) on its boundary
-// faces, M^{-1} = 1 / det J.
-template <int K>
+// One CTA: one element.  Values and physical gradients of every field per
+// (point, species), the pointwise flux (JVP: linearised; VJP: its adjoint with
+// the cotangents det w_q mu, det w_q grad mu), the result mapped back by
+// J^{-1} and tested against the reference gradients, the tested fluxes of its
+// interior faces, the boundary data of Eq. (3) on its boundary faces (apply
+// only: H' = 0), M^{-1} = 1 / det J (not for the VJP).  Dynamic shared memory:
+// U [F][6][nb], then [F][NQ][6][4] point values.
+template <int K, int MODE>
 __global__ void __launch_bounds__(128) tet_elem_kernel(const TetArgs a) {
     using S = TetShape<K>;
-    constexpr int NB = S::NB, NQ = S::NQ, NP = S::NP;
+    constexpr int NB = S::NB, NQ = S::NQ, NP = S::NP, F = MODE == TET_APPLY ? 1 : 2;
     const TetTab& tb = *a.tab;
-    __shared__ double sU[NS][NB];
+    extern __shared__ __align__(16) double tsm[];
+    double (*sU)[NS][NB] = reinterpret_cast<double (*)[NS][NB]>(tsm);                     // [F]
+    double (*sQ)[NQ][NS][4] = reinterpret_cast<double (*)[NQ][NS][4]>(tsm + F * NS * NB);   // [F]
     __shared__ double sG[TGEO];
-    __shared__ double sPhi[NQ][NS][4];   // grad U (3), U at the points; then J^{-1} Phi (3), S
     const long long e = blockIdx.x;
     for (int i = threadIdx.x; i < TGEO; i += blockDim.x) sG[i] = a.geo[e * TGEO + i];
-    for (int i = threadIdx.x; i < NS * NB; i += blockDim.x) sU[i / NB][i % NB] = a.U[e * NS * NB + i];
+    for (int i = threadIdx.x; i < F * NS * NB; i += blockDim.x) {
+        const int fi = i / (NS * NB), r = i % (NS * NB);
+        sU[fi][r / NB][r % NB] = (fi ? a.dU : a.U)[e * NS * NB + r];
+    }
     __syncthreads();
     const double* J = sG + 3;
     const double* Ji = sG + 12;
-    // values and physical gradients at the points, one (point, species) per thread
-    for (int i = threadIdx.x; i < NQ * NS; i += blockDim.x) {
-        const int q = i / NS, s = i % NS;
+    const double det = sG[21];
+    for (int i = threadIdx.x; i < F * NQ * NS; i += blockDim.x) {
+        const int fi = i / (NQ * NS), q = (i / NS) % NQ, s = i % NS;
         double v = 0.0, r0 = 0.0, r1 = 0.0, r2 = 0.0;
         for (int m = 0; m < NB; ++m) {
-            const double c = sU[s][m];
+            const double c = sU[fi][s][m];
             v = fma(tb.VB[q][m], c, v);
             r0 = fma(tb.VD[0][q][m], c, r0);
             r1 = fma(tb.VD[1][q][m], c, r1);
             r2 = fma(tb.VD[2][q][m], c, r2);
         }
 #pragma unroll
-        for (int jj = 0; jj < 3; ++jj) sPhi[q][s][jj] = Ji[jj] * r0 + Ji[3 + jj] * r1 + Ji[6 + jj] * r2;   // J^{-T} grad_ref
-        sPhi[q][s][3] = v;
+        for (int jj = 0; jj < 3; ++jj) sQ[fi][q][s][jj] = Ji[jj] * r0 + Ji[3 + jj] * r1 + Ji[6 + jj] * r2;   // J^{-T} grad_ref
+        sQ[fi][q][s][3] = v;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
         double u[NS], g[NS][3], Phi[NS][3], Sr[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            u[s] = sPhi[q][s][3];
+            u[s] = sQ[0][q][s][3];
 #pragma unroll
-            for (int jj = 0; jj < 3; ++jj) g[s][jj] = sPhi[q][s][jj];
+            for (int jj = 0; jj < 3; ++jj) g[s][jj] = sQ[0][q][s][jj];
         }
-        volume_point<3, double>(a.c, u, g, Phi, Sr);   // (in place: this thread alone owns point q)
+        if constexpr (MODE == TET_APPLY) {
+            volume_point<3, double>(a.c, u, g, Phi, Sr);
+        } else {
+            double du[NS], dg[NS][3];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                du[s] = sQ[F - 1][q][s][3];
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj) dg[s][jj] = sQ[F - 1][q][s][jj];
+            }
+            if constexpr (MODE == TET_JVP) {
+                volume_point_lin<3, double>(a.c, u, g, du, dg, false, Phi, Sr);
+            } else {
+                // mu = M^{-1} lambda = lambda / det (with CDG2_MINV); w_q is applied by the test below
+                const double W = (a.flags & CDG2_MINV) ? 1.0 : det;
+                double sb[NS], gb[NS][3], th[8];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    sb[s] = W * du[s];
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) gb[s][jj] = W * dg[s][jj];
+                }
+                volume_point_adj<3, double>(a.c, u, g, sb, gb, Sr, Phi, th);   // Sr <- ub, Phi <- Gb
+            }
+        }
+        // (in place: this thread alone owns point q of the last field)
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
 #pragma unroll
             for (int m = 0; m < 3; ++m)
-                sPhi[q][s][m] = Ji[3 * m] * Phi[s][0] + Ji[3 * m + 1] * Phi[s][1] + Ji[3 * m + 2] * Phi[s][2];
-            sPhi[q][s][3] = Sr[s];
+                sQ[F - 1][q][s][m] = Ji[3 * m] * Phi[s][0] + Ji[3 * m + 1] * Phi[s][1] + Ji[3 * m + 2] * Phi[s][2];
+            sQ[F - 1][q][s][3] = Sr[s];
         }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < NS * NB; i += blockDim.x) {
         const int s = i / NB, m = i % NB;
-        const double det = sG[21];
         double acc = 0.0;
         for (int q = 0; q < NQ; ++q) {
-            const double t = fma(sPhi[q][s][0], tb.VD[0][q][m],
-                                 fma(sPhi[q][s][1], tb.VD[1][q][m],
-                                     fma(sPhi[q][s][2], tb.VD[2][q][m], sPhi[q][s][3] * tb.VB[q][m])));
+            const double* P = sQ[F - 1][q][s];
+            const double t = fma(P[0], tb.VD[0][q][m], fma(P[1], tb.VD[1][q][m], fma(P[2], tb.VD[2][q][m], P[3] * tb.VB[q][m])));
             acc = fma(tb.VW[q], t, acc);
         }
-        double R = det * acc;
+        double R = MODE == TET_VJP ? acc : det * acc;   // (the VJP's cotangents carry det)
         for (int l = 0; l < 4; ++l) {
             const int code = a.emap[e * 4 + l];
             if (code >= 0) {
                 R += a.fbuf[(long long)code * NS * NB + s * NB + m];
-            } else if (code != -1) {
+            } else if (MODE == TET_APPLY && code != -1) {
                 // boundary face l on Gamma_1 (code -2) or Gamma_2 (code -3), in e's own frame
                 const int f = -code - 2;
                 const int va = l == 0 ? 1 : 0, vb = l <= 1 ? 2 : 1, vc = l <= 2 ? 3 : 2;   // the vertices other than l
@@ -402,7 +505,7 @@ __global__ void __launch_bounds__(128) tet_elem_kernel(const TetArgs a) {
                 for (int p = 0; p < NP; ++p) {
                     double uo[NS] = {0, 0, 0, 0, 0, 0}, sig[NS];
                     double c1 = 0.0;
-                    for (int mm = 0; mm < NB; ++mm) c1 = fma(tb.FB[fr][p][mm], sU[3][mm], c1);
+                    for (int mm = 0; mm < NB; ++mm) c1 = fma(tb.FB[fr][p][mm], sU[0][3][mm], c1);
                     uo[3] = c1;
                     const double x = X[0][0] + tb.FX[p][0] * e1[0] + tb.FX[p][1] * e2[0];
                     boundary_point<double>(a.c, f, x, a.g, uo, sig, a.c.beta1, true);
@@ -411,7 +514,7 @@ __global__ void __launch_bounds__(128) tet_elem_kernel(const TetArgs a) {
                 R += E2 * bacc;
             }
         }
-        a.out[e * NS * NB + s * NB + m] = (a.flags & CDG2_MINV) ? R / det : R;
+        a.out[e * NS * NB + s * NB + m] = (MODE != TET_VJP && (a.flags & CDG2_MINV)) ? R / det : R;
     }
 }
 
@@ -419,11 +522,20 @@ __global__ void __launch_bounds__(128) tet_elem_kernel(const TetArgs a) {
 
 namespace cdg2 {
 
-template <int K>
+template <int K, int MODE>
 static cudaError_t tet_launch(const TetArgs& a, cudaStream_t st) {
-    constexpr int FPB = 2;
-    if (a.NF > 0) tet_face_kernel<K, FPB><<<(unsigned)((a.NF + FPB - 1) / FPB), 128, 0, st>>>(a);
-    tet_elem_kernel<K><<<(unsigned)a.E, 128, 0, st>>>(a);
+    constexpr int FPB = MODE == TET_APPLY ? 2 : 1;   // faces per CTA (static shared memory <= 48 KB)
+    constexpr int F = MODE == TET_APPLY ? 1 : 2;
+    constexpr size_t smem = sizeof(double) * (size_t)F * (NS * TetShape<K>::NB + TetShape<K>::NQ * NS * 4);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tet_elem_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (a.NF > 0) tet_face_kernel<K, FPB, MODE><<<(unsigned)((a.NF + FPB - 1) / FPB), 128, 0, st>>>(a);
+    tet_elem_kernel<K, MODE><<<(unsigned)a.E, 128, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -607,23 +719,24 @@ extern "C" int cdg2_tet_mesh_info(const cdg2_tet_mesh* m, long long* n_elem, int
     return CDG2_OK;
 }
 
-extern "C" int cdg2_tet_apply(const cdg2_tet_mesh* m, const cdg2_params* p, const double* U, double* out, int flags,
-                              void* stream) {
-    if (!m || !p || !U || !out) {
-        set_error("cdg2_tet_apply: NULL argument");
+static int tet_run(const char* who, const cdg2_tet_mesh* m, const cdg2_params* p, const double* U, const double* dU,
+                   double* out, int flags, int mode, void* stream) {
+    if (!m || !p || !U || !out || (mode != TET_APPLY && !dU)) {
+        set_error(std::string(who) + ": NULL argument");
         return CDG2_ERR_INVALID_ARG;
     }
-    if (U == out) {
-        set_error("cdg2_tet_apply: U and out must not overlap");
+    if (U == out || dU == out) {
+        set_error(std::string(who) + ": the inputs and out must not overlap");
         return CDG2_ERR_INVALID_ARG;
     }
     if (flags & ~CDG2_MINV) {
-        set_error("cdg2_tet_apply: only CDG2_MINV is supported on tetrahedral meshes");
+        set_error(std::string(who) + ": only CDG2_MINV is supported on tetrahedral meshes");
         return CDG2_ERR_INVALID_ARG;
     }
     if (int rc = tet_upload(*m)) return rc;
     TetArgs a;
     a.U = U;
+    a.dU = dU;
     a.out = out;
     a.flags = flags;
     a.chi_e = m->chi_e;
@@ -650,11 +763,35 @@ extern "C" int cdg2_tet_apply(const cdg2_tet_mesh* m, const cdg2_params* p, cons
     a.c = make_coefT<double>(make_coef(*p), g, nullptr);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
-    switch (m->k) {
-        case 1: e = tet_launch<1>(a, st); break;
-        case 2: e = tet_launch<2>(a, st); break;
-        default: e = tet_launch<3>(a, st); break;
+#define TET_DISPATCH(MODE)                                       \
+    switch (m->k) {                                              \
+        case 1: e = tet_launch<1, MODE>(a, st); break;           \
+        case 2: e = tet_launch<2, MODE>(a, st); break;           \
+        default: e = tet_launch<3, MODE>(a, st); break;          \
     }
-    if (e != cudaSuccess) return cuda_fail(e, "cdg2_tet_apply");
+    if (mode == TET_APPLY) {
+        TET_DISPATCH(TET_APPLY)
+    } else if (mode == TET_JVP) {
+        TET_DISPATCH(TET_JVP)
+    } else {
+        TET_DISPATCH(TET_VJP)
+    }
+#undef TET_DISPATCH
+    if (e != cudaSuccess) return cuda_fail(e, who);
     return CDG2_OK;
+}
+
+extern "C" int cdg2_tet_apply(const cdg2_tet_mesh* m, const cdg2_params* p, const double* U, double* out, int flags,
+                              void* stream) {
+    return tet_run("cdg2_tet_apply", m, p, U, nullptr, out, flags, TET_APPLY, stream);
+}
+
+extern "C" int cdg2_tet_jvp(const cdg2_tet_mesh* m, const cdg2_params* p, const double* U, const double* dU,
+                            double* out, int flags, void* stream) {
+    return tet_run("cdg2_tet_jvp", m, p, U, dU, out, flags, TET_JVP, stream);
+}
+
+extern "C" int cdg2_tet_vjp(const cdg2_tet_mesh* m, const cdg2_params* p, const double* U, const double* lam,
+                            double* gU, int flags, void* stream) {
+    return tet_run("cdg2_tet_vjp", m, p, U, lam, gU, flags, TET_VJP, stream);
 }

@@ -34,6 +34,15 @@ def _state(om, seed):
     return TT.project(om, lambda x: O.gaussian_field(om, x, cen, amp, 0.08, 1e-3))
 
 
+def _discrete_state(om, seed):
+    """Random coefficients (cell means O(1), so O(1) jumps).  The derivatives
+    are compared on such states: for a smooth projected state the two traces
+    nearly agree, so the LLF maximum |v^- . n| vs |v^+ . n| is a near-tie at
+    almost every face point and rounding picks its branch; a relative 1e-15
+    perturbation of U then moves the oracle's own JVP by ~1e-12."""
+    return torch.from_numpy(I.random_coefficients(om.E, om.nb, seed))
+
+
 def _run(G, xyz, tet, k, p, U, flags):
     gm = G.cdg2_tet_mesh_create(xyz, tet, k)
     out = torch.empty(gm.n_dof, dtype=torch.float64, device="cuda")
@@ -119,3 +128,55 @@ def test_tet_apply_full_size_sampled_rows(G):
         ref = TT.apply(om, U[cells], p)[cells.index(int(e))]
         err = float((got[int(e)] - ref).norm() / ref.norm())
         assert err <= 1e-12, (int(e), err)
+
+
+@pytest.mark.parametrize("cells,k", [((3, 2, 2), 1), ((3, 2, 1), 2), ((2, 2, 1), 3)])
+def test_tet_jvp_matches_oracle(G, cells, k):
+    xyz, tet = I.tet_mesh(*cells, 1.0, 0.2, 0.2, 0.15, 500 + k)
+    om = TT.TetMesh(xyz, tet, k)
+    p = _params()
+    U = _discrete_state(om, 50 + k)
+    dU = torch.from_numpy(np.random.default_rng(k).standard_normal(U.shape))
+    gm = G.cdg2_tet_mesh_create(xyz, tet, k)
+    out = torch.empty(gm.n_dof, dtype=torch.float64, device="cuda")
+    G.cdg2_tet_jvp(gm, p, U.reshape(-1).cuda(), dU.reshape(-1).contiguous().cuda(), out, G.CDG2_MINV)
+    got = out.cpu().reshape(U.shape)
+    assert rel_l2_per_species(got, TT.jvp(om, U, dU, p)) <= 1e-12
+    # the JVP is the derivative of the GPU apply itself (central differences through the C ABI;
+    # the step is small enough that no difference straddles a kink of the LLF max or an upwind
+    # sign on these states, where the oracle's own differences agree to 3e-10)
+    h = 1e-7
+    fd = (_run(G, xyz, tet, k, p, U + h * dU, G.CDG2_MINV) - _run(G, xyz, tet, k, p, U - h * dU, G.CDG2_MINV)) / (2 * h)
+    assert float((fd - got).norm() / got.norm()) <= 1e-6
+
+
+@pytest.mark.parametrize("cells,k", [((3, 2, 2), 1), ((3, 2, 1), 2), ((2, 2, 1), 3)])
+@pytest.mark.parametrize("minv", [True, False])
+def test_tet_vjp_matches_oracle_and_transposes_the_jvp(G, cells, k, minv):
+    xyz, tet = I.tet_mesh(*cells, 1.0, 0.2, 0.2, 0.15, 600 + k)
+    om = TT.TetMesh(xyz, tet, k)
+    p = _params()
+    U = _discrete_state(om, 60 + k)
+    rng = np.random.default_rng(20 + k)
+    lam = torch.from_numpy(rng.standard_normal(U.shape))
+    dU = torch.from_numpy(rng.standard_normal(U.shape))
+    gm = G.cdg2_tet_mesh_create(xyz, tet, k)
+    flags = G.CDG2_MINV if minv else 0
+    gU = torch.empty(gm.n_dof, dtype=torch.float64, device="cuda")
+    G.cdg2_tet_vjp(gm, p, U.reshape(-1).cuda(), lam.reshape(-1).contiguous().cuda(), gU, flags)
+    got = gU.cpu().reshape(U.shape)
+    if minv:
+        ref = TT.vjp(om, U, lam, p)
+    else:
+        _, fn = torch.func.vjp(lambda V: TT.apply_residual(om, V, O.param_vector(p)), U)
+        ref = fn(lam)[0]
+    assert rel_l2_per_species(got, ref) <= 1e-12
+    jv = torch.empty_like(gU)
+    G.cdg2_tet_jvp(gm, p, U.reshape(-1).cuda(), dU.reshape(-1).contiguous().cuda(), jv, flags)
+    lhs = float((lam.reshape(-1) * jv.cpu()).sum())
+    rhs = float((got.reshape(-1) * dU.reshape(-1)).sum())
+    assert abs(lhs - rhs) <= 1e-10 * max(abs(lhs), 1.0)
+    # bitwise reproducible (no atomics)
+    gU2 = torch.empty_like(gU)
+    G.cdg2_tet_vjp(gm, p, U.reshape(-1).cuda(), lam.reshape(-1).contiguous().cuda(), gU2, flags)
+    assert torch.equal(gU, gU2)

@@ -368,6 +368,17 @@ int cdg2_tri_jvp(const cdg2_tri_mesh* mesh, const cdg2_params* params, const dou
 int cdg2_tri_vjp(const cdg2_tri_mesh* mesh, const cdg2_params* params, const double* U, const double* lam,
                  double* gU, int flags, void* stream);
 
+/* One SDIRK step U_n -> U_(n+1) of U' = M^{-1} L_h(U) on a triangle mesh
+ * (Sec. 3.2: each stage by Newton's method, each correction by restarted
+ * GMRES whose matrix-vector product is one cdg2_tri_jvp and one axpby), FP64,
+ * in place on U (device float64, n_dof values).  opts as for cdg2_step with
+ * mixed = 0, precond = 0 (no preconditioner) and flags = 0 (no forcing); the
+ * stage times enter no term.  The mesh owns the workspace, allocated by the
+ * first call and freed by its destroy.  Errors: INVALID_ARG (NULL, options),
+ * NOT_CONVERGED / NONFINITE (stats filled, U unchanged), CUDA. */
+int cdg2_tri_step(const cdg2_tri_mesh* mesh, const cdg2_params* params, double* U, double dt,
+                  const cdg2_solver_opts* opts, cdg2_stats* stats, void* stream);
+
 /* ---- Tetrahedral meshes (Sec. 3.1: P_k on tetrahedra, chi_e = 2) ----------
  * The operator of cdg2_apply on an affine tetrahedral mesh, FP64.  Readings:
  * on the reference tetrahedron the orthonormal Dubiner basis psi_pqr =
@@ -428,6 +439,17 @@ int cdg2_tet_jvp(const cdg2_tet_mesh* mesh, const cdg2_params* params, const dou
  * overlap U or lam.  Errors as cdg2_tet_apply. */
 int cdg2_tet_vjp(const cdg2_tet_mesh* mesh, const cdg2_params* params, const double* U, const double* lam,
                  double* gU, int flags, void* stream);
+
+/* One SDIRK step U_n -> U_(n+1) of U' = M^{-1} L_h(U) on a tetrahedral mesh
+ * (Sec. 3.2: each stage by Newton's method, each correction by restarted
+ * GMRES whose matrix-vector product is one cdg2_tet_jvp and one axpby), FP64,
+ * in place on U (device float64, n_dof values).  opts as for cdg2_step with
+ * mixed = 0, precond = 0 (no preconditioner) and flags = 0 (no forcing); the
+ * stage times enter no term.  The mesh owns the workspace, allocated by the
+ * first call and freed by its destroy.  Errors: INVALID_ARG (NULL, options),
+ * NOT_CONVERGED / NONFINITE (stats filled, U unchanged), CUDA. */
+int cdg2_tet_step(const cdg2_tet_mesh* mesh, const cdg2_params* params, double* U, double dt,
+                  const cdg2_solver_opts* opts, cdg2_stats* stats, void* stream);
 
 const char* cdg2_last_error(void);
 

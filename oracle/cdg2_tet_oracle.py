@@ -205,3 +205,8 @@ def vjp(mesh: TetMesh, U, lam, params: dict):
 
 def project(mesh: TetMesh, func):
     return T.project(mesh, func)
+
+
+def step(mesh: TetMesh, U, params: dict, dt: float, scheme="sdirk2", **kw):
+    """One SDIRK step of U' = M^{-1} L_h(U) on the tetrahedral mesh (Sec. 3.2)."""
+    return T.step(mesh, U, params, dt, scheme, **kw)

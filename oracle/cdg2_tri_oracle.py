@@ -23,7 +23,11 @@ What it computes, with the passages it follows:
     y = L_1 (Gamma_2); Reading: every other boundary edge (the side walls of
     the rectangle; triangle meshes are not periodic here) is no-flow;
   * f = M^{-1} L_h with the quadrature mass matrix and a dense solve, and
-    the derivatives by torch.func automatic differentiation.
+    the derivatives by torch.func automatic differentiation;
+  * one SDIRK step of U' = f(U) (Sec. 3.2: a DIRK method, each stage by
+    Newton's method): the tableaux of ``cdg2_oracle.sdirk_tableau``, each
+    Newton correction by a dense Jacobian and LU on small meshes, by GMRES
+    with the JVP otherwise.
 
 Readings of the quadrature (the paper gives none): volume integrals by the
 collapsed (Duffy) Gauss-Legendre rule with (k+2)^2 points -- Gauss points
@@ -342,3 +346,41 @@ def project(mesh: TriMesh, func):
     fx = func(mesh.qpoints_phys())
     R = torch.einsum("eq,seq,qi->esi", mesh.det[:, None] * mesh.qw[None, :], fx, mesh.phi)
     return minv(mesh, R)
+
+
+def step(mesh: TriMesh, U, params: dict, dt: float, scheme="sdirk2", newton_tol=1e-13, gmres_tol=1e-13,
+         max_newton=30):
+    """One SDIRK step U_n -> U_{n+1} of U' = f(U) = M^{-1} L_h(U) (Sec. 3.2).
+
+    Stage i solves Y_i - dt a_ii f(Y_i) = U_n + dt sum_{j<i} a_ij K_j by Newton's
+    method from the previous stage value (correction: (I - dt a_ii J(Y)) d = -G),
+    until ||G||_2 <= newton_tol max(1, ||rhs_i||_2); K_i = f(Y_i) and
+    U_{n+1} = U_n + dt sum_i b_i K_i.  Works on any mesh these residuals accept
+    (triangles or tetrahedra)."""
+    A, b, _ = O.sdirk_tableau(scheme)
+    n = U.numel()
+    K = []
+    Y = U.clone()
+    for i in range(len(b)):
+        rhs = U.clone()
+        for j in range(i):
+            rhs = rhs + dt * A[i, j] * K[j]
+        gdt = dt * A[i, i]
+        scale = max(1.0, float(torch.linalg.norm(rhs)))
+        for _it in range(max_newton):
+            G = Y - gdt * apply(mesh, Y, params) - rhs
+            if float(torch.linalg.norm(G)) <= newton_tol * scale:
+                break
+            if n <= 3000:
+                Jd = torch.func.jacfwd(lambda V: apply(mesh, V, params))(Y).reshape(n, n)
+                d = torch.linalg.solve(torch.eye(n, dtype=F64) - gdt * Jd, -G.reshape(-1)).reshape(Y.shape)
+            else:
+                d = O._gmres(lambda v: v - gdt * jvp(mesh, Y, v, params), -G, gmres_tol)
+            Y = Y + d
+        else:
+            raise RuntimeError("oracle Newton did not converge")
+        K.append(apply(mesh, Y, params))
+    out = U.clone()
+    for i in range(len(b)):
+        out = out + dt * b[i] * K[i]
+    return out

@@ -184,6 +184,10 @@ def load_library():
     for name in ("cdg2_tet_jvp", "cdg2_tet_vjp"):
         getattr(lib, name).argtypes = [vp, ctypes.POINTER(Params), vp, vp, vp, i, vp]
         getattr(lib, name).restype = i
+    for name in ("cdg2_tri_step", "cdg2_tet_step"):
+        getattr(lib, name).argtypes = [vp, ctypes.POINTER(Params), vp, d, ctypes.POINTER(SolverOpts),
+                                       ctypes.POINTER(Stats), vp]
+        getattr(lib, name).restype = i
     lib.cdg2_element_block.argtypes = [vp, ctypes.POINTER(Params), d, ctypes.c_longlong, i, dp]
     lib.cdg2_element_block.restype = i
     lib.cdg2_last_error.argtypes = []
@@ -543,6 +547,31 @@ def cdg2_step(mesh: Mesh, params, U: torch.Tensor, t: float, dt: float, opts: So
     if rc != 0 and raise_on_error:
         _check(rc)
     return rc, st.as_dict()
+
+
+def _simplex_step(fn, mesh, params, U: torch.Tensor, dt: float, opts, stream, raise_on_error):
+    if not (U.is_cuda and U.dtype == torch.float64 and U.is_contiguous() and U.numel() == mesh.n_dof):
+        raise ValueError(f"U must be a contiguous CUDA float64 tensor of {mesh.n_dof} values")
+    p = _params(params)
+    o = opts if opts is not None else make_opts(precond=0)
+    st = Stats()
+    rc = fn(mesh.handle, ctypes.byref(p), ctypes.c_void_p(U.data_ptr()), float(dt), ctypes.byref(o), ctypes.byref(st),
+            _stream_ptr(stream))
+    if rc != 0 and raise_on_error:
+        _check(rc)
+    return rc, st.as_dict()
+
+
+def cdg2_tri_step(mesh: "TriMesh", params, U: torch.Tensor, dt: float, opts: SolverOpts = None, stream=None,
+                  raise_on_error: bool = True):
+    """One SDIRK step (FP64, no preconditioner) in place on U on a triangle mesh; returns (status, stats)."""
+    return _simplex_step(load_library().cdg2_tri_step, mesh, params, U, dt, opts, stream, raise_on_error)
+
+
+def cdg2_tet_step(mesh: "TetMesh", params, U: torch.Tensor, dt: float, opts: SolverOpts = None, stream=None,
+                  raise_on_error: bool = True):
+    """One SDIRK step (FP64, no preconditioner) in place on U on a tetrahedral mesh; returns (status, stats)."""
+    return _simplex_step(load_library().cdg2_tet_step, mesh, params, U, dt, opts, stream, raise_on_error)
 
 
 def stages_of(opts: SolverOpts) -> int:

@@ -28,6 +28,7 @@
 #include "cdg2_internal.h"
 #include "krylov.h"
 #include "precond.h"
+#include "simplex_step.h"
 
 namespace cdg2 {
 
@@ -118,26 +119,28 @@ struct Precond {
 
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
-static int ensure_work(const cdg2_mesh& m, int kdim, bool mixed, Work& w) {
-    const long long n = m.ndof;
+// Carve the step workspace (grown on demand in *ws, owned by the mesh) for n
+// unknowns, nb basis functions per species and blk_bytes of block table.
+static int ensure_work(long long n, int nb, size_t blk_bytes, void*& ws, size_t& ws_bytes, int kdim, bool mixed,
+                       Work& w) {
     const size_t ks = mixed ? sizeof(float) : sizeof(double);
     const size_t vec64 = align256(sizeof(double) * n);
     const size_t veck = align256(ks * n);
     const size_t red = align256(sizeof(double) * reduction_scratch_doubles(MAX_KRYLOV + 1));
     const size_t out = align256(sizeof(double) * (MAX_KRYLOV + 2));   // projections, then one norm slot
-    const size_t tab = align256(sizeof(double) * NS * m.nb);
-    const size_t blk = align256(block_table_bytes(m));
+    const size_t tab = align256(sizeof(double) * NS * nb);
+    const size_t blk = align256(blk_bytes);
     // 5 + MAX_STAGES FP64 vectors; basis (kdim + 2) + dx + Yk + bk + ptmp in the Krylov precision
     const size_t need = (5 + MAX_STAGES) * vec64 + (size_t)(kdim + 6) * veck + red + out + tab + blk;
-    if (m.step_ws_bytes < need) {
-        if (m.step_ws) cudaFree(m.step_ws);
-        m.step_ws = nullptr;
-        m.step_ws_bytes = 0;
-        cudaError_t e = cudaMalloc(&m.step_ws, need);
+    if (ws_bytes < need) {
+        if (ws) cudaFree(ws);
+        ws = nullptr;
+        ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&ws, need);
         if (e != cudaSuccess) return cuda_fail(e, "cdg2_step: workspace");
-        m.step_ws_bytes = need;
+        ws_bytes = need;
     }
-    char* p = static_cast<char*>(m.step_ws);
+    char* p = static_cast<char*>(ws);
     w.n = n;
     w.m = kdim;
     double** v64[5 + MAX_STAGES] = {&w.rhs, &w.Y, &w.fY, &w.G, &w.b64, &w.K[0], &w.K[1], &w.K[2], &w.K[3], &w.K[4]};
@@ -163,6 +166,10 @@ static int ensure_work(const cdg2_mesh& m, int kdim, bool mixed, Work& w) {
     p += blk;
     w.ptmp = p;
     return CDG2_OK;
+}
+
+static int ensure_work(const cdg2_mesh& m, int kdim, bool mixed, Work& w) {
+    return ensure_work(m.ndof, m.nb, block_table_bytes(m), m.step_ws, m.step_ws_bytes, kdim, mixed, w);
 }
 
 // P^{-1} for every (species, mode): P = 1 - gdt A_s d_i with d_i the modal
@@ -250,16 +257,41 @@ static cudaError_t matvec(bool adjoint, const cdg2_mesh& m, const Coef& c, const
     return launch_jvp_axpby(m, c, Yop, v, 1.0, -gdt, pc.pinv, out, flags, st);
 }
 
+// The Cartesian operator of GMRES: matvec above, and the map of the final
+// iterate back from the right-preconditioned space.
 template <typename T>
-static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, const T* b, T* x, double rtol,
-                 int maxit, const Work& w, cudaStream_t st, int flags, const Precond& pc, int* iters,
-                 int* reorth, double* relres, bool adjoint = false) {
+struct CartKrylovOp {
+    const cdg2_mesh& m;
+    const Coef& c;
+    const T* Yop;
+    double gdt;
+    const Precond& pc;
+    int flags;
+    bool adjoint;
+    int mv(const T* v, T* tmp, T* out, cudaStream_t st) const {
+        const int jflags = CDG2_MINV | ((sizeof(T) == 4) ? CDG2_FP32 : 0) | (flags & CDG2_FORCING);
+        CDG2_TRY(matvec<T>(adjoint, m, c, Yop, v, gdt, pc, tmp, out, jflags, st));
+        return CDG2_OK;
+    }
+    int finish(long long n, T* x, T* tmp, cudaStream_t st) const {
+        // right preconditioning: the Krylov iterate lives in P-space, x = P^{-1} y
+        if (pc.pinv) CDG2_TRY(vec_scale_modes<T>(n, pc.pinv, NS * m.nb, x, st));
+        if (pc.bt) {
+            CDG2_TRY(block_apply<T>(m, *pc.bt, x, tmp, st));
+            CDG2_TRY(cudaMemcpyAsync(x, tmp, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+        }
+        return CDG2_OK;
+    }
+};
+
+template <typename T, typename Op>
+static int gmres_op(const Op& op, const T* b, T* x, double rtol, int maxit, const Work& w, cudaStream_t st,
+                    int* iters, int* reorth, double* relres) {
     const long long n = w.n;
     const int kdim = w.m;
     T* V = static_cast<T*>(w.basis);
     T* wv = V + (size_t)(kdim + 1) * n;
     T* tmp = static_cast<T*>(w.ptmp);
-    const int jflags = CDG2_MINV | ((sizeof(T) == 4) ? CDG2_FP32 : 0) | (flags & CDG2_FORCING);
     CDG2_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
     double beta0 = 0.0;
     if (int rc = norm2<T>(w, b, st, &beta0)) return rc;
@@ -282,7 +314,7 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
         bool done = false;
         for (int j = 0; j < kdim; ++j) {
             T* vj = V + (size_t)j * n;
-            CDG2_TRY(matvec<T>(adjoint, m, c, Yop, vj, gdt, pc, tmp, wv, jflags, st));   // w = (I - gdt J) P^-1 v_j
+            if (int rc = op.mv(vj, tmp, wv, st)) return rc;   // w = (I - gdt J) P^-1 v_j
             std::fill(hcol.begin(), hcol.end(), 0.0);
             // Classical Gram-Schmidt with the DGKS criterion: one projection
             // pass (its multi-dot also gives |w| before, the update |w| after);
@@ -341,7 +373,7 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
         CDG2_TRY(vec_basis_combine<T>(n, jlast + 1, V, n, yc, x, st));
         if (resid <= rtol * beta0 || total >= maxit || !done_cycle_needs_restart(done, jlast, kdim)) break;
         // restart: r = b - A x into V_0
-        CDG2_TRY(matvec<T>(adjoint, m, c, Yop, x, gdt, pc, tmp, wv, jflags, st));
+        if (int rc = op.mv(x, tmp, wv, st)) return rc;
         CDG2_TRY(vec_convert<T, T>(n, b, 1.0, V, st));
         CDG2_TRY(vec_axpby<T>(n, -1.0, wv, 1.0, V, st));
         if (int rc = norm2<T>(w, V, st, &beta)) return rc;
@@ -351,15 +383,18 @@ static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, co
         }
         CDG2_TRY(vec_convert<T, T>(n, V, 1.0 / beta, V, st));
     }
-    // right preconditioning: the Krylov iterate lives in P-space, x = P^{-1} y
-    if (pc.pinv) CDG2_TRY(vec_scale_modes<T>(n, pc.pinv, NS * m.nb, x, st));
-    if (pc.bt) {
-        CDG2_TRY(block_apply<T>(m, *pc.bt, x, tmp, st));
-        CDG2_TRY(cudaMemcpyAsync(x, tmp, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
-    }
+    if (int rc = op.finish(n, x, tmp, st)) return rc;
     *iters = total;
     *relres = resid / beta0;
     return CDG2_OK;
+}
+
+template <typename T>
+static int gmres(const cdg2_mesh& m, const Coef& c, const T* Yop, double gdt, const T* b, T* x, double rtol,
+                 int maxit, const Work& w, cudaStream_t st, int flags, const Precond& pc, int* iters,
+                 int* reorth, double* relres, bool adjoint = false) {
+    const CartKrylovOp<T> op{m, c, Yop, gdt, pc, flags, adjoint};
+    return gmres_op<T>(op, b, x, rtol, maxit, w, st, iters, reorth, relres);
 }
 
 }  // namespace cdg2
@@ -375,6 +410,74 @@ static int check_opts(const cdg2_solver_opts* o, double dt, const char* who) {
         return CDG2_ERR_INVALID_ARG;
     }
     return CDG2_OK;
+}
+
+// The stages of one SDIRK step on any mesh: apply(Y, fY, t_i) evaluates f,
+// correct(gdt, &its, &relres) solves the Newton correction for the residual
+// in w.G about w.Y and adds it into w.Y (both return a CDG2 status).  U is
+// overwritten with U_{n+1}; stages_out (nullable) receives Y_1..Y_s.
+template <typename Apply, typename Correct>
+static int sdirk_run(const Tableau& T, const Work& w, const Apply& apply, const Correct& correct, double* U, double t,
+                     double dt, const cdg2_solver_opts* o, cdg2_stats& S, double* stages_out, cudaStream_t st,
+                     const char* who) {
+    const long long n = w.n;
+    int status = CDG2_OK;
+    CDG2_TRY(cudaMemcpyAsync(w.Y, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    for (int i = 0; i < T.s && status == CDG2_OK; ++i) {
+        const double ti = t + T.c[i] * dt;
+        const double gdt = dt * T.A[i][i];
+        Coeffs a;
+        for (int j = 0; j < i; ++j) a.v[j] = dt * T.A[i][j];
+        // rhs_i = U_n + dt sum_{j<i} a_ij K_j  (K_j are stored back to back)
+        CDG2_TRY(vec_lincomb(n, U, i, w.K[0], w.K[1] - w.K[0], a, w.rhs, st));
+        double g0 = 0.0;
+        bool converged = false;
+        for (int it = 0; it <= o->max_newton; ++it) {
+            if (int rc = apply(w.Y, w.fY, ti)) return rc;
+            CDG2_TRY(vec_newton_residual(n, w.Y, w.fY, gdt, w.rhs, w.G, st));
+            double gn = 0.0;
+            if (int rc = norm2<double>(w, w.G, st, &gn)) return rc;
+            if (!std::isfinite(gn)) {
+                set_error(std::string(who) + ": non-finite Newton residual");
+                status = CDG2_ERR_NONFINITE;
+                break;
+            }
+            if (it == 0) g0 = gn;
+            S.residual0[i] = g0;
+            S.residual[i] = gn;
+            if (gn <= std::fmax(o->newton_rtol * g0, o->newton_atol)) {
+                converged = true;
+                break;
+            }
+            if (it == o->max_newton) break;
+            ++S.newton_iters;
+            int its = 0;
+            double rr = 0.0;
+            const int rc = correct(gdt, &its, &rr);
+            S.gmres_iters += its;
+            if (rc != CDG2_OK) {
+                status = rc;
+                break;
+            }
+        }
+        if (status != CDG2_OK) break;
+        if (!converged) {
+            set_error(std::string(who) + ": Newton did not reach the tolerance within max_newton iterations");
+            status = CDG2_ERR_NOT_CONVERGED;
+            break;
+        }
+        // K_i = f(Y_i): the last residual evaluation was at the converged Y_i
+        CDG2_TRY(cudaMemcpyAsync(w.K[i], w.fY, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        if (stages_out)
+            CDG2_TRY(cudaMemcpyAsync(stages_out + (size_t)i * n, w.Y, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    }
+    if (status == CDG2_OK) {
+        Coeffs bb;
+        for (int i = 0; i < T.s; ++i) bb.v[i] = dt * T.b[i];
+        CDG2_TRY(vec_lincomb(n, U, T.s, w.K[0], w.K[1] - w.K[0], bb, U, st));   // U_{n+1} = U_n + dt sum b_i K_i
+        CDG2_TRY(cudaStreamSynchronize(st));
+    }
+    return status;
 }
 
 static int run_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double t, double dt,
@@ -398,79 +501,87 @@ static int run_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double 
     cdg2_stats S;
     std::memset(&S, 0, sizeof(S));
     S.stages = T.s;
-    int status = CDG2_OK;
-
-    CDG2_TRY(cudaMemcpyAsync(w.Y, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    for (int i = 0; i < T.s && status == CDG2_OK; ++i) {
-        const double ti = t + T.c[i] * dt;
-        const double gdt = dt * T.A[i][i];
-        Coeffs a;
-        for (int j = 0; j < i; ++j) a.v[j] = dt * T.A[i][j];
-        // rhs_i = U_n + dt sum_{j<i} a_ij K_j  (K_j are stored back to back)
-        CDG2_TRY(vec_lincomb(n, U, i, w.K[0], w.K[1] - w.K[0], a, w.rhs, st));
-        double g0 = 0.0;
-        bool converged = false;
-        for (int it = 0; it <= o->max_newton; ++it) {
-            CDG2_TRY(launch_apply(*m, c, w.Y, w.fY, CDG2_MINV | (o->flags & CDG2_FORCING), ti, st));
-            CDG2_TRY(vec_newton_residual(n, w.Y, w.fY, gdt, w.rhs, w.G, st));
-            double gn = 0.0;
-            if (int rc = norm2<double>(w, w.G, st, &gn)) return rc;
-            if (!std::isfinite(gn)) {
-                set_error("cdg2_step: non-finite Newton residual");
-                status = CDG2_ERR_NONFINITE;
-                break;
-            }
-            if (it == 0) g0 = gn;
-            S.residual0[i] = g0;
-            S.residual[i] = gn;
-            if (gn <= std::fmax(o->newton_rtol * g0, o->newton_atol)) {
-                converged = true;
-                break;
-            }
-            if (it == o->max_newton) break;
-            ++S.newton_iters;
-            int its = 0;
-            double rr = 0.0;
-            int rc;
-            if (!mixed) {
-                CDG2_TRY(vec_convert<double, double>(n, w.G, -1.0, w.b64, st));
-                rc = gmres<double>(*m, c, w.Y, gdt, w.b64, static_cast<double*>(w.dx), o->gmres_rtol, o->max_gmres, w,
-                                   st, o->flags, pc, &its, &S.gmres_reorth, &rr);
-                if (rc == CDG2_OK) CDG2_TRY(vec_add_into<double>(n, static_cast<double*>(w.dx), w.Y, st));
-            } else {
-                CDG2_TRY(vec_convert<double, float>(n, w.Y, 1.0, static_cast<float*>(w.Yk), st));
-                CDG2_TRY(vec_convert<double, float>(n, w.G, -1.0, static_cast<float*>(w.bk), st));
-                rc = gmres<float>(*m, c, static_cast<float*>(w.Yk), gdt, static_cast<float*>(w.bk),
-                                  static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, o->flags, pc, &its, &S.gmres_reorth, &rr);
-                if (rc == CDG2_OK) CDG2_TRY(vec_add_into<float>(n, static_cast<float*>(w.dx), w.Y, st));
-            }
-            S.gmres_iters += its;
-            if (rc != CDG2_OK) {
-                status = rc;
-                break;
-            }
+    auto apply = [&](const double* Y, double* fY, double ti) -> int {
+        CDG2_TRY(launch_apply(*m, c, Y, fY, CDG2_MINV | (o->flags & CDG2_FORCING), ti, st));
+        return CDG2_OK;
+    };
+    auto correct = [&](double gdt, int* its, double* rr) -> int {
+        int rc;
+        if (!mixed) {
+            CDG2_TRY(vec_convert<double, double>(n, w.G, -1.0, w.b64, st));
+            rc = gmres<double>(*m, c, w.Y, gdt, w.b64, static_cast<double*>(w.dx), o->gmres_rtol, o->max_gmres, w,
+                               st, o->flags, pc, its, &S.gmres_reorth, rr);
+            if (rc == CDG2_OK) CDG2_TRY(vec_add_into<double>(n, static_cast<double*>(w.dx), w.Y, st));
+        } else {
+            CDG2_TRY(vec_convert<double, float>(n, w.Y, 1.0, static_cast<float*>(w.Yk), st));
+            CDG2_TRY(vec_convert<double, float>(n, w.G, -1.0, static_cast<float*>(w.bk), st));
+            rc = gmres<float>(*m, c, static_cast<float*>(w.Yk), gdt, static_cast<float*>(w.bk),
+                              static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, o->flags, pc, its,
+                              &S.gmres_reorth, rr);
+            if (rc == CDG2_OK) CDG2_TRY(vec_add_into<float>(n, static_cast<float*>(w.dx), w.Y, st));
         }
-        if (status != CDG2_OK) break;
-        if (!converged) {
-            set_error("cdg2_step: Newton did not reach the tolerance within max_newton iterations");
-            status = CDG2_ERR_NOT_CONVERGED;
-            break;
-        }
-        // K_i = f(Y_i): the last residual evaluation was at the converged Y_i
-        CDG2_TRY(cudaMemcpyAsync(w.K[i], w.fY, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-        if (stages_out)
-            CDG2_TRY(cudaMemcpyAsync(stages_out + (size_t)i * n, w.Y, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    }
-    if (status == CDG2_OK) {
-        Coeffs bb;
-        for (int i = 0; i < T.s; ++i) bb.v[i] = dt * T.b[i];
-        CDG2_TRY(vec_lincomb(n, U, T.s, w.K[0], w.K[1] - w.K[0], bb, U, st));   // U_{n+1} = U_n + dt sum b_i K_i
-        CDG2_TRY(cudaStreamSynchronize(st));
-    }
+        return rc;
+    };
+    const int status = sdirk_run(T, w, apply, correct, U, t, dt, o, S, stages_out, st, "cdg2_step");
     S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = S;
     return status;
 }
+
+namespace cdg2 {
+
+// The GMRES operator of a simplicial mesh: w = v - gdt J(Y) v (one JVP launch
+// and one axpby), no preconditioner.
+struct SimplexKrylovOp {
+    const SimplexStepOps& ops;
+    const double* Yop;
+    double gdt;
+    long long n;
+    int mv(const double* v, double*, double* out, cudaStream_t st) const {
+        if (int rc = ops.jvp(ops.ctx, Yop, v, out, st)) return rc;
+        CDG2_TRY(vec_axpby<double>(n, 1.0, v, -gdt, out, st));
+        return CDG2_OK;
+    }
+    int finish(long long, double*, double*, cudaStream_t) const { return CDG2_OK; }
+};
+
+int simplex_step(const SimplexStepOps& ops, double* U, double dt, const cdg2_solver_opts* o, cdg2_stats* stats,
+                 void* stream, const char* who) {
+    const auto t_start = std::chrono::steady_clock::now();
+    if (!U || !o) {
+        set_error(std::string(who) + ": NULL argument");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (int rc = check_opts(o, dt, who)) return rc;
+    if (o->mixed || o->precond != 0 || o->flags != 0) {
+        set_error(std::string(who) + ": simplicial meshes step in FP64 without preconditioner or forcing "
+                  "(mixed = 0, precond = 0, flags = 0)");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Work w;
+    if (int rc = ensure_work(ops.n, ops.nb, 0, *ops.ws, *ops.ws_bytes, o->gmres_restart, false, w)) return rc;
+    const Tableau T = sdirk_tableau(o->scheme);
+    const long long n = w.n;
+    cdg2_stats S;
+    std::memset(&S, 0, sizeof(S));
+    S.stages = T.s;
+    auto apply = [&](const double* Y, double* fY, double) -> int { return ops.apply(ops.ctx, Y, fY, st); };
+    auto correct = [&](double gdt, int* its, double* rr) -> int {
+        CDG2_TRY(vec_convert<double, double>(n, w.G, -1.0, w.b64, st));
+        const SimplexKrylovOp op{ops, w.Y, gdt, n};
+        const int rc = gmres_op<double>(op, w.b64, static_cast<double*>(w.dx), o->gmres_rtol, o->max_gmres, w, st,
+                                        its, &S.gmres_reorth, rr);
+        if (rc == CDG2_OK) CDG2_TRY(vec_add_into<double>(n, static_cast<double*>(w.dx), w.Y, st));
+        return rc;
+    };
+    const int status = sdirk_run(T, w, apply, correct, U, 0.0, dt, o, S, nullptr, st, who);
+    S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (stats) *stats = S;
+    return status;
+}
+
+}  // namespace cdg2
 
 extern "C" int cdg2_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double t, double dt,
                          const cdg2_solver_opts* o, cdg2_stats* stats, void* stream) {

@@ -36,6 +36,7 @@
 
 #include "physics.cuh"
 #include "simplex_host.h"
+#include "simplex_step.h"
 
 namespace cdg2 {
 
@@ -76,6 +77,8 @@ struct cdg2_tet_mesh {
     mutable double* d_fgeo = nullptr;
     mutable cdg2::TetTab* d_tab = nullptr;
     mutable double* d_fbuf = nullptr;   // [NF][2][6][nb]
+    mutable void* step_ws = nullptr;    // cdg2_tet_step workspace
+    mutable size_t step_ws_bytes = 0;
 };
 
 namespace cdg2 {
@@ -703,6 +706,7 @@ extern "C" void cdg2_tet_mesh_destroy(cdg2_tet_mesh* m) {
     cudaFree(m->d_fgeo);
     cudaFree(m->d_fbuf);
     cudaFree(m->d_tab);
+    if (m->step_ws) cudaFree(m->step_ws);
     delete m;
 }
 
@@ -794,4 +798,37 @@ extern "C" int cdg2_tet_jvp(const cdg2_tet_mesh* m, const cdg2_params* p, const 
 extern "C" int cdg2_tet_vjp(const cdg2_tet_mesh* m, const cdg2_params* p, const double* U, const double* lam,
                             double* gU, int flags, void* stream) {
     return tet_run("cdg2_tet_vjp", m, p, U, lam, gU, flags, TET_VJP, stream);
+}
+
+namespace {
+struct TetStepCtx {
+    const cdg2_tet_mesh* m;
+    const cdg2_params* p;
+};
+int tet_step_apply(const void* ctx, const double* Y, double* out, cudaStream_t st) {
+    const auto* c = static_cast<const TetStepCtx*>(ctx);
+    return tet_run("cdg2_tet_step", c->m, c->p, Y, nullptr, out, CDG2_MINV, TET_APPLY, st);
+}
+int tet_step_jvp(const void* ctx, const double* Y, const double* v, double* out, cudaStream_t st) {
+    const auto* c = static_cast<const TetStepCtx*>(ctx);
+    return tet_run("cdg2_tet_step", c->m, c->p, Y, v, out, CDG2_MINV, TET_JVP, st);
+}
+}  // namespace
+
+extern "C" int cdg2_tet_step(const cdg2_tet_mesh* m, const cdg2_params* p, double* U, double dt,
+                             const cdg2_solver_opts* opts, cdg2_stats* stats, void* stream) {
+    if (!m || !p) {
+        set_error("cdg2_tet_step: NULL argument");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    const TetStepCtx ctx{m, p};
+    cdg2::SimplexStepOps ops;
+    ops.n = m->E * NS * m->nb;
+    ops.nb = m->nb;
+    ops.ws = &m->step_ws;
+    ops.ws_bytes = &m->step_ws_bytes;
+    ops.ctx = &ctx;
+    ops.apply = tet_step_apply;
+    ops.jvp = tet_step_jvp;
+    return cdg2::simplex_step(ops, U, dt, opts, stats, stream, "cdg2_tet_step");
 }

@@ -29,6 +29,7 @@
 
 #include "physics.cuh"
 #include "simplex_host.h"
+#include "simplex_step.h"
 
 namespace cdg2 {
 
@@ -71,6 +72,8 @@ struct cdg2_tri_mesh {
     mutable double* d_fgeo = nullptr;
     mutable cdg2::TriTab* d_tab = nullptr;
     mutable double* d_fbuf = nullptr;   // [NF][2][6][nb] tested face fluxes
+    mutable void* step_ws = nullptr;    // cdg2_tri_step workspace
+    mutable size_t step_ws_bytes = 0;
 };
 
 namespace cdg2 {
@@ -655,6 +658,7 @@ extern "C" void cdg2_tri_mesh_destroy(cdg2_tri_mesh* m) {
     cudaFree(m->d_fgeo);
     cudaFree(m->d_fbuf);
     cudaFree(m->d_tab);
+    if (m->step_ws) cudaFree(m->step_ws);
     delete m;
 }
 
@@ -751,4 +755,37 @@ extern "C" int cdg2_tri_jvp(const cdg2_tri_mesh* m, const cdg2_params* p, const 
 extern "C" int cdg2_tri_vjp(const cdg2_tri_mesh* m, const cdg2_params* p, const double* U, const double* lam,
                             double* gU, int flags, void* stream) {
     return tri_run("cdg2_tri_vjp", m, p, U, lam, gU, flags, TRI_VJP, stream);
+}
+
+namespace {
+struct TriStepCtx {
+    const cdg2_tri_mesh* m;
+    const cdg2_params* p;
+};
+int tri_step_apply(const void* ctx, const double* Y, double* out, cudaStream_t st) {
+    const auto* c = static_cast<const TriStepCtx*>(ctx);
+    return tri_run("cdg2_tri_step", c->m, c->p, Y, nullptr, out, CDG2_MINV, TRI_APPLY, st);
+}
+int tri_step_jvp(const void* ctx, const double* Y, const double* v, double* out, cudaStream_t st) {
+    const auto* c = static_cast<const TriStepCtx*>(ctx);
+    return tri_run("cdg2_tri_step", c->m, c->p, Y, v, out, CDG2_MINV, TRI_JVP, st);
+}
+}  // namespace
+
+extern "C" int cdg2_tri_step(const cdg2_tri_mesh* m, const cdg2_params* p, double* U, double dt,
+                             const cdg2_solver_opts* opts, cdg2_stats* stats, void* stream) {
+    if (!m || !p) {
+        set_error("cdg2_tri_step: NULL argument");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    const TriStepCtx ctx{m, p};
+    cdg2::SimplexStepOps ops;
+    ops.n = m->E * NS * m->nb;
+    ops.nb = m->nb;
+    ops.ws = &m->step_ws;
+    ops.ws_bytes = &m->step_ws_bytes;
+    ops.ctx = &ctx;
+    ops.apply = tri_step_apply;
+    ops.jvp = tri_step_jvp;
+    return cdg2::simplex_step(ops, U, dt, opts, stats, stream, "cdg2_tri_step");
 }

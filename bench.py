@@ -239,36 +239,76 @@ def measure_derivatives(G, torch, w, mesh, p, U, flush, steps):
     return out
 
 
+def smooth_simplex_state(torch, mesh, centroids, psi0):
+    """Piecewise-constant positive state: u_s = 0.5 + 0.3 sin(2 pi x + s) cos(pi y / 0.2)
+    at each element's centroid in the mean coefficient (psi_0 = psi0), higher modes 0."""
+    import numpy as np
+    U = np.zeros((mesh.n_elem, 6, mesh.n_basis))
+    x, y = centroids[:, 0], centroids[:, 1]
+    for s in range(6):
+        U[:, s, 0] = (0.5 + 0.3 * np.sin(2 * np.pi * x + s) * np.cos(np.pi * y / 0.2)) / psi0
+    return torch.from_numpy(U).reshape(-1).cuda()
+
+
+def measure_simplex(G, torch, flush, steps, mesh, p, U, apply, jvp, vjp, step, Us, dt):
+    """Apply, JVP and VJP timings (L2 flushed) and one timed SDIRK3 step (FP64,
+    element-block Jacobi, Newton relative residual 1e-10) from the smooth state Us."""
+    out = torch.empty_like(U)
+    dU = torch.ones_like(U)
+    ms = time_op(G, torch, lambda: apply(mesh, p, U, out, G.CDG2_MINV), steps, 3, flush)
+    ms_j = time_op(G, torch, lambda: jvp(mesh, p, U, dU, out, G.CDG2_MINV), steps, 3, flush)
+    ms_v = time_op(G, torch, lambda: vjp(mesh, p, U, dU, out, G.CDG2_MINV), steps, 3, flush)
+    opts = G.make_opts(scheme=G.CDG2_SDIRK3, newton_rtol=1e-10, gmres_rtol=1e-3, precond=2)
+    step(mesh, p, Us.clone(), dt, opts, raise_on_error=False)      # allocates the workspace, probes the blocks
+    torch.cuda.synchronize()
+    V = Us.clone()
+    t0 = time.perf_counter()
+    rc, st = step(mesh, p, V, dt, opts, raise_on_error=False)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    n = mesh.n_dof
+    return {"n_dof": n, "n_elem": mesh.n_elem, "n_faces": mesh.n_faces, "ms": ms,
+            "value": n / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "dtype": "f64",
+            "jvp": {"ms": ms_j, "value": n / (ms_j * 1e-3) / 1e9, "unit": "GDOF/s"},
+            "vjp": {"ms": ms_v, "value": n / (ms_v * 1e-3) / 1e9, "unit": "GDOF/s"},
+            "step": {"scheme": "SDIRK3", "dt": dt, "status": rc, "s_per_step": sec,
+                     "newton_iters": st["newton_iters"], "gmres_iters": st["gmres_iters"],
+                     "newton_rtol": 1e-10, "gmres_rtol": 1e-3, "precond": "element-block Jacobi (blocks cached)",
+                     "state": "piecewise-constant 0.5 + 0.3 sin(2 pi x + s) cos(pi y / 0.2)"}}
+
+
 def measure_tri(G, torch, flush, steps):
-    """FP64 cdg2_tri_apply on the 256x64x2 P3 triangle mesh (seeded jitter,
-    seeded positive coefficients), L2 flushed before every timed apply."""
+    """FP64 cdg2_tri_apply / jvp / vjp on the 256x64x2 P3 triangle mesh (seeded
+    jitter, seeded positive coefficients), L2 flushed before every timed launch
+    pair, and one SDIRK3 step."""
     import cdg2_inputs as I
     w = I.tri_workload(1)
     xy, tri = I.tri_mesh(w.nx, w.ny, w.extent[0], w.extent[1], w.jitter, w.seed)
     mesh = G.cdg2_tri_mesh_create(xy, tri, w.k)
     p = I.default_params()
     U = torch.from_numpy(I.random_coefficients(mesh.n_elem, mesh.n_basis, w.seed, 0.1)).reshape(-1).cuda()
-    out = torch.empty_like(U)
-    ms = time_op(G, torch, lambda: G.cdg2_tri_apply(mesh, p, U, out, G.CDG2_MINV), steps, 3, flush)
-    return {"workload": w.name, "n_dof": mesh.n_dof, "n_elem": mesh.n_elem, "n_faces": mesh.n_faces,
-            "ms": ms, "value": mesh.n_dof / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "dtype": "f64",
-            "kernels": "tri_face_kernel<3> + tri_elem_kernel<3> (one apply)"}
+    Us = smooth_simplex_state(torch, mesh, xy[tri].mean(axis=1), 2.0 ** 0.5)
+    r = measure_simplex(G, torch, flush, steps, mesh, p, U, G.cdg2_tri_apply, G.cdg2_tri_jvp, G.cdg2_tri_vjp,
+                        G.cdg2_tri_step, Us, 1e-3)
+    r.update({"workload": w.name, "kernels": "tri_face_kernel<3> + tri_elem_kernel<3> (one apply)"})
+    return r
 
 
 def measure_tet(G, torch, flush, steps):
-    """FP64 cdg2_tet_apply on the 32x8x8x6 P3 tetrahedral mesh (seeded jitter,
-    seeded positive coefficients), L2 flushed before every timed apply."""
+    """FP64 cdg2_tet_apply / jvp / vjp on the 32x8x8x6 P3 tetrahedral mesh (seeded
+    jitter, seeded positive coefficients), L2 flushed before every timed launch
+    pair, and one SDIRK3 step."""
     import cdg2_inputs as I
     w = I.tet_workload(1)
     xyz, tet = I.tet_mesh(*w.cells, *w.extent, w.jitter, w.seed)
     mesh = G.cdg2_tet_mesh_create(xyz, tet, w.k)
     p = I.default_params()
     U = torch.from_numpy(I.random_coefficients(mesh.n_elem, mesh.n_basis, w.seed, 0.1)).reshape(-1).cuda()
-    out = torch.empty_like(U)
-    ms = time_op(G, torch, lambda: G.cdg2_tet_apply(mesh, p, U, out, G.CDG2_MINV), steps, 3, flush)
-    return {"workload": w.name, "n_dof": mesh.n_dof, "n_elem": mesh.n_elem, "n_faces": mesh.n_faces,
-            "ms": ms, "value": mesh.n_dof / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "dtype": "f64",
-            "kernels": "tet_face_kernel<3> + tet_elem_kernel<3> (one apply)"}
+    Us = smooth_simplex_state(torch, mesh, xyz[tet].mean(axis=1), 6.0 ** 0.5)
+    r = measure_simplex(G, torch, flush, steps, mesh, p, U, G.cdg2_tet_apply, G.cdg2_tet_jvp, G.cdg2_tet_vjp,
+                        G.cdg2_tet_step, Us, 1e-3)
+    r.update({"workload": w.name, "kernels": "tet_face_kernel<3,2,0> + tet_elem_kernel<3,0> (one apply)"})
+    return r
 
 
 def measure_solve(G, torch, cfg: int, steps: int, precond: int):
@@ -416,7 +456,7 @@ def main():
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-tri", action="store_true", help="skip the triangle- and tetrahedral-mesh apply timings")
+    ap.add_argument("--no-tri", action="store_true", help="skip the triangle- and tetrahedral-mesh timings")
     ap.add_argument("--solve-config", type=int, default=3, help="workload of the implicit-solve comparison")
     ap.add_argument("--solve-steps", type=int, default=2, help="timed implicit steps per precision (0: skip)")
     ap.add_argument("--grad-config", type=int, default=2, help="workload of the gradient-through-steps timing")

@@ -372,10 +372,15 @@ int cdg2_tri_vjp(const cdg2_tri_mesh* mesh, const cdg2_params* params, const dou
  * (Sec. 3.2: each stage by Newton's method, each correction by restarted
  * GMRES whose matrix-vector product is one cdg2_tri_jvp and one axpby), FP64,
  * in place on U (device float64, n_dof values).  opts as for cdg2_step with
- * mixed = 0, precond = 0 (no preconditioner) and flags = 0 (no forcing); the
- * stage times enter no term.  The mesh owns the workspace, allocated by the
- * first call and freed by its destroy.  Errors: INVALID_ARG (NULL, options),
- * NOT_CONVERGED / NONFINITE (stats filled, U unchanged), CUDA. */
+ * mixed = 0, flags = 0 (no forcing) and precond = 0 (none) or 2 (right
+ * preconditioning by element-block Jacobi: the diagonal blocks K_(e,s) of the
+ * diffusion part, probed with the diffusion JVP under a distance-1 colouring
+ * of the elements and cached until the diffusivities change, and the inverses
+ * of I - dt a_ii K_(e,s)); the stage times enter no term.  The mesh owns the
+ * workspace and the blocks, allocated by the first call and freed by its
+ * destroy.  Errors: INVALID_ARG (NULL, options),
+ * NOT_CONVERGED / NONFINITE (stats filled, U unchanged; NONFINITE also for a
+ * block that is not positive definite), CUDA. */
 int cdg2_tri_step(const cdg2_tri_mesh* mesh, const cdg2_params* params, double* U, double dt,
                   const cdg2_solver_opts* opts, cdg2_stats* stats, void* stream);
 
@@ -444,10 +449,15 @@ int cdg2_tet_vjp(const cdg2_tet_mesh* mesh, const cdg2_params* params, const dou
  * (Sec. 3.2: each stage by Newton's method, each correction by restarted
  * GMRES whose matrix-vector product is one cdg2_tet_jvp and one axpby), FP64,
  * in place on U (device float64, n_dof values).  opts as for cdg2_step with
- * mixed = 0, precond = 0 (no preconditioner) and flags = 0 (no forcing); the
- * stage times enter no term.  The mesh owns the workspace, allocated by the
- * first call and freed by its destroy.  Errors: INVALID_ARG (NULL, options),
- * NOT_CONVERGED / NONFINITE (stats filled, U unchanged), CUDA. */
+ * mixed = 0, flags = 0 (no forcing) and precond = 0 (none) or 2 (right
+ * preconditioning by element-block Jacobi: the diagonal blocks K_(e,s) of the
+ * diffusion part, probed with the diffusion JVP under a distance-1 colouring
+ * of the elements and cached until the diffusivities change, and the inverses
+ * of I - dt a_ii K_(e,s)); the stage times enter no term.  The mesh owns the
+ * workspace and the blocks, allocated by the first call and freed by its
+ * destroy.  Errors: INVALID_ARG (NULL, options),
+ * NOT_CONVERGED / NONFINITE (stats filled, U unchanged; NONFINITE also for a
+ * block that is not positive definite), CUDA. */
 int cdg2_tet_step(const cdg2_tet_mesh* mesh, const cdg2_params* params, double* U, double dt,
                   const cdg2_solver_opts* opts, cdg2_stats* stats, void* stream);
 

@@ -530,19 +530,30 @@ static int run_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double 
 
 namespace cdg2 {
 
-// The GMRES operator of a simplicial mesh: w = v - gdt J(Y) v (one JVP launch
-// and one axpby), no preconditioner.
+// The GMRES operator of a simplicial mesh: w = (I - gdt J(Y)) P^{-1} v (one
+// block apply when preconditioned, one JVP launch and one axpby).
 struct SimplexKrylovOp {
     const SimplexStepOps& ops;
     const double* Yop;
     double gdt;
     long long n;
-    int mv(const double* v, double*, double* out, cudaStream_t st) const {
+    const SimplexPrecond* pc;   // nullptr: no preconditioner
+    int mv(const double* v, double* tmp, double* out, cudaStream_t st) const {
+        if (pc) {
+            CDG2_TRY(simplex_block_apply(*pc, v, tmp, st));
+            v = tmp;
+        }
         if (int rc = ops.jvp(ops.ctx, Yop, v, out, st)) return rc;
         CDG2_TRY(vec_axpby<double>(n, 1.0, v, -gdt, out, st));
         return CDG2_OK;
     }
-    int finish(long long, double*, double*, cudaStream_t) const { return CDG2_OK; }
+    int finish(long long, double* x, double* tmp, cudaStream_t st) const {
+        if (pc) {
+            CDG2_TRY(simplex_block_apply(*pc, x, tmp, st));
+            CDG2_TRY(cudaMemcpyAsync(x, tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        }
+        return CDG2_OK;
+    }
 };
 
 int simplex_step(const SimplexStepOps& ops, double* U, double dt, const cdg2_solver_opts* o, cdg2_stats* stats,
@@ -553,9 +564,9 @@ int simplex_step(const SimplexStepOps& ops, double* U, double dt, const cdg2_sol
         return CDG2_ERR_INVALID_ARG;
     }
     if (int rc = check_opts(o, dt, who)) return rc;
-    if (o->mixed || o->precond != 0 || o->flags != 0) {
-        set_error(std::string(who) + ": simplicial meshes step in FP64 without preconditioner or forcing "
-                  "(mixed = 0, precond = 0, flags = 0)");
+    if (o->mixed || (o->precond != 0 && o->precond != 2) || o->flags != 0) {
+        set_error(std::string(who) + ": simplicial meshes step in FP64 without forcing, with no preconditioner "
+                  "or element-block Jacobi (mixed = 0, precond 0 or 2, flags = 0)");
         return CDG2_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -563,13 +574,19 @@ int simplex_step(const SimplexStepOps& ops, double* U, double dt, const cdg2_sol
     if (int rc = ensure_work(ops.n, ops.nb, 0, *ops.ws, *ops.ws_bytes, o->gmres_restart, false, w)) return rc;
     const Tableau T = sdirk_tableau(o->scheme);
     const long long n = w.n;
+    const SimplexPrecond* pc = nullptr;
+    if (o->precond == 2) {
+        // SDIRK: one a_ii for every stage, so one set of blocks per step
+        if (int rc = simplex_precond_setup(ops, dt * T.A[0][0], w.b64, w.fY, st, who)) return rc;
+        pc = ops.pc;
+    }
     cdg2_stats S;
     std::memset(&S, 0, sizeof(S));
     S.stages = T.s;
     auto apply = [&](const double* Y, double* fY, double) -> int { return ops.apply(ops.ctx, Y, fY, st); };
     auto correct = [&](double gdt, int* its, double* rr) -> int {
         CDG2_TRY(vec_convert<double, double>(n, w.G, -1.0, w.b64, st));
-        const SimplexKrylovOp op{ops, w.Y, gdt, n};
+        const SimplexKrylovOp op{ops, w.Y, gdt, n, pc};
         const int rc = gmres_op<double>(op, w.b64, static_cast<double*>(w.dx), o->gmres_rtol, o->max_gmres, w, st,
                                         its, &S.gmres_reorth, rr);
         if (rc == CDG2_OK) CDG2_TRY(vec_add_into<double>(n, static_cast<double*>(w.dx), w.Y, st));

@@ -79,6 +79,7 @@ struct cdg2_tet_mesh {
     mutable double* d_fbuf = nullptr;   // [NF][2][6][nb]
     mutable void* step_ws = nullptr;    // cdg2_tet_step workspace
     mutable size_t step_ws_bytes = 0;
+    mutable cdg2::SimplexPrecond spc;   // element-block Jacobi of the step
 };
 
 namespace cdg2 {
@@ -707,6 +708,7 @@ extern "C" void cdg2_tet_mesh_destroy(cdg2_tet_mesh* m) {
     cudaFree(m->d_fbuf);
     cudaFree(m->d_tab);
     if (m->step_ws) cudaFree(m->step_ws);
+    m->spc.release();
     delete m;
 }
 
@@ -813,6 +815,11 @@ int tet_step_jvp(const void* ctx, const double* Y, const double* v, double* out,
     const auto* c = static_cast<const TetStepCtx*>(ctx);
     return tet_run("cdg2_tet_step", c->m, c->p, Y, v, out, CDG2_MINV, TET_JVP, st);
 }
+int tet_step_jvp_diffusion(const void* ctx, const double* v, double* out, cudaStream_t st) {
+    const auto* c = static_cast<const TetStepCtx*>(ctx);
+    const cdg2_params q = cdg2::diffusion_only(*c->p);
+    return tet_run("cdg2_tet_step", c->m, &q, v, v, out, CDG2_MINV, TET_JVP, st);
+}
 }  // namespace
 
 extern "C" int cdg2_tet_step(const cdg2_tet_mesh* m, const cdg2_params* p, double* U, double dt,
@@ -830,5 +837,11 @@ extern "C" int cdg2_tet_step(const cdg2_tet_mesh* m, const cdg2_params* p, doubl
     ops.ctx = &ctx;
     ops.apply = tet_step_apply;
     ops.jvp = tet_step_jvp;
+    ops.jvp_diffusion = tet_step_jvp_diffusion;
+    const Coef co = make_coef(*p);
+    ops.A = co.A;
+    ops.face = m->face.data();
+    ops.NF = m->NF;
+    ops.pc = &m->spc;
     return cdg2::simplex_step(ops, U, dt, opts, stats, stream, "cdg2_tet_step");
 }

@@ -43,6 +43,9 @@ namespace cdg2 {
 constexpr int TTMAXB = 20;    // basis functions for k = 3
 constexpr int TTMAXQ = 125;   // volume points for k = 3
 constexpr int TTMAXP = 25;    // face points for k = 3
+constexpr int TTMAXN = 5;     // Gauss points per collapsed direction for k = 3
+constexpr int TTMAXK1 = 4;    // k + 1
+constexpr int TTMAXPQ = 10;   // pairs (p, q) with p + q <= 3
 constexpr int NFRAME = 64;    // frame code a * 16 + b * 4 + c (24 of them used)
 constexpr int TGEO = 22;      // x0 (3), J (9, row-major), J^{-1} (9, row-major), det J
 
@@ -57,6 +60,21 @@ struct TetTab {
     double LF[NFRAME][TTMAXP][TTMAXP];    // lifting kernel of each frame (read for K^-'s)
     double FW[TTMAXP];                    // face rule weights (sum 1/2)
     double FX[TTMAXP][2];                 // face rule points (s, t)
+    // Warped-product factors on the collapsed volume grid: at xi = u (1-v)(1-w),
+    // eta = v (1-w), zeta = w, psi_pqr = A_p(u) B_pq(v) C_pqr(w) with
+    // A_p = P_p(2u-1), B_pq = (1-v)^p P_q^{(2p+1,0)}(2v-1) and
+    // C_pqr = c_pqr (1-w)^{p+q} P_r^{(2p+2q+2,0)}(2w-1); pairs (p, q) ordered
+    // by p, then q.
+    double SA[TTMAXN][TTMAXK1], SdA[TTMAXN][TTMAXK1];     // [u point][p]
+    double SB[TTMAXN][TTMAXPQ], SdB[TTMAXN][TTMAXPQ];     // [v point][pair]
+    double SC[TTMAXN][TTMAXB], SdC[TTMAXN][TTMAXB];       // [w point][mode]
+    // the reference gradient from the (u, v, w) one at volume point q:
+    // d_xi = a1 d_u, d_eta = u a1 d_u + b1 d_v, d_zeta = u a1 d_u + v b1 d_v + d_w,
+    // a1 = 1 / ((1-v)(1-w)), b1 = 1 / (1-w); stored (a1, u a1, b1, v b1)
+    double SG[TTMAXQ][4];
+    int PQA[TTMAXK1][TTMAXK1];            // pair index of (p, q), p + q <= k
+    int PQM[TTMAXPQ][TTMAXK1];            // mode index of (pair, r), r <= k - p - q
+    int MPQ[TTMAXB];                      // pair index of mode m
 };
 
 }  // namespace cdg2
@@ -175,6 +193,58 @@ void build_tet_tables(int k, TetTab& T) {
             T.FX[p][1] = g[b];
             T.FW[p] = w[a] * w[b] * (1.0 - g[b]);
         }
+    // warped-product factors and the (u, v, w) -> reference gradient map
+    int na = 0;
+    for (int p = 0; p <= k; ++p)
+        for (int q = 0; q <= k - p; ++q) T.PQA[p][q] = na++;
+    for (int a = 0; a < TTMAXPQ; ++a)
+        for (int r = 0; r < TTMAXK1; ++r) T.PQM[a][r] = -1;
+    {
+        int m = 0;
+        for (int d = 0; d <= k; ++d)
+            for (int r = 0; r <= d; ++r)
+                for (int q = 0; q <= d - r; ++q, ++m) {
+                    const int p = d - q - r;
+                    T.PQM[T.PQA[p][q]][r] = m;
+                    T.MPQ[m] = T.PQA[p][q];
+                    const double cst = std::sqrt((2.0 * p + 1) * (2.0 * p + 2 * q + 2) * (2.0 * p + 2 * q + 2 * r + 3));
+                    for (int l = 0; l < n; ++l) {
+                        const double w1 = 1.0 - g[l];
+                        double R, dR;
+                        jacobi_d(r, 2.0 * p + 2.0 * q + 2.0, 2.0 * g[l] - 1.0, R, dR);
+                        const double pw = std::pow(w1, p + q);
+                        const double dpw = (p + q) > 0 ? -(p + q) * std::pow(w1, p + q - 1) : 0.0;
+                        T.SC[l][m] = cst * pw * R;
+                        T.SdC[l][m] = cst * (dpw * R + pw * 2.0 * dR);
+                    }
+                }
+    }
+    for (int j = 0; j < n; ++j) {
+        for (int p = 0; p <= k; ++p) {
+            double P, dP;
+            jacobi_d(p, 0.0, 2.0 * g[j] - 1.0, P, dP);
+            T.SA[j][p] = P;
+            T.SdA[j][p] = 2.0 * dP;
+            for (int q = 0; q <= k - p; ++q) {
+                const double v1 = 1.0 - g[j];
+                double Q, dQ;
+                jacobi_d(q, 2.0 * p + 1.0, 2.0 * g[j] - 1.0, Q, dQ);
+                const double pw = std::pow(v1, p), dpw = p > 0 ? -p * std::pow(v1, p - 1) : 0.0;
+                T.SB[j][T.PQA[p][q]] = pw * Q;
+                T.SdB[j][T.PQA[p][q]] = dpw * Q + pw * 2.0 * dQ;
+            }
+        }
+    }
+    for (int c = 0; c < n; ++c)
+        for (int b = 0; b < n; ++b)
+            for (int a = 0; a < n; ++a) {
+                const int q = a + n * (b + n * c);
+                const double a1 = 1.0 / ((1.0 - g[b]) * (1.0 - g[c])), b1 = 1.0 / (1.0 - g[c]);
+                T.SG[q][0] = a1;
+                T.SG[q][1] = g[a] * a1;
+                T.SG[q][2] = b1;
+                T.SG[q][3] = g[b] * b1;
+            }
     const int np = n * n;
     for (int la = 0; la < 4; ++la)
         for (int lb = 0; lb < 4; ++lb)
@@ -390,53 +460,115 @@ __global__ void __launch_bounds__(128) tet_face_kernel(const TetArgs a) {
 }
 
 // One CTA: one element.  Values and physical gradients of every field per
-// (point, species), the pointwise flux (JVP: linearised; VJP: its adjoint with
-// the cotangents det w_q mu, det w_q grad mu), the result mapped back by
-// J^{-1} and tested against the reference gradients, the tested fluxes of its
-// interior faces, the boundary data of Eq. (3) on its boundary faces (apply
-// only: H' = 0), M^{-1} = 1 / det J (not for the VJP).  Dynamic shared memory:
-// U [F][6][nb], then [F][NQ][6][4] point values.
+// (point, species) by sum factorisation over the warped-product basis on the
+// collapsed grid (coefficients -> C_pqr in w -> B_pq in v -> A_p in u, and the
+// derivative factors for the (u, v, w) gradient, mapped to the reference and
+// then the physical gradient), the pointwise flux (JVP: linearised; VJP: its
+// adjoint with the cotangents det w_q mu, det w_q grad mu), the result mapped
+// back by J^{-1} and by the collapsed map, weighted, and tested by the
+// transposed passes (A_p in u -> B_pq in v -> C_pqr in w), the tested fluxes
+// of its interior faces, the boundary data of Eq. (3) on its boundary faces
+// (apply only: H' = 0), M^{-1} = 1 / det J (not for the VJP).  Dynamic
+// shared memory per field: U [6][nb], the w-pass [2][6][pairs][n], the v-pass
+// [3][6][k+1][n][n], the point values [NQ][6][4].
+template <int K>
+struct TetSF {
+    static constexpr int N = K + 2, NPQ = (K + 1) * (K + 2) / 2, K1 = K + 1;
+    static constexpr int NB = TetShape<K>::NB, NQ = TetShape<K>::NQ;
+    static constexpr int SU = NS * NB, SG1 = 2 * NS * NPQ * N, SH = 3 * NS * K1 * N * N, SQ = NQ * NS * 4;
+    static constexpr int FIELD = SU + SG1 + SH + SQ;   // doubles per field
+};
+
 template <int K, int MODE>
 __global__ void __launch_bounds__(128) tet_elem_kernel(const TetArgs a) {
     using S = TetShape<K>;
+    using SF = TetSF<K>;
     constexpr int NB = S::NB, NQ = S::NQ, NP = S::NP, F = MODE == TET_APPLY ? 1 : 2;
+    constexpr int N = SF::N, NPQ = SF::NPQ, K1 = SF::K1;
     const TetTab& tb = *a.tab;
     extern __shared__ __align__(16) double tsm[];
-    double (*sU)[NS][NB] = reinterpret_cast<double (*)[NS][NB]>(tsm);                     // [F]
-    double (*sQ)[NQ][NS][4] = reinterpret_cast<double (*)[NQ][NS][4]>(tsm + F * NS * NB);   // [F]
+    auto sU = [&](int fi) { return reinterpret_cast<double (*)[NB]>(tsm + fi * SF::FIELD); };
+    auto sG1 = [&](int fi) { return reinterpret_cast<double (*)[NS][NPQ][N]>(tsm + fi * SF::FIELD + SF::SU); };
+    auto sH = [&](int fi) { return reinterpret_cast<double (*)[NS][K1][N][N]>(tsm + fi * SF::FIELD + SF::SU + SF::SG1); };
+    auto sQ = [&](int fi) {
+        return reinterpret_cast<double (*)[NS][4]>(tsm + fi * SF::FIELD + SF::SU + SF::SG1 + SF::SH);
+    };
     __shared__ double sG[TGEO];
     const long long e = blockIdx.x;
     for (int i = threadIdx.x; i < TGEO; i += blockDim.x) sG[i] = a.geo[e * TGEO + i];
     for (int i = threadIdx.x; i < F * NS * NB; i += blockDim.x) {
         const int fi = i / (NS * NB), r = i % (NS * NB);
-        sU[fi][r / NB][r % NB] = (fi ? a.dU : a.U)[e * NS * NB + r];
+        sU(fi)[r / NB][r % NB] = (fi ? a.dU : a.U)[e * NS * NB + r];
     }
     __syncthreads();
     const double* J = sG + 3;
     const double* Ji = sG + 12;
     const double det = sG[21];
+    // w-pass: g_pq(w_l) = sum_r C_pqr(w_l) U_pqr, and with C'
+    for (int i = threadIdx.x; i < F * NS * NPQ * N; i += blockDim.x) {
+        const int fi = i / (NS * NPQ * N), s = (i / (NPQ * N)) % NS, pq = (i / N) % NPQ, l = i % N;
+        double g = 0.0, gw = 0.0;
+#pragma unroll
+        for (int r = 0; r < K1; ++r) {
+            const int m = tb.PQM[pq][r];
+            if (m >= 0) {
+                const double u = sU(fi)[s][m];
+                g = fma(tb.SC[l][m], u, g);
+                gw = fma(tb.SdC[l][m], u, gw);
+            }
+        }
+        sG1(fi)[0][s][pq][l] = g;
+        sG1(fi)[1][s][pq][l] = gw;
+    }
+    __syncthreads();
+    // v-pass: h_p(v_j, w_l) = sum_q B_pq(v_j) g_pq(w_l); with B' (d_v) and with g' (d_w)
+    for (int i = threadIdx.x; i < F * NS * K1 * N * N; i += blockDim.x) {
+        const int fi = i / (NS * K1 * N * N), s = (i / (K1 * N * N)) % NS, p = (i / (N * N)) % K1;
+        const int j = (i / N) % N, l = i % N;
+        double h = 0.0, hv = 0.0, hw = 0.0;
+#pragma unroll
+        for (int q = 0; q < K1; ++q) {
+            if (q <= K - p) {
+                const int pq = tb.PQA[p][q];
+                const double g = sG1(fi)[0][s][pq][l];
+                h = fma(tb.SB[j][pq], g, h);
+                hv = fma(tb.SdB[j][pq], g, hv);
+                hw = fma(tb.SB[j][pq], sG1(fi)[1][s][pq][l], hw);
+            }
+        }
+        sH(fi)[0][s][p][j][l] = h;
+        sH(fi)[1][s][p][j][l] = hv;
+        sH(fi)[2][s][p][j][l] = hw;
+    }
+    __syncthreads();
+    // u-pass: value and (u, v, w) gradient at every point, then reference and physical gradient
     for (int i = threadIdx.x; i < F * NQ * NS; i += blockDim.x) {
         const int fi = i / (NQ * NS), q = (i / NS) % NQ, s = i % NS;
-        double v = 0.0, r0 = 0.0, r1 = 0.0, r2 = 0.0;
-        for (int m = 0; m < NB; ++m) {
-            const double c = sU[fi][s][m];
-            v = fma(tb.VB[q][m], c, v);
-            r0 = fma(tb.VD[0][q][m], c, r0);
-            r1 = fma(tb.VD[1][q][m], c, r1);
-            r2 = fma(tb.VD[2][q][m], c, r2);
-        }
+        const int ii = q % N, j = (q / N) % N, l = q / (N * N);
+        double f = 0.0, fu = 0.0, fv = 0.0, fw = 0.0;
 #pragma unroll
-        for (int jj = 0; jj < 3; ++jj) sQ[fi][q][s][jj] = Ji[jj] * r0 + Ji[3 + jj] * r1 + Ji[6 + jj] * r2;   // J^{-T} grad_ref
-        sQ[fi][q][s][3] = v;
+        for (int p = 0; p < K1; ++p) {
+            const double h = sH(fi)[0][s][p][j][l];
+            f = fma(tb.SA[ii][p], h, f);
+            fu = fma(tb.SdA[ii][p], h, fu);
+            fv = fma(tb.SA[ii][p], sH(fi)[1][s][p][j][l], fv);
+            fw = fma(tb.SA[ii][p], sH(fi)[2][s][p][j][l], fw);
+        }
+        const double r0 = tb.SG[q][0] * fu;
+        const double r1 = fma(tb.SG[q][1], fu, tb.SG[q][2] * fv);
+        const double r2 = fma(tb.SG[q][1], fu, fma(tb.SG[q][3], fv, fw));
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) sQ(fi)[q][s][jj] = Ji[jj] * r0 + Ji[3 + jj] * r1 + Ji[6 + jj] * r2;   // J^{-T} grad_ref
+        sQ(fi)[q][s][3] = f;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
         double u[NS], g[NS][3], Phi[NS][3], Sr[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            u[s] = sQ[0][q][s][3];
+            u[s] = sQ(0)[q][s][3];
 #pragma unroll
-            for (int jj = 0; jj < 3; ++jj) g[s][jj] = sQ[0][q][s][jj];
+            for (int jj = 0; jj < 3; ++jj) g[s][jj] = sQ(0)[q][s][jj];
         }
         if constexpr (MODE == TET_APPLY) {
             volume_point<3, double>(a.c, u, g, Phi, Sr);
@@ -444,14 +576,14 @@ __global__ void __launch_bounds__(128) tet_elem_kernel(const TetArgs a) {
             double du[NS], dg[NS][3];
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                du[s] = sQ[F - 1][q][s][3];
+                du[s] = sQ(F - 1)[q][s][3];
 #pragma unroll
-                for (int jj = 0; jj < 3; ++jj) dg[s][jj] = sQ[F - 1][q][s][jj];
+                for (int jj = 0; jj < 3; ++jj) dg[s][jj] = sQ(F - 1)[q][s][jj];
             }
             if constexpr (MODE == TET_JVP) {
                 volume_point_lin<3, double>(a.c, u, g, du, dg, false, Phi, Sr);
             } else {
-                // mu = M^{-1} lambda = lambda / det (with CDG2_MINV); w_q is applied by the test below
+                // mu = M^{-1} lambda = lambda / det (with CDG2_MINV); w_q is applied below
                 const double W = (a.flags & CDG2_MINV) ? 1.0 : det;
                 double sb[NS], gb[NS][3], th[8];
 #pragma unroll
@@ -463,24 +595,60 @@ __global__ void __launch_bounds__(128) tet_elem_kernel(const TetArgs a) {
                 volume_point_adj<3, double>(a.c, u, g, sb, gb, Sr, Phi, th);   // Sr <- ub, Phi <- Gb
             }
         }
+        // Phi . grad psi = (J_c^{-1} J^{-1} Phi) . grad_(u,v,w) psi; weighted by w_q
         // (in place: this thread alone owns point q of the last field)
+        const double wq = tb.VW[q];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-#pragma unroll
-            for (int m = 0; m < 3; ++m)
-                sQ[F - 1][q][s][m] = Ji[3 * m] * Phi[s][0] + Ji[3 * m + 1] * Phi[s][1] + Ji[3 * m + 2] * Phi[s][2];
-            sQ[F - 1][q][s][3] = Sr[s];
+            const double p0 = Ji[0] * Phi[s][0] + Ji[1] * Phi[s][1] + Ji[2] * Phi[s][2];
+            const double p1 = Ji[3] * Phi[s][0] + Ji[4] * Phi[s][1] + Ji[5] * Phi[s][2];
+            const double p2 = Ji[6] * Phi[s][0] + Ji[7] * Phi[s][1] + Ji[8] * Phi[s][2];
+            sQ(F - 1)[q][s][0] = wq * (tb.SG[q][0] * p0 + tb.SG[q][1] * (p1 + p2));
+            sQ(F - 1)[q][s][1] = wq * (tb.SG[q][2] * p1 + tb.SG[q][3] * p2);
+            sQ(F - 1)[q][s][2] = wq * p2;
+            sQ(F - 1)[q][s][3] = wq * Sr[s];
         }
+    }
+    __syncthreads();
+    // transposed u-pass: X_p(v_j, w_l) = sum_i A_p S + A'_p P_u, A_p P_v, A_p P_w
+    double (*sX)[NS][K1][N][N] = sH(0);
+    for (int i = threadIdx.x; i < NS * K1 * N * N; i += blockDim.x) {
+        const int s = i / (K1 * N * N), p = (i / (N * N)) % K1, j = (i / N) % N, l = i % N;
+        double x0 = 0.0, xv = 0.0, xw = 0.0;
+#pragma unroll
+        for (int ii = 0; ii < N; ++ii) {
+            const double* P = sQ(F - 1)[ii + N * (j + N * l)][s];
+            x0 = fma(tb.SA[ii][p], P[3], fma(tb.SdA[ii][p], P[0], x0));
+            xv = fma(tb.SA[ii][p], P[1], xv);
+            xw = fma(tb.SA[ii][p], P[2], xw);
+        }
+        sX[0][s][p][j][l] = x0;
+        sX[1][s][p][j][l] = xv;
+        sX[2][s][p][j][l] = xw;
+    }
+    __syncthreads();
+    // transposed v-pass: Y_pq(w_l) = sum_j B_pq X + B'_pq X_v; Y^w_pq = sum_j B_pq X_w
+    double (*sY)[NS][NPQ][N] = sG1(0);
+    for (int i = threadIdx.x; i < NS * NPQ * N; i += blockDim.x) {
+        const int s = i / (NPQ * N), pq = (i / N) % NPQ, l = i % N;
+        int p = 0;
+        while (p < K && pq >= tb.PQA[p + 1][0]) ++p;
+        double y = 0.0, yw = 0.0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            y = fma(tb.SB[j][pq], sX[0][s][p][j][l], fma(tb.SdB[j][pq], sX[1][s][p][j][l], y));
+            yw = fma(tb.SB[j][pq], sX[2][s][p][j][l], yw);
+        }
+        sY[0][s][pq][l] = y;
+        sY[1][s][pq][l] = yw;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < NS * NB; i += blockDim.x) {
         const int s = i / NB, m = i % NB;
+        const int pq = tb.MPQ[m];
         double acc = 0.0;
-        for (int q = 0; q < NQ; ++q) {
-            const double* P = sQ[F - 1][q][s];
-            const double t = fma(P[0], tb.VD[0][q][m], fma(P[1], tb.VD[1][q][m], fma(P[2], tb.VD[2][q][m], P[3] * tb.VB[q][m])));
-            acc = fma(tb.VW[q], t, acc);
-        }
+#pragma unroll
+        for (int l = 0; l < N; ++l) acc = fma(tb.SC[l][m], sY[0][s][pq][l], fma(tb.SdC[l][m], sY[1][s][pq][l], acc));
         double R = MODE == TET_VJP ? acc : det * acc;   // (the VJP's cotangents carry det)
         for (int l = 0; l < 4; ++l) {
             const int code = a.emap[e * 4 + l];
@@ -509,7 +677,7 @@ __global__ void __launch_bounds__(128) tet_elem_kernel(const TetArgs a) {
                 for (int p = 0; p < NP; ++p) {
                     double uo[NS] = {0, 0, 0, 0, 0, 0}, sig[NS];
                     double c1 = 0.0;
-                    for (int mm = 0; mm < NB; ++mm) c1 = fma(tb.FB[fr][p][mm], sU[0][3][mm], c1);
+                    for (int mm = 0; mm < NB; ++mm) c1 = fma(tb.FB[fr][p][mm], sU(0)[3][mm], c1);
                     uo[3] = c1;
                     const double x = X[0][0] + tb.FX[p][0] * e1[0] + tb.FX[p][1] * e2[0];
                     boundary_point<double>(a.c, f, x, a.g, uo, sig, a.c.beta1, true);
@@ -530,7 +698,7 @@ template <int K, int MODE>
 static cudaError_t tet_launch(const TetArgs& a, cudaStream_t st) {
     constexpr int FPB = MODE == TET_APPLY ? 2 : 1;   // faces per CTA (static shared memory <= 48 KB)
     constexpr int F = MODE == TET_APPLY ? 1 : 2;
-    constexpr size_t smem = sizeof(double) * (size_t)F * (NS * TetShape<K>::NB + TetShape<K>::NQ * NS * 4);
+    constexpr size_t smem = sizeof(double) * (size_t)F * TetSF<K>::FIELD;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(tet_elem_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,

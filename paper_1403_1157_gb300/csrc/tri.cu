@@ -48,6 +48,13 @@ struct TriTab {
     double EW[TMAXP];
     double ET[TMAXP];
     double LF[3][TMAXP][TMAXP];       // lifting kernel of K^-'s edge l
+    // Warped-product factors on the collapsed volume grid: at xi = u (1-v),
+    // eta = v, psi_pq = A_p(u) B_pq(v) with A_p = P_p(2u-1) and
+    // B_pq = c_pq (1-v)^p P_q^{(2p+1,0)}(2v-1); mode m = (p+q)(p+q+1)/2 + q.
+    double SA[TMAXP][TMAXP], SdA[TMAXP][TMAXP];   // [u point][p]
+    double SB[TMAXP][TMAXB], SdB[TMAXP][TMAXB];   // [v point][mode]
+    // d_xi = a1 d_u, d_eta = u a1 d_u + d_v with a1 = 1 / (1-v): (a1, u a1) per point
+    double SG[TMAXQ][2];
 };
 
 // Element geometry: x0, y0, J (row-major), J^{-1} (row-major), det J.
@@ -138,6 +145,30 @@ void build_tables(int k, TriTab& T) {
             T.VW[q] = w[i] * w[j] * (1.0 - g[j]);
             dubiner(k, xi, eta, T.VB[q], T.VD[0][q], T.VD[1][q]);
         }
+    for (int j = 0; j < n; ++j) {
+        for (int p = 0; p <= k; ++p) {
+            double P, dP;
+            jacobi_d(p, 0.0, 2.0 * g[j] - 1.0, P, dP);
+            T.SA[j][p] = P;
+            T.SdA[j][p] = 2.0 * dP;
+        }
+        int m = 0;
+        for (int d = 0; d <= k; ++d)
+            for (int q = 0; q <= d; ++q, ++m) {
+                const int p = d - q;
+                const double c = std::sqrt(2.0 * (2 * p + 1) * (p + q + 1)), v1 = 1.0 - g[j];
+                double Q, dQ;
+                jacobi_d(q, 2.0 * p + 1.0, 2.0 * g[j] - 1.0, Q, dQ);
+                const double pw = std::pow(v1, p), dpw = p > 0 ? -p * std::pow(v1, p - 1) : 0.0;
+                T.SB[j][m] = c * pw * Q;
+                T.SdB[j][m] = c * (dpw * Q + pw * 2.0 * dQ);
+            }
+        for (int i = 0; i < n; ++i) {
+            const double a1 = 1.0 / (1.0 - g[j]);
+            T.SG[i + n * j][0] = a1;
+            T.SG[i + n * j][1] = g[i] * a1;
+        }
+    }
     for (int p = 0; p < n; ++p) {
         T.EW[p] = w[p];
         T.ET[p] = g[p];
@@ -378,20 +409,24 @@ __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
     }
 }
 
-// One CTA: EPB elements.  Volume terms at the collapsed Gauss points (JVP:
-// linearised), the tested fluxes of the element's interior edges from the
-// face buffer, the boundary data of Eq. (3) on its boundary edges (JVP: none,
-// H' = 0), M^{-1} = 1 / det J.
+// One CTA: EPB elements.  Volume terms at the collapsed Gauss points by sum
+// factorisation over the warped-product basis (coefficients -> B_pq in v ->
+// A_p in u, with the derivative factors for the (u, v) gradient, mapped to the
+// reference and physical gradient; the pointwise flux, JVP: linearised, VJP:
+// its adjoint; the flux mapped back by J^{-1} and the collapsed map, weighted,
+// and tested by the transposed passes), the tested fluxes of the element's
+// interior edges from the face buffer, the boundary data of Eq. (3) on its
+// boundary edges (JVP/VJP: none, H' = 0), M^{-1} = 1 / det J.
 template <int K, int EPB, int MODE>
 __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
     using S = TriShape<K>;
     constexpr int NB = S::NB, NQ = S::NQ, NP = S::NP, F = MODE == TRI_APPLY ? 1 : 2;
-    __shared__ TriTab tb;
+    constexpr int N = K + 2, K1 = K + 1;
+    const TriTab& tb = *a.tab;
     __shared__ double sU[EPB][F][NS][NB];
     __shared__ double sG[EPB][GEO];
-    __shared__ double sPhi[EPB][NQ][NS][3];   // Phi_x, Phi_y, S
-    __shared__ double sGP[EPB][NQ][NB][2];    // physical gradients of the basis at the points
-    load_tritab(tb, a.tab);
+    __shared__ double sH[EPB][F][2][NS][K1][N];   // v-pass (h, h_v); then the transposed u-pass
+    __shared__ double sQ[EPB][F][NQ][NS][3];      // grad_x, grad_y, value; then the weighted flux
     const long long e0 = (long long)blockIdx.x * EPB;
     const int ne = (int)min((long long)EPB, a.E - e0);
     for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) sG[i / GEO][i % GEO] = a.geo[e0 * GEO + i];
@@ -401,12 +436,41 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
         sU[e][fi][r / NB][r % NB] = (fi ? a.dU : a.U)[e0 * NS * NB + r0];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < ne * NQ * NB; i += blockDim.x) {
-        const int e = i / (NQ * NB), q = (i / NB) % NQ, m = i % NB;
+    // v-pass: h_p(v_j) = sum_q B_pq(v_j) U_pq, and with B'
+    for (int i = threadIdx.x; i < ne * F * NS * K1 * N; i += blockDim.x) {
+        const int e = i / (F * NS * K1 * N), fi = (i / (NS * K1 * N)) % F, s = (i / (K1 * N)) % NS;
+        const int p = (i / N) % K1, j = i % N;
+        double h = 0.0, hv = 0.0;
+#pragma unroll
+        for (int q = 0; q < K1; ++q) {
+            if (q <= K - p) {
+                const int m = (p + q) * (p + q + 1) / 2 + q;
+                const double u = sU[e][fi][s][m];
+                h = fma(tb.SB[j][m], u, h);
+                hv = fma(tb.SdB[j][m], u, hv);
+            }
+        }
+        sH[e][fi][0][s][p][j] = h;
+        sH[e][fi][1][s][p][j] = hv;
+    }
+    __syncthreads();
+    // u-pass: value and (u, v) gradient, then the reference and physical gradient
+    for (int i = threadIdx.x; i < ne * F * NQ * NS; i += blockDim.x) {
+        const int e = i / (F * NQ * NS), fi = (i / (NQ * NS)) % F, q = (i / NS) % NQ, s = i % NS;
+        const int ii = q % N, j = q / N;
+        double f = 0.0, fu = 0.0, fv = 0.0;
+#pragma unroll
+        for (int p = 0; p < K1; ++p) {
+            const double h = sH[e][fi][0][s][p][j];
+            f = fma(tb.SA[ii][p], h, f);
+            fu = fma(tb.SdA[ii][p], h, fu);
+            fv = fma(tb.SA[ii][p], sH[e][fi][1][s][p][j], fv);
+        }
+        const double r0 = tb.SG[q][0] * fu, r1 = fma(tb.SG[q][1], fu, fv);
         const double* Ji = sG[e] + 6;
-        const double gx = tb.VD[0][q][m], gy = tb.VD[1][q][m];
-        sGP[e][q][m][0] = Ji[0] * gx + Ji[2] * gy;
-        sGP[e][q][m][1] = Ji[1] * gx + Ji[3] * gy;
+        sQ[e][fi][q][s][0] = Ji[0] * r0 + Ji[2] * r1;
+        sQ[e][fi][q][s][1] = Ji[1] * r0 + Ji[3] * r1;
+        sQ[e][fi][q][s][2] = f;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ne * NQ; i += blockDim.x) {
@@ -416,16 +480,9 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
         for (int fi = 0; fi < F; ++fi)
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                double v = 0.0, gx = 0.0, gy = 0.0;
-#pragma unroll
-                for (int m = 0; m < NB; ++m) {
-                    v = fma(tb.VB[q][m], sU[e][fi][s][m], v);
-                    gx = fma(sGP[e][q][m][0], sU[e][fi][s][m], gx);
-                    gy = fma(sGP[e][q][m][1], sU[e][fi][s][m], gy);
-                }
-                u[fi][s] = v;
-                g[fi][s][0] = gx;
-                g[fi][s][1] = gy;
+                u[fi][s] = sQ[e][fi][q][s][2];
+                g[fi][s][0] = sQ[e][fi][q][s][0];
+                g[fi][s][1] = sQ[e][fi][q][s][1];
             }
         if constexpr (MODE == TRI_APPLY) {
             volume_point<2, double>(a.c, u[0], g[0], Phi, Sr);
@@ -434,7 +491,7 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
         } else {
             // cotangents of S and Phi at the point: det w_q mu and det w_q grad mu,
             // mu = M^{-1} lambda = lambda / det (with CDG2_MINV); back through the
-            // flux (w_q is applied by the test loop below)
+            // flux (w_q is applied below)
             const double det = sG[e][10];
             const double W = (a.flags & CDG2_MINV) ? 1.0 : det;
             double sb[NS], gb[NS][2], th[8];
@@ -446,25 +503,44 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
             }
             volume_point_adj<2, double>(a.c, u[0], g[0], sb, gb, Sr, Phi, th);   // Sr <- ub, Phi <- Gb
         }
+        // Phi . grad psi = (J_c^{-1} J^{-1} Phi) . grad_(u,v) psi, weighted by w_q
+        // (in place: this thread alone owns point q of the last field)
+        const double* Ji = sG[e] + 6;
+        const double wq = tb.VW[q];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            sPhi[e][q][s][0] = Phi[s][0];
-            sPhi[e][q][s][1] = Phi[s][1];
-            sPhi[e][q][s][2] = Sr[s];
+            const double p0 = Ji[0] * Phi[s][0] + Ji[1] * Phi[s][1];
+            const double p1 = Ji[2] * Phi[s][0] + Ji[3] * Phi[s][1];
+            sQ[e][F - 1][q][s][0] = wq * fma(tb.SG[q][0], p0, tb.SG[q][1] * p1);
+            sQ[e][F - 1][q][s][1] = wq * p1;
+            sQ[e][F - 1][q][s][2] = wq * Sr[s];
         }
+    }
+    __syncthreads();
+    // transposed u-pass: X_p(v_j) = sum_i A_p S + A'_p P_u; X^v_p(v_j) = sum_i A_p P_v
+    for (int i = threadIdx.x; i < ne * NS * K1 * N; i += blockDim.x) {
+        const int e = i / (NS * K1 * N), s = (i / (K1 * N)) % NS, p = (i / N) % K1, j = i % N;
+        double x0 = 0.0, xv = 0.0;
+#pragma unroll
+        for (int ii = 0; ii < N; ++ii) {
+            const double* P = sQ[e][F - 1][ii + N * j][s];
+            x0 = fma(tb.SA[ii][p], P[2], fma(tb.SdA[ii][p], P[0], x0));
+            xv = fma(tb.SA[ii][p], P[1], xv);
+        }
+        sH[e][0][0][s][p][j] = x0;
+        sH[e][0][1][s][p][j] = xv;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ne * NS * NB; i += blockDim.x) {
         const int e = i / (NS * NB), s = (i / NB) % NS, m = i % NB;
         const double* G = sG[e];
         const double det = G[10];
+        int d = 0;
+        while ((d + 1) * (d + 2) / 2 <= m) ++d;
+        const int p = d - (m - d * (d + 1) / 2);
         double acc = 0.0;
-#pragma unroll 5
-        for (int q = 0; q < NQ; ++q) {
-            const double t = fma(sPhi[e][q][s][0], sGP[e][q][m][0],
-                                 fma(sPhi[e][q][s][1], sGP[e][q][m][1], sPhi[e][q][s][2] * tb.VB[q][m]));
-            acc = fma(tb.VW[q], t, acc);
-        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc = fma(tb.SB[j][m], sH[e][0][0][s][p][j], fma(tb.SdB[j][m], sH[e][0][1][s][p][j], acc));
         // forward: R = det sum_q w_q (Phi . grad phi + S phi); VJP: the cotangents carry det
         double R = MODE == TRI_VJP ? acc : det * acc;
         const long long ge = e0 + e;
@@ -511,8 +587,9 @@ static cudaError_t tri_launch(const TriArgs& a, cudaStream_t st) {
         const unsigned fb = (unsigned)((a.NF + FPB - 1) / FPB);
         tri_face_kernel<K, FPB, MODE><<<fb, 128, 0, st>>>(a);
     }
-    const unsigned eb = (unsigned)((a.E + TRI_EPB - 1) / TRI_EPB);
-    tri_elem_kernel<K, TRI_EPB, MODE><<<eb, 128, 0, st>>>(a);
+    constexpr int EPB = MODE == TRI_APPLY ? TRI_EPB : TRI_EPB / 2;   // static shared memory <= 48 KB
+    const unsigned eb = (unsigned)((a.E + EPB - 1) / EPB);
+    tri_elem_kernel<K, EPB, MODE><<<eb, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 

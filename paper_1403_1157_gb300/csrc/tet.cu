@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "physics.cuh"
+#include "simplex_elem.cuh"
 #include "simplex_host.h"
 #include "simplex_step.h"
 
@@ -72,6 +73,11 @@ struct TetTab {
     // d_xi = a1 d_u, d_eta = u a1 d_u + b1 d_v, d_zeta = u a1 d_u + v b1 d_v + d_w,
     // a1 = 1 / ((1-v)(1-w)), b1 = 1 / (1-w); stored (a1, u a1, b1, v b1)
     double SG[TTMAXQ][4];
+    // reference stiffness matrices, exact under the volume rule: KS[c][i][j] =
+    // sum_q w_q d_a psi_i d_b psi_j for c = (a, b) in {00, 11, 22}, and that plus
+    // its transpose for c = (a, b) in {01, 02, 12}; so that int_K grad psi_i .
+    // grad psi_j = det J sum_c G_c KS[c][i][j] with G = J^{-1} J^{-T}
+    double KS[6][TTMAXB][TTMAXB];
     int PQA[TTMAXK1][TTMAXK1];            // pair index of (p, q), p + q <= k
     int PQM[TTMAXPQ][TTMAXK1];            // mode index of (pair, r), r <= k - p - q
     int MPQ[TTMAXB];                      // pair index of mode m
@@ -186,6 +192,20 @@ void build_tet_tables(int k, TetTab& T) {
                 T.VW[q] = w[a] * w[b] * w[c] * (1.0 - g[b]) * (1.0 - g[c]) * (1.0 - g[c]);
                 dubiner3(k, xi, eta, zeta, T.VB[q], T.VD[0][q], T.VD[1][q], T.VD[2][q]);
             }
+    {
+        const int PA[6] = {0, 1, 2, 0, 0, 1}, PB[6] = {0, 1, 2, 1, 2, 2};
+        for (int c = 0; c < 6; ++c)
+            for (int i = 0; i < nb; ++i)
+                for (int j = 0; j < nb; ++j) {
+                    double acc = 0.0;
+                    for (int q = 0; q < n * n * n; ++q) {
+                        double v = T.VD[PA[c]][q][i] * T.VD[PB[c]][q][j];
+                        if (PA[c] != PB[c]) v += T.VD[PB[c]][q][i] * T.VD[PA[c]][q][j];
+                        acc += T.VW[q] * v;
+                    }
+                    T.KS[c][i][j] = acc;
+                }
+    }
     for (int b = 0; b < n; ++b)
         for (int a = 0; a < n; ++a) {
             const int p = a + n * b;
@@ -310,13 +330,14 @@ __global__ void __launch_bounds__(128) tet_face_kernel(const TetArgs a) {
     constexpr int NB = S::NB, NP = S::NP, F = MODE == TET_APPLY ? 1 : 2;
     const TetTab& tb = *a.tab;
     __shared__ double sU[FPB][2][F][NS][NB];
-    __shared__ double sJ[FPB][2][9];          // J^{-1} of each side (row-major)
+    __shared__ double sM[FPB][2][3];          // J^{-1} n^- of each side: n^- . J^{-T} g = (J^{-1} n^-) . g
     __shared__ double sDet[FPB][2];
     __shared__ double sF[FPB][5];             // n (3), E, det_-
     __shared__ int sI[FPB][4];                // eM, eP, frame of K^-, frame of K^+
     __shared__ double sDN[FPB][2][NP][NB];    // n^- . grad phi_m of each side at the face points
     __shared__ double sT[FPB][2][F][2][NS][NP];  // [side][field][value, normal derivative][s][p]
-    __shared__ double sS[FPB][2][NS][NP];     // sigma, tau (VJP: their cotangents)
+    __shared__ double sD[MODE == TET_VJP ? 1 : FPB][NS][NP];  // jump of the last field (the lifted one)
+    __shared__ double sS[FPB][2][NS][NP];     // w_p sigma, w_p tau (VJP: the cotangents of sigma, tau)
     __shared__ double sA[MODE == TET_VJP ? FPB : 1][2][2][NS][NP];   // VJP: trace cotangents
     const long long f0 = (long long)blockIdx.x * FPB;
     const int nf = (int)min((long long)FPB, a.NF - f0);
@@ -326,10 +347,13 @@ __global__ void __launch_bounds__(128) tet_face_kernel(const TetArgs a) {
         sF[j][c] = a.fgeo[(f0 + j) * 5 + c];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nf * 2 * 9; i += blockDim.x) {
-        const int j = i / 18, side = (i / 9) % 2, c = i % 9;
-        sJ[j][side][c] = a.geo[(long long)sI[j][side] * TGEO + 12 + c];
-        if (c == 0) sDet[j][side] = a.geo[(long long)sI[j][side] * TGEO + 21];
+    for (int i = threadIdx.x; i < nf * 2; i += blockDim.x) {
+        const int j = i / 2, side = i % 2;
+        const double* Ji = a.geo + (long long)sI[j][side] * TGEO + 12;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            sM[j][side][r] = fma(Ji[3 * r], sF[j][0], fma(Ji[3 * r + 1], sF[j][1], Ji[3 * r + 2] * sF[j][2]));
+        sDet[j][side] = Ji[9];
     }
     for (int i = threadIdx.x; i < nf * 2 * F * NS * NB; i += blockDim.x) {
         const int j = i / (2 * F * NS * NB), side = (i / (F * NS * NB)) % 2, fi = (i / (NS * NB)) % F;
@@ -340,29 +364,34 @@ __global__ void __launch_bounds__(128) tet_face_kernel(const TetArgs a) {
     for (int i = threadIdx.x; i < nf * 2 * NP * NB; i += blockDim.x) {
         const int j = i / (2 * NP * NB), side = (i / (NP * NB)) % 2, p = (i / NB) % NP, m = i % NB;
         const int fr = sI[j][2 + side];
-        const double* Ji = sJ[j][side];
-        const double g0 = tb.FD[0][fr][p][m], g1 = tb.FD[1][fr][p][m], g2 = tb.FD[2][fr][p][m];
-        double dn = 0.0;
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) dn = fma(sF[j][jj], Ji[jj] * g0 + Ji[3 + jj] * g1 + Ji[6 + jj] * g2, dn);
-        sDN[j][side][p][m] = dn;
+        const double* mv = sM[j][side];
+        sDN[j][side][p][m] = fma(mv[0], tb.FD[0][fr][p][m], fma(mv[1], tb.FD[1][fr][p][m], mv[2] * tb.FD[2][fr][p][m]));
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nf * 2 * F * NS * NP; i += blockDim.x) {
-        const int j = i / (2 * F * NS * NP), side = (i / (F * NS * NP)) % 2, fi = (i / (NS * NP)) % F;
+    // traces of both sides per (face, field, species, point), and the jump of the last field
+    for (int i = threadIdx.x; i < nf * F * NS * NP; i += blockDim.x) {
+        const int j = i / (F * NS * NP), fi = (i / (NS * NP)) % F;
         const int s = (i / NP) % NS, p = i % NP;
-        const int fr = sI[j][2 + side];
-        double v = 0.0, dn = 0.0;
+        double val[2];
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int fr = sI[j][2 + side];
+            double v = 0.0, dn = 0.0;
 #pragma unroll 4
-        for (int m = 0; m < NB; ++m) {
-            const double u = sU[j][side][fi][s][m];
-            v = fma(tb.FB[fr][p][m], u, v);
-            dn = fma(sDN[j][side][p][m], u, dn);
+            for (int m = 0; m < NB; ++m) {
+                const double u = sU[j][side][fi][s][m];
+                v = fma(tb.FB[fr][p][m], u, v);
+                dn = fma(sDN[j][side][p][m], u, dn);
+            }
+            // VJP: the cotangent field enters as mu = M^{-1} lambda = lambda / det J (with CDG2_MINV)
+            const double sc = (MODE == TET_VJP && fi == 1 && (a.flags & CDG2_MINV)) ? 1.0 / sDet[j][side] : 1.0;
+            val[side] = v * sc;
+            sT[j][side][fi][0][s][p] = v * sc;
+            sT[j][side][fi][1][s][p] = dn * sc;
         }
-        // VJP: the cotangent field enters as mu = M^{-1} lambda = lambda / det J (with CDG2_MINV)
-        const double sc = (MODE == TET_VJP && fi == 1 && (a.flags & CDG2_MINV)) ? 1.0 / sDet[j][side] : 1.0;
-        sT[j][side][fi][0][s][p] = v * sc;
-        sT[j][side][fi][1][s][p] = dn * sc;
+        if constexpr (MODE != TET_VJP) {
+            if (fi == F - 1) sD[j][s][p] = val[0] - val[1];
+        }
     }
     __syncthreads();
     if constexpr (MODE == TET_VJP) {
@@ -438,24 +467,26 @@ __global__ void __launch_bounds__(128) tet_face_kernel(const TetArgs a) {
             }
             face_point_lin<double>(a.c, 0.0, uM, dM, uP, dP, del, duM, ddM, duP, ddP, ddel, sig, tau);
         }
+        const double w = tb.FW[p];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             double rn = 0.0;
-            for (int q = 0; q < NP; ++q)
-                rn = fma(tb.LF[frM][p][q], sT[j][0][F - 1][0][s][q] - sT[j][1][F - 1][0][s][q], rn);
-            sS[j][0][s][p] = sig[s] + 2.0 * a.chi_e * a.c.A[s] * lift * rn;
-            sS[j][1][s][p] = tau[s];
+            for (int q = 0; q < NP; ++q) rn = fma(tb.LF[frM][p][q], sD[j][s][q], rn);
+            sS[j][0][s][p] = w * fma(2.0 * a.chi_e * a.c.A[s] * lift, rn, sig[s]);
+            sS[j][1][s][p] = w * tau[s];
         }
     }
     __syncthreads();
+    // test: K^- gets sigma phi^- + tau d_n phi^-, K^+ gets -sigma phi^+ + tau d_n phi^+
     for (int i = threadIdx.x; i < nf * 2 * NS * NB; i += blockDim.x) {
         const int j = i / (2 * NS * NB), side = (i / (NS * NB)) % 2, s = (i / NB) % NS, m = i % NB;
         const int fr = sI[j][2 + side];
-        const double sg = side ? -1.0 : 1.0;
-        double acc = 0.0;
-        for (int p = 0; p < NP; ++p)
-            acc = fma(tb.FW[p], fma(sS[j][0][s][p], sg * tb.FB[fr][p][m], sS[j][1][s][p] * sDN[j][side][p][m]), acc);
-        a.fbuf[((f0 + j) * 2 + side) * NS * NB + s * NB + m] = sF[j][3] * acc;
+        double as = 0.0, at = 0.0;
+        for (int p = 0; p < NP; ++p) {
+            as = fma(sS[j][0][s][p], tb.FB[fr][p][m], as);
+            at = fma(sS[j][1][s][p], sDN[j][side][p][m], at);
+        }
+        a.fbuf[((f0 + j) * 2 + side) * NS * NB + s * NB + m] = sF[j][3] * (side ? at - as : at + as);
     }
 }
 
@@ -468,30 +499,53 @@ __global__ void __launch_bounds__(128) tet_face_kernel(const TetArgs a) {
 // back by J^{-1} and by the collapsed map, weighted, and tested by the
 // transposed passes (A_p in u -> B_pq in v -> C_pqr in w), the tested fluxes
 // of its interior faces, the boundary data of Eq. (3) on its boundary faces
-// (apply only: H' = 0), M^{-1} = 1 / det J (not for the VJP).  Dynamic
-// shared memory per field: U [6][nb], the w-pass [2][6][pairs][n], the v-pass
-// [3][6][k+1][n][n], the point values [NQ][6][4].
-template <int K>
+// (apply only: H' = 0), M^{-1} = 1 / det J (not for the VJP).
+// Apply and JVP take the diffusion of n2..c3 in modal form: -A_s K_e U_s with
+// the element stiffness K_e = det J sum_c G_c KS[c] (G = J^{-1} J^{-T}; exact,
+// as the volume rule integrates the stiffness exactly), so the forward passes
+// carry gradients for n1, c1, c3 only (what the fluxes read) and the test
+// passes carry the flux for n1, n2 only; the other species are tested against
+// the source alone.  The VJP keeps the full passes.  Dynamic shared memory per
+// field: U [6][nb], the w-pass [2][6][pairs][n], the v-pass [3][6][k+1][n][n],
+// the point values [NQ][6 * 4 + 1] (an odd stride per point: threads on
+// consecutive points hit distinct banks).  The w- and v-pass buffers hold the
+// values of all six species and the derivatives of the NGF species carrying
+// gradients (their slots); the test passes reuse them for the six values and
+// the derivative parts of the species with a flux.
+template <int K, bool MODAL>
 struct TetSF {
     static constexpr int N = K + 2, NPQ = (K + 1) * (K + 2) / 2, K1 = K + 1;
     static constexpr int NB = TetShape<K>::NB, NQ = TetShape<K>::NQ;
-    static constexpr int SU = NS * NB, SG1 = 2 * NS * NPQ * N, SH = 3 * NS * K1 * N * N, SQ = NQ * NS * 4;
+    static constexpr int NGF = MODAL ? 3 : NS;   // species carrying gradients in the forward passes
+    static constexpr int QS = NS * 4 + 1;
+    static constexpr int SU = NS * NB, SG1 = (NS + NGF) * NPQ * N, SH = (NS + 2 * NGF) * K1 * N * N, SQ = NQ * QS;
     static constexpr int FIELD = SU + SG1 + SH + SQ;   // doubles per field
 };
 
 template <int K, int MODE>
 __global__ void __launch_bounds__(128) tet_elem_kernel(const TetArgs a) {
     using S = TetShape<K>;
-    using SF = TetSF<K>;
+    constexpr bool MODAL = MODE != TET_VJP;
+    using SF = TetSF<K, MODAL>;
     constexpr int NB = S::NB, NQ = S::NQ, NP = S::NP, F = MODE == TET_APPLY ? 1 : 2;
-    constexpr int N = SF::N, NPQ = SF::NPQ, K1 = SF::K1;
+    constexpr int N = SF::N, NPQ = SF::NPQ, K1 = SF::K1, QS = SF::QS;
+    constexpr int NGF = SF::NGF;          // forward slots carrying gradients
+    constexpr int NGT = MODAL ? 2 : NS;   // species tested against a flux (<= NGF)
     const TetTab& tb = *a.tab;
     extern __shared__ __align__(16) double tsm[];
     auto sU = [&](int fi) { return reinterpret_cast<double (*)[NB]>(tsm + fi * SF::FIELD); };
-    auto sG1 = [&](int fi) { return reinterpret_cast<double (*)[NS][NPQ][N]>(tsm + fi * SF::FIELD + SF::SU); };
-    auto sH = [&](int fi) { return reinterpret_cast<double (*)[NS][K1][N][N]>(tsm + fi * SF::FIELD + SF::SU + SF::SG1); };
-    auto sQ = [&](int fi) {
-        return reinterpret_cast<double (*)[NS][4]>(tsm + fi * SF::FIELD + SF::SU + SF::SG1 + SF::SH);
+    // w-pass (and test v-pass) buffers: the values of species s, the derivative of slot sl
+    auto Gv = [&](int fi, int s) { return reinterpret_cast<double (*)[N]>(tsm + fi * SF::FIELD + SF::SU + s * NPQ * N); };
+    auto Gg = [&](int fi, int sl) {
+        return reinterpret_cast<double (*)[N]>(tsm + fi * SF::FIELD + SF::SU + (NS + sl) * NPQ * N);
+    };
+    // v-pass (and test u-pass) buffers: c = 0 values of species idx, c = 1, 2 the derivatives of slot idx
+    auto Hc = [&](int fi, int c, int idx) {
+        return reinterpret_cast<double (*)[N][N]>(tsm + fi * SF::FIELD + SF::SU + SF::SG1 +
+                                                  ((c == 0 ? 0 : c == 1 ? NS : NS + NGF) + idx) * K1 * N * N);
+    };
+    auto sQ = [&](int fi, int q, int s) {   // (d_x, d_y, d_z, value) of species s at point q
+        return tsm + fi * SF::FIELD + SF::SU + SF::SG1 + SF::SH + q * QS + s * 4;
     };
     __shared__ double sG[TGEO];
     const long long e = blockIdx.x;
@@ -504,84 +558,118 @@ __global__ void __launch_bounds__(128) tet_elem_kernel(const TetArgs a) {
     const double* J = sG + 3;
     const double* Ji = sG + 12;
     const double det = sG[21];
-    // w-pass: g_pq(w_l) = sum_r C_pqr(w_l) U_pqr, and with C'
+    // w-pass: g_pq(w_l) = sum_r C_pqr(w_l) U_pqr, and with C' where gradients are carried
     for (int i = threadIdx.x; i < F * NS * NPQ * N; i += blockDim.x) {
-        const int fi = i / (NS * NPQ * N), s = (i / (NPQ * N)) % NS, pq = (i / N) % NPQ, l = i % N;
+        const int fi = i / (NS * NPQ * N), sl = (i / (NPQ * N)) % NS, pq = (i / N) % NPQ, l = i % N;
+        const int s = MODAL ? modal_fwd_species(sl) : sl;
         double g = 0.0, gw = 0.0;
+        if (sl < NGF) {
 #pragma unroll
-        for (int r = 0; r < K1; ++r) {
-            const int m = tb.PQM[pq][r];
-            if (m >= 0) {
-                const double u = sU(fi)[s][m];
-                g = fma(tb.SC[l][m], u, g);
-                gw = fma(tb.SdC[l][m], u, gw);
+            for (int r = 0; r < K1; ++r) {
+                const int m = tb.PQM[pq][r];
+                if (m >= 0) {
+                    const double u = sU(fi)[s][m];
+                    g = fma(tb.SC[l][m], u, g);
+                    gw = fma(tb.SdC[l][m], u, gw);
+                }
+            }
+            Gg(fi, sl)[pq][l] = gw;
+        } else {
+#pragma unroll
+            for (int r = 0; r < K1; ++r) {
+                const int m = tb.PQM[pq][r];
+                if (m >= 0) g = fma(tb.SC[l][m], sU(fi)[s][m], g);
             }
         }
-        sG1(fi)[0][s][pq][l] = g;
-        sG1(fi)[1][s][pq][l] = gw;
+        Gv(fi, s)[pq][l] = g;
     }
     __syncthreads();
     // v-pass: h_p(v_j, w_l) = sum_q B_pq(v_j) g_pq(w_l); with B' (d_v) and with g' (d_w)
     for (int i = threadIdx.x; i < F * NS * K1 * N * N; i += blockDim.x) {
-        const int fi = i / (NS * K1 * N * N), s = (i / (K1 * N * N)) % NS, p = (i / (N * N)) % K1;
+        const int fi = i / (NS * K1 * N * N), sl = (i / (K1 * N * N)) % NS, p = (i / (N * N)) % K1;
         const int j = (i / N) % N, l = i % N;
+        const int s = MODAL ? modal_fwd_species(sl) : sl;
         double h = 0.0, hv = 0.0, hw = 0.0;
+        if (sl < NGF) {
 #pragma unroll
-        for (int q = 0; q < K1; ++q) {
-            if (q <= K - p) {
-                const int pq = tb.PQA[p][q];
-                const double g = sG1(fi)[0][s][pq][l];
-                h = fma(tb.SB[j][pq], g, h);
-                hv = fma(tb.SdB[j][pq], g, hv);
-                hw = fma(tb.SB[j][pq], sG1(fi)[1][s][pq][l], hw);
+            for (int q = 0; q < K1; ++q) {
+                if (q <= K - p) {
+                    const int pq = tb.PQA[p][q];
+                    const double g = Gv(fi, s)[pq][l];
+                    h = fma(tb.SB[j][pq], g, h);
+                    hv = fma(tb.SdB[j][pq], g, hv);
+                    hw = fma(tb.SB[j][pq], Gg(fi, sl)[pq][l], hw);
+                }
+            }
+            Hc(fi, 1, sl)[p][j][l] = hv;
+            Hc(fi, 2, sl)[p][j][l] = hw;
+        } else {
+#pragma unroll
+            for (int q = 0; q < K1; ++q) {
+                if (q <= K - p) {
+                    const int pq = tb.PQA[p][q];
+                    h = fma(tb.SB[j][pq], Gv(fi, s)[pq][l], h);
+                }
             }
         }
-        sH(fi)[0][s][p][j][l] = h;
-        sH(fi)[1][s][p][j][l] = hv;
-        sH(fi)[2][s][p][j][l] = hw;
+        Hc(fi, 0, s)[p][j][l] = h;
     }
     __syncthreads();
-    // u-pass: value and (u, v, w) gradient at every point, then reference and physical gradient
-    for (int i = threadIdx.x; i < F * NQ * NS; i += blockDim.x) {
-        const int fi = i / (NQ * NS), q = (i / NS) % NQ, s = i % NS;
+    // u-pass: value, and where carried the (u, v, w) gradient mapped to the
+    // reference and physical gradient, at every point (consecutive threads on
+    // consecutive points)
+    for (int i = threadIdx.x; i < F * NS * NQ; i += blockDim.x) {
+        const int fi = i / (NS * NQ), sl = (i / NQ) % NS, q = i % NQ;
+        const int s = MODAL ? modal_fwd_species(sl) : sl;
         const int ii = q % N, j = (q / N) % N, l = q / (N * N);
-        double f = 0.0, fu = 0.0, fv = 0.0, fw = 0.0;
+        double* Q = sQ(fi, q, s);
+        double f = 0.0;
+        if (sl < NGF) {
+            double fu = 0.0, fv = 0.0, fw = 0.0;
 #pragma unroll
-        for (int p = 0; p < K1; ++p) {
-            const double h = sH(fi)[0][s][p][j][l];
-            f = fma(tb.SA[ii][p], h, f);
-            fu = fma(tb.SdA[ii][p], h, fu);
-            fv = fma(tb.SA[ii][p], sH(fi)[1][s][p][j][l], fv);
-            fw = fma(tb.SA[ii][p], sH(fi)[2][s][p][j][l], fw);
+            for (int p = 0; p < K1; ++p) {
+                const double h = Hc(fi, 0, s)[p][j][l];
+                f = fma(tb.SA[ii][p], h, f);
+                fu = fma(tb.SdA[ii][p], h, fu);
+                fv = fma(tb.SA[ii][p], Hc(fi, 1, sl)[p][j][l], fv);
+                fw = fma(tb.SA[ii][p], Hc(fi, 2, sl)[p][j][l], fw);
+            }
+            const double r0 = tb.SG[q][0] * fu;
+            const double r1 = fma(tb.SG[q][1], fu, tb.SG[q][2] * fv);
+            const double r2 = fma(tb.SG[q][1], fu, fma(tb.SG[q][3], fv, fw));
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj) Q[jj] = Ji[jj] * r0 + Ji[3 + jj] * r1 + Ji[6 + jj] * r2;   // J^{-T} grad_ref
+        } else {
+#pragma unroll
+            for (int p = 0; p < K1; ++p) f = fma(tb.SA[ii][p], Hc(fi, 0, s)[p][j][l], f);
         }
-        const double r0 = tb.SG[q][0] * fu;
-        const double r1 = fma(tb.SG[q][1], fu, tb.SG[q][2] * fv);
-        const double r2 = fma(tb.SG[q][1], fu, fma(tb.SG[q][3], fv, fw));
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) sQ(fi)[q][s][jj] = Ji[jj] * r0 + Ji[3 + jj] * r1 + Ji[6 + jj] * r2;   // J^{-T} grad_ref
-        sQ(fi)[q][s][3] = f;
+        Q[3] = f;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
         double u[NS], g[NS][3], Phi[NS][3], Sr[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            u[s] = sQ(0)[q][s][3];
+            const double* Q = sQ(0, q, s);
+            u[s] = Q[3];
+            const bool hasg = !MODAL || s == 0 || s == 3 || s == 5;
 #pragma unroll
-            for (int jj = 0; jj < 3; ++jj) g[s][jj] = sQ(0)[q][s][jj];
+            for (int jj = 0; jj < 3; ++jj) g[s][jj] = hasg ? Q[jj] : 0.0;
         }
         if constexpr (MODE == TET_APPLY) {
-            volume_point<3, double>(a.c, u, g, Phi, Sr);
+            volume_point<3, double, true>(a.c, u, g, Phi, Sr);
         } else {
             double du[NS], dg[NS][3];
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                du[s] = sQ(F - 1)[q][s][3];
+                const double* Q = sQ(F - 1, q, s);
+                du[s] = Q[3];
+                const bool hasg = !MODAL || s == 0 || s == 3 || s == 5;
 #pragma unroll
-                for (int jj = 0; jj < 3; ++jj) dg[s][jj] = sQ(F - 1)[q][s][jj];
+                for (int jj = 0; jj < 3; ++jj) dg[s][jj] = hasg ? Q[jj] : 0.0;
             }
             if constexpr (MODE == TET_JVP) {
-                volume_point_lin<3, double>(a.c, u, g, du, dg, false, Phi, Sr);
+                volume_point_lin<3, double, true>(a.c, u, g, du, dg, false, Phi, Sr);
             } else {
                 // mu = M^{-1} lambda = lambda / det (with CDG2_MINV); w_q is applied below
                 const double W = (a.flags & CDG2_MINV) ? 1.0 : det;
@@ -600,55 +688,99 @@ __global__ void __launch_bounds__(128) tet_elem_kernel(const TetArgs a) {
         const double wq = tb.VW[q];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            const double p0 = Ji[0] * Phi[s][0] + Ji[1] * Phi[s][1] + Ji[2] * Phi[s][2];
-            const double p1 = Ji[3] * Phi[s][0] + Ji[4] * Phi[s][1] + Ji[5] * Phi[s][2];
-            const double p2 = Ji[6] * Phi[s][0] + Ji[7] * Phi[s][1] + Ji[8] * Phi[s][2];
-            sQ(F - 1)[q][s][0] = wq * (tb.SG[q][0] * p0 + tb.SG[q][1] * (p1 + p2));
-            sQ(F - 1)[q][s][1] = wq * (tb.SG[q][2] * p1 + tb.SG[q][3] * p2);
-            sQ(F - 1)[q][s][2] = wq * p2;
-            sQ(F - 1)[q][s][3] = wq * Sr[s];
+            double* Q = sQ(F - 1, q, s);
+            if (s < NGT) {
+                const double p0 = Ji[0] * Phi[s][0] + Ji[1] * Phi[s][1] + Ji[2] * Phi[s][2];
+                const double p1 = Ji[3] * Phi[s][0] + Ji[4] * Phi[s][1] + Ji[5] * Phi[s][2];
+                const double p2 = Ji[6] * Phi[s][0] + Ji[7] * Phi[s][1] + Ji[8] * Phi[s][2];
+                Q[0] = wq * (tb.SG[q][0] * p0 + tb.SG[q][1] * (p1 + p2));
+                Q[1] = wq * (tb.SG[q][2] * p1 + tb.SG[q][3] * p2);
+                Q[2] = wq * p2;
+            }
+            Q[3] = wq * Sr[s];
         }
     }
     __syncthreads();
     // transposed u-pass: X_p(v_j, w_l) = sum_i A_p S + A'_p P_u, A_p P_v, A_p P_w
-    double (*sX)[NS][K1][N][N] = sH(0);
+    // (species without a flux: A_p S only), into the v-pass buffers of field 0
     for (int i = threadIdx.x; i < NS * K1 * N * N; i += blockDim.x) {
         const int s = i / (K1 * N * N), p = (i / (N * N)) % K1, j = (i / N) % N, l = i % N;
         double x0 = 0.0, xv = 0.0, xw = 0.0;
+        if (s < NGT) {
 #pragma unroll
-        for (int ii = 0; ii < N; ++ii) {
-            const double* P = sQ(F - 1)[ii + N * (j + N * l)][s];
-            x0 = fma(tb.SA[ii][p], P[3], fma(tb.SdA[ii][p], P[0], x0));
-            xv = fma(tb.SA[ii][p], P[1], xv);
-            xw = fma(tb.SA[ii][p], P[2], xw);
+            for (int ii = 0; ii < N; ++ii) {
+                const double* P = sQ(F - 1, ii + N * (j + N * l), s);
+                x0 = fma(tb.SA[ii][p], P[3], fma(tb.SdA[ii][p], P[0], x0));
+                xv = fma(tb.SA[ii][p], P[1], xv);
+                xw = fma(tb.SA[ii][p], P[2], xw);
+            }
+            Hc(0, 1, s)[p][j][l] = xv;
+            Hc(0, 2, s)[p][j][l] = xw;
+        } else {
+#pragma unroll
+            for (int ii = 0; ii < N; ++ii) x0 = fma(tb.SA[ii][p], sQ(F - 1, ii + N * (j + N * l), s)[3], x0);
         }
-        sX[0][s][p][j][l] = x0;
-        sX[1][s][p][j][l] = xv;
-        sX[2][s][p][j][l] = xw;
+        Hc(0, 0, s)[p][j][l] = x0;
     }
     __syncthreads();
+    // K_e / det J = sum_c G_c KS[c] with G_ab = sum_c (J^{-1})_ac (J^{-1})_bc for ab = 00, 11, 22, 01,
+    // 02, 12, over the point values of the last field (dead once the transposed u-pass has read them)
+    double (*sKe)[NB] = reinterpret_cast<double (*)[NB]>(sQ(F - 1, 0, 0));
+    if constexpr (MODAL) {
+        double G[6];
+        const int PA[6] = {0, 1, 2, 0, 0, 1}, PB[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+            G[c] = fma(Ji[3 * PA[c]], Ji[3 * PB[c]],
+                       fma(Ji[3 * PA[c] + 1], Ji[3 * PB[c] + 1], Ji[3 * PA[c] + 2] * Ji[3 * PB[c] + 2]));
+        for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+            const int r = i / NB, cc = i % NB;
+            double kk = 0.0;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) kk = fma(G[c], tb.KS[c][r][cc], kk);
+            sKe[r][cc] = kk;
+        }
+    }
     // transposed v-pass: Y_pq(w_l) = sum_j B_pq X + B'_pq X_v; Y^w_pq = sum_j B_pq X_w
-    double (*sY)[NS][NPQ][N] = sG1(0);
     for (int i = threadIdx.x; i < NS * NPQ * N; i += blockDim.x) {
         const int s = i / (NPQ * N), pq = (i / N) % NPQ, l = i % N;
         int p = 0;
         while (p < K && pq >= tb.PQA[p + 1][0]) ++p;
         double y = 0.0, yw = 0.0;
+        if (s < NGT) {
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            y = fma(tb.SB[j][pq], sX[0][s][p][j][l], fma(tb.SdB[j][pq], sX[1][s][p][j][l], y));
-            yw = fma(tb.SB[j][pq], sX[2][s][p][j][l], yw);
+            for (int j = 0; j < N; ++j) {
+                y = fma(tb.SB[j][pq], Hc(0, 0, s)[p][j][l], fma(tb.SdB[j][pq], Hc(0, 1, s)[p][j][l], y));
+                yw = fma(tb.SB[j][pq], Hc(0, 2, s)[p][j][l], yw);
+            }
+            Gg(0, s)[pq][l] = yw;
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) y = fma(tb.SB[j][pq], Hc(0, 0, s)[p][j][l], y);
         }
-        sY[0][s][pq][l] = y;
-        sY[1][s][pq][l] = yw;
+        Gv(0, s)[pq][l] = y;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < NS * NB; i += blockDim.x) {
         const int s = i / NB, m = i % NB;
         const int pq = tb.MPQ[m];
         double acc = 0.0;
+        if (s < NGT) {
 #pragma unroll
-        for (int l = 0; l < N; ++l) acc = fma(tb.SC[l][m], sY[0][s][pq][l], fma(tb.SdC[l][m], sY[1][s][pq][l], acc));
+            for (int l = 0; l < N; ++l)
+                acc = fma(tb.SC[l][m], Gv(0, s)[pq][l], fma(tb.SdC[l][m], Gg(0, s)[pq][l], acc));
+        } else {
+#pragma unroll
+            for (int l = 0; l < N; ++l) acc = fma(tb.SC[l][m], Gv(0, s)[pq][l], acc);
+        }
+        if constexpr (MODAL) {
+            if (s > 0) {   // the diffusion of n2..c3 (of the tangent in the JVP): -A_s (K_e U_s)_m / det J
+                double kd = 0.0;
+#pragma unroll 4
+                for (int jj = 0; jj < NB; ++jj) kd = fma(sKe[m][jj], sU(F - 1)[s][jj], kd);
+                acc = fma(-a.c.A[s], kd, acc);
+            }
+        }
         double R = MODE == TET_VJP ? acc : det * acc;   // (the VJP's cotangents carry det)
         for (int l = 0; l < 4; ++l) {
             const int code = a.emap[e * 4 + l];
@@ -698,7 +830,7 @@ template <int K, int MODE>
 static cudaError_t tet_launch(const TetArgs& a, cudaStream_t st) {
     constexpr int FPB = MODE == TET_APPLY ? 2 : 1;   // faces per CTA (static shared memory <= 48 KB)
     constexpr int F = MODE == TET_APPLY ? 1 : 2;
-    constexpr size_t smem = sizeof(double) * (size_t)F * TetSF<K>::FIELD;
+    constexpr size_t smem = sizeof(double) * (size_t)F * TetSF<K, MODE != TET_VJP>::FIELD;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(tet_elem_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,

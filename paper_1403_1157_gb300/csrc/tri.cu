@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "physics.cuh"
+#include "simplex_elem.cuh"
 #include "simplex_host.h"
 #include "simplex_step.h"
 
@@ -55,6 +56,11 @@ struct TriTab {
     double SB[TMAXP][TMAXB], SdB[TMAXP][TMAXB];   // [v point][mode]
     // d_xi = a1 d_u, d_eta = u a1 d_u + d_v with a1 = 1 / (1-v): (a1, u a1) per point
     double SG[TMAXQ][2];
+    // reference stiffness matrices, exact under the volume rule: KS[c][i][j] =
+    // sum_q w_q d_a psi_i d_b psi_j for c = (a, b) in {00, 11}, and that plus its
+    // transpose for c = 01; so that int_K grad psi_i . grad psi_j = det J sum_c
+    // G_c KS[c][i][j] with G = J^{-1} J^{-T}
+    double KS[3][TMAXB][TMAXB];
 };
 
 // Element geometry: x0, y0, J (row-major), J^{-1} (row-major), det J.
@@ -174,6 +180,20 @@ void build_tables(int k, TriTab& T) {
         T.ET[p] = g[p];
     }
     const int nb = (k + 1) * (k + 2) / 2;
+    {
+        const int PA[3] = {0, 1, 0}, PB[3] = {0, 1, 1};
+        for (int c = 0; c < 3; ++c)
+            for (int i = 0; i < nb; ++i)
+                for (int j = 0; j < nb; ++j) {
+                    double acc = 0.0;
+                    for (int q = 0; q < n * n; ++q) {
+                        double v = T.VD[PA[c]][q][i] * T.VD[PB[c]][q][j];
+                        if (PA[c] != PB[c]) v += T.VD[PB[c]][q][i] * T.VD[PA[c]][q][j];
+                        acc += T.VW[q] * v;
+                    }
+                    T.KS[c][i][j] = acc;
+                }
+    }
     for (int l = 0; l < 3; ++l) {
         for (int p = 0; p < n; ++p) {
             double xi, eta;
@@ -241,12 +261,13 @@ __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
     constexpr int NB = S::NB, NP = S::NP, F = MODE == TRI_APPLY ? 1 : 2;
     __shared__ TriTab tb;
     __shared__ double sU[FPB][2][F][NS][NB];
-    __shared__ double sG[FPB][2][4];         // J^{-1} of each side
+    __shared__ double sM[FPB][2][2];         // J^{-1} n^- of each side: n^- . J^{-T} g = (J^{-1} n^-) . g
     __shared__ double sF[FPB][4];            // n_x, n_y, |e|, det_-
     __shared__ int sI[FPB][4];               // eM, eP, lM, lP
     __shared__ double sT[FPB][2][F][2][NS][NP];  // [side][field][value, normal derivative][s][p]
     __shared__ double sDN[FPB][2][NP][NB];    // n^- . grad phi_m of each side at the face points
-    __shared__ double sS[FPB][2][NS][NP];     // sigma, tau (VJP: their cotangents)
+    __shared__ double sD[MODE == TRI_VJP ? 1 : FPB][NS][NP];  // jump of the last field (the lifted one)
+    __shared__ double sS[FPB][2][NS][NP];     // w_p sigma, w_p tau (VJP: the cotangents of sigma, tau)
     __shared__ double sA[MODE == TRI_VJP ? FPB : 1][2][2][NS][NP];   // VJP: [side][value, d_n] trace cotangents
     __shared__ double sDet[FPB][2];
     load_tritab(tb, a.tab);
@@ -258,44 +279,52 @@ __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
         sF[j][c] = a.fgeo[(f0 + j) * 4 + c];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nf * 2 * 4; i += blockDim.x) {
-        const int j = i / 8, side = (i / 4) % 2, c = i % 4;
-        sG[j][side][c] = a.geo[(long long)sI[j][side] * GEO + 6 + c];
-        if (c == 0) sDet[j][side] = a.geo[(long long)sI[j][side] * GEO + 10];
+    for (int i = threadIdx.x; i < nf * 2; i += blockDim.x) {
+        const int j = i / 2, side = i % 2;
+        const double* Ji = a.geo + (long long)sI[j][side] * GEO + 6;
+        sM[j][side][0] = fma(Ji[0], sF[j][0], Ji[1] * sF[j][1]);
+        sM[j][side][1] = fma(Ji[2], sF[j][0], Ji[3] * sF[j][1]);
+        sDet[j][side] = Ji[4];
     }
     for (int i = threadIdx.x; i < nf * 2 * F * NS * NB; i += blockDim.x) {
         const int j = i / (2 * F * NS * NB), side = (i / (F * NS * NB)) % 2, fi = (i / (NS * NB)) % F;
         const int r = i % (NS * NB);
         sU[j][side][fi][r / NB][r % NB] = (fi ? a.dU : a.U)[(long long)sI[j][side] * NS * NB + r];
     }
-    __syncthreads();   // sG, sDet and sU are read by other threads below
+    __syncthreads();   // sM, sDet and sU are read by other threads below
     // normal derivatives of the basis at the face points (K^-'s order; K^+ reads its edge reversed)
     for (int i = threadIdx.x; i < nf * 2 * NP * NB; i += blockDim.x) {
         const int j = i / (2 * NP * NB), side = (i / (NP * NB)) % 2, p = (i / NB) % NP, m = i % NB;
         const int l = sI[j][2 + side];
         const int pp = side ? NP - 1 - p : p;
-        const double* Ji = sG[j][side];
-        const double gx = tb.ED[0][l][pp][m], gy = tb.ED[1][l][pp][m];
-        sDN[j][side][p][m] = sF[j][0] * (Ji[0] * gx + Ji[2] * gy) + sF[j][1] * (Ji[1] * gx + Ji[3] * gy);
+        sDN[j][side][p][m] = fma(sM[j][side][0], tb.ED[0][l][pp][m], sM[j][side][1] * tb.ED[1][l][pp][m]);
     }
     __syncthreads();
-    // traces at the face points
-    for (int i = threadIdx.x; i < nf * 2 * F * NS * NP; i += blockDim.x) {
-        const int j = i / (2 * F * NS * NP), side = (i / (F * NS * NP)) % 2, fi = (i / (NS * NP)) % F;
+    // traces of both sides at the face points, and the jump of the last field
+    for (int i = threadIdx.x; i < nf * F * NS * NP; i += blockDim.x) {
+        const int j = i / (F * NS * NP), fi = (i / (NS * NP)) % F;
         const int s = (i / NP) % NS, p = i % NP;
-        const int l = sI[j][2 + side];
-        const int pp = side ? NP - 1 - p : p;
-        double v = 0.0, dn = 0.0;
+        double val[2];
 #pragma unroll
-        for (int m = 0; m < NB; ++m) {
-            const double u = sU[j][side][fi][s][m];
-            v = fma(tb.EB[l][pp][m], u, v);
-            dn = fma(sDN[j][side][p][m], u, dn);
+        for (int side = 0; side < 2; ++side) {
+            const int l = sI[j][2 + side];
+            const int pp = side ? NP - 1 - p : p;
+            double v = 0.0, dn = 0.0;
+#pragma unroll
+            for (int m = 0; m < NB; ++m) {
+                const double u = sU[j][side][fi][s][m];
+                v = fma(tb.EB[l][pp][m], u, v);
+                dn = fma(sDN[j][side][p][m], u, dn);
+            }
+            // VJP: the cotangent field enters as mu = M^{-1} lambda = lambda / det J (with CDG2_MINV)
+            const double sc = (MODE == TRI_VJP && fi == 1 && (a.flags & CDG2_MINV)) ? 1.0 / sDet[j][side] : 1.0;
+            val[side] = v * sc;
+            sT[j][side][fi][0][s][p] = v * sc;
+            sT[j][side][fi][1][s][p] = dn * sc;
         }
-        // VJP: the cotangent field enters as mu = M^{-1} lambda = lambda / det J (with CDG2_MINV)
-        const double sc = (MODE == TRI_VJP && fi == 1 && (a.flags & CDG2_MINV)) ? 1.0 / sDet[j][side] : 1.0;
-        sT[j][side][fi][0][s][p] = v * sc;
-        sT[j][side][fi][1][s][p] = dn * sc;
+        if constexpr (MODE != TRI_VJP) {
+            if (fi == F - 1) sD[j][s][p] = val[0] - val[1];
+        }
     }
     __syncthreads();
     if constexpr (MODE == TRI_VJP) {
@@ -382,15 +411,15 @@ __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
             }
             face_point_lin<double>(a.c, 0.0, uM, dM, uP, dP, del, duM, ddM, duP, ddP, ddel, sig, tau);
         }
-        // the lifting of the (tangent) jump of the last field
+        // the lifting of the (tangent) jump of the last field; the Gauss weight goes into sigma and tau
+        const double w = tb.EW[p];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             double rn = 0.0;
 #pragma unroll
-            for (int q = 0; q < NP; ++q)
-                rn = fma(tb.LF[lM][p][q], sT[j][0][F - 1][0][s][q] - sT[j][1][F - 1][0][s][q], rn);
-            sS[j][0][s][p] = sig[s] + 2.0 * a.chi_e * a.c.A[s] * lift * rn;
-            sS[j][1][s][p] = tau[s];
+            for (int q = 0; q < NP; ++q) rn = fma(tb.LF[lM][p][q], sD[j][s][q], rn);
+            sS[j][0][s][p] = w * fma(2.0 * a.chi_e * a.c.A[s] * lift, rn, sig[s]);
+            sS[j][1][s][p] = w * tau[s];
         }
     }
     __syncthreads();
@@ -398,14 +427,14 @@ __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
     for (int i = threadIdx.x; i < nf * 2 * NS * NB; i += blockDim.x) {
         const int j = i / (2 * NS * NB), side = (i / (NS * NB)) % 2, s = (i / NB) % NS, m = i % NB;
         const int l = sI[j][2 + side];
-        double acc = 0.0;
+        double as = 0.0, at = 0.0;
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             const int pp = side ? NP - 1 - p : p;
-            const double ph = side ? -tb.EB[l][pp][m] : tb.EB[l][pp][m];
-            acc = fma(tb.EW[p], fma(sS[j][0][s][p], ph, sS[j][1][s][p] * sDN[j][side][p][m]), acc);
+            as = fma(sS[j][0][s][p], tb.EB[l][pp][m], as);
+            at = fma(sS[j][1][s][p], sDN[j][side][p][m], at);
         }
-        a.fbuf[((f0 + j) * 2 + side) * NS * NB + s * NB + m] = sF[j][2] * acc;
+        a.fbuf[((f0 + j) * 2 + side) * NS * NB + s * NB + m] = sF[j][2] * (side ? at - as : at + as);
     }
 }
 
@@ -416,17 +445,27 @@ __global__ void __launch_bounds__(128) tri_face_kernel(const TriArgs a) {
 // its adjoint; the flux mapped back by J^{-1} and the collapsed map, weighted,
 // and tested by the transposed passes), the tested fluxes of the element's
 // interior edges from the face buffer, the boundary data of Eq. (3) on its
-// boundary edges (JVP/VJP: none, H' = 0), M^{-1} = 1 / det J.
+// boundary edges (JVP/VJP: none, H' = 0), M^{-1} = 1 / det J.  Apply and JVP
+// take the diffusion of n2..c3 in modal form, -A_s K_e U_s with K_e = det J
+// sum_c G_c KS[c] (G = J^{-1} J^{-T}; exact, as the volume rule integrates the
+// stiffness exactly): the forward passes carry gradients for n1, c1, c3 only
+// and the test passes the flux of n1, n2 only.  The VJP keeps the full passes.
+// The point values have an odd stride (6 * 3 + 1) so that threads on
+// consecutive points hit distinct banks.
 template <int K, int EPB, int MODE>
 __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
     using S = TriShape<K>;
     constexpr int NB = S::NB, NQ = S::NQ, NP = S::NP, F = MODE == TRI_APPLY ? 1 : 2;
-    constexpr int N = K + 2, K1 = K + 1;
+    constexpr int N = K + 2, K1 = K + 1, QS = NS * 3 + 1;
+    constexpr bool MODAL = MODE != TRI_VJP;
+    constexpr int NGF = MODAL ? 3 : NS;   // forward slots carrying gradients (species n1, c1, c3 first)
+    constexpr int NGT = MODAL ? 2 : NS;   // species tested against a flux
+    static_assert(EPB * NB * NB <= EPB * F * NQ * QS, "K_e overlays the point values");
     const TriTab& tb = *a.tab;
     __shared__ double sU[EPB][F][NS][NB];
     __shared__ double sG[EPB][GEO];
     __shared__ double sH[EPB][F][2][NS][K1][N];   // v-pass (h, h_v); then the transposed u-pass
-    __shared__ double sQ[EPB][F][NQ][NS][3];      // grad_x, grad_y, value; then the weighted flux
+    __shared__ double sQ[EPB][F][NQ][QS];         // [s * 3 + (grad_x, grad_y, value)]; then the weighted flux
     const long long e0 = (long long)blockIdx.x * EPB;
     const int ne = (int)min((long long)EPB, a.E - e0);
     for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) sG[i / GEO][i % GEO] = a.geo[e0 * GEO + i];
@@ -436,10 +475,11 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
         sU[e][fi][r / NB][r % NB] = (fi ? a.dU : a.U)[e0 * NS * NB + r0];
     }
     __syncthreads();
-    // v-pass: h_p(v_j) = sum_q B_pq(v_j) U_pq, and with B'
+    // v-pass: h_p(v_j) = sum_q B_pq(v_j) U_pq, and with B' where gradients are carried
     for (int i = threadIdx.x; i < ne * F * NS * K1 * N; i += blockDim.x) {
-        const int e = i / (F * NS * K1 * N), fi = (i / (NS * K1 * N)) % F, s = (i / (K1 * N)) % NS;
+        const int e = i / (F * NS * K1 * N), fi = (i / (NS * K1 * N)) % F, sl = (i / (K1 * N)) % NS;
         const int p = (i / N) % K1, j = i % N;
+        const int s = MODAL ? modal_fwd_species(sl) : sl;
         double h = 0.0, hv = 0.0;
 #pragma unroll
         for (int q = 0; q < K1; ++q) {
@@ -447,30 +487,39 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
                 const int m = (p + q) * (p + q + 1) / 2 + q;
                 const double u = sU[e][fi][s][m];
                 h = fma(tb.SB[j][m], u, h);
-                hv = fma(tb.SdB[j][m], u, hv);
+                if (sl < NGF) hv = fma(tb.SdB[j][m], u, hv);
             }
         }
         sH[e][fi][0][s][p][j] = h;
-        sH[e][fi][1][s][p][j] = hv;
+        if (sl < NGF) sH[e][fi][1][s][p][j] = hv;
     }
     __syncthreads();
-    // u-pass: value and (u, v) gradient, then the reference and physical gradient
-    for (int i = threadIdx.x; i < ne * F * NQ * NS; i += blockDim.x) {
-        const int e = i / (F * NQ * NS), fi = (i / (NQ * NS)) % F, q = (i / NS) % NQ, s = i % NS;
+    // u-pass: value and, where carried, the (u, v) gradient, then the reference
+    // and physical gradient (consecutive threads on consecutive points)
+    for (int i = threadIdx.x; i < ne * F * NS * NQ; i += blockDim.x) {
+        const int e = i / (F * NS * NQ), fi = (i / (NS * NQ)) % F, sl = (i / NQ) % NS, q = i % NQ;
+        const int s = MODAL ? modal_fwd_species(sl) : sl;
         const int ii = q % N, j = q / N;
-        double f = 0.0, fu = 0.0, fv = 0.0;
+        double* Q = &sQ[e][fi][q][s * 3];
+        double f = 0.0;
+        if (sl < NGF) {
+            double fu = 0.0, fv = 0.0;
 #pragma unroll
-        for (int p = 0; p < K1; ++p) {
-            const double h = sH[e][fi][0][s][p][j];
-            f = fma(tb.SA[ii][p], h, f);
-            fu = fma(tb.SdA[ii][p], h, fu);
-            fv = fma(tb.SA[ii][p], sH[e][fi][1][s][p][j], fv);
+            for (int p = 0; p < K1; ++p) {
+                const double h = sH[e][fi][0][s][p][j];
+                f = fma(tb.SA[ii][p], h, f);
+                fu = fma(tb.SdA[ii][p], h, fu);
+                fv = fma(tb.SA[ii][p], sH[e][fi][1][s][p][j], fv);
+            }
+            const double r0 = tb.SG[q][0] * fu, r1 = fma(tb.SG[q][1], fu, fv);
+            const double* Ji = sG[e] + 6;
+            Q[0] = Ji[0] * r0 + Ji[2] * r1;
+            Q[1] = Ji[1] * r0 + Ji[3] * r1;
+        } else {
+#pragma unroll
+            for (int p = 0; p < K1; ++p) f = fma(tb.SA[ii][p], sH[e][fi][0][s][p][j], f);
         }
-        const double r0 = tb.SG[q][0] * fu, r1 = fma(tb.SG[q][1], fu, fv);
-        const double* Ji = sG[e] + 6;
-        sQ[e][fi][q][s][0] = Ji[0] * r0 + Ji[2] * r1;
-        sQ[e][fi][q][s][1] = Ji[1] * r0 + Ji[3] * r1;
-        sQ[e][fi][q][s][2] = f;
+        Q[2] = f;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ne * NQ; i += blockDim.x) {
@@ -480,14 +529,15 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
         for (int fi = 0; fi < F; ++fi)
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                u[fi][s] = sQ[e][fi][q][s][2];
-                g[fi][s][0] = sQ[e][fi][q][s][0];
-                g[fi][s][1] = sQ[e][fi][q][s][1];
+                const bool hasg = !MODAL || s == 0 || s == 3 || s == 5;
+                u[fi][s] = sQ[e][fi][q][s * 3 + 2];
+                g[fi][s][0] = hasg ? sQ[e][fi][q][s * 3] : 0.0;
+                g[fi][s][1] = hasg ? sQ[e][fi][q][s * 3 + 1] : 0.0;
             }
         if constexpr (MODE == TRI_APPLY) {
-            volume_point<2, double>(a.c, u[0], g[0], Phi, Sr);
+            volume_point<2, double, true>(a.c, u[0], g[0], Phi, Sr);
         } else if constexpr (MODE == TRI_JVP) {
-            volume_point_lin<2, double>(a.c, u[0], g[0], u[F - 1], g[F - 1], false, Phi, Sr);
+            volume_point_lin<2, double, true>(a.c, u[0], g[0], u[F - 1], g[F - 1], false, Phi, Sr);
         } else {
             // cotangents of S and Phi at the point: det w_q mu and det w_q grad mu,
             // mu = M^{-1} lambda = lambda / det (with CDG2_MINV); back through the
@@ -509,28 +559,50 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
         const double wq = tb.VW[q];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            const double p0 = Ji[0] * Phi[s][0] + Ji[1] * Phi[s][1];
-            const double p1 = Ji[2] * Phi[s][0] + Ji[3] * Phi[s][1];
-            sQ[e][F - 1][q][s][0] = wq * fma(tb.SG[q][0], p0, tb.SG[q][1] * p1);
-            sQ[e][F - 1][q][s][1] = wq * p1;
-            sQ[e][F - 1][q][s][2] = wq * Sr[s];
+            double* Q = &sQ[e][F - 1][q][s * 3];
+            if (s < NGT) {
+                const double p0 = Ji[0] * Phi[s][0] + Ji[1] * Phi[s][1];
+                const double p1 = Ji[2] * Phi[s][0] + Ji[3] * Phi[s][1];
+                Q[0] = wq * fma(tb.SG[q][0], p0, tb.SG[q][1] * p1);
+                Q[1] = wq * p1;
+            }
+            Q[2] = wq * Sr[s];
         }
     }
     __syncthreads();
     // transposed u-pass: X_p(v_j) = sum_i A_p S + A'_p P_u; X^v_p(v_j) = sum_i A_p P_v
+    // (species without a flux: A_p S only)
     for (int i = threadIdx.x; i < ne * NS * K1 * N; i += blockDim.x) {
         const int e = i / (NS * K1 * N), s = (i / (K1 * N)) % NS, p = (i / N) % K1, j = i % N;
         double x0 = 0.0, xv = 0.0;
+        if (s < NGT) {
 #pragma unroll
-        for (int ii = 0; ii < N; ++ii) {
-            const double* P = sQ[e][F - 1][ii + N * j][s];
-            x0 = fma(tb.SA[ii][p], P[2], fma(tb.SdA[ii][p], P[0], x0));
-            xv = fma(tb.SA[ii][p], P[1], xv);
+            for (int ii = 0; ii < N; ++ii) {
+                const double* P = &sQ[e][F - 1][ii + N * j][s * 3];
+                x0 = fma(tb.SA[ii][p], P[2], fma(tb.SdA[ii][p], P[0], x0));
+                xv = fma(tb.SA[ii][p], P[1], xv);
+            }
+            sH[e][0][1][s][p][j] = xv;
+        } else {
+#pragma unroll
+            for (int ii = 0; ii < N; ++ii) x0 = fma(tb.SA[ii][p], sQ[e][F - 1][ii + N * j][s * 3 + 2], x0);
         }
         sH[e][0][0][s][p][j] = x0;
-        sH[e][0][1][s][p][j] = xv;
     }
     __syncthreads();
+    // K_e / det J = sum_c G_c KS[c], G_ab = sum_c (J^{-1})_ac (J^{-1})_bc for ab = 00, 11, 01, over the
+    // point values (read by the transposed u-pass only)
+    double (*sKe)[NB][NB] = reinterpret_cast<double (*)[NB][NB]>(&sQ[0][0][0][0]);
+    if constexpr (MODAL) {
+        for (int i = threadIdx.x; i < ne * NB * NB; i += blockDim.x) {
+            const int e = i / (NB * NB), r = (i / NB) % NB, cc = i % NB;
+            const double* Ji = sG[e] + 6;
+            const double G0 = fma(Ji[0], Ji[0], Ji[1] * Ji[1]), G1 = fma(Ji[2], Ji[2], Ji[3] * Ji[3]);
+            const double G2 = fma(Ji[0], Ji[2], Ji[1] * Ji[3]);
+            sKe[e][r][cc] = fma(G0, tb.KS[0][r][cc], fma(G1, tb.KS[1][r][cc], G2 * tb.KS[2][r][cc]));
+        }
+        __syncthreads();
+    }
     for (int i = threadIdx.x; i < ne * NS * NB; i += blockDim.x) {
         const int e = i / (NS * NB), s = (i / NB) % NS, m = i % NB;
         const double* G = sG[e];
@@ -539,8 +611,22 @@ __global__ void __launch_bounds__(128) tri_elem_kernel(const TriArgs a) {
         while ((d + 1) * (d + 2) / 2 <= m) ++d;
         const int p = d - (m - d * (d + 1) / 2);
         double acc = 0.0;
+        if (s < NGT) {
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc = fma(tb.SB[j][m], sH[e][0][0][s][p][j], fma(tb.SdB[j][m], sH[e][0][1][s][p][j], acc));
+            for (int j = 0; j < N; ++j)
+                acc = fma(tb.SB[j][m], sH[e][0][0][s][p][j], fma(tb.SdB[j][m], sH[e][0][1][s][p][j], acc));
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc = fma(tb.SB[j][m], sH[e][0][0][s][p][j], acc);
+        }
+        if constexpr (MODAL) {
+            if (s > 0) {   // the diffusion of n2..c3 (of the tangent in the JVP): -A_s (K_e U_s)_m / det J
+                double kd = 0.0;
+#pragma unroll
+                for (int jj = 0; jj < NB; ++jj) kd = fma(sKe[e][m][jj], sU[e][F - 1][s][jj], kd);
+                acc = fma(-a.c.A[s], kd, acc);
+            }
+        }
         // forward: R = det sum_q w_q (Phi . grad phi + S phi); VJP: the cotangents carry det
         double R = MODE == TRI_VJP ? acc : det * acc;
         const long long ge = e0 + e;

@@ -383,8 +383,9 @@ def measure_gradient(G, torch, cfg: int, steps: int | None, mixed: bool, precond
             "dJ_dU0_norm": float(U.grad.norm())}
 
 
-def cpu_oracle_baseline(w, seconds: float = 12.0):
-    """The oracle (plain FP64 PyTorch CPU) timed on this host on the same workload."""
+def cpu_oracle_baseline(w, seconds: float = 12.0, seconds_1_thread: float = 6.0):
+    """The oracle (plain FP64 PyTorch CPU) timed on this host on the same workload,
+    on all the threads torch uses and then on one thread."""
     import torch
 
     import cdg2_inputs as I
@@ -392,14 +393,26 @@ def cpu_oracle_baseline(w, seconds: float = 12.0):
     om = O.Mesh(w.dim, w.cells, w.extent, w.periodic, w.k)
     p = I.default_params()
     U = torch.from_numpy(I.random_coefficients(om.E, om.nb, w.seed))
-    O.apply(om, U, p)
-    reps, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
+
+    def timed(limit):
         O.apply(om, U, p)
-        reps += 1
-    dt = time.perf_counter() - t0
-    return {"value": w.n_dof * reps / dt / 1e9, "unit": "GDOF/s", "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"{reps} full-mesh applies of {w.name} ({w.n_dof} DOF) in {dt:.1f} s"}
+        reps, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < limit:
+            O.apply(om, U, p)
+            reps += 1
+        return reps, time.perf_counter() - t0
+
+    cores = torch.get_num_threads()
+    reps, dt = timed(seconds)
+    torch.set_num_threads(1)
+    try:
+        reps1, dt1 = timed(seconds_1_thread)
+    finally:
+        torch.set_num_threads(cores)
+    return {"value": w.n_dof * reps / dt / 1e9, "unit": "GDOF/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} full-mesh applies of {w.name} ({w.n_dof} DOF) in {dt:.1f} s",
+            "value_1_thread": w.n_dof * reps1 / dt1 / 1e9,
+            "sample_1_thread": f"{reps1} full-mesh applies on one thread in {dt1:.1f} s"}
 
 
 def run_reference(args):

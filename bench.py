@@ -4,10 +4,15 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference] [--c
 
 A step is one application of f(U) = M^{-1} L_h(U) (volume terms, face fluxes
 with the CDG2 lifting, boundary influxes, inverse mass matrix) over the whole
-mesh, in FP64, through the C ABI.  The default workload is the 2D 256x64 DG
-Q3 manufactured-solution mesh (1,572,864 DOF).  Its state (12.6 MB) fits in
-L2, so L2 is flushed (a 512 MB write) before every timed step, outside the
-step's CUDA events.  Prints one JSON line on rank 0.
+mesh, in FP64, through the C ABI.  The default workload is the largest one
+that the paper's 3D test suggests and one GPU holds: 3D 128x32x32 DG Q2
+(21,233,664 DOF, 170 MB of state).  L2 is flushed (a 512 MB write) before
+every timed step, outside the step's CUDA events.  The line also carries the
+FP32 apply with its error against FP64, the JVP and VJP, the same figures on
+3D 64x16x16 Q3 and 2D 256x64 Q3, the implicit solve (FP64 vs mixed), the
+gradient through the implicit steps, the simplicial meshes, the end-to-end
+rate through the API with host buffers, and the oracle timed on the host.
+Prints one JSON line on rank 0.
 """
 from __future__ import annotations
 
@@ -188,18 +193,22 @@ def make_inputs(G, w, I, mesh, dtype_flag=0):
 
 
 def time_applies(G, torch, mesh, p, U, out, flags, steps, warmup, flush):
+    """CUDA-event times (ms) of `steps` applies, L2 flushed before each.  The
+    applies are queued with CDG2_ASYNC (no host wait for the domain check) and
+    the domain status is read once afterwards."""
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         flush.fill_(1)
-        G.cdg2_apply(mesh, p, U, out, flags)
+        G.cdg2_apply(mesh, p, U, out, flags | G.CDG2_ASYNC)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for a, b in ev:
         flush.fill_(1)
         a.record(stream)
-        G.cdg2_apply(mesh, p, U, out, flags)
+        G.cdg2_apply(mesh, p, U, out, flags | G.CDG2_ASYNC)
         b.record(stream)
     torch.cuda.synchronize()
+    G.cdg2_mesh_status(mesh)
     return [a.elapsed_time(b) for a, b in ev]
 
 
@@ -220,23 +229,110 @@ def time_op(G, torch, fn, steps, warmup, flush):
     return statistics.mean(a.elapsed_time(b) for a, b in ev)
 
 
-def measure_derivatives(G, torch, w, mesh, p, U, flush, steps):
-    """JVP and VJP throughput (GDOF/s) in FP64 and FP32 on the bench workload."""
-    out = {}
+# Algorithmic HBM bytes per DOF of one launch sequence: read the inputs and
+# write the result once (neighbour traces re-read from L2 are not counted).
+BYTES_PER_DOF = {("apply", "f64"): 16, ("apply", "f32"): 8, ("jvp", "f64"): 24, ("jvp", "f32"): 12,
+                 ("vjp", "f64"): 24, ("vjp", "f32"): 12}
+
+# Floating-point operations per element of one launch sequence (face kernels +
+# element kernel), measured: 2 x FMA + ADD + MUL instructions executed
+# (smsp__sass_thread_inst_executed_op_{d,f}{fma,add,mul}_pred_on.sum, ncu, one
+# launch of each kernel on a small mesh of the same dimension and degree,
+# divided by its elements), keyed by (dim, k, op, dtype) and valid only for the
+# kernel sources the counters were taken with (first 16 hex of their sha256).
+FLOPS_PER_ELEMENT = {
+    (3, 2, 'apply', 'f64'): (49387, '4183afe65d9b56bb'),
+    (3, 2, 'apply', 'f32'): (76207, '4183afe65d9b56bb'),
+    (3, 2, 'jvp', 'f64'): (74197, '4183afe65d9b56bb'),
+    (3, 2, 'jvp', 'f32'): (122393, '4183afe65d9b56bb'),
+    (3, 2, 'vjp', 'f64'): (126836, '4183afe65d9b56bb'),
+    (3, 2, 'vjp', 'f32'): (122345, '4183afe65d9b56bb'),
+    (3, 3, 'apply', 'f64'): (105688, '4183afe65d9b56bb'),
+    (3, 3, 'apply', 'f32'): (160596, '4183afe65d9b56bb'),
+    (3, 3, 'jvp', 'f64'): (158746, '4183afe65d9b56bb'),
+    (3, 3, 'jvp', 'f32'): (257828, '4183afe65d9b56bb'),
+    (3, 3, 'vjp', 'f64'): (266801, '4183afe65d9b56bb'),
+    (3, 3, 'vjp', 'f32'): (259292, '4183afe65d9b56bb'),
+    (2, 3, 'apply', 'f64'): (13700, '4183afe65d9b56bb'),
+    (2, 3, 'apply', 'f32'): (14605, '4183afe65d9b56bb'),
+    (2, 3, 'jvp', 'f64'): (20346, '4183afe65d9b56bb'),
+    (2, 3, 'jvp', 'f32'): (22794, '4183afe65d9b56bb'),
+    (2, 3, 'vjp', 'f64'): (32662, '4183afe65d9b56bb'),
+    (2, 3, 'vjp', 'f32'): (31423, '4183afe65d9b56bb'),
+}
+
+
+def flops_per_element(dim, k, op, dtype):
+    """(flops per element, source) for the ALU roofline: the ncu count when it
+    matches the current kernel sources, else the loop model for the FP64 apply,
+    else None."""
+    entry = FLOPS_PER_ELEMENT.get((dim, k, op, dtype))
+    if entry is not None and entry[1] == kernel_source_hash():
+        return entry[0], "ncu instruction count"
+    if op == "apply" and dtype == "f64":
+        return apply_flops_per_element(dim, k), "loop model"
+    return None, None
+
+
+def leg(w, ms, op, dtype, peaks):
+    """One timed launch sequence: GDOF/s, HBM fraction, ALU fraction (of the measured FMA peak)."""
+    n = w.n_dof
+    gb_s = BYTES_PER_DOF[(op, dtype)] * n / (ms * 1e-3) / 1e9
+    out = {"ms": ms, "value": n / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "hbm_frac": gb_s / peaks["hbm_gbs"]}
+    fl, src = flops_per_element(w.dim, w.k, op, dtype)
+    if fl is not None:
+        tf = fl * w.n_elem / (ms * 1e-3) / 1e12
+        out.update({"tflops": tf, "alu_frac": tf / peaks["fp64_tflops" if dtype == "f64" else "fp32_tflops"],
+                    "flops_source": src})
+    return out
+
+
+def rel_err_per_species(torch, got, ref, w):
+    e = got.double().view(w.n_elem, 6, -1) - ref.double().view(w.n_elem, 6, -1)
+    r = ref.double().view(w.n_elem, 6, -1)
+    return float((e.pow(2).sum(dim=(0, 2)).sqrt() / r.pow(2).sum(dim=(0, 2)).sqrt()).max())
+
+
+def measure_operator(G, torch, w, mesh, p, U, flush, steps, peaks, with_fp64_apply=True):
+    """FP64 and FP32 apply, JVP and VJP of one workload (L2 flushed before every
+    launch sequence), each with its HBM and ALU fractions, and the FP32 apply's
+    error against FP64 on the same (rounded) input."""
+    A = G.CDG2_ASYNC
     lam = torch.sin(torch.arange(U.numel(), device="cuda", dtype=torch.float64) * 0.37)
     res = torch.empty_like(U)
     gth = torch.zeros(8, dtype=torch.float64, device="cuda")
     U32, lam32, res32 = U.float(), lam.float(), torch.empty_like(U, dtype=torch.float32)
     cases = {
-        "jvp_fp64": lambda: G.cdg2_jvp(mesh, p, U, lam, res, G.CDG2_MINV),
-        "jvp_fp32": lambda: G.cdg2_jvp(mesh, p, U32, lam32, res32, G.CDG2_MINV | G.CDG2_FP32),
-        "vjp_fp64": lambda: G.cdg2_vjp(mesh, p, U, lam, res, gth, G.CDG2_MINV),
-        "vjp_fp32": lambda: G.cdg2_vjp(mesh, p, U32, lam32, res32, gth, G.CDG2_MINV | G.CDG2_FP32),
+        ("apply", "f32"): lambda: G.cdg2_apply(mesh, p, U32, res32, G.CDG2_MINV | G.CDG2_FP32 | A),
+        ("jvp", "f64"): lambda: G.cdg2_jvp(mesh, p, U, lam, res, G.CDG2_MINV | A),
+        ("jvp", "f32"): lambda: G.cdg2_jvp(mesh, p, U32, lam32, res32, G.CDG2_MINV | G.CDG2_FP32 | A),
+        ("vjp", "f64"): lambda: G.cdg2_vjp(mesh, p, U, lam, res, gth, G.CDG2_MINV | A),
+        ("vjp", "f32"): lambda: G.cdg2_vjp(mesh, p, U32, lam32, res32, gth, G.CDG2_MINV | G.CDG2_FP32 | A),
     }
-    for name, fn in cases.items():
+    if with_fp64_apply:
+        cases[("apply", "f64")] = lambda: G.cdg2_apply(mesh, p, U, res, G.CDG2_MINV | A)
+    out = {}
+    for (op, dt), fn in cases.items():
         ms = time_op(G, torch, fn, steps, 3, flush)
-        out[name] = {"value": w.n_dof / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "ms": ms}
+        out[f"{op}_{dt}"] = leg(w, ms, op, dt, peaks)
+    G.cdg2_mesh_status(mesh)
+    out32 = torch.empty_like(U32)
+    G.cdg2_apply(mesh, p, U32, out32, G.CDG2_MINV | G.CDG2_FP32)
+    ref64 = torch.empty_like(U)
+    G.cdg2_apply(mesh, p, U32.double(), ref64, G.CDG2_MINV)
+    out["apply_f32"]["rel_l2_err_vs_fp64_max_species"] = rel_err_per_species(torch, out32, ref64, w)
     return out
+
+
+def measure_workload(G, torch, I, cfg, flush, steps, peaks):
+    """measure_operator on workload cfg, with its name and sizes."""
+    w = I.workload(cfg)
+    mesh = G.cdg2_mesh_create(w.dim, w.cells, w.extent, w.periodic, w.k)
+    U, p = make_inputs(G, w, I, mesh)
+    r = measure_operator(G, torch, w, mesh, p, U, flush, steps, peaks)
+    r.update({"workload": w.name, "n_dof": w.n_dof, "n_elem": w.n_elem})
+    del mesh
+    return r
 
 
 def smooth_simplex_state(torch, mesh, centroids, psi0):
@@ -255,9 +351,11 @@ def measure_simplex(G, torch, flush, steps, mesh, p, U, apply, jvp, vjp, step, U
     element-block Jacobi, Newton relative residual 1e-10) from the smooth state Us."""
     out = torch.empty_like(U)
     dU = torch.ones_like(U)
-    ms = time_op(G, torch, lambda: apply(mesh, p, U, out, G.CDG2_MINV), steps, 3, flush)
-    ms_j = time_op(G, torch, lambda: jvp(mesh, p, U, dU, out, G.CDG2_MINV), steps, 3, flush)
-    ms_v = time_op(G, torch, lambda: vjp(mesh, p, U, dU, out, G.CDG2_MINV), steps, 3, flush)
+    f = G.CDG2_MINV | G.CDG2_ASYNC
+    ms = time_op(G, torch, lambda: apply(mesh, p, U, out, f), steps, 3, flush)
+    ms_j = time_op(G, torch, lambda: jvp(mesh, p, U, dU, out, f), steps, 3, flush)
+    ms_v = time_op(G, torch, lambda: vjp(mesh, p, U, dU, out, f), steps, 3, flush)
+    apply(mesh, p, U, out, G.CDG2_MINV)      # waits, and reports a domain error of the timed calls
     opts = G.make_opts(scheme=G.CDG2_SDIRK3, newton_rtol=1e-10, gmres_rtol=1e-3, precond=2)
     step(mesh, p, Us.clone(), dt, opts, raise_on_error=False)      # allocates the workspace, probes the blocks
     torch.cuda.synchronize()
@@ -383,16 +481,30 @@ def measure_gradient(G, torch, cfg: int, steps: int | None, mixed: bool, precond
             "dJ_dU0_norm": float(U.grad.norm())}
 
 
+def oracle_sample(w):
+    """A bounded sample of workload w for the oracle: the full mesh when its
+    apply is small, else a slab of the full cross-section (the first axis and
+    y in full, the last axis cut to 2 cells, still periodic) with the same
+    element size and state recipe."""
+    cells = list(w.cells[: w.dim])
+    if w.n_dof > 2_000_000:
+        cells[-1] = 2
+    ext = [w.extent[a] * cells[a] / w.cells[a] for a in range(w.dim)]
+    return cells, ext
+
+
 def cpu_oracle_baseline(w, seconds: float = 12.0, seconds_1_thread: float = 6.0):
-    """The oracle (plain FP64 PyTorch CPU) timed on this host on the same workload,
-    on all the threads torch uses and then on one thread."""
+    """The oracle (plain FP64 PyTorch CPU) timed on this host on a bounded
+    sample of the same workload, on all the threads torch uses and then on one thread."""
     import torch
 
     import cdg2_inputs as I
     from oracle import cdg2_oracle as O
-    om = O.Mesh(w.dim, w.cells, w.extent, w.periodic, w.k)
+    cells, ext = oracle_sample(w)
+    om = O.Mesh(w.dim, cells, ext, w.periodic, w.k)
     p = I.default_params()
     U = torch.from_numpy(I.random_coefficients(om.E, om.nb, w.seed))
+    ndof = 6 * om.E * om.nb
 
     def timed(limit):
         O.apply(om, U, p)
@@ -409,14 +521,15 @@ def cpu_oracle_baseline(w, seconds: float = 12.0, seconds_1_thread: float = 6.0)
         reps1, dt1 = timed(seconds_1_thread)
     finally:
         torch.set_num_threads(cores)
-    return {"value": w.n_dof * reps / dt / 1e9, "unit": "GDOF/s", "cores": cores, "kind": "oracle",
-            "sample": f"{reps} full-mesh applies of {w.name} ({w.n_dof} DOF) in {dt:.1f} s",
-            "value_1_thread": w.n_dof * reps1 / dt1 / 1e9,
-            "sample_1_thread": f"{reps1} full-mesh applies on one thread in {dt1:.1f} s"}
+    return {"value": ndof * reps / dt / 1e9, "unit": "GDOF/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} oracle applies on {cells} cells ({ndof} DOF each) of {w.name} in {dt:.1f} s",
+            "value_1_thread": ndof * reps1 / dt1 / 1e9,
+            "sample_1_thread": f"{reps1} applies on one thread in {dt1:.1f} s"}
 
 
 def run_reference(args):
-    """--impl reference: the oracle on the host cores, K timed steps (rank 0 only)."""
+    """--impl reference: the oracle on the host cores, K timed steps (rank 0 only),
+    each step one oracle apply on a bounded sample of the workload."""
     import torch
 
     import cdg2_inputs as I
@@ -425,19 +538,23 @@ def run_reference(args):
     if rank != 0:
         return
     w = I.workload(args.config, args.k)
-    om = O.Mesh(w.dim, w.cells, w.extent, w.periodic, w.k)
+    cells, ext = oracle_sample(w)
     p = I.default_params()
-    U = torch.from_numpy(I.random_coefficients(om.E, om.nb, w.seed))
+
+    def sample(cells, ext):
+        om = O.Mesh(w.dim, cells, ext, w.periodic, w.k)
+        return om, torch.from_numpy(I.random_coefficients(om.E, om.nb, w.seed))
+
+    om, U = sample(cells, ext)
     t0 = time.perf_counter()
     O.apply(om, U, p)
     t_one = time.perf_counter() - t0
-    # bound the whole run to about two minutes: shrink the sample mesh along y if needed
+    # bound the whole run to about two minutes: shrink the sample along y if needed
     budget = 120.0 / max(1, args.steps + args.warmup)
-    cells = list(w.cells)
     if t_one > budget:
         cells[1] = max(2, int(cells[1] * budget / t_one))
-        om = O.Mesh(w.dim, cells, w.extent, w.periodic, w.k)
-        U = torch.from_numpy(I.random_coefficients(om.E, om.nb, w.seed))
+        ext[1] = w.extent[1] * cells[1] / w.cells[1]
+        om, U = sample(cells, ext)
     ndof = 6 * om.E * om.nb
     for _ in range(args.warmup):
         O.apply(om, U, p)
@@ -448,16 +565,27 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = ndof * args.steps / total / 1e9
-    sample = f"{args.steps} oracle applies on {cells[:w.dim]} cells of {w.name} ({ndof} DOF each)"
+    sample_txt = f"{args.steps} oracle applies on {cells} cells of {w.name} ({ndof} DOF each)"
     line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": w.name, "n_dof": ndof, "sample_cells": cells[:w.dim]},
+            "config": {"workload": w.name, "n_dof": w.n_dof, "sample_cells": cells, "sample_dof": ndof},
             "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": torch.get_num_threads(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample_txt},
             "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def measured_peaks(G, torch):
+    """HBM and bf16 from MEASURED_PEAKS.json; the FP64 and FP32 FMA rates measured
+    here with the library's FMA-loop probe (best of 3)."""
+    peaks, kind = load_peaks()
+    peaks = dict(peaks)
+    peaks["fp64_tflops"] = max(G.cdg2_probe_peak(0, 1 << 15) for _ in range(3))
+    peaks["fp32_tflops"] = max(G.cdg2_probe_peak(1, 1 << 19) for _ in range(3))
+    torch.cuda.synchronize()
+    return peaks, kind
 
 
 def main():
@@ -466,8 +594,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
-    ap.add_argument("--config", type=int, default=1)
-    ap.add_argument("--k", type=int, default=3)
+    ap.add_argument("--config", type=int, default=4)
+    ap.add_argument("--k", type=int, default=None)
+    ap.add_argument("--extra-configs", default="3,1", help="workloads timed beside the headline (comma list; '' none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tri", action="store_true", help="skip the triangle- and tetrahedral-mesh timings")
     ap.add_argument("--solve-config", type=int, default=3, help="workload of the implicit-solve comparison")
@@ -475,6 +604,10 @@ def main():
     ap.add_argument("--grad-config", type=int, default=2, help="workload of the gradient-through-steps timing")
     ap.add_argument("--profile-solve", choices=["mixed", "fp64"], default=None,
                     help="run one implicit step of the solve workload and exit (for ncu launch lists)")
+    ap.add_argument("--profile-op", default=None,
+                    help="cfg:op:dtype[:reps[:cells]] (several separated by ';'), e.g. 3:jvp:f32:1:16x8x8: only "
+                         "those launch sequences, reps times each, on the workload's mesh or a smaller one with "
+                         "the given cells, then exit (for ncu captures)")
     ap.add_argument("--precond", type=int, default=2, choices=[0, 1, 2],
                     help="GMRES preconditioner of the solve timing (1: modal diagonal, 2: element blocks)")
     ap.add_argument("--grad-precond", type=int, default=1, choices=[0, 1, 2],
@@ -503,6 +636,38 @@ def main():
         print(json.dumps({"profile_solve": args.profile_solve, "precond": args.precond, "workload": w.name,
                           "stats": st}))
         return
+    if args.profile_op:
+        import torch
+
+        import cdg2_inputs as I
+        import paper_1403_1157_gb300 as G
+        done = []
+        for spec in args.profile_op.split(";"):
+            parts = spec.split(":")
+            cfg, op, dt = int(parts[0]), parts[1], parts[2]
+            reps = int(parts[3]) if len(parts) > 3 else 3
+            w = I.workload(cfg)
+            cells = tuple(int(c) for c in parts[4].split("x")) if len(parts) > 4 else w.cells[: w.dim]
+            ext = tuple(w.extent[a] * cells[a] / w.cells[a] for a in range(w.dim))
+            mesh = G.cdg2_mesh_create(w.dim, cells, ext, w.periodic, w.k)
+            U, p = make_inputs(G, w, I, mesh)
+            fl = G.CDG2_MINV | (G.CDG2_FP32 if dt == "f32" else 0)
+            if dt == "f32":
+                U = U.float()
+            lam = torch.sin(torch.arange(U.numel(), device="cuda", dtype=U.dtype) * 0.37)
+            out = torch.empty_like(U)
+            gth = torch.zeros(8, dtype=torch.float64, device="cuda")
+            for _ in range(reps):
+                if op == "apply":
+                    G.cdg2_apply(mesh, p, U, out, fl)
+                elif op == "jvp":
+                    G.cdg2_jvp(mesh, p, U, lam, out, fl)
+                else:
+                    G.cdg2_vjp(mesh, p, U, lam, out, gth, fl)
+            torch.cuda.synchronize()
+            done.append({"spec": spec, "workload": w.name, "cells": list(cells), "n_elem": mesh.n_elem})
+        print(json.dumps({"profile_op": done}))
+        return
 
     import torch
     import torch.distributed as dist
@@ -520,6 +685,7 @@ def main():
     U, p = make_inputs(G, w, I, mesh)
     out = torch.empty_like(U)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    peaks, kind = measured_peaks(G, torch)
     torch.cuda.synchronize()
 
     # ---- timed region: K FP64 applies, L2 flushed before each ----
@@ -544,54 +710,52 @@ def main():
     ms_step = total_ms / args.steps
     value = job_throughput(world, w.n_dof, args.steps, total_ms)
 
-    # ---- roofline of the dominant kernel (the fused FP64 apply kernel) ----
-    fl = apply_flops_per_element(w.dim, w.k) * w.n_elem
+    # ---- roofline of the timed launch sequence (the face kernels + the element kernel) ----
+    head = leg(w, ms_step, "apply", "f64", peaks)
+    fl_el, fl_src = flops_per_element(w.dim, w.k, "apply", "f64")
+    fl = fl_el * w.n_elem
     achieved_tf = fl / (ms_step * 1e-3) / 1e12
-    fp64_peak = 1.25
-    peaks, kind = load_peaks()
-    hbm_bytes = 16 * w.n_dof
-    hbm_frac = hbm_bytes / (ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"]
 
-    # ---- FP32 apply (the inner-solve operator) and its raw error vs FP64 ----
-    U32 = U.float()
-    out32 = torch.empty_like(U32)
-    ms32 = time_applies(G, torch, mesh, p, U32, out32, G.CDG2_MINV | G.CDG2_FP32, max(20, args.steps // 4), 3, flush)
-    ref64 = torch.empty_like(U)
-    G.cdg2_apply(mesh, p, U32.double(), ref64, G.CDG2_MINV)
-    torch.cuda.synchronize()
-    e = out32.double().view(w.n_elem, 6, -1) - ref64.view(w.n_elem, 6, -1)
-    rel32 = float((e.pow(2).sum(dim=(0, 2)).sqrt() / ref64.view(w.n_elem, 6, -1).pow(2).sum(dim=(0, 2)).sqrt()).max())
-    fp32 = {"value": w.n_dof / (statistics.mean(ms32) * 1e-3) / 1e9, "unit": "GDOF/s",
-            "rel_l2_err_vs_fp64_max_species": rel32,
-            "hbm_frac": 8 * w.n_dof / (statistics.mean(ms32) * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    # ---- FP32 apply, JVP and VJP on the headline workload, then the extra workloads ----
+    nsub = max(10, args.steps // 8)
+    ops = measure_operator(G, torch, w, mesh, p, U, flush, nsub, peaks, with_fp64_apply=False)
+    extras = {}
+    for c in [int(x) for x in args.extra_configs.split(",") if x.strip()]:
+        if c != args.config:
+            r = measure_workload(G, torch, I, c, flush, nsub, peaks)
+            extras[r["workload"]] = r
 
-    # ---- end to end through the API: pinned host U -> device, apply, result -> pinned host ----
+    # ---- end to end through the API: pinned host U -> device, apply, result -> pinned host,
+    # then the domain status (the call a user makes to know the result is valid) ----
     hU = U.cpu().pin_memory()
     hout = torch.empty_like(hU).pin_memory()
     dU = torch.empty_like(U)
     stream = torch.cuda.current_stream()
     n_e2e = max(10, args.steps // 4)
-    for _ in range(3):
+
+    def e2e_step():
         dU.copy_(hU, non_blocking=True)
-        G.cdg2_apply(mesh, p, dU, out, G.CDG2_MINV)
+        G.cdg2_apply(mesh, p, dU, out, G.CDG2_MINV | G.CDG2_ASYNC)
         hout.copy_(out, non_blocking=True)
+        G.cdg2_mesh_status(mesh)
+
+    for _ in range(3):
+        e2e_step()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for _ in range(n_e2e):
-        dU.copy_(hU, non_blocking=True)
-        G.cdg2_apply(mesh, p, dU, out, G.CDG2_MINV)
-        hout.copy_(out, non_blocking=True)
+        e2e_step()
     b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = a.elapsed_time(b) / n_e2e
     nbytes = U.numel() * U.element_size()
     e2e = {"value": world * w.n_dof / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
+    del dU, hU, hout
 
-    derivs = measure_derivatives(G, torch, w, mesh, p, U, flush, max(10, args.steps // 8))
-    tri = measure_tri(G, torch, flush, max(10, args.steps // 8)) if not args.no_tri else None
-    tet = measure_tet(G, torch, flush, max(10, args.steps // 8)) if not args.no_tri else None
+    tri = measure_tri(G, torch, flush, nsub) if not args.no_tri else None
+    tet = measure_tet(G, torch, flush, nsub) if not args.no_tri else None
     solve = measure_solve(G, torch, args.solve_config, args.solve_steps, args.precond) if args.solve_steps > 0 else None
     grad = None
     if args.grad_steps != 0:
@@ -609,16 +773,21 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "n_dof": w.n_dof, "n_elem": w.n_elem, "degree": w.k,
-                   "l2": "flushed before every timed step (512 MB write outside the step events)",
+                   "l2": "flushed before every timed step (512 MB write outside the step events); "
+                         "the state (FP64, in and out) is also larger than L2",
                    "step": "one cdg2_apply (M^-1 L_h, FP64) over the whole mesh"},
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tf / fp64_peak, "traffic": ncu_traffic(w.name, "double"),
-                     "peak_note": "nominal FP64 FMA rate of GB300 (2 DFMA/clk/SM x 152 SMs); an FMA-loop probe measured 1.253; achieved = counted flops of one apply / its event time (all its launches)",
-                     "flops_per_apply": fl,
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved_tf / peaks["fp64_tflops"], "traffic": ncu_traffic(w.name, "double"),
+                     "peak_note": "FP64 FMA rate measured in this run by cdg2_probe_peak (FMA loop, 8 chains per "
+                                  "thread, 8 x SMs blocks of 256 threads); achieved = flops of one apply / its "
+                                  "event time (all its launches)",
+                     "flops_per_apply": fl, "flops_source": fl_src,
                      "kernels": f"{w.dim} x face_kernel<{w.dim},{w.k},0,A,double> + op_kernel<{w.dim},{w.k},0,double> (one apply)",
-                     "hbm_frac": hbm_frac, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_kind": kind},
-        "fp32": fp32,
-        "derivatives": derivs,
+                     "hbm_frac": head["hbm_frac"], "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_kind": kind,
+                     "fp32_peak_tflops": peaks["fp32_tflops"]},
+        "fp32": ops.pop("apply_f32"),
+        "derivatives": ops,
+        "workloads": extras,
         "triangles": tri,
         "tetrahedra": tet,
         "solve": solve,

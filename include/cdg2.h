@@ -28,6 +28,22 @@
  *   Calls are asynchronous with respect to the host unless stated.
  * Errors: every int-returning call returns CDG2_OK (0) or a negative code;
  *   cdg2_last_error() then describes it.  No call aborts or throws.
+ * Domain: the tactic sensitivities chi0 x / (y + chith) of Sec. 2 have a pole
+ *   at y = -chith.  Every kernel that evaluates them records, in a status
+ *   word of the mesh, whether some quadrature point had y + chith <= 0 (a
+ *   test on the sign bits; no trap, no abort).  The operator entry points
+ *   (cdg2_apply, cdg2_jvp, cdg2_vjp and their triangle / tetrahedral
+ *   counterparts) then wait for their kernels and return CDG2_ERR_DOMAIN if
+ *   the word is set (out is then undefined), clearing it.  With CDG2_ASYNC
+ *   in flags they return as soon as the work is queued and leave the word
+ *   set; the next call without CDG2_ASYNC on the mesh, or
+ *   cdg2_mesh_status(), reports it.  The steps judge the converged stage
+ *   values: a stage value with y + chith <= 0 at a quadrature point returns
+ *   CDG2_ERR_DOMAIN (U unchanged), while Newton may pass through iterates
+ *   outside the domain on the way; the adjoint step reports stage values
+ *   outside it.  The steps leave the word clear.  The status
+ *   word (one int of device memory) is allocated by the first call on the
+ *   mesh that launches a kernel.
  */
 #ifndef CDG2_H
 #define CDG2_H
@@ -41,11 +57,14 @@ extern "C" {
 #define CDG2_ERR_CUDA (-2)          /* a CUDA runtime call or kernel launch failed */
 #define CDG2_ERR_NOT_CONVERGED (-3) /* Newton or GMRES hit its iteration cap */
 #define CDG2_ERR_NONFINITE (-4)     /* a NaN or Inf appeared in a solver residual */
+#define CDG2_ERR_DOMAIN (-5)        /* c + chi^th <= 0 at a quadrature point: the pole of
+                                       chi(x, y, a, b) = a x / (y + b) (Sec. 2) */
 
 /* flags of cdg2_apply / cdg2_jvp / cdg2_vjp */
 #define CDG2_MINV 1      /* return M^{-1} L_h (else the residual <phi, L_h>) */
 #define CDG2_FORCING 2   /* add the manufactured-solution forcing at time t */
 #define CDG2_FP32 4      /* arrays are float32 and the kernel computes in FP32 */
+#define CDG2_ASYNC 8     /* do not wait for the domain check (see "Domain" below) */
 
 /* diffusion fluxes of cdg2_mesh_desc.flux */
 #define CDG2_FLUX_CDG2 0
@@ -125,8 +144,13 @@ typedef struct cdg2_params {
  * Newton stops when ||G||_2 <= max(newton_rtol ||G(Y^0)||_2, newton_atol),
  *   G(Y) = Y - dt a_ii f(Y) - rhs_i, Y^0 the previous stage value (U_n first);
  *   at most max_newton corrections per stage.
- * GMRES(gmres_restart) (Arnoldi by classical Gram-Schmidt, a second pass
- *   when the DGKS criterion |w'| < |w|/sqrt(2) flags cancellation) stops at
+ * GMRES(gmres_restart) (Arnoldi by classical Gram-Schmidt applied twice,
+ *   CGS2, in two passes over the basis: one pass forms V^T w and the new
+ *   column of the basis' Gram matrix G, one pass subtracts V (2I - G) V^T w,
+ *   which equals the second classical pass in exact arithmetic; a third,
+ *   plain pass when |w| falls below 1e-2 of its size; on vector layouts that
+ *   the 16-byte kernels cannot take, one classical pass and a second when the
+ *   DGKS criterion |w'| < |w|/sqrt(2) flags cancellation) stops at
  *   ||r||_2 <= gmres_rtol ||G||_2 or
  *   after max_gmres iterations per Newton correction; 1 <= gmres_restart <= 64.
  * precond: 0 = none; 1 = right preconditioning by the modal diagonal
@@ -161,7 +185,7 @@ typedef struct cdg2_stats {
     double residual0[5];  /* ||G(Y^0)||_2 per stage */
     double residual[5];   /* final ||G||_2 per stage */
     double seconds;       /* host wall time of the call */
-    int gmres_reorth;     /* Arnoldi steps that needed a second Gram-Schmidt pass */
+    int gmres_reorth;     /* Arnoldi steps that needed an extra Gram-Schmidt pass */
 } cdg2_stats;
 
 /* Build a mesh (host call, synchronous).  Tabulates the 1D basis and Gauss
@@ -177,6 +201,12 @@ void cdg2_mesh_destroy(cdg2_mesh* mesh);
  * (= 6 * n_elem * n_basis).  Any output pointer may be NULL. */
 int cdg2_mesh_info(const cdg2_mesh* mesh, long long* n_elem, int* n_basis, long long* n_dof);
 
+/* Wait for `stream` and report the mesh's domain status word (see "Domain"
+ * above): CDG2_ERR_DOMAIN if a kernel queued on the mesh since the last
+ * report met y + chith <= 0 at a quadrature point (the pole of chi, Sec. 2),
+ * else CDG2_OK.  Clears the word.  Meant for calls made with CDG2_ASYNC. */
+int cdg2_mesh_status(const cdg2_mesh* mesh, void* stream);
+
 /* out = M^{-1} L_h(U) (flags & CDG2_MINV) or out = <phi, L_h(U)>.
  * Sec. 3.1 Eq. convDiscr: element integrals int_K (F - A grad U):grad phi
  * + S.phi; interior faces: symmetric terms {A grad phi}:[U], consistency
@@ -188,7 +218,8 @@ int cdg2_mesh_info(const cdg2_mesh* mesh, long long* n_elem, int* n_basis, long 
  * Each face is evaluated once into a per-mesh face buffer that the first
  * cdg2_apply or cdg2_jvp on the mesh allocates (cudaMalloc, about
  * 2*6*(k+1)^(dim-1) doubles per face); calls sharing a mesh must therefore
- * be ordered on one stream. */
+ * be ordered on one stream.  flags may add CDG2_ASYNC.  Errors: INVALID_ARG,
+ * CUDA, DOMAIN (y + chith <= 0 at a quadrature point; out undefined). */
 int cdg2_apply(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, void* out,
                int flags, double t, void* stream);
 
@@ -201,7 +232,8 @@ int cdg2_apply(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, 
  * k_ox, beta1) (the reaction coefficients of Eq. (1) and the immune-cell
  * inflow rate of Eq. (3)); dtheta is a HOST array of 8 doubles or NULL.
  * U, dU, out: device [n_elem][6][n_basis], float64 or float32 (CDG2_FP32);
- * out must not overlap U or dU.  t is accepted for symmetry and unused. */
+ * out must not overlap U or dU.  t is accepted for symmetry and unused.
+ * flags may add CDG2_ASYNC.  Errors: INVALID_ARG, CUDA, DOMAIN (at U). */
 int cdg2_jvp(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, const void* dU,
              const double* dtheta, void* out, int flags, double t, void* stream);
 
@@ -214,7 +246,8 @@ int cdg2_jvp(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, co
  * The first call allocates a per-mesh workspace (cudaMalloc; 8 state vectors
  * plus gmres_restart + 5 Krylov vectors); calls sharing a mesh must be
  * ordered.  Errors: NOT_CONVERGED (U unchanged, stats filled), NONFINITE
- * (a NaN/Inf residual), INVALID_ARG, CUDA. */
+ * (a NaN/Inf residual), DOMAIN (a converged stage value with y + chith <= 0
+ * at a quadrature point; U unchanged), INVALID_ARG, CUDA. */
 int cdg2_step(const cdg2_mesh* mesh, const cdg2_params* params, double* U, double t, double dt,
               const cdg2_solver_opts* opts, cdg2_stats* stats, void* stream);
 
@@ -249,7 +282,8 @@ int cdg2_step_adjoint(const cdg2_mesh* mesh, const cdg2_params* params, const do
  * float64 or float32 (CDG2_FP32; gtheta is float64 either way); gU must not
  * overlap U or lam.  gtheta: DEVICE array of 8 doubles or NULL.  The first
  * call with gtheta allocates a per-mesh workspace (8 doubles per CTA,
- * cudaMalloc); calls sharing a mesh must then be ordered on one stream. */
+ * cudaMalloc); calls sharing a mesh must then be ordered on one stream.
+ * flags may add CDG2_ASYNC.  Errors: INVALID_ARG, CUDA, DOMAIN (at U). */
 int cdg2_vjp(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, const void* lam, void* gU,
              double* gtheta, int flags, double t, void* stream);
 
@@ -267,10 +301,16 @@ int cdg2_vjp(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, co
  * 3D Q3 elements); larger meshes return CDG2_ERR_INVALID_ARG.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array and nothing in it
+ * before any stream capture.  Under CUDA's lazy module loading (the
+ * default) that first call is also when the library's module holding the
+ * array is loaded on the device and the array takes its device memory;
+ * later calls take none.  All calls share the array and nothing in it
  * needs to start at zero (each block overwrites its own slots), but calls
- * that overlap on the GPU race on it: order them on one stream.
- * Arguments, layouts and results are those of cdg2_vjp. */
+ * that overlap on the GPU race on it: order them on one stream.  The domain
+ * check (see "Domain") uses a second static device word of the library, not
+ * the mesh's, so the call needs nothing allocated on the mesh either; the
+ * call always waits for its kernels and reads it (flags must not hold
+ * CDG2_ASYNC).  Arguments, layouts and results are those of cdg2_vjp. */
 int cdg2_vjp_noalloc(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, const void* lam, void* gU,
                      double* gtheta, int flags, double t, void* stream);
 
@@ -341,13 +381,16 @@ int cdg2_tri_mesh_create(const cdg2_tri_desc* desc, cdg2_tri_mesh** out);
 void cdg2_tri_mesh_destroy(cdg2_tri_mesh* mesh);
 int cdg2_tri_mesh_info(const cdg2_tri_mesh* mesh, long long* n_elem, int* n_basis, long long* n_dof,
                        long long* n_faces);
+/* The domain status of a triangle mesh, as cdg2_mesh_status. */
+int cdg2_tri_mesh_status(const cdg2_tri_mesh* mesh, void* stream);
 
 /* out = M^{-1} L_h(U) (flags = CDG2_MINV) or <phi, L_h(U)> (flags = 0) on a
  * triangle mesh; U, out: device float64 [n_tri][6][n_basis], not
  * overlapping.  Two kernels: every interior edge once (traces, the CDG2
  * lifting on K^-, the face flux, its test against both sides) into a face
  * buffer, then every element (volume terms, its edges, boundary data,
- * M^{-1}).  Errors: INVALID_ARG (NULL, overlap, other flags), CUDA. */
+ * M^{-1}).  flags may add CDG2_ASYNC.  Errors: INVALID_ARG (NULL, overlap,
+ * other flags), CUDA, DOMAIN (y + chith <= 0 at a quadrature point). */
 int cdg2_tri_apply(const cdg2_tri_mesh* mesh, const cdg2_params* params, const double* U, double* out, int flags,
                    void* stream);
 
@@ -418,13 +461,16 @@ int cdg2_tet_mesh_create(const cdg2_tet_desc* desc, cdg2_tet_mesh** out);
 void cdg2_tet_mesh_destroy(cdg2_tet_mesh* mesh);
 int cdg2_tet_mesh_info(const cdg2_tet_mesh* mesh, long long* n_elem, int* n_basis, long long* n_dof,
                        long long* n_faces);
+/* The domain status of a tetrahedral mesh, as cdg2_mesh_status. */
+int cdg2_tet_mesh_status(const cdg2_tet_mesh* mesh, void* stream);
 
 /* out = M^{-1} L_h(U) (flags = CDG2_MINV) or <phi, L_h(U)> (flags = 0) on a
  * tetrahedral mesh; U, out: device float64, not overlapping.  A face kernel
  * (every interior face once: traces of both sides at K^-'s face points, the
  * CDG2 lifting on K^-, the face flux, its test against both sides into a face
  * buffer) and an element kernel (volume terms, its faces, boundary data,
- * M^{-1}).  Errors: INVALID_ARG (NULL, overlap, other flags), CUDA. */
+ * M^{-1}).  flags may add CDG2_ASYNC.  Errors: INVALID_ARG (NULL, overlap,
+ * other flags), CUDA, DOMAIN (y + chith <= 0 at a quadrature point). */
 int cdg2_tet_apply(const cdg2_tet_mesh* mesh, const cdg2_params* params, const double* U, double* out, int flags,
                    void* stream);
 
@@ -460,6 +506,15 @@ int cdg2_tet_vjp(const cdg2_tet_mesh* mesh, const cdg2_params* params, const dou
  * block that is not positive definite), CUDA. */
 int cdg2_tet_step(const cdg2_tet_mesh* mesh, const cdg2_params* params, double* U, double dt,
                   const cdg2_solver_opts* opts, cdg2_stats* stats, void* stream);
+
+/* Measured FMA throughput of the current GPU (the paper has no counterpart;
+ * a measurement utility for the roofline of the operator kernels, which are
+ * bound by the FP64 or FP32 pipes): kind 0 = FP64, 1 = FP32.  Runs an FMA
+ * loop of `iters` (>= 8) steps on 8 independent chains in every thread of
+ * 8 x (SM count) blocks of 256 threads on `stream`, timed with CUDA events,
+ * and writes 2 x FMAs / time in TFLOP/s to the host double *tflops.
+ * Synchronous.  Errors: INVALID_ARG, CUDA. */
+int cdg2_probe_peak(int kind, int iters, double* tflops, void* stream);
 
 const char* cdg2_last_error(void);
 

@@ -18,12 +18,19 @@ __all__ = [
     "make_params", "cdg2_mesh_create", "cdg2_mesh_destroy", "cdg2_mesh_info", "cdg2_apply", "cdg2_last_error",
     "cdg2_project_gaussians", "cdg2_project_mms", "cdg2_jvp", "cdg2_vjp", "cdg2_step",
     "CDG2_SDIRK2", "CDG2_SDIRK3", "CDG2_SDIRK4", "SolverOpts", "Stats", "make_opts", "cdg2_step_stages", "cdg2_step_adjoint",
-    "stages_of",
+    "stages_of", "CDG2_ASYNC", "CDG2_ERR_DOMAIN", "cdg2_mesh_status", "cdg2_tri_mesh_status", "cdg2_tet_mesh_status",
+    "cdg2_probe_peak",
 ]
 
 CDG2_MINV = 1
 CDG2_FORCING = 2
 CDG2_FP32 = 4
+CDG2_ASYNC = 8
+CDG2_ERR_INVALID_ARG = -1
+CDG2_ERR_CUDA = -2
+CDG2_ERR_NOT_CONVERGED = -3
+CDG2_ERR_NONFINITE = -4
+CDG2_ERR_DOMAIN = -5
 CDG2_SDIRK2 = 2
 CDG2_SDIRK3 = 3
 CDG2_SDIRK4 = 4
@@ -139,6 +146,9 @@ def load_library():
     lib.cdg2_mesh_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i),
                                    ctypes.POINTER(ctypes.c_longlong)]
     lib.cdg2_mesh_info.restype = i
+    for name in ("cdg2_mesh_status", "cdg2_tri_mesh_status", "cdg2_tet_mesh_status"):
+        getattr(lib, name).argtypes = [vp, vp]
+        getattr(lib, name).restype = i
     lib.cdg2_apply.argtypes = [vp, ctypes.POINTER(Params), vp, vp, i, d, vp]
     lib.cdg2_apply.restype = i
     dp = ctypes.POINTER(ctypes.c_double)
@@ -190,6 +200,8 @@ def load_library():
         getattr(lib, name).restype = i
     lib.cdg2_element_block.argtypes = [vp, ctypes.POINTER(Params), d, ctypes.c_longlong, i, dp]
     lib.cdg2_element_block.restype = i
+    lib.cdg2_probe_peak.argtypes = [i, i, ctypes.POINTER(ctypes.c_double), vp]
+    lib.cdg2_probe_peak.restype = i
     lib.cdg2_last_error.argtypes = []
     lib.cdg2_last_error.restype = ctypes.c_char_p
     _LIB = lib
@@ -280,6 +292,29 @@ def cdg2_mesh_destroy(mesh: Mesh):
 
 def cdg2_mesh_info(mesh: Mesh):
     return mesh.n_elem, mesh.n_basis, mesh.n_dof
+
+
+def cdg2_probe_peak(kind: int, iters: int, stream=None) -> float:
+    """Measured FMA throughput in TFLOP/s of the current GPU: kind 0 = FP64, 1 = FP32."""
+    out = ctypes.c_double()
+    _check(load_library().cdg2_probe_peak(int(kind), int(iters), ctypes.byref(out), _stream_ptr(stream)))
+    return out.value
+
+
+def cdg2_mesh_status(mesh: Mesh, stream=None):
+    """Wait for the stream and raise Cdg2Error(CDG2_ERR_DOMAIN) if a kernel queued on
+    the mesh (with CDG2_ASYNC) met the pole of chi; clears the status."""
+    _check(load_library().cdg2_mesh_status(mesh.handle, _stream_ptr(stream)))
+
+
+def cdg2_tri_mesh_status(mesh, stream=None):
+    """cdg2_mesh_status of a triangle mesh."""
+    _check(load_library().cdg2_tri_mesh_status(mesh.handle, _stream_ptr(stream)))
+
+
+def cdg2_tet_mesh_status(mesh, stream=None):
+    """cdg2_mesh_status of a tetrahedral mesh."""
+    _check(load_library().cdg2_tet_mesh_status(mesh.handle, _stream_ptr(stream)))
 
 
 def _stream_ptr(stream):

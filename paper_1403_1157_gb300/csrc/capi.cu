@@ -19,6 +19,34 @@ int cuda_fail(cudaError_t e, const char* what) {
     return CDG2_ERR_CUDA;
 }
 
+cudaError_t ensure_status(int** word) {
+    if (*word) return cudaSuccess;
+    int* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(int));
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(p, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return e;
+    }
+    *word = p;
+    return cudaSuccess;
+}
+
+int take_domain_status(int* word, cudaStream_t st, const char* who) {
+    if (!word) return CDG2_OK;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, word, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    if (h == 0) return CDG2_OK;
+    e = cudaMemsetAsync(word, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    set_error(std::string(who) + ": a chemotactic sensitivity chi0 x / (y + chith) met y + chith <= 0 at a "
+              "quadrature point (the pole of chi, Sec. 2): the state is outside the model's domain");
+    return CDG2_ERR_DOMAIN;
+}
+
 Coef make_coef(const cdg2_params& p) {
     Coef c;
     c.A[0] = p.mu[0];
@@ -198,6 +226,7 @@ void cdg2_mesh_destroy(cdg2_mesh* m) {
     if (m->theta_part) cudaFree(m->theta_part);   // synchronises work queued on it
     if (m->step_ws) cudaFree(m->step_ws);
     if (m->fbuf) cudaFree(m->fbuf);
+    if (m->status) cudaFree(m->status);
     delete m;
 }
 
@@ -212,6 +241,14 @@ int cdg2_mesh_info(const cdg2_mesh* m, long long* n_elem, int* n_basis, long lon
     return CDG2_OK;
 }
 
+int cdg2_mesh_status(const cdg2_mesh* m, void* stream) {
+    if (!m) {
+        set_error("cdg2_mesh_status: NULL mesh");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    return take_domain_status(m->status, (cudaStream_t)stream, "cdg2_mesh_status");
+}
+
 int cdg2_apply(const cdg2_mesh* m, const cdg2_params* p, const void* U, void* out, int flags, double t,
                void* stream) {
     if (!m || !p || !U || !out) {
@@ -222,14 +259,15 @@ int cdg2_apply(const cdg2_mesh* m, const cdg2_params* p, const void* U, void* ou
         set_error("cdg2_apply: U and out must not overlap");
         return CDG2_ERR_INVALID_ARG;
     }
-    if (flags & ~(CDG2_MINV | CDG2_FORCING | CDG2_FP32)) {
+    if (flags & ~(CDG2_MINV | CDG2_FORCING | CDG2_FP32 | CDG2_ASYNC)) {
         set_error("cdg2_apply: unknown flag bits");
         return CDG2_ERR_INVALID_ARG;
     }
     Coef c = make_coef(*p);
     cudaError_t e = launch_apply(*m, c, U, out, flags, t, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cdg2_apply");
-    return CDG2_OK;
+    if (flags & CDG2_ASYNC) return CDG2_OK;
+    return take_domain_status(m->status, (cudaStream_t)stream, "cdg2_apply");
 }
 
 int cdg2_jvp(const cdg2_mesh* m, const cdg2_params* p, const void* U, const void* dU, const double* dtheta,
@@ -243,14 +281,15 @@ int cdg2_jvp(const cdg2_mesh* m, const cdg2_params* p, const void* U, const void
         set_error("cdg2_jvp: out must not overlap U or dU");
         return CDG2_ERR_INVALID_ARG;
     }
-    if (flags & ~(CDG2_MINV | CDG2_FORCING | CDG2_FP32)) {
+    if (flags & ~(CDG2_MINV | CDG2_FORCING | CDG2_FP32 | CDG2_ASYNC)) {
         set_error("cdg2_jvp: unknown flag bits");
         return CDG2_ERR_INVALID_ARG;
     }
     Coef c = make_coef(*p);
     cudaError_t e = launch_jvp(*m, c, U, dU, dtheta, out, flags, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cdg2_jvp");
-    return CDG2_OK;
+    if (flags & CDG2_ASYNC) return CDG2_OK;
+    return take_domain_status(m->status, (cudaStream_t)stream, "cdg2_jvp");
 }
 
 int cdg2_vjp(const cdg2_mesh* m, const cdg2_params* p, const void* U, const void* lam, void* gU, double* gtheta,
@@ -264,7 +303,7 @@ int cdg2_vjp(const cdg2_mesh* m, const cdg2_params* p, const void* U, const void
         set_error("cdg2_vjp: gU must not overlap U or lam");
         return CDG2_ERR_INVALID_ARG;
     }
-    if (flags & ~(CDG2_MINV | CDG2_FORCING | CDG2_FP32)) {
+    if (flags & ~(CDG2_MINV | CDG2_FORCING | CDG2_FP32 | CDG2_ASYNC)) {
         set_error("cdg2_vjp: unknown flag bits");
         return CDG2_ERR_INVALID_ARG;
     }
@@ -284,7 +323,8 @@ int cdg2_vjp(const cdg2_mesh* m, const cdg2_params* p, const void* U, const void
     Coef c = make_coef(*p);
     cudaError_t e = launch_vjp(*m, c, U, lam, gU, part, gtheta, flags, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cdg2_vjp");
-    return CDG2_OK;
+    if (flags & CDG2_ASYNC) return CDG2_OK;
+    return take_domain_status(m->status, (cudaStream_t)stream, "cdg2_vjp");
 }
 
 }  // extern "C"

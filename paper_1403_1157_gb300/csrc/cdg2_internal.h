@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <string>
 
 #include "cdg2.h"
@@ -119,6 +120,8 @@ struct cdg2_mesh {
     // Workspace of cdg2_step: 8 FP64 state vectors, the Krylov basis, reduction scratch.
     mutable void* step_ws = nullptr;
     mutable size_t step_ws_bytes = 0;
+    // Domain status word (device int): set by a kernel that meets c + chi^th <= 0.
+    mutable int* status = nullptr;
 };
 
 namespace cdg2 {
@@ -126,7 +129,38 @@ namespace cdg2 {
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
+// One-time set-up that has to be repeated on every device a process uses
+// (a kernel's opt-in dynamic shared-memory size is a property of the kernel
+// on one device): `setup` runs with the device current, once per device
+// ordinal below 64 (every call beyond that).  Two threads may both run it
+// the first time; the set-ups used here are idempotent.
+struct DeviceOnce {
+    std::atomic<unsigned long long> done{0};   // bit d: device d is set up
+};
+
+template <typename F>
+inline cudaError_t once_per_device(DeviceOnce& o, F&& setup) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return setup();
+    const unsigned long long bit = 1ull << dev;
+    if (o.done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = setup();
+    if (e == cudaSuccess) o.done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
+// The domain status word of a mesh (one device int, zero until a kernel
+// meets a pole of chi): allocated and cleared by the first call.
+cudaError_t ensure_status(int** word);
+// Wait for `st`, read *word and clear it if set: CDG2_OK, CDG2_ERR_DOMAIN
+// (with the message) or CDG2_ERR_CUDA.  word may be null (nothing launched).
+int take_domain_status(int* word, cudaStream_t st, const char* who);
+
 // Kernel launchers (operator.cu).  Return the cudaError_t of the launch.
+// Every launcher records domain errors in `domain` when it is given, else in
+// the mesh's status word (allocating it on the first launch).
 cudaError_t launch_apply(const cdg2_mesh& m, const Coef& c, const void* U, void* out, int flags, double t,
                          cudaStream_t stream);
 cudaError_t launch_jvp(const cdg2_mesh& m, const Coef& c, const void* U, const void* dU, const double* dtheta,
@@ -142,7 +176,7 @@ cudaError_t launch_vjp_axpby(const cdg2_mesh& m, const Coef& c, const void* U, c
 // VJP: gU = (df/dU)^T lam; when gtheta is non-null also (df/dtheta)^T lam via
 // theta_part ([vjp_grid(m)][8] doubles of scratch) and a fixed-order reduction.
 cudaError_t launch_vjp(const cdg2_mesh& m, const Coef& c, const void* U, const void* lam, void* gU,
-                       double* theta_part, double* gtheta, int flags, cudaStream_t stream);
+                       double* theta_part, double* gtheta, int flags, cudaStream_t stream, int* domain = nullptr);
 long long vjp_grid(const cdg2_mesh& m);
 size_t face_buffer_bytes(const Geo& g);
 

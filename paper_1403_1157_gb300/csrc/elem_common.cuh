@@ -309,6 +309,7 @@ struct CoefT {
     T invh[3];      // 1 / h_j
     T pen_c;        // face penalty constant (chi_e for CDG2, eta/2 for BR2, C for SIPG)
     T death1;       // 1: Eq. (1); 0: the reduced model of Eq. (2) (no n1 death term)
+    int* domain;    // device status word: set to 1 where c + chi^th <= 0 (a pole of chi), or null
 };
 
 // Host-side conversion (kernel parameters live in the constant bank, so the
@@ -343,6 +344,7 @@ inline CoefT<T> make_coefT(const Coef& c, const Geo& g, const double* dtheta) {
     for (int j = 0; j < 3; ++j) d.invh[j] = T(1.0 / g.h[j]);
     d.pen_c = T(g.pen_c);
     d.death1 = T(c.model == 1 ? 0.0 : 1.0);
+    d.domain = nullptr;
     return d;
 }
 

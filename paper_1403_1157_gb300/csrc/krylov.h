@@ -34,6 +34,22 @@ cudaError_t vec_mdot_self(long long n, int nv, const T* V, long long ldv, const 
 template <typename T>
 cudaError_t vec_update_norm(long long n, int nv, const T* V, long long ldv, const double* h, T* w, double* part,
                             double* norm2_out, cudaStream_t st);
+// True when the 16-byte (packed) kernels below apply: n and ldv multiples of
+// 16 / sizeof(T) and both base pointers 16-byte aligned.
+template <typename T>
+bool vec_packed(long long n, const void* V, long long ldv, const void* w);
+// The dot pass of one Arnoldi step with nv = j + 1 basis vectors (packed
+// layout): dots[0..nv) = V^T w, dots[nv..2nv) = V^T V_j, dots[2nv] = w . w;
+// then column j of the Gram matrix G (ldg x ldg, device) and the CGS2
+// coefficients h = 2 V^T w - G V^T w (device, nv doubles).  part:
+// reduction_scratch_doubles(2 nv + 1) doubles.
+template <typename T>
+cudaError_t vec_gs_dots(long long n, int nv, const T* V, long long ldv, const T* w, double* part, double* dots,
+                        double* G, int ldg, double* h, cudaStream_t st);
+// vec_update_norm over 16-byte packs (packed layout)
+template <typename T>
+cudaError_t vec_update_norm16(long long n, int nv, const T* V, long long ldv, const double* h, T* w, double* part,
+                              double* norm2_out, cudaStream_t st);
 template <typename T>
 cudaError_t vec_basis_combine(long long n, int nv, const T* V, long long ldv, const Coeffs& y, T* x,
                               cudaStream_t st);

@@ -84,6 +84,7 @@ struct OpArgs {
     CoefT<T> c;           // coefficients and geometry in the kernel's precision
     T* fbuf;              // face-once path: tested face fluxes, per axis at fb_off[axis], or null
     long long fb_off[3];
+    int* domain;          // domain status word of this launch, or null: the mesh's
 };
 
 constexpr int MODE_APPLY = 0, MODE_JVP = 1, MODE_VJP = 2;
@@ -732,6 +733,16 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const TabP<T> tab,
     constexpr int OFF = (F - 1) * EPB * NS * NQ;
     for (int idx = threadIdx.x; idx < EPB * NQ; idx += blockDim.x) {
         const int q = idx % NQ, e = idx / NQ;
+        if (e0 + e >= g.E) {
+            // padding of a ragged last CTA (U = 0, never stored): no pointwise
+            // model there, so its zero state neither trips the domain check
+            // nor feeds the theta partials
+#pragma unroll
+            for (int s = 0; s < NS; ++s)
+#pragma unroll
+                for (int j = 0; j <= D; ++j) Q[j * P::QSZ + OFF + (e * NS + s) * NQ + q] = T(0);
+            continue;
+        }
         T u[NS], gr[NS][D], Phi[NS][D], Sr[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
@@ -993,15 +1004,22 @@ static cudaError_t launch_one(const cdg2_mesh& m, const Coef& c, OpArgs<T> a, cu
     static_assert(smem <= 227 * 1024, "operator kernel shared memory exceeds 227 KB");
     static_assert(MODE != MODE_VJP || sizeof(T) * P::WORK >= 8 * 128 * sizeof(double),
                   "theta reduction buffer does not fit the work area");
-    static bool attr_done = false;   // per instantiation; benign race: both writers set the same value
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(op_kernel<D, K, MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    static DeviceOnce attr;   // per instantiation and device
+    {
+        cudaError_t e = once_per_device(attr, [] {
+            return cudaFuncSetAttribute(op_kernel<D, K, MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem);
+        });
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     const long long blocks = grid_of<MODE>(m);
     a.c = make_coefT<T>(c, m.geo, a.has_dtheta ? a.dtheta : nullptr);
+    if (!a.domain) {
+        cudaError_t e = ensure_status(&m.status);
+        if (e != cudaSuccess) return e;
+        a.domain = m.status;
+    }
+    a.c.domain = a.domain;
     a.fbuf = nullptr;
     // Face-once for FP64 (bound by the FP64 pipe: halving the face arithmetic
     // pays) and for 2D; the fused path stays for FP32 in 3D, where the extra
@@ -1018,17 +1036,20 @@ static cudaError_t launch_one(const cdg2_mesh& m, const Coef& c, OpArgs<T> a, cu
             using FPl = FacePlan<D, K, fields_of(MODE)>;
             constexpr size_t fsmem = FPl::template smem_bytes<T>();
             static_assert(fsmem <= 227 * 1024, "face kernel shared memory exceeds 227 KB");
-            static bool fattr_done = false;
-            if (!fattr_done) {
-                cudaError_t e = cudaSuccess;
-                e = cudaFuncSetAttribute(face_kernel<D, K, MODE, 0, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
-                if (e == cudaSuccess)
-                    e = cudaFuncSetAttribute(face_kernel<D, K, MODE, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
-                if (e == cudaSuccess && D == 3)
-                    e = cudaFuncSetAttribute(face_kernel<D, K, MODE, D == 3 ? 2 : 1, T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+            static DeviceOnce fattr;
+            {
+                cudaError_t e = once_per_device(fattr, [] {
+                    cudaError_t r = cudaFuncSetAttribute(face_kernel<D, K, MODE, 0, T>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+                    if (r == cudaSuccess)
+                        r = cudaFuncSetAttribute(face_kernel<D, K, MODE, 1, T>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+                    if (r == cudaSuccess && D == 3)
+                        r = cudaFuncSetAttribute(face_kernel<D, K, MODE, D == 3 ? 2 : 1, T>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+                    return r;
+                });
                 if (e != cudaSuccess) return e;
-                fattr_done = true;
             }
             a.fbuf = static_cast<T*>(m.fbuf);
             constexpr long long per_face = 2LL * NS * Shape<D, K>::NBT;
@@ -1076,6 +1097,7 @@ static OpArgs<T> make_args(const void* U, const void* dU, void* out, int flags, 
     a.pscale = nullptr;
     a.fbuf = nullptr;
     for (int i = 0; i < 3; ++i) a.fb_off[i] = 0;
+    a.domain = nullptr;
     return a;
 }
 
@@ -1136,12 +1158,17 @@ cudaError_t launch_vjp_axpby(const cdg2_mesh& m, const Coef& c, const void* U, c
 }
 
 cudaError_t launch_vjp(const cdg2_mesh& m, const Coef& c, const void* U, const void* lam, void* gU,
-                       double* theta_part, double* gtheta, int flags, cudaStream_t st) {
+                       double* theta_part, double* gtheta, int flags, cudaStream_t st, int* domain) {
     cudaError_t e;
-    if (flags & CDG2_FP32)
-        e = dispatch<MODE_VJP, float>(m, c, make_args<float>(U, lam, gU, flags, 0.0, nullptr, theta_part), st);
-    else
-        e = dispatch<MODE_VJP, double>(m, c, make_args<double>(U, lam, gU, flags, 0.0, nullptr, theta_part), st);
+    if (flags & CDG2_FP32) {
+        OpArgs<float> a = make_args<float>(U, lam, gU, flags, 0.0, nullptr, theta_part);
+        a.domain = domain;
+        e = dispatch<MODE_VJP, float>(m, c, a, st);
+    } else {
+        OpArgs<double> a = make_args<double>(U, lam, gU, flags, 0.0, nullptr, theta_part);
+        a.domain = domain;
+        e = dispatch<MODE_VJP, double>(m, c, a, st);
+    }
     if (e != cudaSuccess || gtheta == nullptr) return e;
     theta_reduce_kernel<<<1, 256, 0, st>>>(theta_part, grid_of<MODE_VJP>(m), gtheta);
     return cudaGetLastError();

@@ -12,14 +12,25 @@ namespace cdg2 {
 // Pointwise physics (Sec. 2)
 // ---------------------------------------------------------------------------
 
+// Sign test of a denominator without a floating-point compare (those run on
+// the narrow FP64 pipe): the high word of an IEEE value is <= 0 exactly for
+// negative values, zeros and the smallest subnormals.
+__device__ __forceinline__ int hi_word(double x) { return __double2hiint(x); }
+__device__ __forceinline__ int hi_word(float x) { return __float_as_int(x); }
+
 // Denominators of the chemotactic sensitivities (Sec. 2) at one point:
 // kappa11(c1), kappa13(c3), kappa21(c1), kappa22(n1) = chi0_i / den_i.
+// chi(x, y, a, b) = a x / (y + b) has a pole at y + b = 0: a point with a
+// denominator <= 0 lies outside the model's domain, and the kernel records
+// it in the status word (the host returns CDG2_ERR_DOMAIN).
 template <typename T>
 __device__ __forceinline__ void kappa_den(const CoefT<T>& c, const T u[NS], T* den) {
     den[0] = u[3] + T(c.chith[0]);
     den[1] = u[5] + T(c.chith[1]);
     den[2] = u[3] + T(c.chith[2]);
     den[3] = u[0] + T(c.chith[3]);
+    const int m = min(min(hi_word(den[0]), hi_word(den[1])), min(hi_word(den[2]), hi_word(den[3])));
+    if (m <= 0 && c.domain != nullptr) *c.domain = 1;
 }
 
 // Volume flux at one quadrature point (Eq. elementint): Phi_s = F_s(U, grad U)

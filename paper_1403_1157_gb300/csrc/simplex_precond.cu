@@ -39,7 +39,10 @@ void SimplexPrecond::release() {
 
 cdg2_params diffusion_only(const cdg2_params& p) {
     cdg2_params q = p;
-    for (int i = 0; i < 4; ++i) q.chi0[i] = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        q.chi0[i] = 0.0;
+        q.chith[i] = 1.0;   // no sensitivity left: keeps the probe states (0 / 1 entries) off the pole of chi
+    }
     q.d1 = q.d2 = q.gamma = q.alpha1 = q.alpha2 = q.f1 = q.k_ox = 0.0;
     q.beta1 = q.beta2 = q.sigma = 0.0;
     return q;

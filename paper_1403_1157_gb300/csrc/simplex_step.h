@@ -50,6 +50,7 @@ struct SimplexStepOps {
     const int* face;             // host [NF][4], the first two entries the elements of an interior face
     long long NF;
     SimplexPrecond* pc;          // the mesh's block-Jacobi state
+    int* dom;                    // the mesh's domain status word (device), set by its kernels
 };
 
 // Build (or reuse) the blocks K of pc for ops, then form Binv for gdt.

@@ -104,7 +104,10 @@ struct Work {
     void* Yk;         // primal state in the Krylov precision (mixed) / unused
     void* bk;         // right-hand side in the Krylov precision (mixed)
     double* red;      // reduction partials
-    double* red_out;  // reduction results (MAX_KRYLOV + 1)
+    double* red_out;  // reduction results: Gram-Schmidt dots (2 MAX_KRYLOV + 3), then one norm slot
+    double* hdev;     // Gram-Schmidt coefficients of the current Arnoldi step (MAX_KRYLOV + 1)
+    double* gram;     // Gram matrix of the Krylov basis, (MAX_KRYLOV + 1)^2
+    double* gth;      // 8 doubles: the theta gradient of one adjoint stage
     double* pinv;     // [6][n_basis] right preconditioner P^{-1}
     void* blk;        // element-block table (precond.cu)
     void* ptmp;       // P^{-1} v in the Krylov precision
@@ -126,12 +129,15 @@ static int ensure_work(long long n, int nb, size_t blk_bytes, void*& ws, size_t&
     const size_t ks = mixed ? sizeof(float) : sizeof(double);
     const size_t vec64 = align256(sizeof(double) * n);
     const size_t veck = align256(ks * n);
-    const size_t red = align256(sizeof(double) * reduction_scratch_doubles(MAX_KRYLOV + 1));
-    const size_t out = align256(sizeof(double) * (MAX_KRYLOV + 2));   // projections, then one norm slot
+    const size_t red = align256(sizeof(double) * reduction_scratch_doubles(2 * MAX_KRYLOV + 3));
+    const size_t out = align256(sizeof(double) * (2 * MAX_KRYLOV + 4));   // dots, then one norm slot
+    const size_t hgs = align256(sizeof(double) * (MAX_KRYLOV + 1));
+    const size_t gram = align256(sizeof(double) * (MAX_KRYLOV + 1) * (MAX_KRYLOV + 1));
+    const size_t gth = align256(sizeof(double) * 8);
     const size_t tab = align256(sizeof(double) * NS * nb);
     const size_t blk = align256(blk_bytes);
     // 5 + MAX_STAGES FP64 vectors; basis (kdim + 2) + dx + Yk + bk + ptmp in the Krylov precision
-    const size_t need = (5 + MAX_STAGES) * vec64 + (size_t)(kdim + 6) * veck + red + out + tab + blk;
+    const size_t need = (5 + MAX_STAGES) * vec64 + (size_t)(kdim + 6) * veck + red + out + hgs + gram + gth + tab + blk;
     if (ws_bytes < need) {
         if (ws) cudaFree(ws);
         ws = nullptr;
@@ -160,6 +166,12 @@ static int ensure_work(long long n, int nb, size_t blk_bytes, void*& ws, size_t&
     p += red;
     w.red_out = reinterpret_cast<double*>(p);
     p += out;
+    w.hdev = reinterpret_cast<double*>(p);
+    p += hgs;
+    w.gram = reinterpret_cast<double*>(p);
+    p += gram;
+    w.gth = reinterpret_cast<double*>(p);
+    p += gth;
     w.pinv = reinterpret_cast<double*>(p);
     p += tab;
     w.blk = p;
@@ -241,7 +253,7 @@ static int norm2(const Work& w, const T* x, cudaStream_t st, double* out) {
 static bool done_cycle_needs_restart(bool done, int jlast, int kdim) { return !done && jlast == kdim - 1; }
 
 // Restarted GMRES(m) for (I - gdt J(Yop)) x = b, x0 = 0, Arnoldi by classical
-// Gram-Schmidt with DGKS reorthogonalisation (*reorth counts second passes).
+// Gram-Schmidt applied twice (CGS2; *reorth counts the rare extra passes).
 // Stops when ||b - A x||_2 <= rtol ||b||_2 (the Arnoldi estimate) or after
 // maxit inner iterations.  T is the Krylov precision.
 // The operator's matvec: w = (I - gdt J) P^{-1} v, or with J^T (adjoint).
@@ -292,6 +304,7 @@ static int gmres_op(const Op& op, const T* b, T* x, double rtol, int maxit, cons
     T* V = static_cast<T*>(w.basis);
     T* wv = V + (size_t)(kdim + 1) * n;
     T* tmp = static_cast<T*>(w.ptmp);
+    const bool packed = vec_packed<T>(n, V, n, wv);
     CDG2_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
     double beta0 = 0.0;
     if (int rc = norm2<T>(w, b, st, &beta0)) return rc;
@@ -316,23 +329,52 @@ static int gmres_op(const Op& op, const T* b, T* x, double rtol, int maxit, cons
             T* vj = V + (size_t)j * n;
             if (int rc = op.mv(vj, tmp, wv, st)) return rc;   // w = (I - gdt J) P^-1 v_j
             std::fill(hcol.begin(), hcol.end(), 0.0);
-            // Classical Gram-Schmidt with the DGKS criterion: one projection
-            // pass (its multi-dot also gives |w| before, the update |w| after);
-            // a second pass only when |w'| < |w| / sqrt(2) (cancellation).
-            double* nslot = w.red_out + (MAX_KRYLOV + 1);
+            double* nslot = w.red_out + (2 * MAX_KRYLOV + 3);
             double hn = 0.0;
-            for (int pass = 0; pass < 2; ++pass) {
-                if (pass == 0) CDG2_TRY(vec_mdot_self<T>(n, j + 1, V, n, wv, w.red, w.red_out, st));
-                else CDG2_TRY(vec_mdot<T>(n, j + 1, V, n, wv, w.red, w.red_out, st));
-                CDG2_TRY(vec_update_norm<T>(n, j + 1, V, n, w.red_out, wv, w.red, nslot, st));
-                std::vector<double> hp(MAX_KRYLOV + 2);
-                CDG2_TRY(cudaMemcpyAsync(hp.data(), w.red_out, sizeof(double) * (MAX_KRYLOV + 2),
+            if (packed) {
+                // Classical Gram-Schmidt applied twice (CGS2) in two passes over the
+                // basis: one pass forms V^T w and V^T v_j (the new Gram column), a
+                // small kernel the coefficients h = (2I - G) V^T w, one pass
+                // w -= V h with |w|^2.  A third pass, a plain classical one, only
+                // when |w| fell below 1e-2 of its size (severe cancellation, where
+                // the rounding of the update itself needs removing).
+                CDG2_TRY(vec_gs_dots<T>(n, j + 1, V, n, wv, w.red, w.red_out, w.gram, MAX_KRYLOV + 1, w.hdev, st));
+                CDG2_TRY(vec_update_norm16<T>(n, j + 1, V, n, w.hdev, wv, w.red, nslot, st));
+                std::vector<double> hp(2 * MAX_KRYLOV + 4), hh(j + 1);
+                CDG2_TRY(cudaMemcpyAsync(hp.data(), w.red_out, sizeof(double) * (2 * MAX_KRYLOV + 4),
                                          cudaMemcpyDeviceToHost, st));
+                CDG2_TRY(cudaMemcpyAsync(hh.data(), w.hdev, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
                 CDG2_TRY(cudaStreamSynchronize(st));
-                for (int i = 0; i <= j; ++i) hcol[i] += hp[i];
-                hn = std::sqrt(std::max(hp[MAX_KRYLOV + 1], 0.0));
-                if (pass == 1) ++*reorth;
-                if (pass == 1 || !(hn < 0.7071067811865476 * std::sqrt(std::max(hp[j + 1], 0.0)))) break;
+                for (int i = 0; i <= j; ++i) hcol[i] = hh[i];
+                const double w0 = std::sqrt(std::max(hp[2 * (j + 1)], 0.0));
+                hn = std::sqrt(std::max(hp[2 * MAX_KRYLOV + 3], 0.0));
+                if (hn < 1e-2 * w0) {
+                    CDG2_TRY(vec_mdot<T>(n, j + 1, V, n, wv, w.red, w.red_out, st));
+                    CDG2_TRY(vec_update_norm16<T>(n, j + 1, V, n, w.red_out, wv, w.red, nslot, st));
+                    CDG2_TRY(cudaMemcpyAsync(hp.data(), w.red_out, sizeof(double) * (2 * MAX_KRYLOV + 4),
+                                             cudaMemcpyDeviceToHost, st));
+                    CDG2_TRY(cudaStreamSynchronize(st));
+                    for (int i = 0; i <= j; ++i) hcol[i] += hp[i];
+                    hn = std::sqrt(std::max(hp[2 * MAX_KRYLOV + 3], 0.0));
+                    ++*reorth;
+                }
+            } else {
+                // Unaligned layouts: classical Gram-Schmidt with the DGKS criterion:
+                // one projection pass (its multi-dot also gives |w| before, the
+                // update |w| after); a second pass only when |w'| < |w| / sqrt(2).
+                for (int pass = 0; pass < 2; ++pass) {
+                    if (pass == 0) CDG2_TRY(vec_mdot_self<T>(n, j + 1, V, n, wv, w.red, w.red_out, st));
+                    else CDG2_TRY(vec_mdot<T>(n, j + 1, V, n, wv, w.red, w.red_out, st));
+                    CDG2_TRY(vec_update_norm<T>(n, j + 1, V, n, w.red_out, wv, w.red, nslot, st));
+                    std::vector<double> hp(2 * MAX_KRYLOV + 4);
+                    CDG2_TRY(cudaMemcpyAsync(hp.data(), w.red_out, sizeof(double) * (2 * MAX_KRYLOV + 4),
+                                             cudaMemcpyDeviceToHost, st));
+                    CDG2_TRY(cudaStreamSynchronize(st));
+                    for (int i = 0; i <= j; ++i) hcol[i] += hp[i];
+                    hn = std::sqrt(std::max(hp[2 * MAX_KRYLOV + 3], 0.0));
+                    if (pass == 1) ++*reorth;
+                    if (pass == 1 || !(hn < 0.7071067811865476 * std::sqrt(std::max(hp[j + 1], 0.0)))) break;
+                }
             }
             hcol[j + 1] = hn;
             // previous Givens rotations, then a new one zeroing hcol[j + 1]
@@ -416,10 +458,15 @@ static int check_opts(const cdg2_solver_opts* o, double dt, const char* who) {
 // correct(gdt, &its, &relres) solves the Newton correction for the residual
 // in w.G about w.Y and adds it into w.Y (both return a CDG2 status).  U is
 // overwritten with U_{n+1}; stages_out (nullable) receives Y_1..Y_s.
+// dom: the mesh's domain status word.  It is cleared before every residual
+// evaluation and read when Newton has converged: the converged stage value
+// must lie in the model's domain, while Newton may pass through iterates
+// outside it (the JVPs at such an iterate set the word too; the next
+// evaluation clears it).
 template <typename Apply, typename Correct>
 static int sdirk_run(const Tableau& T, const Work& w, const Apply& apply, const Correct& correct, double* U, double t,
                      double dt, const cdg2_solver_opts* o, cdg2_stats& S, double* stages_out, cudaStream_t st,
-                     const char* who) {
+                     const char* who, int* dom) {
     const long long n = w.n;
     int status = CDG2_OK;
     CDG2_TRY(cudaMemcpyAsync(w.Y, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -433,6 +480,7 @@ static int sdirk_run(const Tableau& T, const Work& w, const Apply& apply, const 
         double g0 = 0.0;
         bool converged = false;
         for (int it = 0; it <= o->max_newton; ++it) {
+            if (dom) CDG2_TRY(cudaMemsetAsync(dom, 0, sizeof(int), st));
             if (int rc = apply(w.Y, w.fY, ti)) return rc;
             CDG2_TRY(vec_newton_residual(n, w.Y, w.fY, gdt, w.rhs, w.G, st));
             double gn = 0.0;
@@ -446,6 +494,10 @@ static int sdirk_run(const Tableau& T, const Work& w, const Apply& apply, const 
             S.residual0[i] = g0;
             S.residual[i] = gn;
             if (gn <= std::fmax(o->newton_rtol * g0, o->newton_atol)) {
+                if (int rc = take_domain_status(dom, st, who)) {
+                    status = rc;
+                    break;
+                }
                 converged = true;
                 break;
             }
@@ -475,8 +527,9 @@ static int sdirk_run(const Tableau& T, const Work& w, const Apply& apply, const 
         Coeffs bb;
         for (int i = 0; i < T.s; ++i) bb.v[i] = dt * T.b[i];
         CDG2_TRY(vec_lincomb(n, U, T.s, w.K[0], w.K[1] - w.K[0], bb, U, st));   // U_{n+1} = U_n + dt sum b_i K_i
-        CDG2_TRY(cudaStreamSynchronize(st));
     }
+    if (dom) CDG2_TRY(cudaMemsetAsync(dom, 0, sizeof(int), st));   // leave nothing for the next call
+    CDG2_TRY(cudaStreamSynchronize(st));
     return status;
 }
 
@@ -492,6 +545,7 @@ static int run_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double 
     const bool mixed = o->mixed != 0;
     Work w;
     if (int rc = ensure_work(*m, o->gmres_restart, mixed, w)) return rc;
+    CDG2_TRY(ensure_status(&m->status));
     const Coef c = make_coef(*p);
     const Tableau T = sdirk_tableau(o->scheme);
     const long long n = w.n;
@@ -522,7 +576,7 @@ static int run_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double 
         }
         return rc;
     };
-    const int status = sdirk_run(T, w, apply, correct, U, t, dt, o, S, stages_out, st, "cdg2_step");
+    const int status = sdirk_run(T, w, apply, correct, U, t, dt, o, S, stages_out, st, "cdg2_step", m->status);
     S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = S;
     return status;
@@ -592,7 +646,7 @@ int simplex_step(const SimplexStepOps& ops, double* U, double dt, const cdg2_sol
         if (rc == CDG2_OK) CDG2_TRY(vec_add_into<double>(n, static_cast<double*>(w.dx), w.Y, st));
         return rc;
     };
-    const int status = sdirk_run(T, w, apply, correct, U, 0.0, dt, o, S, nullptr, st, who);
+    const int status = sdirk_run(T, w, apply, correct, U, 0.0, dt, o, S, nullptr, st, who, ops.dom);
     S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = S;
     return status;
@@ -637,6 +691,8 @@ extern "C" int cdg2_step_adjoint(const cdg2_mesh* m, const cdg2_params* p, const
         return CDG2_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    CDG2_TRY(ensure_status(&m->status));
+    CDG2_TRY(cudaMemsetAsync(m->status, 0, sizeof(int), st));   // the call owns the status word
     const bool mixed = o->mixed != 0;
     Work w;
     if (int rc = ensure_work(*m, o->gmres_restart, mixed, w)) return rc;
@@ -644,7 +700,7 @@ extern "C" int cdg2_step_adjoint(const cdg2_mesh* m, const cdg2_params* p, const
     const Tableau T = sdirk_tableau(o->scheme);
     const long long n = w.n;
     const long long ldk = w.K[1] - w.K[0];
-    double* gth = w.red_out + (MAX_KRYLOV + 1) - 8;   // 8 doubles at the end of the result area
+    double* gth = w.gth;
     double* part = nullptr;
     if (gtheta) {
         const long long need = vjp_grid(*m) * 8;
@@ -683,6 +739,7 @@ extern "C" int cdg2_step_adjoint(const cdg2_mesh* m, const cdg2_params* p, const
             double rn = 0.0;
             if (int rc = norm2<double>(w, w.G, st, &rn)) return rc;
             S.residual[i] = rn;
+            if (int rc = take_domain_status(m->status, st, "cdg2_step_adjoint")) return rc;
             if (!std::isfinite(rn)) {
                 set_error("cdg2_step_adjoint: non-finite residual");
                 return CDG2_ERR_NONFINITE;
@@ -731,6 +788,7 @@ extern "C" int cdg2_step_adjoint(const cdg2_mesh* m, const cdg2_params* p, const
     for (int i = 0; i < T.s; ++i) ones.v[i] = 1.0;
     CDG2_TRY(vec_lincomb(n, lam, T.s, w.K[0], ldk, ones, lam, st));
     CDG2_TRY(cudaStreamSynchronize(st));
+    if (int rc = take_domain_status(m->status, st, "cdg2_step_adjoint")) return rc;
     S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = S;
     return CDG2_OK;

@@ -104,6 +104,7 @@ struct cdg2_tet_mesh {
     mutable void* step_ws = nullptr;    // cdg2_tet_step workspace
     mutable size_t step_ws_bytes = 0;
     mutable cdg2::SimplexPrecond spc;   // element-block Jacobi of the step
+    mutable int* status = nullptr;      // domain status word (device int)
 };
 
 namespace cdg2 {
@@ -831,12 +832,13 @@ static cudaError_t tet_launch(const TetArgs& a, cudaStream_t st) {
     constexpr int FPB = MODE == TET_APPLY ? 2 : 1;   // faces per CTA (static shared memory <= 48 KB)
     constexpr int F = MODE == TET_APPLY ? 1 : 2;
     constexpr size_t smem = sizeof(double) * (size_t)F * TetSF<K, MODE != TET_VJP>::FIELD;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tet_elem_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    static DeviceOnce attr;   // per instantiation and device
+    {
+        cudaError_t e = once_per_device(attr, [] {
+            return cudaFuncSetAttribute(tet_elem_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem);
+        });
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     if (a.NF > 0) tet_face_kernel<K, FPB, MODE><<<(unsigned)((a.NF + FPB - 1) / FPB), 128, 0, st>>>(a);
     tet_elem_kernel<K, MODE><<<(unsigned)a.E, 128, smem, st>>>(a);
@@ -1008,6 +1010,7 @@ extern "C" void cdg2_tet_mesh_destroy(cdg2_tet_mesh* m) {
     cudaFree(m->d_fbuf);
     cudaFree(m->d_tab);
     if (m->step_ws) cudaFree(m->step_ws);
+    if (m->status) cudaFree(m->status);
     m->spc.release();
     delete m;
 }
@@ -1035,11 +1038,12 @@ static int tet_run(const char* who, const cdg2_tet_mesh* m, const cdg2_params* p
         set_error(std::string(who) + ": the inputs and out must not overlap");
         return CDG2_ERR_INVALID_ARG;
     }
-    if (flags & ~CDG2_MINV) {
-        set_error(std::string(who) + ": only CDG2_MINV is supported on tetrahedral meshes");
+    if (flags & ~(CDG2_MINV | CDG2_ASYNC)) {
+        set_error(std::string(who) + ": only CDG2_MINV and CDG2_ASYNC are supported on tetrahedral meshes");
         return CDG2_ERR_INVALID_ARG;
     }
     if (int rc = tet_upload(*m)) return rc;
+    if (cudaError_t e = ensure_status(&m->status)) return cuda_fail(e, who);
     TetArgs a;
     a.U = U;
     a.dU = dU;
@@ -1067,6 +1071,7 @@ static int tet_run(const char* who, const cdg2_tet_mesh* m, const cdg2_params* p
     g.g1in[1] = m->g1in[1];
     a.g = g;
     a.c = make_coefT<double>(make_coef(*p), g, nullptr);
+    a.c.domain = m->status;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
 #define TET_DISPATCH(MODE)                                       \
@@ -1084,7 +1089,16 @@ static int tet_run(const char* who, const cdg2_tet_mesh* m, const cdg2_params* p
     }
 #undef TET_DISPATCH
     if (e != cudaSuccess) return cuda_fail(e, who);
-    return CDG2_OK;
+    if (flags & CDG2_ASYNC) return CDG2_OK;
+    return take_domain_status(m->status, st, who);
+}
+
+extern "C" int cdg2_tet_mesh_status(const cdg2_tet_mesh* m, void* stream) {
+    if (!m) {
+        set_error("cdg2_tet_mesh_status: NULL mesh");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    return take_domain_status(m->status, (cudaStream_t)stream, "cdg2_tet_mesh_status");
 }
 
 extern "C" int cdg2_tet_apply(const cdg2_tet_mesh* m, const cdg2_params* p, const double* U, double* out, int flags,
@@ -1109,16 +1123,16 @@ struct TetStepCtx {
 };
 int tet_step_apply(const void* ctx, const double* Y, double* out, cudaStream_t st) {
     const auto* c = static_cast<const TetStepCtx*>(ctx);
-    return tet_run("cdg2_tet_step", c->m, c->p, Y, nullptr, out, CDG2_MINV, TET_APPLY, st);
+    return tet_run("cdg2_tet_step", c->m, c->p, Y, nullptr, out, CDG2_MINV | CDG2_ASYNC, TET_APPLY, st);
 }
 int tet_step_jvp(const void* ctx, const double* Y, const double* v, double* out, cudaStream_t st) {
     const auto* c = static_cast<const TetStepCtx*>(ctx);
-    return tet_run("cdg2_tet_step", c->m, c->p, Y, v, out, CDG2_MINV, TET_JVP, st);
+    return tet_run("cdg2_tet_step", c->m, c->p, Y, v, out, CDG2_MINV | CDG2_ASYNC, TET_JVP, st);
 }
 int tet_step_jvp_diffusion(const void* ctx, const double* v, double* out, cudaStream_t st) {
     const auto* c = static_cast<const TetStepCtx*>(ctx);
     const cdg2_params q = cdg2::diffusion_only(*c->p);
-    return tet_run("cdg2_tet_step", c->m, &q, v, v, out, CDG2_MINV, TET_JVP, st);
+    return tet_run("cdg2_tet_step", c->m, &q, v, v, out, CDG2_MINV | CDG2_ASYNC, TET_JVP, st);
 }
 }  // namespace
 
@@ -1143,5 +1157,7 @@ extern "C" int cdg2_tet_step(const cdg2_tet_mesh* m, const cdg2_params* p, doubl
     ops.face = m->face.data();
     ops.NF = m->NF;
     ops.pc = &m->spc;
+    if (cudaError_t e = ensure_status(&m->status)) return cuda_fail(e, "cdg2_tet_step");
+    ops.dom = m->status;
     return cdg2::simplex_step(ops, U, dt, opts, stats, stream, "cdg2_tet_step");
 }

@@ -88,6 +88,7 @@ struct cdg2_tri_mesh {
     mutable void* step_ws = nullptr;    // cdg2_tri_step workspace
     mutable size_t step_ws_bytes = 0;
     mutable cdg2::SimplexPrecond spc;   // element-block Jacobi of the step
+    mutable int* status = nullptr;      // domain status word (device int)
 };
 
 namespace cdg2 {
@@ -823,6 +824,7 @@ extern "C" void cdg2_tri_mesh_destroy(cdg2_tri_mesh* m) {
     cudaFree(m->d_fbuf);
     cudaFree(m->d_tab);
     if (m->step_ws) cudaFree(m->step_ws);
+    if (m->status) cudaFree(m->status);
     m->spc.release();
     delete m;
 }
@@ -850,11 +852,12 @@ static int tri_run(const char* who, const cdg2_tri_mesh* m, const cdg2_params* p
         set_error(std::string(who) + ": the inputs and out must not overlap");
         return CDG2_ERR_INVALID_ARG;
     }
-    if (flags & ~CDG2_MINV) {
-        set_error(std::string(who) + ": only CDG2_MINV is supported on triangle meshes");
+    if (flags & ~(CDG2_MINV | CDG2_ASYNC)) {
+        set_error(std::string(who) + ": only CDG2_MINV and CDG2_ASYNC are supported on triangle meshes");
         return CDG2_ERR_INVALID_ARG;
     }
     if (int rc = tri_upload(*m)) return rc;
+    if (cudaError_t e = ensure_status(&m->status)) return cuda_fail(e, who);
     TriArgs a;
     a.U = U;
     a.dU = dU;
@@ -882,6 +885,7 @@ static int tri_run(const char* who, const cdg2_tri_mesh* m, const cdg2_params* p
     g.g1in[1] = m->g1in[1];
     a.g = g;
     a.c = make_coefT<double>(make_coef(*p), g, nullptr);
+    a.c.domain = m->status;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     if (mode == TRI_APPLY) {
@@ -904,7 +908,16 @@ static int tri_run(const char* who, const cdg2_tri_mesh* m, const cdg2_params* p
         }
     }
     if (e != cudaSuccess) return cuda_fail(e, who);
-    return CDG2_OK;
+    if (flags & CDG2_ASYNC) return CDG2_OK;
+    return take_domain_status(m->status, st, who);
+}
+
+extern "C" int cdg2_tri_mesh_status(const cdg2_tri_mesh* m, void* stream) {
+    if (!m) {
+        set_error("cdg2_tri_mesh_status: NULL mesh");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    return take_domain_status(m->status, (cudaStream_t)stream, "cdg2_tri_mesh_status");
 }
 
 extern "C" int cdg2_tri_apply(const cdg2_tri_mesh* m, const cdg2_params* p, const double* U, double* out, int flags,
@@ -929,16 +942,16 @@ struct TriStepCtx {
 };
 int tri_step_apply(const void* ctx, const double* Y, double* out, cudaStream_t st) {
     const auto* c = static_cast<const TriStepCtx*>(ctx);
-    return tri_run("cdg2_tri_step", c->m, c->p, Y, nullptr, out, CDG2_MINV, TRI_APPLY, st);
+    return tri_run("cdg2_tri_step", c->m, c->p, Y, nullptr, out, CDG2_MINV | CDG2_ASYNC, TRI_APPLY, st);
 }
 int tri_step_jvp(const void* ctx, const double* Y, const double* v, double* out, cudaStream_t st) {
     const auto* c = static_cast<const TriStepCtx*>(ctx);
-    return tri_run("cdg2_tri_step", c->m, c->p, Y, v, out, CDG2_MINV, TRI_JVP, st);
+    return tri_run("cdg2_tri_step", c->m, c->p, Y, v, out, CDG2_MINV | CDG2_ASYNC, TRI_JVP, st);
 }
 int tri_step_jvp_diffusion(const void* ctx, const double* v, double* out, cudaStream_t st) {
     const auto* c = static_cast<const TriStepCtx*>(ctx);
     const cdg2_params q = cdg2::diffusion_only(*c->p);
-    return tri_run("cdg2_tri_step", c->m, &q, v, v, out, CDG2_MINV, TRI_JVP, st);
+    return tri_run("cdg2_tri_step", c->m, &q, v, v, out, CDG2_MINV | CDG2_ASYNC, TRI_JVP, st);
 }
 }  // namespace
 
@@ -963,5 +976,7 @@ extern "C" int cdg2_tri_step(const cdg2_tri_mesh* m, const cdg2_params* p, doubl
     ops.face = m->face.data();
     ops.NF = m->NF;
     ops.pc = &m->spc;
+    if (cudaError_t e = ensure_status(&m->status)) return cuda_fail(e, "cdg2_tri_step");
+    ops.dom = m->status;
     return cdg2::simplex_step(ops, U, dt, opts, stats, stream, "cdg2_tri_step");
 }

@@ -12,6 +12,7 @@ import cdg2_inputs as I
 from oracle import cdg2_oracle as O
 from oracle import cdg2_tet_oracle as TT
 from oracle import cdg2_tri_oracle as T
+from helpers import lift_into_domain, psi_max_tet, psi_max_tri
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +51,7 @@ def test_tri_step_matches_oracle(G, nx, ny, k, scheme, name, precond):
     om = T.TriMesh(xy, tri, k)
     p = _params()
     cen, amp = I.gaussian_draws(2, (1.0, 0.2), 4, 70 + k)
-    U0 = T.project(om, lambda x: O.gaussian_field(om, x, cen, amp, 0.15, 0.05))
+    U0 = lift_into_domain(T.project(om, lambda x: O.gaussian_field(om, x, cen, amp, 0.15, 0.05)), psi_max_tri(k))
     dt, nsteps = 1e-3, 2
     key = (nx, ny, k, name)
     if key not in _ORACLE_RUNS:
@@ -74,7 +75,7 @@ def test_tet_step_matches_oracle(G, k, precond):
     om = TT.TetMesh(xyz, tet, k)
     p = _params()
     cen, amp = I.gaussian_draws(3, (1.0, 0.2, 0.2), 4, 71 + k)
-    U0 = TT.project(om, lambda x: O.gaussian_field(om, x, cen, amp, 0.15, 0.05))
+    U0 = lift_into_domain(TT.project(om, lambda x: O.gaussian_field(om, x, cen, amp, 0.15, 0.05)), psi_max_tet(k))
     if ("tet", k) not in _ORACLE_RUNS:
         _ORACLE_RUNS[("tet", k)] = TT.step(om, U0, p, 2e-3, "sdirk2")
     ref = _ORACLE_RUNS[("tet", k)]
@@ -92,7 +93,9 @@ def test_simplex_step_status_codes(G):
     xy, tri = I.tri_mesh(3, 2, 1.0, 0.2, 0.2, 720)
     gm = G.cdg2_tri_mesh_create(xy, tri, 1)
     p = _params()
-    U = torch.full((gm.n_dof,), 0.1, dtype=torch.float64, device="cuda")
+    U = torch.zeros(gm.n_elem, 6, gm.n_basis, dtype=torch.float64, device="cuda")
+    U[:, :, 0] = 0.1                    # constant fields, inside the model's domain
+    U = U.reshape(-1)
     for bad in (G.make_opts(mixed=True, precond=0), G.make_opts(precond=1), G.make_opts(precond=3),
                 G.make_opts(precond=0, flags=G.CDG2_FORCING)):
         rc, _ = G.cdg2_tri_step(gm, p, U, 1e-3, bad, raise_on_error=False)

@@ -10,7 +10,7 @@ import torch
 import cdg2_inputs as I
 from oracle import cdg2_oracle as O
 from oracle import cdg2_tet_oracle as TT
-from helpers import rel_l2_per_species
+from helpers import lift_into_domain, psi_max_tet, rel_l2_per_species
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +31,8 @@ def _params():
 
 def _state(om, seed):
     cen, amp = I.gaussian_draws(3, (1.0, 0.2, 0.2), 4, seed)
-    return TT.project(om, lambda x: O.gaussian_field(om, x, cen, amp, 0.08, 1e-3))
+    U = TT.project(om, lambda x: O.gaussian_field(om, x, cen, amp, 0.08, 1e-3))
+    return lift_into_domain(U, psi_max_tet(om.k))
 
 
 def _discrete_state(om, seed):
@@ -40,7 +41,7 @@ def _discrete_state(om, seed):
     nearly agree, so the LLF maximum |v^- . n| vs |v^+ . n| is a near-tie at
     almost every face point and rounding picks its branch; a relative 1e-15
     perturbation of U then moves the oracle's own JVP by ~1e-12."""
-    return torch.from_numpy(I.random_coefficients(om.E, om.nb, seed))
+    return lift_into_domain(torch.from_numpy(I.random_coefficients(om.E, om.nb, seed)), psi_max_tet(om.k))
 
 
 def _run(G, xyz, tet, k, p, U, flags):
@@ -74,7 +75,7 @@ def test_tet_apply_ties_and_relabelled_vertices(G, k):
     for t in (tet, rel):
         om = TT.TetMesh(xyz, t, k)
         p = _params()
-        U = torch.from_numpy(I.random_coefficients(om.E, om.nb, 3, 0.1))
+        U = lift_into_domain(torch.from_numpy(I.random_coefficients(om.E, om.nb, 3, 0.1)), psi_max_tet(om.k))
         got = _run(G, xyz, t, k, p, U, G.CDG2_MINV)
         assert rel_l2_per_species(got, TT.apply(om, U, p)) <= 1e-12
 
@@ -103,7 +104,7 @@ def test_tet_apply_full_size_sampled_rows(G):
     xyz, tet = I.tet_mesh(*w.cells, *w.extent, w.jitter, w.seed)
     gm = G.cdg2_tet_mesh_create(xyz, tet, w.k)
     p = _params()
-    U = torch.from_numpy(I.random_coefficients(gm.n_elem, gm.n_basis, w.seed, 0.1))
+    U = lift_into_domain(torch.from_numpy(I.random_coefficients(gm.n_elem, gm.n_basis, w.seed, 0.1)), psi_max_tet(w.k))
     out = torch.empty(gm.n_dof, dtype=torch.float64, device="cuda")
     G.cdg2_tet_apply(gm, p, U.reshape(-1).cuda(), out, G.CDG2_MINV)
     got = out.cpu().reshape(U.shape)

@@ -12,7 +12,7 @@ import torch
 import cdg2_inputs as I
 from oracle import cdg2_oracle as O
 from oracle import cdg2_tri_oracle as T
-from helpers import rel_l2_per_species
+from helpers import lift_into_domain, psi_max_tri, rel_l2_per_species
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +33,8 @@ def _params():
 
 def _state(om, seed):
     cen, amp = I.gaussian_draws(2, (1.0, 0.2), 4, seed)
-    return T.project(om, lambda x: O.gaussian_field(om, x, cen, amp, 0.08, 1e-3))
+    U = T.project(om, lambda x: O.gaussian_field(om, x, cen, amp, 0.08, 1e-3))
+    return lift_into_domain(U, psi_max_tri(om.k))
 
 
 def _run(G, xy, tri, k, p, U, flags):
@@ -66,7 +67,7 @@ def test_tri_apply_ties_and_relabelled_vertices(G, k):
     for t in (tri, rel):
         om = T.TriMesh(xy, t, k)
         p = _params()
-        U = torch.from_numpy(I.random_coefficients(om.E, om.nb, 3, 0.1))
+        U = lift_into_domain(torch.from_numpy(I.random_coefficients(om.E, om.nb, 3, 0.1)), psi_max_tri(om.k))
         got = _run(G, xy, t, k, p, U, G.CDG2_MINV)
         assert rel_l2_per_species(got, T.apply(om, U, p)) <= 1e-12
 
@@ -103,7 +104,7 @@ def test_tri_apply_full_size_sampled_rows(G):
     xy, tri = I.tri_mesh(w.nx, w.ny, 1.0, 0.2, w.jitter, w.seed)
     gm = G.cdg2_tri_mesh_create(xy, tri, w.k)
     p = _params()
-    U = torch.from_numpy(I.random_coefficients(gm.n_elem, gm.n_basis, w.seed, 0.1))
+    U = lift_into_domain(torch.from_numpy(I.random_coefficients(gm.n_elem, gm.n_basis, w.seed, 0.1)), psi_max_tri(w.k))
     out = torch.empty(gm.n_dof, dtype=torch.float64, device="cuda")
     G.cdg2_tri_apply(gm, p, U.reshape(-1).cuda(), out, G.CDG2_MINV)
     got = out.cpu().reshape(U.shape)

@@ -3,7 +3,10 @@
 Its scratch is a fixed device array inside the library instead of a cudaMalloc'd
 workspace.  Checked through the C ABI against cdg2_vjp on two calls in a row
 (the array is reused and must not carry state between calls), within the VJP
-tests' tolerance, and oversize meshes must be refused with an error.  This
+tests' tolerance; the second call must leave the device's free memory
+unchanged (the first call on a device may load the module that holds the
+array); a call without gtheta needs no scratch; and oversize meshes must be
+refused with an error.  This
 file sorts last so a run that stops at the first failure has run every other
 test first; it also passes alone in a fresh process.
 """
@@ -57,10 +60,29 @@ def test_noalloc_matches_cdg2_vjp_twice(lib, dim, cells, k):
         G.cdg2_vjp(mesh, p, U, lam, ref_gU, ref_gth, G.CDG2_MINV)
         gU = torch.full_like(U, float("nan"))
         gth = torch.full((8,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         _noalloc(lib, G, mesh, p, U, lam, gU, gth, G.CDG2_MINV)
         torch.cuda.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free_before
         assert rel_l2_per_species(gU, ref_gU.cpu().reshape(mesh.shape)) <= TOL
         assert float((gth - ref_gth).abs().max() / ref_gth.abs().max()) <= TOL
+
+
+def test_noalloc_without_gtheta(lib):
+    import paper_1403_1157_gb300 as G
+    mesh = G.cdg2_mesh_create(2, (13, 5), (1.0, 0.2), (1, 0), 2)
+    p = I.default_params()
+    U = torch.from_numpy(I.random_coefficients(mesh.n_elem, mesh.n_basis, 12)).cuda()
+    lam = (torch.from_numpy(I.random_coefficients(mesh.n_elem, mesh.n_basis, 13)) - 1.0).cuda()
+    ref = torch.empty_like(U)
+    G.cdg2_vjp(mesh, p, U, lam, ref, None, G.CDG2_MINV)
+    for _ in range(2):
+        gU = torch.full_like(U, float("nan"))
+        _noalloc(lib, G, mesh, p, U, lam, gU, None, G.CDG2_MINV)
+        torch.cuda.synchronize()
+        assert rel_l2_per_species(gU, ref.cpu().reshape(mesh.shape)) <= TOL
 
 
 def test_noalloc_refuses_meshes_beyond_its_scratch(lib):

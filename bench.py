@@ -232,7 +232,12 @@ def time_op(G, torch, fn, steps, warmup, flush):
 # Algorithmic HBM bytes per DOF of one launch sequence: read the inputs and
 # write the result once (neighbour traces re-read from L2 are not counted).
 BYTES_PER_DOF = {("apply", "f64"): 16, ("apply", "f32"): 8, ("jvp", "f64"): 24, ("jvp", "f32"): 12,
-                 ("vjp", "f64"): 24, ("vjp", "f32"): 12}
+                 ("vjp", "f64"): 24, ("vjp", "f32"): 12, ("apply", "tf32"): 8, ("jvp", "tf32"): 12}
+
+# Tensor-core flops per element of the TF32 element kernel (3D Q3, dense per
+# element, padded to 128 points): forward 128 x 64 x (6 values + 3 x 3
+# gradients) x 2 per field, test 64 x 128 x (6 + 3 x 2) x 2.
+TC_FLOPS_PER_ELEMENT = {"apply": 2 * 128 * 64 * 15 + 2 * 64 * 128 * 12, "jvp": 2 * 2 * 128 * 64 * 15 + 2 * 64 * 128 * 12}
 
 # Floating-point operations per element of one launch sequence (face kernels +
 # element kernel), measured: 2 x FMA + ADD + MUL instructions executed
@@ -279,6 +284,12 @@ def leg(w, ms, op, dtype, peaks):
     n = w.n_dof
     gb_s = BYTES_PER_DOF[(op, dtype)] * n / (ms * 1e-3) / 1e9
     out = {"ms": ms, "value": n / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "hbm_frac": gb_s / peaks["hbm_gbs"]}
+    if dtype == "tf32":
+        tf = TC_FLOPS_PER_ELEMENT[op] * w.n_elem / (ms * 1e-3) / 1e12
+        out.update({"tensor_tflops": tf, "tensor_frac_of_tf32_nominal": tf / 1125.0,
+                    "tensor_note": "dense TF32 GEMM flops of the element kernel's contractions (all its launches "
+                                   "in the time); nominal dense TF32 rate 1.125 PFLOP/s (half of bf16)"})
+        return out
     fl, src = flops_per_element(w.dim, w.k, op, dtype)
     if fl is not None:
         tf = fl * w.n_elem / (ms * 1e-3) / 1e12
@@ -311,6 +322,10 @@ def measure_operator(G, torch, w, mesh, p, U, flush, steps, peaks, with_fp64_app
     }
     if with_fp64_apply:
         cases[("apply", "f64")] = lambda: G.cdg2_apply(mesh, p, U, res, G.CDG2_MINV | A)
+    if w.dim == 3 and w.k == 3:
+        TF = G.CDG2_MINV | G.CDG2_FP32 | G.CDG2_TF32 | A
+        cases[("apply", "tf32")] = lambda: G.cdg2_apply(mesh, p, U32, res32, TF)
+        cases[("jvp", "tf32")] = lambda: G.cdg2_jvp(mesh, p, U32, lam32, res32, TF)
     out = {}
     for (op, dt), fn in cases.items():
         ms = time_op(G, torch, fn, steps, 3, flush)
@@ -321,6 +336,9 @@ def measure_operator(G, torch, w, mesh, p, U, flush, steps, peaks, with_fp64_app
     ref64 = torch.empty_like(U)
     G.cdg2_apply(mesh, p, U32.double(), ref64, G.CDG2_MINV)
     out["apply_f32"]["rel_l2_err_vs_fp64_max_species"] = rel_err_per_species(torch, out32, ref64, w)
+    if w.dim == 3 and w.k == 3:
+        G.cdg2_apply(mesh, p, U32, out32, G.CDG2_MINV | G.CDG2_FP32 | G.CDG2_TF32)
+        out["apply_tf32"]["rel_l2_err_vs_fp64_max_species"] = rel_err_per_species(torch, out32, ref64, w)
     return out
 
 
@@ -419,7 +437,10 @@ def measure_solve(G, torch, cfg: int, steps: int, precond: int):
     result = {"workload": w.name, "n_dof": w.n_dof, "dt": w.dt, "steps": steps, "scheme": f"SDIRK{scheme}",
               "newton_rtol": 1e-10, "precond": {1: "modal diagonal", 2: "element-block Jacobi"}.get(precond, "none")}
     finals = {}
-    for mode, mixed, eta in (("fp64", False, 1e-3), ("mixed", True, 1e-4)):
+    modes = [("fp64", 0, 1e-3), ("mixed", 1, 1e-4)]
+    if w.dim == 3 and w.k == 3:
+        modes.append(("mixed_tf32", 2, 1e-4))
+    for mode, mixed, eta in modes:
         U = U0.clone()
         # one untimed step warms up the kernels and allocates the workspace
         G.cdg2_step(mesh, p, U.clone(), 0.0, w.dt, G.make_opts(scheme=scheme, mixed=mixed, newton_rtol=1e-10,
@@ -443,6 +464,10 @@ def measure_solve(G, torch, cfg: int, steps: int, precond: int):
     d = finals["mixed"] - finals["fp64"]
     result["mixed_vs_fp64_rel_l2"] = float(d.norm() / finals["fp64"].norm())
     result["speedup_mixed_over_fp64"] = result["fp64"]["s_per_step"] / result["mixed"]["s_per_step"]
+    if "mixed_tf32" in finals:
+        d = finals["mixed_tf32"] - finals["fp64"]
+        result["mixed_tf32_vs_fp64_rel_l2"] = float(d.norm() / finals["fp64"].norm())
+        result["speedup_mixed_tf32_over_fp64"] = result["fp64"]["s_per_step"] / result["mixed_tf32"]["s_per_step"]
     return result
 
 
@@ -651,8 +676,8 @@ def main():
             ext = tuple(w.extent[a] * cells[a] / w.cells[a] for a in range(w.dim))
             mesh = G.cdg2_mesh_create(w.dim, cells, ext, w.periodic, w.k)
             U, p = make_inputs(G, w, I, mesh)
-            fl = G.CDG2_MINV | (G.CDG2_FP32 if dt == "f32" else 0)
-            if dt == "f32":
+            fl = G.CDG2_MINV | (G.CDG2_FP32 if dt in ("f32", "tf32") else 0) | (G.CDG2_TF32 if dt == "tf32" else 0)
+            if dt in ("f32", "tf32"):
                 U = U.float()
             lam = torch.sin(torch.arange(U.numel(), device="cuda", dtype=U.dtype) * 0.37)
             out = torch.empty_like(U)

@@ -65,6 +65,8 @@ extern "C" {
 #define CDG2_FORCING 2   /* add the manufactured-solution forcing at time t */
 #define CDG2_FP32 4      /* arrays are float32 and the kernel computes in FP32 */
 #define CDG2_ASYNC 8     /* do not wait for the domain check (see "Domain" below) */
+#define CDG2_TF32 16     /* with CDG2_FP32 on 3D Q3 meshes (apply, JVP): the element
+                            contractions on the tensor cores in TF32 (FP32 accumulation) */
 
 /* diffusion fluxes of cdg2_mesh_desc.flux */
 #define CDG2_FLUX_CDG2 0
@@ -139,7 +141,9 @@ typedef struct cdg2_params {
  *   SDIRK methods of Alexander (orders 2, 3) and Hairer-Wanner (order 4)).
  * mixed: 0 = FP64 Krylov vectors and FP64 JVP; 1 = FP32 Krylov vectors, FP32
  *   JVP about an FP32 copy of the stage iterate, FP64 Newton residual and
- *   update (iterative refinement).
+ *   update (iterative refinement); 2 = as 1 with the JVP's element
+ *   contractions on the tensor cores in TF32 (CDG2_TF32; 3D Q3 meshes only).
+ *   The adjoint step treats 2 as 1.
  * flags: 0 or CDG2_FORCING (manufactured-solution forcing at stage times).
  * Newton stops when ||G||_2 <= max(newton_rtol ||G(Y^0)||_2, newton_atol),
  *   G(Y) = Y - dt a_ii f(Y) - rhs_i, Y^0 the previous stage value (U_n first);
@@ -218,7 +222,15 @@ int cdg2_mesh_status(const cdg2_mesh* mesh, void* stream);
  * Each face is evaluated once into a per-mesh face buffer that the first
  * cdg2_apply or cdg2_jvp on the mesh allocates (cudaMalloc, about
  * 2*6*(k+1)^(dim-1) doubles per face); calls sharing a mesh must therefore
- * be ordered on one stream.  flags may add CDG2_ASYNC.  Errors: INVALID_ARG,
+ * be ordered on one stream.  flags may add CDG2_ASYNC, and on 3D Q3 meshes
+ * with CDG2_FP32 also CDG2_TF32: the volume terms' basis-to-quadrature and
+ * quadrature-to-basis contractions then run as TF32 GEMMs on the tensor
+ * cores (16 elements per thread block, accumulators in tensor memory); the
+ * pointwise model, the faces and the modal diffusion stay in FP32.  Meant
+ * for the inner Krylov operator of the mixed solver: the JVP along a rough
+ * tangent keeps about 5e-5 relative to FP64; on smooth states the apply of
+ * n1 and n2 (whose fluxes go through the tensor cores) loses 1e-3 to 4e-3 to
+ * the cancellation of the weak form.  Errors: INVALID_ARG,
  * CUDA, DOMAIN (y + chith <= 0 at a quadrature point; out undefined). */
 int cdg2_apply(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, void* out,
                int flags, double t, void* stream);

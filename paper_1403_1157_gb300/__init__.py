@@ -19,13 +19,14 @@ __all__ = [
     "cdg2_project_gaussians", "cdg2_project_mms", "cdg2_jvp", "cdg2_vjp", "cdg2_step",
     "CDG2_SDIRK2", "CDG2_SDIRK3", "CDG2_SDIRK4", "SolverOpts", "Stats", "make_opts", "cdg2_step_stages", "cdg2_step_adjoint",
     "stages_of", "CDG2_ASYNC", "CDG2_ERR_DOMAIN", "cdg2_mesh_status", "cdg2_tri_mesh_status", "cdg2_tet_mesh_status",
-    "cdg2_probe_peak",
+    "cdg2_probe_peak", "CDG2_TF32",
 ]
 
 CDG2_MINV = 1
 CDG2_FORCING = 2
 CDG2_FP32 = 4
 CDG2_ASYNC = 8
+CDG2_TF32 = 16
 CDG2_ERR_INVALID_ARG = -1
 CDG2_ERR_CUDA = -2
 CDG2_ERR_NOT_CONVERGED = -3
@@ -564,7 +565,8 @@ def cdg2_vjp(mesh: Mesh, params, U: torch.Tensor, lam: torch.Tensor, gU: torch.T
 def make_opts(scheme=CDG2_SDIRK2, mixed=False, flags=0, max_newton=20, gmres_restart=30, max_gmres=300,
               newton_rtol=1e-10, newton_atol=0.0, gmres_rtol=1e-3, precond=1) -> SolverOpts:
     o = SolverOpts()
-    o.scheme, o.mixed, o.flags, o.max_newton = int(scheme), int(bool(mixed)), int(flags), int(max_newton)
+    o.scheme, o.flags, o.max_newton = int(scheme), int(flags), int(max_newton)
+    o.mixed = int(mixed) if not isinstance(mixed, bool) else int(mixed)   # 0, 1 (FP32) or 2 (TF32 tensor cores)
     o.gmres_restart, o.max_gmres = int(gmres_restart), int(max_gmres)
     o.newton_rtol, o.newton_atol, o.gmres_rtol = float(newton_rtol), float(newton_atol), float(gmres_rtol)
     o.precond = int(precond)

@@ -42,6 +42,11 @@ int take_domain_status(int* word, cudaStream_t st, const char* who) {
     if (h == 0) return CDG2_OK;
     e = cudaMemsetAsync(word, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(e, who);
+    if (h & 2) {
+        set_error(std::string(who) + ": a wait for the tensor cores timed out in the element kernel; its result is "
+                  "undefined");
+        return CDG2_ERR_CUDA;
+    }
     set_error(std::string(who) + ": a chemotactic sensitivity chi0 x / (y + chith) met y + chith <= 0 at a "
               "quadrature point (the pole of chi, Sec. 2): the state is outside the model's domain");
     return CDG2_ERR_DOMAIN;
@@ -227,6 +232,7 @@ void cdg2_mesh_destroy(cdg2_mesh* m) {
     if (m->step_ws) cudaFree(m->step_ws);
     if (m->fbuf) cudaFree(m->fbuf);
     if (m->status) cudaFree(m->status);
+    if (m->tc_tables) cudaFree(m->tc_tables);
     delete m;
 }
 
@@ -238,6 +244,16 @@ int cdg2_mesh_info(const cdg2_mesh* m, long long* n_elem, int* n_basis, long lon
     if (n_elem) *n_elem = m->geo.E;
     if (n_basis) *n_basis = m->nb;
     if (n_dof) *n_dof = m->ndof;
+    return CDG2_OK;
+}
+
+// CDG2_TF32 (tensor-core contractions) is built for FP32 arrays on 3D Q3 meshes.
+static int check_tf32(const cdg2_mesh& m, int flags, const char* who) {
+    if (!(flags & CDG2_TF32)) return CDG2_OK;
+    if (!(flags & CDG2_FP32) || m.geo.dim != 3 || m.geo.k != 3) {
+        set_error(std::string(who) + ": CDG2_TF32 needs CDG2_FP32 and a 3D mesh of degree 3");
+        return CDG2_ERR_INVALID_ARG;
+    }
     return CDG2_OK;
 }
 
@@ -259,10 +275,11 @@ int cdg2_apply(const cdg2_mesh* m, const cdg2_params* p, const void* U, void* ou
         set_error("cdg2_apply: U and out must not overlap");
         return CDG2_ERR_INVALID_ARG;
     }
-    if (flags & ~(CDG2_MINV | CDG2_FORCING | CDG2_FP32 | CDG2_ASYNC)) {
+    if (flags & ~(CDG2_MINV | CDG2_FORCING | CDG2_FP32 | CDG2_ASYNC | CDG2_TF32)) {
         set_error("cdg2_apply: unknown flag bits");
         return CDG2_ERR_INVALID_ARG;
     }
+    if (int rc = check_tf32(*m, flags, "cdg2_apply")) return rc;
     Coef c = make_coef(*p);
     cudaError_t e = launch_apply(*m, c, U, out, flags, t, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cdg2_apply");
@@ -281,10 +298,11 @@ int cdg2_jvp(const cdg2_mesh* m, const cdg2_params* p, const void* U, const void
         set_error("cdg2_jvp: out must not overlap U or dU");
         return CDG2_ERR_INVALID_ARG;
     }
-    if (flags & ~(CDG2_MINV | CDG2_FORCING | CDG2_FP32 | CDG2_ASYNC)) {
+    if (flags & ~(CDG2_MINV | CDG2_FORCING | CDG2_FP32 | CDG2_ASYNC | CDG2_TF32)) {
         set_error("cdg2_jvp: unknown flag bits");
         return CDG2_ERR_INVALID_ARG;
     }
+    if (int rc = check_tf32(*m, flags, "cdg2_jvp")) return rc;
     Coef c = make_coef(*p);
     cudaError_t e = launch_jvp(*m, c, U, dU, dtheta, out, flags, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cdg2_jvp");

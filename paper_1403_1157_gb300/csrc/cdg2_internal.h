@@ -122,6 +122,8 @@ struct cdg2_mesh {
     mutable size_t step_ws_bytes = 0;
     // Domain status word (device int): set by a kernel that meets c + chi^th <= 0.
     mutable int* status = nullptr;
+    // Table images of the tensor-core element kernel (3D Q3, CDG2_TF32), built by its first launch.
+    mutable void* tc_tables = nullptr;
 };
 
 namespace cdg2 {

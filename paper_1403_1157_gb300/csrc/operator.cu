@@ -646,6 +646,12 @@ __device__ __forceinline__ void faces_expand(const Geo& g, const STab<K, T>& tb,
     __syncthreads();
 }
 
+}  // namespace cdg2
+
+#include "tc_elem.cuh"
+
+namespace cdg2 {
+
 template <int D, int K, int MODE, typename T>
 __global__ void __launch_bounds__(128) op_kernel(const Geo g, const TabP<T> tab, const OpArgs<T> args) {
     constexpr int F = fields_of(MODE);
@@ -997,6 +1003,77 @@ static long long grid_of(const cdg2_mesh& m) {
     return (m.geo.E + epb - 1) / epb;
 }
 
+// The face kernels of the face-once path for axis 0..D-1 (each face once, its
+// tested fluxes into the mesh's face buffer), with their one-time attributes.
+template <int D, int K, int MODE, typename T>
+static cudaError_t launch_faces(const cdg2_mesh& m, OpArgs<T>& a, cudaStream_t st) {
+    if (!m.fbuf) {
+        const size_t bytes = face_buffer_bytes(m.geo);
+        cudaError_t e = cudaMalloc(&m.fbuf, bytes);
+        if (e != cudaSuccess) return e;
+        m.fbuf_bytes = bytes;
+    }
+    using FPl = FacePlan<D, K, fields_of(MODE)>;
+    constexpr size_t fsmem = FPl::template smem_bytes<T>();
+    static_assert(fsmem <= 227 * 1024, "face kernel shared memory exceeds 227 KB");
+    static DeviceOnce fattr;
+    {
+        cudaError_t e = once_per_device(fattr, [] {
+            cudaError_t r = cudaFuncSetAttribute(face_kernel<D, K, MODE, 0, T>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(face_kernel<D, K, MODE, 1, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+            if (r == cudaSuccess && D == 3)
+                r = cudaFuncSetAttribute(face_kernel<D, K, MODE, D == 3 ? 2 : 1, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+            return r;
+        });
+        if (e != cudaSuccess) return e;
+    }
+    a.fbuf = static_cast<T*>(m.fbuf);
+    constexpr long long per_face = 2LL * NS * Shape<D, K>::NBT;
+    long long off = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        a.fb_off[ax] = off;
+        if (ax < D) off += faces_of_axis(m.geo, ax) * per_face;
+    }
+    auto fgrid = [&](int ax) { return (unsigned)((faces_of_axis(m.geo, ax) + FPl::FPB - 1) / FPl::FPB); };
+    face_kernel<D, K, MODE, 0, T><<<fgrid(0), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
+    face_kernel<D, K, MODE, 1, T><<<fgrid(1), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
+    if constexpr (D == 3) face_kernel<D, K, MODE, 2, T><<<fgrid(2), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
+    return cudaSuccess;
+}
+
+// CDG2_TF32 on a 3D Q3 mesh: the face kernels (FP32), then the tensor-core
+// element kernel (16 elements per CTA).
+template <int MODE>
+static cudaError_t launch_tc(const cdg2_mesh& m, OpArgs<float> a, cudaStream_t st) {
+    if (!m.tc_tables) {
+        std::vector<float> img;
+        tc::build_tables(m.tab, m.geo, img);
+        cudaError_t e = cudaMalloc(&m.tc_tables, img.size() * sizeof(float));
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(m.tc_tables, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+    }
+    if (reinterpret_cast<uintptr_t>(a.U[0]) % 16 || reinterpret_cast<uintptr_t>(a.U[1]) % 16) return cudaErrorMisalignedAddress;
+    static DeviceOnce attr;
+    {
+        cudaError_t e = once_per_device(attr, [] {
+            return cudaFuncSetAttribute(tc_elem_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        tc::SMEM_BYTES);
+        });
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = launch_faces<3, 3, MODE, float>(m, a, st);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((m.geo.E + tc::NE - 1) / tc::NE);
+    tc_elem_kernel<MODE><<<blocks, 256, tc::SMEM_BYTES, st>>>(m.geo, m.tp32, a,
+                                                               static_cast<const float4*>(m.tc_tables));
+    return cudaGetLastError();
+}
+
 template <int D, int K, int MODE, typename T>
 static cudaError_t launch_one(const cdg2_mesh& m, const Coef& c, OpArgs<T> a, cudaStream_t st) {
     using P = OpPlan<D, K, fields_of(MODE)>;
@@ -1020,49 +1097,17 @@ static cudaError_t launch_one(const cdg2_mesh& m, const Coef& c, OpArgs<T> a, cu
         a.domain = m.status;
     }
     a.c.domain = a.domain;
+    if constexpr (D == 3 && K == 3 && std::is_same<T, float>::value && MODE != MODE_VJP) {
+        if (a.flags & CDG2_TF32) return launch_tc<MODE>(m, a, st);
+    }
     a.fbuf = nullptr;
     // Face-once for FP64 (bound by the FP64 pipe: halving the face arithmetic
     // pays) and for 2D; the fused path stays for FP32 in 3D, where the extra
     // launches and face loads cost more than the arithmetic they save.
     constexpr bool face_once = MODE != MODE_VJP && (sizeof(T) == 8 || D == 2);
     if constexpr (face_once) {
-        if (!m.fbuf) {
-            const size_t bytes = face_buffer_bytes(m.geo);
-            cudaError_t e = cudaMalloc(&m.fbuf, bytes);
-            if (e != cudaSuccess) return e;
-            m.fbuf_bytes = bytes;
-        }
-        {
-            using FPl = FacePlan<D, K, fields_of(MODE)>;
-            constexpr size_t fsmem = FPl::template smem_bytes<T>();
-            static_assert(fsmem <= 227 * 1024, "face kernel shared memory exceeds 227 KB");
-            static DeviceOnce fattr;
-            {
-                cudaError_t e = once_per_device(fattr, [] {
-                    cudaError_t r = cudaFuncSetAttribute(face_kernel<D, K, MODE, 0, T>,
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
-                    if (r == cudaSuccess)
-                        r = cudaFuncSetAttribute(face_kernel<D, K, MODE, 1, T>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
-                    if (r == cudaSuccess && D == 3)
-                        r = cudaFuncSetAttribute(face_kernel<D, K, MODE, D == 3 ? 2 : 1, T>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
-                    return r;
-                });
-                if (e != cudaSuccess) return e;
-            }
-            a.fbuf = static_cast<T*>(m.fbuf);
-            constexpr long long per_face = 2LL * NS * Shape<D, K>::NBT;
-            long long off = 0;
-            for (int ax = 0; ax < 3; ++ax) {
-                a.fb_off[ax] = off;
-                if (ax < D) off += faces_of_axis(m.geo, ax) * per_face;
-            }
-            auto fgrid = [&](int ax) { return (unsigned)((faces_of_axis(m.geo, ax) + FPl::FPB - 1) / FPl::FPB); };
-            face_kernel<D, K, MODE, 0, T><<<fgrid(0), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
-            face_kernel<D, K, MODE, 1, T><<<fgrid(1), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
-            if constexpr (D == 3) face_kernel<D, K, MODE, 2, T><<<fgrid(2), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
-        }
+        cudaError_t e = launch_faces<D, K, MODE, T>(m, a, st);
+        if (e != cudaSuccess) return e;
     }
     op_kernel<D, K, MODE, T><<<(unsigned)blocks, P::NT, smem, st>>>(m.geo, tab_of<T>(m), a);
     return cudaGetLastError();

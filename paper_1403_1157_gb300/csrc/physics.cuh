@@ -30,7 +30,7 @@ __device__ __forceinline__ void kappa_den(const CoefT<T>& c, const T u[NS], T* d
     den[2] = u[3] + T(c.chith[2]);
     den[3] = u[0] + T(c.chith[3]);
     const int m = min(min(hi_word(den[0]), hi_word(den[1])), min(hi_word(den[2]), hi_word(den[3])));
-    if (m <= 0 && c.domain != nullptr) *c.domain = 1;
+    if (m <= 0 && c.domain != nullptr) atomicOr(c.domain, 1);
 }
 
 // Volume flux at one quadrature point (Eq. elementint): Phi_s = F_s(U, grad U)

@@ -281,7 +281,7 @@ struct CartKrylovOp {
     int flags;
     bool adjoint;
     int mv(const T* v, T* tmp, T* out, cudaStream_t st) const {
-        const int jflags = CDG2_MINV | ((sizeof(T) == 4) ? CDG2_FP32 : 0) | (flags & CDG2_FORCING);
+        const int jflags = CDG2_MINV | ((sizeof(T) == 4) ? CDG2_FP32 | (flags & CDG2_TF32) : 0) | (flags & CDG2_FORCING);
         CDG2_TRY(matvec<T>(adjoint, m, c, Yop, v, gdt, pc, tmp, out, jflags, st));
         return CDG2_OK;
     }
@@ -446,9 +446,9 @@ using namespace cdg2;
 static int check_opts(const cdg2_solver_opts* o, double dt, const char* who) {
     if ((o->scheme != CDG2_SDIRK2 && o->scheme != CDG2_SDIRK3 && o->scheme != CDG2_SDIRK4) || o->gmres_restart < 1 ||
         o->gmres_restart > MAX_KRYLOV || o->max_newton < 1 || o->max_gmres < 1 || !(dt > 0.0) ||
-        (o->flags & ~CDG2_FORCING) || (o->precond < 0 || o->precond > 2)) {
+        (o->flags & ~CDG2_FORCING) || (o->precond < 0 || o->precond > 2) || o->mixed < 0 || o->mixed > 2) {
         set_error(std::string(who) + ": invalid options (scheme 2|3|4, 1 <= gmres_restart <= 64, max_newton, "
-                  "max_gmres >= 1, dt > 0, flags in {0, CDG2_FORCING}, precond in {0, 1, 2})");
+                  "max_gmres >= 1, dt > 0, flags in {0, CDG2_FORCING}, precond in {0, 1, 2}, mixed in {0, 1, 2})");
         return CDG2_ERR_INVALID_ARG;
     }
     return CDG2_OK;
@@ -541,8 +541,13 @@ static int run_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double 
         return CDG2_ERR_INVALID_ARG;
     }
     if (int rc = check_opts(o, dt, "cdg2_step")) return rc;
+    if (o->mixed == 2 && (m->geo.dim != 3 || m->geo.k != 3)) {
+        set_error("cdg2_step: mixed = 2 (tensor-core TF32 Krylov operator) needs a 3D mesh of degree 3");
+        return CDG2_ERR_INVALID_ARG;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const bool mixed = o->mixed != 0;
+    const int kflags = o->flags | (o->mixed == 2 ? CDG2_TF32 : 0);   // flags of the Krylov operator
     Work w;
     if (int rc = ensure_work(*m, o->gmres_restart, mixed, w)) return rc;
     CDG2_TRY(ensure_status(&m->status));
@@ -570,7 +575,7 @@ static int run_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double 
             CDG2_TRY(vec_convert<double, float>(n, w.Y, 1.0, static_cast<float*>(w.Yk), st));
             CDG2_TRY(vec_convert<double, float>(n, w.G, -1.0, static_cast<float*>(w.bk), st));
             rc = gmres<float>(*m, c, static_cast<float*>(w.Yk), gdt, static_cast<float*>(w.bk),
-                              static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, o->flags, pc, its,
+                              static_cast<float*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, kflags, pc, its,
                               &S.gmres_reorth, rr);
             if (rc == CDG2_OK) CDG2_TRY(vec_add_into<float>(n, static_cast<float*>(w.dx), w.Y, st));
         }

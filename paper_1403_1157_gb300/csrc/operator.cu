@@ -90,6 +90,13 @@ struct OpArgs {
 constexpr int MODE_APPLY = 0, MODE_JVP = 1, MODE_VJP = 2;
 constexpr int fields_of(int mode) { return mode == MODE_APPLY ? 1 : 2; }
 
+// The input field fi without a run-time index into the kernel arguments (an
+// indexed parameter access goes through slow indexed constant loads).
+template <typename T>
+__device__ __forceinline__ const T* field(const OpArgs<T>& a, int fi) {
+    return fi == 0 ? a.U[0] : a.U[1];
+}
+
 // ---------------------------------------------------------------------------
 // The two faces normal to axis A of every element of the CTA
 // ---------------------------------------------------------------------------
@@ -138,7 +145,7 @@ __device__ __forceinline__ void op_faces(const Geo& g, const STab<K, T>& tb, con
         }
         const long long nb = nbr[e][f];
         if (nb >= 0) {
-            const T* nbg = args.U[fi] + (nb * NS + s) * NB;
+            const T* nbg = field(args, fi) + (nb * NS + s) * NB;
             T nbv[NB1];   // the neighbour's coefficients along the normal line (tangent: preconditioned)
             const bool scaled = MODE != MODE_APPLY && fi == 1 && ps != nullptr;
 #pragma unroll
@@ -432,16 +439,39 @@ __global__ void __launch_bounds__(128) face_kernel(const Geo g, const TabP<T> ta
         kind[threadIdx.x] = kd;
     }
     __syncthreads();
-    // coalesced loads of both cells of every face (the tangent pre-scaled)
-    for (int i = threadIdx.x; i < 2 * F * P::UB; i += blockDim.x) {
-        const int side = i / (F * P::UB);
-        const int r0 = i % (F * P::UB);
-        const int fi = r0 / P::UB, r = r0 % P::UB;
-        const int j = r / (NS * NB), q = r % (NS * NB);
-        const long long cell = side ? cp[j] : cm[j];
-        T v = cell >= 0 ? args.U[fi][cell * NS * NB + q] : T(0);
-        if (MODE == MODE_JVP && fi == 1 && ps) v *= ps[q];
-        (side ? sP : sM)[r0] = v;
+    // coalesced loads of both cells of every face (the tangent pre-scaled), a
+    // batch of independent loads per thread in flight at once
+    {
+        constexpr int TOT = 2 * F * P::UB, BATCH = 8;
+        for (int i0 = threadIdx.x; i0 < TOT; i0 += BATCH * blockDim.x) {
+            T v[BATCH];
+#pragma unroll
+            for (int b = 0; b < BATCH; ++b) {
+                const int i = i0 + b * blockDim.x;
+                v[b] = T(0);
+                if (i < TOT) {
+                    const int side = i / (F * P::UB);
+                    const int r0 = i % (F * P::UB);
+                    const int fi = r0 / P::UB, r = r0 % P::UB;
+                    const int j = r / (NS * NB), q = r % (NS * NB);
+                    const long long cell = side ? cp[j] : cm[j];
+                    if (cell >= 0) v[b] = field(args, fi)[cell * NS * NB + q];
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < BATCH; ++b) {
+                const int i = i0 + b * blockDim.x;
+                if (i < TOT) {
+                    const int side = i / (F * P::UB);
+                    const int r0 = i % (F * P::UB);
+                    const int fi = r0 / P::UB, r = r0 % P::UB;
+                    const int q = r % (NS * NB);
+                    T w = v[b];
+                    if (MODE == MODE_JVP && fi == 1 && ps) w *= ps[q];
+                    (side ? sP : sM)[r0] = w;
+                }
+            }
+        }
     }
     __syncthreads();
 
@@ -678,12 +708,30 @@ __global__ void __launch_bounds__(128) op_kernel(const Geo g, const TabP<T> tab,
     }
     __syncthreads();
     const CoefT<T>& c = args.c;
-    for (int i = threadIdx.x; i < F * P::UR; i += blockDim.x) {
-        const int fi = i / P::UR, r = i % P::UR;
-        const long long ge = e0 + r / (NS * NB);
-        T v = ge < g.E ? args.U[fi][e0 * NS * NB + r] : T(0);
-        if (MODE != MODE_APPLY && fi == 1 && ps) v *= ps[r % (NS * NB)];
-        sU[i] = v;
+    {
+        constexpr int TOT = F * P::UR, BATCH = 8;
+        for (int i0 = threadIdx.x; i0 < TOT; i0 += BATCH * blockDim.x) {
+            T v[BATCH];
+#pragma unroll
+            for (int b = 0; b < BATCH; ++b) {
+                const int i = i0 + b * blockDim.x;
+                v[b] = T(0);
+                if (i < TOT) {
+                    const int fi = i / P::UR, r = i % P::UR;
+                    if (e0 + r / (NS * NB) < g.E) v[b] = field(args, fi)[e0 * NS * NB + r];
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < BATCH; ++b) {
+                const int i = i0 + b * blockDim.x;
+                if (i < TOT) {
+                    const int fi = i / P::UR, r = i % P::UR;
+                    T w = v[b];
+                    if (MODE != MODE_APPLY && fi == 1 && ps) w *= ps[r % (NS * NB)];
+                    sU[i] = w;
+                }
+            }
+        }
     }
     __syncthreads();
 
@@ -1069,7 +1117,7 @@ static cudaError_t launch_tc(const cdg2_mesh& m, OpArgs<float> a, cudaStream_t s
     cudaError_t e = launch_faces<3, 3, MODE, float>(m, a, st);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((m.geo.E + tc::NE - 1) / tc::NE);
-    tc_elem_kernel<MODE><<<blocks, 256, tc::SMEM_BYTES, st>>>(m.geo, m.tp32, a,
+    tc_elem_kernel<MODE><<<blocks, tc::NT, tc::SMEM_BYTES, st>>>(m.geo, m.tp32, a,
                                                                static_cast<const float4*>(m.tc_tables));
     return cudaGetLastError();
 }

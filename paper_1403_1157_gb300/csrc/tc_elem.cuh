@@ -3,7 +3,7 @@
 // Eq. elementint) as TF32 GEMMs on the fifth-generation tensor cores
 // (tcgen05.mma, accumulators in tensor memory), batched over 16 elements.
 //
-// Per CTA (16 consecutive elements, 256 threads, one CTA per SM):
+// Per CTA (16 consecutive elements, 512 threads, one CTA per SM):
 //   1. the forward table image (128 points x 64 modes: psi, dpsi/dx, dpsi/dy,
 //      dpsi/dz at the 5^3 Gauss points, rows 125..127 zero) is copied to shared
 //      memory, and the coefficients of both fields, rounded to TF32, are
@@ -20,9 +20,11 @@
 //      (linearised) flux and source, and writes them as the test MMAs' B
 //      operands;
 //   4. the test MMAs (M = 64 modes) accumulate the volume residual in tensor
-//      memory; it goes to shared memory, the modal diffusion of n2..c3 and the
-//      two tested face fluxes per axis (face buffer of the face kernels) are
-//      added, and the epilogue (M^{-1}, alpha w + beta J w) stores.
+//      memory; it goes to shared memory while bulk copies bring the tile's
+//      coefficients and the tested fluxes of its faces (the face kernels'
+//      buffer) into the freed table region; the modal diffusion of n2..c3 and
+//      the two tested face fluxes per axis are added from shared memory, and
+//      the epilogue (M^{-1}, alpha w + beta J w) stores.
 // Operands use the 128-byte-swizzled K-major layout (TF32 operands must be
 // K-major).  Every wait on an mbarrier is bounded: on time-out the kernel sets
 // bit 1 of the status word, frees its tensor memory and returns.
@@ -39,6 +41,7 @@ namespace cdg2 {
 namespace tc {
 
 constexpr int NE = 16;                        // elements per CTA
+constexpr int NT = 512;                       // threads per CTA: 4 groups of 4 elements x 4 lane quarters
 constexpr int NB = 64, NQ = 125, NP = 128;    // modes, Gauss points, padded points (3D Q3)
 constexpr int TAB_BYTES = 4 * NP * NB * 4;    // one table set: 4 tables of 128 x 64 (or 64 x 128) floats
 constexpr int TAB1 = NP * NB * 4;             // one table
@@ -52,7 +55,11 @@ constexpr int FIELD_COLS = 240;               // per field: 96 value columns, 3 
 // dynamic shared memory: 1 KB of slack to align the swizzled images to 1024 B,
 // the table set, the operand region, then the small arrays
 constexpr int SMALL_OFF = TAB_BYTES + OPS_BYTES;
-constexpr int SMALL_BYTES = 2048;             // STab<3, float> (1000 B), fid (256 B), 2 mbarriers, tmem slot
+constexpr int SMALL_BYTES = 2048;             // STab<3, float> (1000 B), 5 mbarriers, tmem slot
+// epilogue staging in the table region: the tested fluxes of each element's two faces
+// per axis ([axis][element][lo, hi] records of 2 x 6 x 16 floats), then the tile's coefficients
+constexpr int FACE_REC = 2 * NS * 16 * 4;     // 768 B
+constexpr int EPI_COEF = 3 * NE * 2 * FACE_REC;   // 73728: offset of the coefficients (NE x 1536 B)
 constexpr int SMEM_BYTES = 1024 + SMALL_OFF + SMALL_BYTES;
 
 // forward species order -> species; the first three have gradients
@@ -134,10 +141,23 @@ __device__ __forceinline__ void ld_x8(uint32_t a, float* v) {
 
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Round to the nearest TF32 value (ties away from zero) with two integer
+// operations (finite inputs; the conversion instruction is slower here).
 __device__ __forceinline__ float to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// One thread: expect `bytes` on the mbarrier and copy them from global to
+// shared memory with bulk asynchronous copies of 16 KB (16-byte aligned,
+// sizes multiples of 16), completing on the mbarrier.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+    for (uint32_t off = 0; off < bytes; off += 16384) {
+        const uint32_t n = bytes - off < 16384 ? bytes - off : 16384;
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(dst + off), "l"(static_cast<const char*>(src) + off), "r"(n), "r"(bar)
+                     : "memory");
+    }
 }
 
 // Host: round to the nearest TF32 value (10-bit mantissa), ties away from zero.
@@ -183,7 +203,7 @@ inline void build_tables(const Tab1D& t, const Geo& g, std::vector<float>& img) 
 
 // The tensor-core element kernel.  F = 1 (apply) or 2 (JVP: U and the tangent).
 template <int MODE>
-__global__ void __launch_bounds__(256, 1) tc_elem_kernel(const Geo g, const TabP<float> tab, const OpArgs<float> args,
+__global__ void __launch_bounds__(512, 1) tc_elem_kernel(const Geo g, const TabP<float> tab, const OpArgs<float> args,
                                                         const float4* __restrict__ tables) {
     using namespace tc;
     constexpr int F = fields_of(MODE);
@@ -195,47 +215,60 @@ __global__ void __launch_bounds__(256, 1) tc_elem_kernel(const Geo g, const TabP
     unsigned char* sOps = smem + TAB_BYTES;              // forward operands, then test operands, then sR
     float* sR = reinterpret_cast<float*>(sOps);          // [NE][6][64] volume residual / |K|
     STab<K, float>& tb = *reinterpret_cast<STab<K, float>*>(smem + SMALL_OFF);
-    long long (*fid)[2] = reinterpret_cast<long long (*)[2]>(smem + SMALL_OFF + 1024);
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + SMALL_OFF + 1024 + 256);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SMALL_OFF + 1024 + 256 + 16);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SMALL_OFF + 1024 + 256 + 48);
     static_assert(sizeof(STab<K, float>) <= 1024, "tables of the face expansion exceed their slot");
     const int t = threadIdx.x;
     const long long e0 = (long long)blockIdx.x * NE;
     const uint32_t sbase = smem_u32(smem);
+    // bar0: forward MMAs done; bar1: test MMAs done; bar2 / bar3: forward / test tables copied;
+    // bar4: the epilogue's face records and coefficients copied
     const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+    const uint32_t bar2 = smem_u32(&bars[2]), bar3 = smem_u32(&bars[3]), bar4 = smem_u32(&bars[4]);
     const CoefT<float>& c = args.c;
 
-    load_tab<K, float>(tb, tab);
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar0));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar2));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar3));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar4));
         asm volatile("fence.mbarrier_init.release.cluster;");
+        // forward tables (already swizzled in global memory), copied while the coefficients are staged
+        bulk_load(sbase, tables, TAB_BYTES, bar2);
     }
-    // forward tables (already swizzled in global memory)
-    {
-        float4* dst = reinterpret_cast<float4*>(sTab);
-        for (int i = t; i < TAB_BYTES / 16; i += blockDim.x) dst[i] = __ldg(tables + i);
-    }
-    // coefficients of the 16 elements, TF32, species-major rows (tangent pre-scaled)
+    load_tab<K, float>(tb, tab);
+    // coefficients of the 16 elements, TF32, species-major rows (tangent pre-scaled);
+    // each thread's loads are issued together
+    constexpr int CH = NE * NS * (NB / 4);   // 16-byte chunks per field
+    static_assert(CH % NT == 0, "chunks per field must divide among the threads");
+#pragma unroll
     for (int fi = 0; fi < F; ++fi) {
-        const float* src = args.U[fi];
+        const float* src = fi == 0 ? args.U[0] : args.U[1];
         unsigned char* img = sOps + fi * FWD_FIELD;
-        for (int idx = t; idx < NE * NS * (NB / 4); idx += blockDim.x) {
+        float4 v[CH / NT];
+#pragma unroll
+        for (int j = 0; j < CH / NT; ++j) {
+            const int idx = t + NT * j;
             const int ch = idx % (NB / 4), s = (idx / (NB / 4)) % NS, e = idx / (NS * (NB / 4));
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (e0 + e < g.E) {
-                v = __ldg(reinterpret_cast<const float4*>(src + (e0 + e) * (NS * NB) + s * NB) + ch);
-                if (MODE == MODE_JVP && fi == 1 && args.pscale) {
-                    const double* ps = args.pscale + s * NB + 4 * ch;
-                    v.x *= float(ps[0]);
-                    v.y *= float(ps[1]);
-                    v.z *= float(ps[2]);
-                    v.w *= float(ps[3]);
-                }
+            v[j] = e0 + e < g.E ? __ldg(reinterpret_cast<const float4*>(src + (e0 + e) * (NS * NB) + s * NB) + ch)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < CH / NT; ++j) {
+            const int idx = t + NT * j;
+            const int ch = idx % (NB / 4), s = (idx / (NB / 4)) % NS, e = idx / (NS * (NB / 4));
+            float4 w = v[j];
+            if (MODE == MODE_JVP && fi == 1 && args.pscale) {
+                const double* ps = args.pscale + s * NB + 4 * ch;
+                w.x *= float(ps[0]);
+                w.y *= float(ps[1]);
+                w.z *= float(ps[2]);
+                w.w *= float(ps[3]);
             }
             const int r = fwd_slot(s) * NE + e, k = 4 * ch;
             *reinterpret_cast<float4*>(img + (k >> 5) * (ROWS * 128) + sw128(r, k & 31)) =
-                make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
+                make_float4(to_tf32(w.x), to_tf32(w.y), to_tf32(w.z), to_tf32(w.w));
         }
     }
     if (t < 32) {
@@ -250,7 +283,8 @@ __global__ void __launch_bounds__(256, 1) tc_elem_kernel(const Geo g, const TabP
     const uint32_t tm = *reinterpret_cast<volatile uint32_t*>(tslot);
 
     // ---- forward MMAs: values (N = 96) and gradients of n1, c1, c3 (N = 48) ----
-    if (t == 0) {
+    const bool tabs_in = __syncthreads_and(wait(bar2, 0)) != 0;
+    if (t == 0 && tabs_in) {
         for (int fi = 0; fi < F; ++fi) {
             const uint32_t bimg = sbase + TAB_BYTES + fi * FWD_FIELD;
             for (int tt = 0; tt < 4; ++tt) {
@@ -266,26 +300,25 @@ __global__ void __launch_bounds__(256, 1) tc_elem_kernel(const Geo g, const TabP
         }
         commit(bar0);
     }
-    bool ok = __syncthreads_and(wait(bar0, 0)) != 0;   // CTA-uniform: the tensor-memory loads below are warp-collective
+    // CTA-uniform: the tensor-memory loads below are warp-collective
+    bool ok = tabs_in && __syncthreads_and(wait(bar0, 0)) != 0;
     fence_after();
 
-    // ---- the test tables replace the forward ones (the forward MMAs are done) ----
-    if (ok) {
-        float4* dst = reinterpret_cast<float4*>(sTab);
-        for (int i = t; i < TAB_BYTES / 16; i += blockDim.x) dst[i] = __ldg(tables + TAB_BYTES / 16 + i);
-    }
+    // ---- the test tables replace the forward ones (the forward MMAs are done), copied during the pointwise phase ----
+    if (ok && t == 0) bulk_load(sbase, tables + TAB_BYTES / 16, TAB_BYTES, bar3);
 
-    // ---- pointwise: one point per thread, 8 elements per thread (two halves of the CTA) ----
+    // ---- pointwise: one point per thread, 4 elements per thread (4 groups of warps) ----
     const int warp = t >> 5, lane = t & 31;
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, group = warp >> 2;
     const int q = quarter * 32 + lane;
     const uint32_t tlane = tm + ((uint32_t)(quarter * 32) << 16);
     // (all warps read tensor memory before any thread overwrites the operand region:
     // the forward operands are dead once bar0 has completed, so writes may start at once)
     if (ok) {
         const int q0 = q % 5, q1 = (q / 5) % 5;
-        for (int pr = 0; pr < 4; ++pr) {
-            const int ea = half * 8 + 2 * pr;
+#pragma unroll
+        for (int pr = 0; pr < 2; ++pr) {
+            const int ea = group * 4 + 2 * pr;
             float u[2][F][NS], gr[2][F][3][3];   // [element][field][...]
 #pragma unroll
             for (int fi = 0; fi < F; ++fi) {
@@ -372,6 +405,7 @@ __global__ void __launch_bounds__(256, 1) tc_elem_kernel(const Geo g, const TabP
     fence_after();
 
     // ---- test MMAs: R[mode][species x element] (M = 64, weights in the test tables) ----
+    if (ok) ok = __syncthreads_and(wait(bar3, 0)) != 0;
     if (t == 0 && ok) {
         for (int tt = 0; tt < 4; ++tt) {
             const int n = tt == 0 ? ROWS : 2 * NE;
@@ -388,10 +422,45 @@ __global__ void __launch_bounds__(256, 1) tc_elem_kernel(const Geo g, const TabP
     }
     if (ok) ok = __syncthreads_and(wait(bar1, 0)) != 0;
     fence_after();
+    // ---- the epilogue's data into the freed table region: face records and coefficients ----
+    const int ne_real = (int)(g.E - e0 < NE ? g.E - e0 : NE);
+    if (ok) {
+        if (t == 0) {
+            const uint32_t bytes = (uint32_t)ne_real * (NS * NB * 4 + 6 * FACE_REC);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar4), "r"(bytes) : "memory");
+        }
+        __syncthreads();
+        if (t < 3 * NE * 2) {
+            const int a = t / (2 * NE), e = (t / 2) % NE, side = t & 1;
+            const long long ge = e0 + e;
+            if (ge < g.E) {
+                long long f = ge;
+                if (side == 0) {
+                    const long long nb = neighbour(g, ge, a, 0);
+                    f = nb >= 0 ? nb : g.E + low_layer_index(g, ge, a);
+                }
+                const float* src = args.fbuf + args.fb_off[a] + f * (2 * NS * 16);
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             :: "r"(sbase + (uint32_t)(((a * NE + e) * 2 + side) * FACE_REC)), "l"(src),
+                                "r"((uint32_t)FACE_REC), "r"(bar4)
+                             : "memory");
+            }
+        } else if (t == 3 * NE * 2) {
+            const float* src = (F == 1 ? args.U[0] : args.U[1]) + e0 * (NS * NB);
+            const uint32_t bytes = (uint32_t)ne_real * (NS * NB * 4);
+            for (uint32_t off = 0; off < bytes; off += 16384) {
+                const uint32_t n = bytes - off < 16384 ? bytes - off : 16384;
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             :: "r"(sbase + EPI_COEF + off), "l"(reinterpret_cast<const char*>(src) + off), "r"(n),
+                                "r"(bar4)
+                             : "memory");
+            }
+        }
+    }
     // residual to shared memory: M = 64 puts mode i in lane (i / 16) * 32 + i % 16
     if (ok) {
-        const int cbase = half * (ROWS / 2);
-        for (int c0 = 0; c0 < ROWS / 2; c0 += 8) {
+        const int cbase = group * (ROWS / 4);
+        for (int c0 = 0; c0 < ROWS / 4; c0 += 8) {
             float v[8];
             ld_x8(tlane + cbase + c0, v);
             wait_ld();
@@ -406,58 +475,78 @@ __global__ void __launch_bounds__(256, 1) tc_elem_kernel(const Geo g, const TabP
         }
     } else if (t == 0) {
         atomicOr(c.domain, 2);   // a tensor-core wait timed out
-        // give the MMAs in flight one more bounded wait before their tensor memory is freed
-        wait(bar1, 0);
+        // give the copies and MMAs in flight one more bounded wait before the block's
+        // tensor memory is freed and its shared memory released
+        wait(bar2, 0);
         wait(bar0, 0);
+        wait(bar3, 0);
+        wait(bar1, 0);
     }
     fence_before();
     __syncthreads();
     if (t < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tm), "r"(TMEM_COLS));
     if (!ok) return;
+    if (__syncthreads_and(wait(bar4, 0)) == 0) {
+        if (t == 0) {
+            atomicOr(c.domain, 2);
+            wait(bar4, 0);
+        }
+        __syncthreads();
+        return;
+    }
+    const float* sC = reinterpret_cast<const float*>(sTab + EPI_COEF);   // [e][s][i] of the last field
+    const float* sF = reinterpret_cast<const float*>(sTab);              // face records [axis][e][lo, hi][2][6][16]
 
     // ---- modal diffusion of n2..c3 (exact on the orthonormal basis), from the field's coefficients ----
-    {
-        const float* Uf = args.U[F - 1];
-        for (int idx = t; idx < NE * SpeciesSet<4>::N * NB; idx += blockDim.x) {
-            const int i = idx % NB, es = idx / NB;
-            const int e = es / SpeciesSet<4>::N, s = SpeciesSet<4>::s(es % SpeciesSet<4>::N);
-            if (e0 + e >= g.E) continue;
-            const float* uf = Uf + (e0 + e) * (NS * NB) + s * NB;
-            const double* ps = (MODE == MODE_JVP && args.pscale) ? args.pscale + s * NB : nullptr;
-            float acc = 0.f;
-            int stride = 1, rest = i;
+    for (int idx = t; idx < NE * SpeciesSet<4>::N * NB; idx += NT) {
+        const int i = idx % NB, es = idx / NB;
+        const int e = es / SpeciesSet<4>::N, s = SpeciesSet<4>::s(es % SpeciesSet<4>::N);
+        if (e >= ne_real) continue;
+        const float* uf = sC + (e * NS + s) * NB;
+        const double* ps = (MODE == MODE_JVP && args.pscale) ? args.pscale + s * NB : nullptr;
+        float acc = 0.f;
+        int stride = 1, rest = i;
 #pragma unroll
-            for (int j = 0; j < D; ++j) {
-                const int a = rest % 4;
-                rest /= 4;
-                const int base = i - a * stride;
-                for (int bb = (a & 1) ? 1 : 2; a > 0 && bb <= K; bb += 2) {
-                    const int ci = base + bb * stride;
-                    const float uv = ps ? __ldg(uf + ci) * float(ps[ci]) : __ldg(uf + ci);
-                    acc = fma(tb.K1h[j][a][bb], uv, acc);
-                }
-                stride *= 4;
+        for (int j = 0; j < D; ++j) {
+            const int a = rest % 4;
+            rest /= 4;
+            const int base = i - a * stride;
+            for (int bb = (a & 1) ? 1 : 2; a > 0 && bb <= K; bb += 2) {
+                const int ci = base + bb * stride;
+                const float uv = ps ? uf[ci] * float(ps[ci]) : uf[ci];
+                acc = fma(tb.K1h[j][a][bb], uv, acc);
             }
-            sR[(e * NS + s) * NB + i] = fma(-c.A[s], acc, sR[(e * NS + s) * NB + i]);
+            stride *= 4;
         }
+        sR[(e * NS + s) * NB + i] = fma(-c.A[s], acc, sR[(e * NS + s) * NB + i]);
     }
     __syncthreads();
-    // ---- the two tested face fluxes per axis ----
-    faces_expand<D, K, 0, float>(g, tb, c, args.fbuf + args.fb_off[0], sR, e0, NE, fid);
-    faces_expand<D, K, 1, float>(g, tb, c, args.fbuf + args.fb_off[1], sR, e0, NE, fid);
-    faces_expand<D, K, 2, float>(g, tb, c, args.fbuf + args.fb_off[2], sR, e0, NE, fid);
-    // ---- M^{-1} and the store (forward modes accumulate R / |K|) ----
+    // ---- the two tested face fluxes per axis (from the staged records), M^{-1}, store ----
     const float scale = (args.flags & CDG2_MINV) ? 1.f : c.vol;
     const float alphaT = float(args.alpha), betaT = float(args.beta);
-    for (int i = t; i < NE * NS * NB; i += blockDim.x) {
-        const long long ge = e0 + i / (NS * NB);
-        if (ge >= g.E) continue;
+    for (int idx = t; idx < NE * NS * NB; idx += NT) {
+        const int i = idx % NB, es = idx / NB, e = es / NS, s = es % NS;
+        if (e >= ne_real) continue;
+        const int a0 = i % 4, a1 = (i / 4) % 4, a2 = i / 16;
+        float acc = sR[idx];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            // normal mode m and tangential index t (the other two in increasing axis order)
+            const int m = a == 0 ? a0 : (a == 1 ? a1 : a2);
+            const int tt = a == 0 ? a1 + 4 * a2 : (a == 1 ? a0 + 4 * a2 : a0 + 4 * a1);
+            const float* lo = sF + ((a * NE + e) * 2 + 0) * (FACE_REC / 4) + s * 16 + tt;
+            const float* hi = sF + ((a * NE + e) * 2 + 1) * (FACE_REC / 4) + s * 16 + tt;
+            acc = fma(-tb.e[0][m], lo[0], acc);
+            acc = fma(tb.dh[a][0][m], lo[NS * 16], acc);
+            acc = fma(tb.e[1][m], hi[0], acc);
+            acc = fma(tb.dh[a][1][m], hi[NS * 16], acc);
+        }
         if constexpr (MODE == MODE_JVP) {
-            float w = __ldg(args.U[1] + e0 * (NS * NB) + i);
-            if (args.pscale) w *= float(args.pscale[i % (NS * NB)]);
-            args.out[e0 * (NS * NB) + i] = alphaT * w + betaT * (sR[i] * scale);
+            float w = sC[idx];
+            if (args.pscale) w *= float(args.pscale[idx % (NS * NB)]);
+            args.out[e0 * (NS * NB) + idx] = alphaT * w + betaT * (acc * scale);
         } else {
-            args.out[e0 * (NS * NB) + i] = sR[i] * scale;
+            args.out[e0 * (NS * NB) + idx] = acc * scale;
         }
     }
 }

@@ -90,7 +90,7 @@ def apply_flops_per_element(dim: int, k: int) -> int:
 # of their sha256).
 NCU_TRAFFIC = {("2D 256x64 Q3 manufactured solution", "double"): (50636477, "6d354302f83ea1ce")}
 KERNEL_SOURCES = ("paper_1403_1157_gb300/csrc/operator.cu", "paper_1403_1157_gb300/csrc/elem_common.cuh",
-                  "paper_1403_1157_gb300/csrc/physics.cuh")
+                  "paper_1403_1157_gb300/csrc/physics.cuh", "paper_1403_1157_gb300/csrc/tc_elem.cuh")
 
 
 def kernel_source_hash() -> str:
@@ -471,6 +471,47 @@ def measure_solve(G, torch, cfg: int, steps: int, precond: int):
     return result
 
 
+def measure_assembled(G, torch, cfg: int, flush, steps: int, peaks):
+    """The assembled Jacobian (the paper's deferred alternative to the matrix-free
+    JVP) on one workload: its assembly by JVP probing, its SpMV against the JVP
+    (time, HBM fraction of the SpMV), and one SDIRK step solved with each."""
+    import cdg2_inputs as I
+    w = I.workload(cfg)
+    mesh = G.cdg2_mesh_create(w.dim, w.cells, w.extent, w.periodic, w.k)
+    U, p = make_inputs(G, w, I, mesh)
+    A = G.cdg2_matrix_create(mesh)
+    G.cdg2_assemble_jacobian(A, p, U)                 # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G.cdg2_assemble_jacobian(A, p, U)
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter() - t0
+    x = torch.sin(torch.arange(U.numel(), device="cuda", dtype=torch.float64) * 0.37)
+    y = torch.empty_like(x)
+    ms_spmv = time_op(G, torch, lambda: G.cdg2_spmv(A, x, y), steps, 3, flush)
+    ms_jvp = time_op(G, torch, lambda: G.cdg2_jvp(mesh, p, U, x, y, G.CDG2_MINV | G.CDG2_ASYNC), steps, 3, flush)
+    spmv_bytes = A.bytes + 2 * 8 * w.n_dof
+    res = {"workload": w.name, "n_dof": w.n_dof, "block_size": A.block_size, "blocks_per_row": A.slots,
+           "colours": A.colours, "matrix_bytes": A.bytes, "assembly_s": t_asm,
+           "assembly_jvps": A.colours * A.block_size,
+           "spmv": {"ms": ms_spmv, "gb_s": spmv_bytes / (ms_spmv * 1e-3) / 1e9,
+                    "hbm_frac": spmv_bytes / (ms_spmv * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+           "jvp_fp64_ms": ms_jvp}
+    scheme = G.CDG2_SDIRK2 if w.k == 1 else G.CDG2_SDIRK3
+    for name, jac in (("matrix_free", 0), ("assembled", 1)):
+        opts = G.make_opts(scheme=scheme, newton_rtol=1e-10, gmres_rtol=1e-3, precond=2, jacobian=jac)
+        G.cdg2_step(mesh, p, U.clone(), 0.0, w.dt, opts)
+        torch.cuda.synchronize()
+        V = U.clone()
+        t0 = time.perf_counter()
+        rc, st = G.cdg2_step(mesh, p, V, 0.0, w.dt, opts)
+        torch.cuda.synchronize()
+        res["step_" + name] = {"s": time.perf_counter() - t0, "newton_iters": st["newton_iters"],
+                               "gmres_iters": st["gmres_iters"], "status": rc}
+    del A
+    return res
+
+
 def measure_gradient(G, torch, cfg: int, steps: int | None, mixed: bool, precond: int):
     """Forward + checkpointed discrete-adjoint backward of J = int n3(T) w.r.t. (U0, theta)."""
     import numpy as np
@@ -627,6 +668,8 @@ def main():
     ap.add_argument("--solve-config", type=int, default=3, help="workload of the implicit-solve comparison")
     ap.add_argument("--solve-steps", type=int, default=2, help="timed implicit steps per precision (0: skip)")
     ap.add_argument("--grad-config", type=int, default=2, help="workload of the gradient-through-steps timing")
+    ap.add_argument("--assembled-config", type=int, default=2,
+                    help="workload of the assembled-Jacobian comparison (-1: skip)")
     ap.add_argument("--profile-solve", choices=["mixed", "fp64"], default=None,
                     help="run one implicit step of the solve workload and exit (for ncu launch lists)")
     ap.add_argument("--profile-op", default=None,
@@ -782,6 +825,8 @@ def main():
     tri = measure_tri(G, torch, flush, nsub) if not args.no_tri else None
     tet = measure_tet(G, torch, flush, nsub) if not args.no_tri else None
     solve = measure_solve(G, torch, args.solve_config, args.solve_steps, args.precond) if args.solve_steps > 0 else None
+    assembled = measure_assembled(G, torch, args.assembled_config, flush, nsub, peaks) \
+        if args.assembled_config >= 0 else None
     grad = None
     if args.grad_steps != 0:
         grad = measure_gradient(G, torch, args.grad_config, None if args.grad_steps < 0 else args.grad_steps, True,
@@ -817,6 +862,7 @@ def main():
         "tetrahedra": tet,
         "solve": solve,
         "gradient": grad,
+        "assembled": assembled,
         "e2e": e2e,
         "gpu_launches": args.steps * (1 + w.dim),
         "clocks": clk,

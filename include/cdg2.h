@@ -167,7 +167,12 @@ typedef struct cdg2_params {
  *   on the host once per call (a few distinct blocks per mesh) and applied
  *   by a kernel before every JVP/VJP.  The preconditioner changes the
  *   iteration count, not the converged result.  The adjoint uses the same
- *   P (K_e is symmetric). */
+ *   P (K_e is symmetric).
+ * jacobian: 0 = matrix-free (the JVP kernel in every Krylov iteration);
+ *   1 = assembled: before every Newton correction the Jacobian at the
+ *   current iterate is assembled (cdg2_assemble_jacobian) and GMRES applies
+ *   it with cdg2_spmv; FP64 only (mixed = 0), Cartesian meshes whose
+ *   periodic axes have at least 3 cells.  The adjoint step ignores it. */
 typedef struct cdg2_solver_opts {
     int scheme;
     int mixed;
@@ -179,6 +184,7 @@ typedef struct cdg2_solver_opts {
     double newton_atol;
     double gmres_rtol;
     int precond;
+    int jacobian;
 } cdg2_solver_opts;
 
 /* Statistics of one cdg2_step call. */
@@ -342,6 +348,35 @@ int cdg2_project_gaussians(const cdg2_mesh* mesh, int n_gauss, const double* cen
  * out: device [n_elem][6][n_basis], float64 or float32 (CDG2_FP32). */
 int cdg2_project_mms(const cdg2_mesh* mesh, const cdg2_params* params, double t, void* out, int flags,
                      void* stream);
+
+/* ---- Assembled Jacobian (Sec. 3.2) -----------------------------------------
+ * Sec. 3.2 solves the stage systems matrix-free and sets a "fully assembled
+ * approach" aside; this is that alternative, for comparison: the Jacobian
+ * J = d(M^{-1} L_h)/dU at a state U, element-block sparse.  Row block e holds
+ * b x b blocks (b = 6 n_basis) for e itself and its 2 dim face neighbours
+ * (absent on walls), column-major, in device memory owned by the handle:
+ * E (2 dim + 1) b^2 doubles (e.g. 6.0 GB for 2D 256x64 Q3, 0.48 GB for 2D
+ * 128x32 Q2).  Assembly probes the JVP (cdg2_jvp's kernel, with M^{-1}) with
+ * one (species, mode) of all the elements of one colour of a distance-2
+ * element colouring at a time: colours x b JVP launches.  The matrix is
+ * tied to its mesh (which must outlive it); calls on one matrix must be
+ * ordered on one stream. */
+typedef struct cdg2_matrix cdg2_matrix;
+
+/* Allocate the blocks, the neighbour table and the colouring (host call,
+ * synchronous; device memory as above).  Errors: INVALID_ARG (NULL, a
+ * periodic axis with fewer than 3 cells), CUDA (out of device memory). */
+int cdg2_matrix_create(const cdg2_mesh* mesh, cdg2_matrix** out);
+void cdg2_matrix_destroy(cdg2_matrix* A);
+/* Block size b, blocks per row (2 dim + 1), colours of the colouring, device bytes of the blocks. */
+int cdg2_matrix_info(const cdg2_matrix* A, int* block_size, int* slots, int* colours, long long* bytes);
+/* A = J(U) (U: device float64 [n_elem][6][n_basis]).  Waits for the stream.
+ * Errors: INVALID_ARG, CUDA, DOMAIN (U outside the model's domain). */
+int cdg2_assemble_jacobian(cdg2_matrix* A, const cdg2_params* params, const double* U, void* stream);
+/* y = alpha A x + beta y (device float64 vectors of n_dof, not overlapping);
+ * beta = 0 ignores the old y.  One thread block per row element, the blocks
+ * read column by column (coalesced).  Errors: INVALID_ARG, CUDA. */
+int cdg2_spmv(const cdg2_matrix* A, double alpha, const double* x, double beta, double* y, void* stream);
 
 /* Human-readable description of the last error on this thread. */
 /* The block that precond = 2 inverts, for element `elem` and species

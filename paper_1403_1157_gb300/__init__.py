@@ -19,7 +19,7 @@ __all__ = [
     "cdg2_project_gaussians", "cdg2_project_mms", "cdg2_jvp", "cdg2_vjp", "cdg2_step",
     "CDG2_SDIRK2", "CDG2_SDIRK3", "CDG2_SDIRK4", "SolverOpts", "Stats", "make_opts", "cdg2_step_stages", "cdg2_step_adjoint",
     "stages_of", "CDG2_ASYNC", "CDG2_ERR_DOMAIN", "cdg2_mesh_status", "cdg2_tri_mesh_status", "cdg2_tet_mesh_status",
-    "cdg2_probe_peak", "CDG2_TF32",
+    "cdg2_probe_peak", "CDG2_TF32", "Matrix", "cdg2_matrix_create", "cdg2_assemble_jacobian", "cdg2_spmv",
 ]
 
 CDG2_MINV = 1
@@ -85,7 +85,7 @@ class SolverOpts(ctypes.Structure):
         ("scheme", ctypes.c_int), ("mixed", ctypes.c_int), ("flags", ctypes.c_int), ("max_newton", ctypes.c_int),
         ("gmres_restart", ctypes.c_int), ("max_gmres", ctypes.c_int),
         ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double), ("gmres_rtol", ctypes.c_double),
-        ("precond", ctypes.c_int),
+        ("precond", ctypes.c_int), ("jacobian", ctypes.c_int),
     ]
 
 
@@ -201,6 +201,17 @@ def load_library():
         getattr(lib, name).restype = i
     lib.cdg2_element_block.argtypes = [vp, ctypes.POINTER(Params), d, ctypes.c_longlong, i, dp]
     lib.cdg2_element_block.restype = i
+    lib.cdg2_matrix_create.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.cdg2_matrix_create.restype = i
+    lib.cdg2_matrix_destroy.argtypes = [vp]
+    lib.cdg2_matrix_destroy.restype = None
+    lib.cdg2_matrix_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                     ctypes.POINTER(ctypes.c_longlong)]
+    lib.cdg2_matrix_info.restype = i
+    lib.cdg2_assemble_jacobian.argtypes = [vp, ctypes.POINTER(Params), vp, vp]
+    lib.cdg2_assemble_jacobian.restype = i
+    lib.cdg2_spmv.argtypes = [vp, d, vp, d, vp, vp]
+    lib.cdg2_spmv.restype = i
     lib.cdg2_probe_peak.argtypes = [i, i, ctypes.POINTER(ctypes.c_double), vp]
     lib.cdg2_probe_peak.restype = i
     lib.cdg2_last_error.argtypes = []
@@ -293,6 +304,42 @@ def cdg2_mesh_destroy(mesh: Mesh):
 
 def cdg2_mesh_info(mesh: Mesh):
     return mesh.n_elem, mesh.n_basis, mesh.n_dof
+
+
+class Matrix:
+    """Owning handle of a cdg2_matrix (the assembled Jacobian of a Cartesian mesh)."""
+
+    def __init__(self, mesh: Mesh):
+        h = ctypes.c_void_p()
+        _check(load_library().cdg2_matrix_create(mesh.handle, ctypes.byref(h)))
+        self.handle, self.mesh = h.value, mesh
+        b, sl, nc, nb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        _check(load_library().cdg2_matrix_info(self.handle, ctypes.byref(b), ctypes.byref(sl), ctypes.byref(nc),
+                                               ctypes.byref(nb)))
+        self.block_size, self.slots, self.colours, self.bytes = b.value, sl.value, nc.value, nb.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.cdg2_matrix_destroy(self.handle)
+            self.handle = None
+
+
+def cdg2_matrix_create(mesh: Mesh) -> Matrix:
+    return Matrix(mesh)
+
+
+def cdg2_assemble_jacobian(A: Matrix, params, U: torch.Tensor, stream=None):
+    """A = J(U) (the Jacobian of M^{-1} L_h at the float64 CUDA state U)."""
+    p = _params(params)
+    _check(load_library().cdg2_assemble_jacobian(A.handle, ctypes.byref(p), _dev(U, A.mesh, torch.float64, "U"),
+                                                 _stream_ptr(stream)))
+
+
+def cdg2_spmv(A: Matrix, x: torch.Tensor, y: torch.Tensor, alpha: float = 1.0, beta: float = 0.0, stream=None):
+    """y = alpha A x + beta y (float64 CUDA vectors of n_dof)."""
+    _check(load_library().cdg2_spmv(A.handle, float(alpha), _dev(x, A.mesh, torch.float64, "x"), float(beta),
+                                    _dev(y, A.mesh, torch.float64, "y"), _stream_ptr(stream)))
+    return y
 
 
 def cdg2_probe_peak(kind: int, iters: int, stream=None) -> float:
@@ -563,13 +610,14 @@ def cdg2_vjp(mesh: Mesh, params, U: torch.Tensor, lam: torch.Tensor, gU: torch.T
 
 
 def make_opts(scheme=CDG2_SDIRK2, mixed=False, flags=0, max_newton=20, gmres_restart=30, max_gmres=300,
-              newton_rtol=1e-10, newton_atol=0.0, gmres_rtol=1e-3, precond=1) -> SolverOpts:
+              newton_rtol=1e-10, newton_atol=0.0, gmres_rtol=1e-3, precond=1, jacobian=0) -> SolverOpts:
     o = SolverOpts()
     o.scheme, o.flags, o.max_newton = int(scheme), int(flags), int(max_newton)
     o.mixed = int(mixed) if not isinstance(mixed, bool) else int(mixed)   # 0, 1 (FP32) or 2 (TF32 tensor cores)
     o.gmres_restart, o.max_gmres = int(gmres_restart), int(max_gmres)
     o.newton_rtol, o.newton_atol, o.gmres_rtol = float(newton_rtol), float(newton_atol), float(gmres_rtol)
     o.precond = int(precond)
+    o.jacobian = int(jacobian)
     return o
 
 

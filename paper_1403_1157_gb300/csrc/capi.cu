@@ -233,6 +233,7 @@ void cdg2_mesh_destroy(cdg2_mesh* m) {
     if (m->fbuf) cudaFree(m->fbuf);
     if (m->status) cudaFree(m->status);
     if (m->tc_tables) cudaFree(m->tc_tables);
+    if (m->jac) cdg2_matrix_destroy(m->jac);
     delete m;
 }
 

@@ -124,6 +124,8 @@ struct cdg2_mesh {
     mutable int* status = nullptr;
     // Table images of the tensor-core element kernel (3D Q3, CDG2_TF32), built by its first launch.
     mutable void* tc_tables = nullptr;
+    // Assembled Jacobian of cdg2_step with jacobian = 1, created by its first use.
+    mutable cdg2_matrix* jac = nullptr;
 };
 
 namespace cdg2 {
@@ -180,6 +182,9 @@ cudaError_t launch_vjp_axpby(const cdg2_mesh& m, const Coef& c, const void* U, c
 cudaError_t launch_vjp(const cdg2_mesh& m, const Coef& c, const void* U, const void* lam, void* gU,
                        double* theta_part, double* gtheta, int flags, cudaStream_t stream, int* domain = nullptr);
 long long vjp_grid(const cdg2_mesh& m);
+// The assembled Jacobian (assembled.cu): A = J(U) by JVP probing; y = alpha A x + beta y.
+int assemble(cdg2_matrix& A, const Coef& c, const double* U, cudaStream_t st, const char* who);
+cudaError_t spmv(const cdg2_matrix& A, double alpha, const double* x, double beta, double* y, cudaStream_t st);
 size_t face_buffer_bytes(const Geo& g);
 
 }  // namespace cdg2

@@ -296,6 +296,37 @@ struct CartKrylovOp {
     }
 };
 
+// The GMRES operator with the assembled Jacobian: w = (I - gdt A) P^{-1} v
+// (FP64), P the modal diagonal or the element blocks as for the JVP.
+struct AssembledKrylovOp {
+    const cdg2_mesh& m;
+    const cdg2_matrix& A;
+    double gdt;
+    const Precond& pc;
+    int mv(const double* v, double* tmp, double* out, cudaStream_t st) const {
+        const long long n = m.ndof;
+        if (pc.bt) {
+            CDG2_TRY(block_apply<double>(m, *pc.bt, v, tmp, st));
+            v = tmp;
+        } else if (pc.pinv) {
+            CDG2_TRY(cudaMemcpyAsync(tmp, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            CDG2_TRY(vec_scale_modes<double>(n, pc.pinv, NS * m.nb, tmp, st));
+            v = tmp;
+        }
+        CDG2_TRY(spmv(A, -gdt, v, 0.0, out, st));
+        CDG2_TRY(vec_axpby<double>(n, 1.0, v, 1.0, out, st));
+        return CDG2_OK;
+    }
+    int finish(long long n, double* x, double* tmp, cudaStream_t st) const {
+        if (pc.pinv) CDG2_TRY(vec_scale_modes<double>(n, pc.pinv, NS * m.nb, x, st));
+        if (pc.bt) {
+            CDG2_TRY(block_apply<double>(m, *pc.bt, x, tmp, st));
+            CDG2_TRY(cudaMemcpyAsync(x, tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        }
+        return CDG2_OK;
+    }
+};
+
 template <typename T, typename Op>
 static int gmres_op(const Op& op, const T* b, T* x, double rtol, int maxit, const Work& w, cudaStream_t st,
                     int* iters, int* reorth, double* relres) {
@@ -545,6 +576,13 @@ static int run_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double 
         set_error("cdg2_step: mixed = 2 (tensor-core TF32 Krylov operator) needs a 3D mesh of degree 3");
         return CDG2_ERR_INVALID_ARG;
     }
+    if (o->jacobian != 0 && (o->jacobian != 1 || o->mixed != 0)) {
+        set_error("cdg2_step: jacobian must be 0 (matrix-free) or 1 (assembled, with mixed = 0)");
+        return CDG2_ERR_INVALID_ARG;
+    }
+    if (o->jacobian == 1 && !m->jac) {
+        if (int rc = cdg2_matrix_create(m, &m->jac)) return rc;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const bool mixed = o->mixed != 0;
     const int kflags = o->flags | (o->mixed == 2 ? CDG2_TF32 : 0);   // flags of the Krylov operator
@@ -566,7 +604,15 @@ static int run_step(const cdg2_mesh* m, const cdg2_params* p, double* U, double 
     };
     auto correct = [&](double gdt, int* its, double* rr) -> int {
         int rc;
-        if (!mixed) {
+        if (o->jacobian == 1) {
+            // assemble J at the current iterate, then GMRES on the assembled operator
+            if (int arc = assemble(*m->jac, c, w.Y, st, "cdg2_step")) return arc;
+            CDG2_TRY(vec_convert<double, double>(n, w.G, -1.0, w.b64, st));
+            const AssembledKrylovOp op{*m, *m->jac, gdt, pc};
+            rc = gmres_op<double>(op, w.b64, static_cast<double*>(w.dx), o->gmres_rtol, o->max_gmres, w, st, its,
+                                  &S.gmres_reorth, rr);
+            if (rc == CDG2_OK) CDG2_TRY(vec_add_into<double>(n, static_cast<double*>(w.dx), w.Y, st));
+        } else if (!mixed) {
             CDG2_TRY(vec_convert<double, double>(n, w.G, -1.0, w.b64, st));
             rc = gmres<double>(*m, c, w.Y, gdt, w.b64, static_cast<double*>(w.dx), o->gmres_rtol, o->max_gmres, w,
                                st, o->flags, pc, its, &S.gmres_reorth, rr);

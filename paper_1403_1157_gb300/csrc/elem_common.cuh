@@ -115,7 +115,8 @@ struct Ident {
 // Species subsets of the forward volume terms (the diffusion of n2..c3 is
 // applied in modal form, see op_kernel): 0 all six; 1 {n1, c1, c3}, whose
 // gradients the fluxes need at the points; 2 {n1, n2}, the fluxes tested with
-// grad phi; 3 {n3, c1, c2, c3}, tested with phi only; 4 {n2, .., c3}.
+// grad phi; 3 {n3, c1, c2, c3}, tested with phi only; 4 {n2, .., c3};
+// 5 {n1, n2, c1, c3}, the face-point traces the chemotactic fluxes need.
 template <int SEL>
 struct SpeciesSet;
 template <>
@@ -142,6 +143,11 @@ template <>
 struct SpeciesSet<4> {
     static constexpr int N = 5;
     __device__ static constexpr int s(int k) { return k + 1; }
+};
+template <>
+struct SpeciesSet<5> {
+    static constexpr int N = 4;
+    __device__ static constexpr int s(int k) { return k < 2 ? k : (k == 2 ? 3 : 5); }
 };
 
 // One 1D pass of sum factorisation.  Input tensors have extents (I0, I1, I2)

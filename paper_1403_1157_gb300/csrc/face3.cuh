@@ -1,0 +1,366 @@
+// Face kernel of the face-once path on 3D meshes (apply and JVP): the same
+// face terms as face_kernel (Sec. 3.1: symmetric diffusive flux with the
+// CDG2 penalty, local Lax-Friedrichs chemotactic flux, the boundary
+// conditions of Eq. 3), laid out for issue efficiency:
+//   - both cells of every face arrive by bulk asynchronous copies (one
+//     thread, one mbarrier) where a cell's block is a multiple of 16 bytes
+//     and the fields are 16-byte aligned, else by batched loads;
+//   - enough faces per CTA that the pointwise flux phase has one face point
+//     per thread (FPB x n_q^2 <= 128);
+//   - the stage buffers alias one another along their lifetimes (cells ->
+//     interpolated half-stage -> tested fluxes in one region, the normal
+//     contraction and the face-point values in another), which keeps three
+//     or more CTAs per SM.
+// Interior-only CTAs take the modal shortcut of face_kernel (n3, c1, c2, c3
+// tested from the normal contraction; only n1, n2, c1, c3 go to the face
+// points).  Output: the same face records, [2][6][n_bt] per face.
+#pragma once
+
+namespace cdg2 {
+
+template <int K, int F, typename T>
+struct Face3Plan {
+    using S = Shape<3, K>;
+    static constexpr int NB = S::NB, NB1 = S::NB1, NQ1 = S::NQ1, NBT = S::NBT, NQT = S::NQT;
+    static constexpr int NT = 128;
+    // faces per CTA: one thread per face point in the pointwise phase; the
+    // FP64 JVP on Q3 keeps to 3 faces so that three CTAs fit on an SM
+    static constexpr int FPB = K == 1 ? 14 : (K == 2 ? 8 : ((F == 2 && sizeof(T) == 8) ? 3 : 5));
+    static_assert(FPB * NQT <= NT, "one face point per thread");
+    static constexpr int CELL = NS * NB;                          // one cell, one field
+    static constexpr int CELLS = 2 * F * FPB * CELL;              // [side][field][face][6][n_b]
+    static constexpr int FC = F * FPB * 4 * NS * NBT;             // normal contraction
+    static constexpr int FT = F * FPB * 4 * NS * NQ1 * NB1;       // half-interpolated
+    static constexpr int FP = F * FPB * 4 * NS * NQT;             // face-point values
+    static constexpr int FS = FPB * 2 * NS * NQT;                 // weighted sigma, tau at the points
+    static constexpr int TS1 = FPB * 2 * NS * NB1 * NQ1;          // half-tested
+    static constexpr int TS = FPB * 2 * NS * NBT;                 // tested fluxes (the output records)
+    static constexpr int XN = cmax(cmax(CELLS, FT), FS + TS1);    // region X: cells, FT, FS + TS1
+    static constexpr int YN = cmax(FC, FP);                       // region Y: FC, FP
+    static constexpr bool BULK = (CELL * sizeof(T)) % 16 == 0;
+    static constexpr int TAB_OFF = 16;                            // after the mbarrier
+    static constexpr int X_OFF = (TAB_OFF + (int)sizeof(STab<K, T>) + 15) / 16 * 16;
+    static constexpr size_t smem_bytes() { return (size_t)X_OFF + sizeof(T) * (size_t)(XN + YN + TS); }
+};
+
+// Bounded wait for phase 0 of the CTA's copy barrier (2^22 polls, far above
+// any legitimate copy time): false on time-out.
+__device__ __forceinline__ bool face3_wait(uint32_t bar) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(ok) : "r"(bar) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <int K, int MODE, int A, typename T>
+__global__ void __launch_bounds__(128) face3_kernel(const Geo g, const TabP<T> tab, const OpArgs<T> args,
+                                                    const int use_bulk) {
+    constexpr int D = 3;
+    constexpr int F = fields_of(MODE);
+    using P = Face3Plan<K, F, T>;
+    constexpr int FPB = P::FPB, NB = P::NB, NB1 = P::NB1, NQ1 = P::NQ1, NBT = P::NBT, NQT = P::NQT;
+    constexpr int CELL = P::CELL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    STab<K, T>& tb = *reinterpret_cast<STab<K, T>*>(smem_raw + P::TAB_OFF);
+    T* X = reinterpret_cast<T*>(smem_raw + P::X_OFF);
+    T* Y = X + P::XN;
+    T* Z = Y + P::YN;
+    T* FC = Y;
+    T* FT = X;
+    T* FPt = Y;
+    T* FS = X;
+    T* TS1 = X + P::FS;
+    T* TS = Z;
+    __shared__ long long cm[FPB], cp[FPB];   // minus / plus cell (-1: none)
+    __shared__ int kind[FPB];                // -1 unused, 0 interior, 1 high boundary, 2 low boundary
+    __shared__ int any_boundary;             // a boundary face in this CTA: no modal shortcut
+    __shared__ int copies_ok;
+    __shared__ T psT[MODE == MODE_JVP ? NS * NB : 1];
+    const CoefT<T>& c = args.c;
+    const long long nf = faces_of_axis(g, A);
+    const long long f0 = (long long)blockIdx.x * FPB;
+    const int tid = threadIdx.x;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const bool bulk = P::BULK && use_bulk;   // the host checked the fields' 16-byte alignment
+
+    if (tid == 0) {
+        any_boundary = 0;
+        if (bulk) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
+    if (tid < FPB) {
+        const long long fid = f0 + tid;
+        int kd = -1;
+        long long em = -1, ep = -1;
+        if (fid < g.E) {
+            em = fid;
+            ep = neighbour(g, fid, A, 1);
+            kd = ep >= 0 ? 0 : 1;
+        } else if (fid < nf) {
+            const long long l = fid - g.E;
+            long long ix = 0, iy = 0, iz = 0;
+            if (A == 0) { iy = l % g.n[1]; iz = l / g.n[1]; }
+            else if (A == 1) { ix = l % g.n[0]; iz = l / g.n[0]; }
+            else { ix = l % g.n[0]; iy = l / g.n[0]; }
+            ep = ix + (long long)g.n[0] * (iy + (long long)g.n[1] * iz);
+            kd = 2;
+        }
+        cm[tid] = em;
+        cp[tid] = ep;
+        kind[tid] = kd;
+    }
+    __syncthreads();
+    if (tid < FPB && kind[tid] > 0) any_boundary = 1;
+    if (bulk) {
+        if (tid == 0) {
+            uint32_t bytes = 0;
+#pragma unroll 1
+            for (int b = 0; b < 2 * F * FPB; ++b) {
+                const int j = b % FPB, side = b / (F * FPB);
+                if ((side ? cp[j] : cm[j]) >= 0) bytes += CELL * (uint32_t)sizeof(T);
+            }
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+#pragma unroll 1
+            for (int b = 0; b < 2 * F * FPB; ++b) {
+                const int j = b % FPB, fi = (b / FPB) % F, side = b / (F * FPB);
+                const long long cell = side ? cp[j] : cm[j];
+                if (cell < 0) continue;
+                const T* src = field(args, fi) + cell * CELL;
+                const uint32_t dst = (uint32_t)__cvta_generic_to_shared(X + b * CELL);
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             :: "r"(dst), "l"(src), "r"((uint32_t)(CELL * sizeof(T))), "r"(bar)
+                             : "memory");
+            }
+        }
+    } else {
+        // batched loads: a batch of independent loads per thread in flight at once
+        constexpr int TOT = P::CELLS, BATCH = 8;
+        for (int i0 = tid; i0 < TOT; i0 += BATCH * P::NT) {
+            T v[BATCH];
+#pragma unroll
+            for (int b = 0; b < BATCH; ++b) {
+                const int i = i0 + b * P::NT;
+                v[b] = T(0);
+                if (i < TOT) {
+                    const int blk = i / CELL, q = i - blk * CELL;
+                    const int j = blk % FPB, fi = (blk / FPB) % F, side = blk / (F * FPB);
+                    const long long cell = side ? cp[j] : cm[j];
+                    if (cell >= 0) v[b] = field(args, fi)[cell * CELL + q];
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < BATCH; ++b) {
+                const int i = i0 + b * P::NT;
+                if (i < TOT) X[i] = v[b];
+            }
+        }
+    }
+    load_tab<K, T>(tb, tab);
+    const T* ps = nullptr;
+    if constexpr (MODE == MODE_JVP) {
+        if (args.pscale) {
+            for (int i = tid; i < NS * NB; i += P::NT) psT[i] = T(args.pscale[i]);
+            ps = psT;
+        }
+    }
+    if (bulk) {
+        if (tid == 0) {
+            bool ok = face3_wait(bar);
+            if (!ok) {
+                if (c.domain) atomicOr(c.domain, 2);
+                face3_wait(bar);   // let the copies in flight land before the CTA exits
+            }
+            copies_ok = ok;
+        }
+    }
+    __syncthreads();
+    if (bulk && !copies_ok) return;
+
+    const T invh = c.invh[A];
+    // normal contraction: 0 the owning trace (K^- at xi = 1, or K^+ at xi = 0 on a
+    // low boundary), 1 the jump (difference-first), 2 d_n U^-, 3 d_n U^+
+    for (int idx = tid; idx < F * FPB * NS * NBT; idx += P::NT) {
+        const int t = idx % NBT;
+        const int s = (idx / NBT) % NS;
+        const int j = (idx / (NBT * NS)) % FPB;
+        const int fi = idx / (NBT * NS * FPB);
+        const int b0 = t % NB1, b1 = t / NB1;
+        const T* um = X + (fi * FPB + j) * CELL + s * NB;
+        const T* up = X + ((F + fi) * FPB + j) * CELL + s * NB;
+        T vm[NB1], vp[NB1];
+#pragma unroll
+        for (int m = 0; m < NB1; ++m) {
+            const int ci = coef_index<D, K, A>(m, b0, b1);
+            vm[m] = um[ci];
+            vp[m] = up[ci];
+            if (MODE == MODE_JVP && fi == 1 && ps) {
+                vm[m] *= ps[s * NB + ci];
+                vp[m] *= ps[s * NB + ci];
+            }
+        }
+        const int kd = kind[j];
+        T uo = 0, del = 0, dm = 0, dp = 0;
+        if (kd == 2) {
+#pragma unroll
+            for (int m = 0; m < NB1; ++m) uo = fma(tb.e[0][m], vp[m], uo);
+        } else {
+#pragma unroll
+            for (int m = 0; m < NB1; ++m) uo = fma(tb.e[1][m], vm[m], uo);
+        }
+        if (kd == 0) {
+            del = vm[0] - vp[0];
+#pragma unroll
+            for (int m = 1; m < NB1; ++m) {
+                del = fma(tb.e[1][m], vm[m], del);
+                del = fma(-tb.e[0][m], vp[m], del);
+            }
+#pragma unroll
+            for (int m = 0; m < NB1; ++m) {
+                dm = fma(tb.dh[A][1][m], vm[m], dm);
+                dp = fma(tb.dh[A][0][m], vp[m], dp);
+            }
+        }
+        T* o = FC + ((fi * FPB + j) * 4) * NS * NBT + s * NBT + t;
+        o[0 * NS * NBT] = uo;
+        o[1 * NS * NBT] = del;
+        o[2 * NS * NBT] = dm;
+        o[3 * NS * NBT] = dp;
+    }
+    __syncthreads();
+    const bool modal = any_boundary == 0;
+    const T pen = c.pen_c * T((K + 1) * (K + 1)) * invh;
+    if (modal) {
+        // n3, c1, c2, c3 in modal form (orthonormal tangential basis, exact face
+        // quadrature): sigma_t = A (d_n U^-_t + d_n U^+_t) / 2 - pen A Delta_t,
+        // tau_t = A Delta_t / 2 (of the tangent in the JVP), weighted by 1 / h_A
+        constexpr int fl = F - 1;
+        constexpr int NM = SpeciesSet<3>::N;
+        for (int idx = tid; idx < FPB * NM * NBT; idx += P::NT) {
+            const int t = idx % NBT, ss = (idx / NBT) % NM, j = idx / (NBT * NM);
+            const int s = SpeciesSet<3>::s(ss);
+            const T* f = FC + ((fl * FPB + j) * 4) * NS * NBT + s * NBT + t;
+            const T del = f[1 * NS * NBT], dm = f[2 * NS * NBT], dp = f[3 * NS * NBT];
+            T As;   // c.A[s] without an indexed parameter load
+            switch (s) {
+                case 2: As = c.A[2]; break;
+                case 3: As = c.A[3]; break;
+                case 4: As = c.A[4]; break;
+                default: As = c.A[5]; break;
+            }
+            T* o = TS + (j * 2) * NS * NBT + s * NBT + t;
+            o[0] = kind[j] == 0 ? invh * As * (T(0.5) * (dm + dp) - pen * del) : T(0);
+            o[NS * NBT] = kind[j] == 0 ? invh * T(0.5) * As * del : T(0);
+        }
+        sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, 1, 1, T, 5>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT,
+                                                                   NQ1 * NB1, F * FPB * 4 * SpeciesSet<5>::N);
+        __syncthreads();
+        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1, T, 5>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1,
+                                                                   FPt, NQT, F * FPB * 4 * SpeciesSet<5>::N);
+    } else {
+        sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT,
+                                                           NQ1 * NB1, F * FPB * 4 * NS);
+        __syncthreads();
+        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, FPt,
+                                                           NQT, F * FPB * 4 * NS);
+    }
+    __syncthreads();
+
+    // pointwise fluxes: one face point per thread
+    if (tid < FPB * NQT) {
+        const int p = tid % NQT, j = tid / NQT;
+        const int kd = kind[j];
+        T sig[NS], tau[NS];
+        const int p0 = p % NQ1, p1 = p / NQ1;
+        const T Wp = tb.w[p0] * tb.w[p1] * invh;   // the element kernel accumulates the residual divided by |K|
+        T uo[NS], del[NS], dm[NS], dp[NS];
+        {
+            const T* base = FPt + (j * 4) * NS * NQT + p;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                uo[s] = base[(0 * NS + s) * NQT];
+                del[s] = base[(1 * NS + s) * NQT];
+                dm[s] = base[(2 * NS + s) * NQT];
+                dp[s] = base[(3 * NS + s) * NQT];
+            }
+        }
+        if (kd == 0) {
+            T uP[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) uP[s] = uo[s] - del[s];
+            if constexpr (MODE == MODE_APPLY) {
+                face_point<T>(c, pen, uo, dm, uP, dp, del, sig, tau);
+            } else {
+                T tuo[NS], tdel[NS], tdm[NS], tdp[NS], tuP[NS];
+                const T* base = FPt + ((FPB + j) * 4) * NS * NQT + p;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    tuo[s] = base[(0 * NS + s) * NQT];
+                    tdel[s] = base[(1 * NS + s) * NQT];
+                    tdm[s] = base[(2 * NS + s) * NQT];
+                    tdp[s] = base[(3 * NS + s) * NQT];
+                    tuP[s] = tuo[s] - tdel[s];
+                }
+                face_point_lin<T>(c, pen, uo, dm, uP, dp, del, tuo, tdm, tuP, tdp, tdel, sig, tau);
+            }
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                sig[s] = Wp * sig[s];
+                tau[s] = Wp * tau[s];
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                sig[s] = T(0);
+                tau[s] = T(0);
+            }
+            if (A == 1 && kd > 0) {
+                const int f = kd == 2 ? 0 : 1;             // Gamma_1 (y = 0) or Gamma_2 (y = L1)
+                const long long cell = kd == 2 ? cp[j] : cm[j];
+                const T x = T((cell % g.n[0]) * g.h[0]) + T(g.h[0]) * tb.xi[p0];
+                if constexpr (MODE == MODE_APPLY)
+                    boundary_point<T>(c, f, x, g, uo, sig, c.beta1, true);
+                else
+                    boundary_point<T>(c, f, x, g, uo, sig, c.dth[7], false);
+                const T sg = kd == 2 ? -Wp : Wp;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) sig[s] = sg * sig[s];
+            }
+        }
+        T* o = FS + (j * 2) * NS * NQT + p;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            o[(0 * NS + s) * NQT] = sig[s];
+            o[(1 * NS + s) * NQT] = tau[s];
+        }
+    }
+    __syncthreads();
+    if (modal) {
+        // n1, n2 through the face points
+        sf_sym<0, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1, T, 2>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1,
+                                                                  NB1 * NQ1, FPB * 2 * SpeciesSet<2>::N);
+        __syncthreads();
+        sf_sym<1, NB1, NQ1, 1, NB1, true, K + 1, false, 1, 1, T, 2>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1,
+                                                                  TS, NBT, FPB * 2 * SpeciesSet<2>::N);
+    } else {
+        sf_sym<0, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1,
+                                                          NB1 * NQ1, FPB * 2 * NS);
+        __syncthreads();
+        sf_sym<1, NB1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1, TS,
+                                                          NBT, FPB * 2 * NS);
+    }
+    __syncthreads();
+    // coalesced store of the faces' tested fluxes
+    T* dst = args.fbuf + args.fb_off[A];
+    for (int i = tid; i < P::TS; i += P::NT) {
+        const long long fid = f0 + i / (2 * NS * NBT);
+        if (fid < nf) dst[f0 * 2 * NS * NBT + i] = TS[i];
+    }
+}
+
+}  // namespace cdg2

@@ -404,6 +404,7 @@ __global__ void __launch_bounds__(128) face_kernel(const Geo g, const TabP<T> ta
     T* TS = TS1 + P::TS1;
     __shared__ long long cm[FPB], cp[FPB];   // minus / plus cell (-1: none)
     __shared__ int kind[FPB];                // -1 unused, 0 interior, 1 high boundary, 2 low boundary
+    __shared__ int any_boundary;             // a boundary face in this CTA: no modal shortcut
     __shared__ T psT[MODE == MODE_JVP ? NS * NB : 1];
     const CoefT<T>& c = args.c;
     const long long nf = faces_of_axis(g, A);
@@ -438,7 +439,9 @@ __global__ void __launch_bounds__(128) face_kernel(const Geo g, const TabP<T> ta
         cp[threadIdx.x] = ep;
         kind[threadIdx.x] = kd;
     }
+    if (threadIdx.x == 0) any_boundary = 0;
     __syncthreads();
+    if (threadIdx.x < FPB && kind[threadIdx.x] > 0) any_boundary = 1;
     // coalesced loads of both cells of every face (the tangent pre-scaled), a
     // batch of independent loads per thread in flight at once
     {
@@ -521,15 +524,33 @@ __global__ void __launch_bounds__(128) face_kernel(const Geo g, const TabP<T> ta
         o[3 * NS * NBT] = dp;
     }
     __syncthreads();
-    if constexpr (D == 2) {
-        sf_sym<0, NB1, 1, 1, NQ1, false, K + 1, false, 1, 1>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FPt, NQT,
-                                                         F * FPB * 4 * NS);
+    // Interior faces: the fluxes of n3, c1, c2, c3 are purely diffusive and
+    // linear, and with the orthonormal tangential basis and exact face
+    // quadrature their tested fluxes follow from the normal contraction in
+    // modal form (below); only n1, n2, c1, c3 go to the face points.
+    const bool modal = any_boundary == 0;
+    if (modal) {
+        if constexpr (D == 2) {
+            sf_sym<0, NB1, 1, 1, NQ1, false, K + 1, false, 1, 1, T, 5>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FPt,
+                                                                     NQT, F * FPB * 4 * SpeciesSet<5>::N);
+        } else {
+            sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, 1, 1, T, 5>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT,
+                                                                       NQ1 * NB1, F * FPB * 4 * SpeciesSet<5>::N);
+            __syncthreads();
+            sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1, T, 5>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1,
+                                                                       FPt, NQT, F * FPB * 4 * SpeciesSet<5>::N);
+        }
     } else {
-        sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT, NQ1 * NB1,
-                                                           F * FPB * 4 * NS);
-        __syncthreads();
-        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, FPt, NQT,
-                                                           F * FPB * 4 * NS);
+        if constexpr (D == 2) {
+            sf_sym<0, NB1, 1, 1, NQ1, false, K + 1, false, 1, 1>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FPt, NQT,
+                                                             F * FPB * 4 * NS);
+        } else {
+            sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT,
+                                                               NQ1 * NB1, F * FPB * 4 * NS);
+            __syncthreads();
+            sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, FPt,
+                                                               NQT, F * FPB * 4 * NS);
+        }
     }
     __syncthreads();
 
@@ -604,15 +625,42 @@ __global__ void __launch_bounds__(128) face_kernel(const Geo g, const TabP<T> ta
         }
     }
     __syncthreads();
-    if constexpr (D == 2) {
-        sf_sym<0, NQ1, 1, 1, NB1, true, K + 1, false, 1, 1>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS, NBT,
-                                                        FPB * 2 * NS);
+    if (modal) {
+        // n1, n2 through the face points
+        if constexpr (D == 2) {
+            sf_sym<0, NQ1, 1, 1, NB1, true, K + 1, false, 1, 1, T, 2>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS, NBT,
+                                                                    FPB * 2 * SpeciesSet<2>::N);
+        } else {
+            sf_sym<0, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1, T, 2>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1,
+                                                                      NB1 * NQ1, FPB * 2 * SpeciesSet<2>::N);
+            __syncthreads();
+            sf_sym<1, NB1, NQ1, 1, NB1, true, K + 1, false, 1, 1, T, 2>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1,
+                                                                      TS, NBT, FPB * 2 * SpeciesSet<2>::N);
+        }
+        // n3, c1, c2, c3 in modal form: sigma_t = A (d_n U^-_t + d_n U^+_t) / 2 - pen A Delta_t,
+        // tau_t = A Delta_t / 2 (of the tangent in the JVP), weighted like the point values (1 / h_A)
+        constexpr int fl = F - 1;   // the field whose flux is tested
+        for (int idx = threadIdx.x; idx < FPB * SpeciesSet<3>::N * NBT; idx += blockDim.x) {
+            const int t = idx % NBT, ss = (idx / NBT) % SpeciesSet<3>::N, j = idx / (NBT * SpeciesSet<3>::N);
+            const int s = SpeciesSet<3>::s(ss);
+            const T* f = FC + ((fl * FPB + j) * 4) * NS * NBT + s * NBT + t;
+            const T del = f[1 * NS * NBT], dm = f[2 * NS * NBT], dp = f[3 * NS * NBT];
+            const T A_s = c.A[s];
+            T* o = TS + (j * 2) * NS * NBT + s * NBT + t;
+            o[0] = kind[j] == 0 ? invh * A_s * (T(0.5) * (dm + dp) - pen * del) : T(0);
+            o[NS * NBT] = kind[j] == 0 ? invh * T(0.5) * A_s * del : T(0);
+        }
     } else {
-        sf_sym<0, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1, NB1 * NQ1,
-                                                          FPB * 2 * NS);
-        __syncthreads();
-        sf_sym<1, NB1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1, TS, NBT,
-                                                          FPB * 2 * NS);
+        if constexpr (D == 2) {
+            sf_sym<0, NQ1, 1, 1, NB1, true, K + 1, false, 1, 1>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS, NBT,
+                                                            FPB * 2 * NS);
+        } else {
+            sf_sym<0, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1,
+                                                              NB1 * NQ1, FPB * 2 * NS);
+            __syncthreads();
+            sf_sym<1, NB1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1, TS,
+                                                              NBT, FPB * 2 * NS);
+        }
     }
     __syncthreads();
     // coalesced store of the faces' tested fluxes
@@ -678,6 +726,7 @@ __device__ __forceinline__ void faces_expand(const Geo& g, const STab<K, T>& tb,
 
 }  // namespace cdg2
 
+#include "face3.cuh"
 #include "tc_elem.cuh"
 
 namespace cdg2 {
@@ -1061,24 +1110,6 @@ static cudaError_t launch_faces(const cdg2_mesh& m, OpArgs<T>& a, cudaStream_t s
         if (e != cudaSuccess) return e;
         m.fbuf_bytes = bytes;
     }
-    using FPl = FacePlan<D, K, fields_of(MODE)>;
-    constexpr size_t fsmem = FPl::template smem_bytes<T>();
-    static_assert(fsmem <= 227 * 1024, "face kernel shared memory exceeds 227 KB");
-    static DeviceOnce fattr;
-    {
-        cudaError_t e = once_per_device(fattr, [] {
-            cudaError_t r = cudaFuncSetAttribute(face_kernel<D, K, MODE, 0, T>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
-            if (r == cudaSuccess)
-                r = cudaFuncSetAttribute(face_kernel<D, K, MODE, 1, T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
-            if (r == cudaSuccess && D == 3)
-                r = cudaFuncSetAttribute(face_kernel<D, K, MODE, D == 3 ? 2 : 1, T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
-            return r;
-        });
-        if (e != cudaSuccess) return e;
-    }
     a.fbuf = static_cast<T*>(m.fbuf);
     constexpr long long per_face = 2LL * NS * Shape<D, K>::NBT;
     long long off = 0;
@@ -1086,10 +1117,47 @@ static cudaError_t launch_faces(const cdg2_mesh& m, OpArgs<T>& a, cudaStream_t s
         a.fb_off[ax] = off;
         if (ax < D) off += faces_of_axis(m.geo, ax) * per_face;
     }
-    auto fgrid = [&](int ax) { return (unsigned)((faces_of_axis(m.geo, ax) + FPl::FPB - 1) / FPl::FPB); };
-    face_kernel<D, K, MODE, 0, T><<<fgrid(0), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
-    face_kernel<D, K, MODE, 1, T><<<fgrid(1), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
-    if constexpr (D == 3) face_kernel<D, K, MODE, 2, T><<<fgrid(2), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
+    if constexpr (D == 3) {
+        using FPl = Face3Plan<K, fields_of(MODE), T>;
+        constexpr size_t fsmem = FPl::smem_bytes();
+        static_assert(fsmem <= 227 * 1024, "face kernel shared memory exceeds 227 KB");
+        static DeviceOnce fattr;
+        cudaError_t e = once_per_device(fattr, [] {
+            cudaError_t r = cudaFuncSetAttribute(face3_kernel<K, MODE, 0, T>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(face3_kernel<K, MODE, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fsmem);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(face3_kernel<K, MODE, 2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fsmem);
+            return r;
+        });
+        if (e != cudaSuccess) return e;
+        auto al16 = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+        const int bulk = FPl::BULK && al16(a.U[0]) && (fields_of(MODE) == 1 || al16(a.U[1]));
+        auto fgrid = [&](int ax) { return (unsigned)((faces_of_axis(m.geo, ax) + FPl::FPB - 1) / FPl::FPB); };
+        face3_kernel<K, MODE, 0, T><<<fgrid(0), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a, bulk);
+        face3_kernel<K, MODE, 1, T><<<fgrid(1), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a, bulk);
+        face3_kernel<K, MODE, 2, T><<<fgrid(2), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a, bulk);
+    } else {
+        using FPl = FacePlan<D, K, fields_of(MODE)>;
+        constexpr size_t fsmem = FPl::template smem_bytes<T>();
+        static_assert(fsmem <= 227 * 1024, "face kernel shared memory exceeds 227 KB");
+        static DeviceOnce fattr;
+        cudaError_t e = once_per_device(fattr, [] {
+            cudaError_t r = cudaFuncSetAttribute(face_kernel<D, K, MODE, 0, T>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(face_kernel<D, K, MODE, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fsmem);
+            return r;
+        });
+        if (e != cudaSuccess) return e;
+        auto fgrid = [&](int ax) { return (unsigned)((faces_of_axis(m.geo, ax) + FPl::FPB - 1) / FPl::FPB); };
+        face_kernel<D, K, MODE, 0, T><<<fgrid(0), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
+        face_kernel<D, K, MODE, 1, T><<<fgrid(1), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a);
+    }
     return cudaSuccess;
 }
 

@@ -43,8 +43,8 @@ int take_domain_status(int* word, cudaStream_t st, const char* who) {
     e = cudaMemsetAsync(word, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(e, who);
     if (h & 2) {
-        set_error(std::string(who) + ": a wait for the tensor cores timed out in the element kernel; its result is "
-                  "undefined");
+        set_error(std::string(who) + ": a bounded wait for the tensor cores or for bulk asynchronous copies timed "
+                  "out in a kernel; its result is undefined");
         return CDG2_ERR_CUDA;
     }
     set_error(std::string(who) + ": a chemotactic sensitivity chi0 x / (y + chith) met y + chith <= 0 at a "

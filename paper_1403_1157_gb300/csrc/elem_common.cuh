@@ -165,8 +165,10 @@ struct SpeciesSet<5> {
 // each mode takes the pair combination of its parity.  For k = 3 this is 14
 // operations per line and matrix instead of 20.  SEL restricts the pass to
 // the species of SpeciesSet<SEL>: tensor t is then (t / N, species s(t % N))
-// of an element-major [..][6] layout, and nt counts only those tensors.
-template <int AX, int I0, int I1, int I2, int NO, bool TR, int LD, bool TWO, int P1, int P2, typename T, int SEL = 0>
+// of an element-major [..][6] layout, and nt counts only those tensors; with
+// IN_COMPACT the input holds only those tensors, back to back.
+template <int AX, int I0, int I1, int I2, int NO, bool TR, int LD, bool TWO, int P1, int P2, typename T, int SEL = 0,
+          bool IN_COMPACT = false>
 __device__ __forceinline__ void sf_sym(const T* __restrict__ in1, const T* __restrict__ M1,
                                        const typename Ident<T>::type* __restrict__ in2,
                                        const typename Ident<T>::type* __restrict__ M2, int in_stride,
@@ -205,7 +207,8 @@ __device__ __forceinline__ void sf_sym(const T* __restrict__ in1, const T* __res
         }
         using SS = SpeciesSet<SEL>;
         const int tm = SEL == 0 ? tt : (tt / SS::N) * NS + SS::s(tt % SS::N);
-        const T* s1 = in1 + tm * in_stride + ib;
+        const int ti = IN_COMPACT ? tt : tm;
+        const T* s1 = in1 + ti * in_stride + ib;
         T* d = out + tm * out_stride + ob;
         if constexpr (!TR) {
             T v[NM];
@@ -238,7 +241,7 @@ __device__ __forceinline__ void sf_sym(const T* __restrict__ in1, const T* __res
             }
             if constexpr (MID) mid1 = s1[H * ST];
             if constexpr (TWO) {
-                const T* s2 = in2 + tm * in_stride + ib;
+                const T* s2 = in2 + ti * in_stride + ib;
 #pragma unroll
                 for (int q = 0; q < H; ++q) {
                     const T x = s2[q * ST], y = s2[(NQ - 1 - q) * ST];

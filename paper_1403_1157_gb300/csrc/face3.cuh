@@ -5,18 +5,24 @@
 //   - both cells of every face arrive by bulk asynchronous copies (one
 //     thread, one mbarrier) where a cell's block is a multiple of 16 bytes
 //     and the fields are 16-byte aligned, else by batched loads;
-//   - enough faces per CTA that the pointwise flux phase has one face point
-//     per thread (FPB x n_q^2 <= 128);
-//   - the stage buffers alias one another along their lifetimes (cells ->
-//     interpolated half-stage -> tested fluxes in one region, the normal
-//     contraction and the face-point values in another), which keeps three
-//     or more CTAs per SM.
-// Interior-only CTAs take the modal shortcut of face_kernel (n3, c1, c2, c3
-// tested from the normal contraction; only n1, n2, c1, c3 go to the face
-// points).  Output: the same face records, [2][6][n_bt] per face.
+//   - the fluxes of n3, c1, c2, c3 are purely diffusive and linear: with the
+//     orthonormal tangential basis and exact face quadrature their tested
+//     fluxes follow from the normal contraction in modal form, so only n1,
+//     n2, c1, c3 go to the face points and only n1, n2 are tested there;
+//     the stage buffers hold just those species;
+//   - the boundary data of Eq. 3 at the points of the owning trace (n1, n2
+//     through the points; the c2 influx on Gamma_1, which does not depend on
+//     U, tested directly);
+//   - enough faces per CTA that the pointwise phase has one face point per
+//     thread (FPB x n_q^2 <= 128), and the stage buffers alias one another
+//     along their lifetimes.
+// Output: the same face records as face_kernel, [2][6][n_bt] per face.
 #pragma once
 
 namespace cdg2 {
+
+// slot of a species in the face-point stage buffers ({n1, n2, c1, c3}), -1 if none
+__host__ __device__ constexpr int set5_slot(int s) { return s < 2 ? s : (s == 3 ? 2 : (s == 5 ? 3 : -1)); }
 
 template <int K, int F, typename T>
 struct Face3Plan {
@@ -27,13 +33,14 @@ struct Face3Plan {
     // FP64 JVP on Q3 keeps to 3 faces so that three CTAs fit on an SM
     static constexpr int FPB = K == 1 ? 14 : (K == 2 ? 8 : ((F == 2 && sizeof(T) == 8) ? 3 : 5));
     static_assert(FPB * NQT <= NT, "one face point per thread");
+    static constexpr int N5 = SpeciesSet<5>::N;                   // n1, n2, c1, c3
     static constexpr int CELL = NS * NB;                          // one cell, one field
     static constexpr int CELLS = 2 * F * FPB * CELL;              // [side][field][face][6][n_b]
-    static constexpr int FC = F * FPB * 4 * NS * NBT;             // normal contraction
-    static constexpr int FT = F * FPB * 4 * NS * NQ1 * NB1;       // half-interpolated
-    static constexpr int FP = F * FPB * 4 * NS * NQT;             // face-point values
-    static constexpr int FS = FPB * 2 * NS * NQT;                 // weighted sigma, tau at the points
-    static constexpr int TS1 = FPB * 2 * NS * NB1 * NQ1;          // half-tested
+    static constexpr int FC = F * FPB * 4 * N5 * NBT;             // normal contraction [field][face][4][N5][n_bt]
+    static constexpr int FT = F * FPB * 4 * N5 * NQ1 * NB1;       // half-interpolated
+    static constexpr int FP = F * FPB * 4 * N5 * NQT;             // face-point values
+    static constexpr int FS = FPB * 2 * 2 * NQT;                  // weighted sigma, tau of n1, n2 at the points
+    static constexpr int TS1 = FPB * 2 * 2 * NB1 * NQ1;           // half-tested
     static constexpr int TS = FPB * 2 * NS * NBT;                 // tested fluxes (the output records)
     static constexpr int XN = cmax(cmax(CELLS, FT), FS + TS1);    // region X: cells, FT, FS + TS1
     static constexpr int YN = cmax(FC, FP);                       // region Y: FC, FP
@@ -69,6 +76,7 @@ __global__ void __launch_bounds__(128) face3_kernel(const Geo g, const TabP<T> t
     T* X = reinterpret_cast<T*>(smem_raw + P::X_OFF);
     T* Y = X + P::XN;
     T* Z = Y + P::YN;
+    constexpr int N5 = P::N5;
     T* FC = Y;
     T* FT = X;
     T* FPt = Y;
@@ -77,8 +85,8 @@ __global__ void __launch_bounds__(128) face3_kernel(const Geo g, const TabP<T> t
     T* TS = Z;
     __shared__ long long cm[FPB], cp[FPB];   // minus / plus cell (-1: none)
     __shared__ int kind[FPB];                // -1 unused, 0 interior, 1 high boundary, 2 low boundary
-    __shared__ int any_boundary;             // a boundary face in this CTA: no modal shortcut
     __shared__ int copies_ok;
+    __shared__ T sA[NS];
     __shared__ T psT[MODE == MODE_JVP ? NS * NB : 1];
     const CoefT<T>& c = args.c;
     const long long nf = faces_of_axis(g, A);
@@ -88,7 +96,8 @@ __global__ void __launch_bounds__(128) face3_kernel(const Geo g, const TabP<T> t
     const bool bulk = P::BULK && use_bulk;   // the host checked the fields' 16-byte alignment
 
     if (tid == 0) {
-        any_boundary = 0;
+#pragma unroll
+        for (int sp = 0; sp < NS; ++sp) sA[sp] = c.A[sp];
         if (bulk) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -116,7 +125,6 @@ __global__ void __launch_bounds__(128) face3_kernel(const Geo g, const TabP<T> t
         kind[tid] = kd;
     }
     __syncthreads();
-    if (tid < FPB && kind[tid] > 0) any_boundary = 1;
     if (bulk) {
         if (tid == 0) {
             uint32_t bytes = 0;
@@ -183,112 +191,110 @@ __global__ void __launch_bounds__(128) face3_kernel(const Geo g, const TabP<T> t
     if (bulk && !copies_ok) return;
 
     const T invh = c.invh[A];
+    const T pen = c.pen_c * T((K + 1) * (K + 1)) * invh;
     // normal contraction: 0 the owning trace (K^- at xi = 1, or K^+ at xi = 0 on a
-    // low boundary), 1 the jump (difference-first), 2 d_n U^-, 3 d_n U^+
-    for (int idx = tid; idx < F * FPB * NS * NBT; idx += P::NT) {
-        const int t = idx % NBT;
-        const int s = (idx / NBT) % NS;
-        const int j = (idx / (NBT * NS)) % FPB;
-        const int fi = idx / (NBT * NS * FPB);
-        const int b0 = t % NB1, b1 = t / NB1;
-        const T* um = X + (fi * FPB + j) * CELL + s * NB;
-        const T* up = X + ((F + fi) * FPB + j) * CELL + s * NB;
-        T vm[NB1], vp[NB1];
-#pragma unroll
-        for (int m = 0; m < NB1; ++m) {
-            const int ci = coef_index<D, K, A>(m, b0, b1);
-            vm[m] = um[ci];
-            vp[m] = up[ci];
-            if (MODE == MODE_JVP && fi == 1 && ps) {
-                vm[m] *= ps[s * NB + ci];
-                vp[m] *= ps[s * NB + ci];
+    // low boundary), 1 the jump (difference-first), 2 d_n U^-, 3 d_n U^+.  The
+    // last field (the tangent in the JVP) over all species: n1, n2, c1, c3 to
+    // the stage buffer, the modal fluxes of n3, c1, c2, c3 straight to the
+    // output records; the JVP's first field (U) over n1, n2, c1, c3 only.
+    {
+        constexpr int NLAST = FPB * NS * NBT, NFIRST = (F - 1) * FPB * N5 * NBT;
+        for (int idx = tid; idx < NLAST + NFIRST; idx += P::NT) {
+            int fi, s, j, t;
+            if (idx < NLAST) {
+                fi = F - 1;
+                t = idx % NBT;
+                s = (idx / NBT) % NS;
+                j = idx / (NBT * NS);
+            } else {
+                const int r = idx - NLAST;
+                fi = 0;
+                t = r % NBT;
+                s = SpeciesSet<5>::s((r / NBT) % N5);
+                j = r / (NBT * N5);
             }
-        }
-        const int kd = kind[j];
-        T uo = 0, del = 0, dm = 0, dp = 0;
-        if (kd == 2) {
-#pragma unroll
-            for (int m = 0; m < NB1; ++m) uo = fma(tb.e[0][m], vp[m], uo);
-        } else {
-#pragma unroll
-            for (int m = 0; m < NB1; ++m) uo = fma(tb.e[1][m], vm[m], uo);
-        }
-        if (kd == 0) {
-            del = vm[0] - vp[0];
-#pragma unroll
-            for (int m = 1; m < NB1; ++m) {
-                del = fma(tb.e[1][m], vm[m], del);
-                del = fma(-tb.e[0][m], vp[m], del);
-            }
+            const int b0 = t % NB1, b1 = t / NB1;
+            const T* um = X + (fi * FPB + j) * CELL + s * NB;
+            const T* up = X + ((F + fi) * FPB + j) * CELL + s * NB;
+            T vm[NB1], vp[NB1];
 #pragma unroll
             for (int m = 0; m < NB1; ++m) {
-                dm = fma(tb.dh[A][1][m], vm[m], dm);
-                dp = fma(tb.dh[A][0][m], vp[m], dp);
+                const int ci = coef_index<D, K, A>(m, b0, b1);
+                vm[m] = um[ci];
+                vp[m] = up[ci];
+                if (MODE == MODE_JVP && fi == 1 && ps) {
+                    vm[m] *= ps[s * NB + ci];
+                    vp[m] *= ps[s * NB + ci];
+                }
+            }
+            const int kd = kind[j];
+            T uo = 0, del = 0, dm = 0, dp = 0;
+            if (kd == 2) {
+#pragma unroll
+                for (int m = 0; m < NB1; ++m) uo = fma(tb.e[0][m], vp[m], uo);
+            } else {
+#pragma unroll
+                for (int m = 0; m < NB1; ++m) uo = fma(tb.e[1][m], vm[m], uo);
+            }
+            if (kd == 0) {
+                del = vm[0] - vp[0];
+#pragma unroll
+                for (int m = 1; m < NB1; ++m) {
+                    del = fma(tb.e[1][m], vm[m], del);
+                    del = fma(-tb.e[0][m], vp[m], del);
+                }
+#pragma unroll
+                for (int m = 0; m < NB1; ++m) {
+                    dm = fma(tb.dh[A][1][m], vm[m], dm);
+                    dp = fma(tb.dh[A][0][m], vp[m], dp);
+                }
+            }
+            const int ss = set5_slot(s);
+            if (ss >= 0) {
+                T* o = FC + ((fi * FPB + j) * 4) * N5 * NBT + ss * NBT + t;
+                o[0 * N5 * NBT] = uo;
+                o[1 * N5 * NBT] = del;
+                o[2 * N5 * NBT] = dm;
+                o[3 * N5 * NBT] = dp;
+            }
+            if (fi == F - 1 && s >= 2) {
+                // sigma_t = A (d_n U^-_t + d_n U^+_t) / 2 - pen A Delta_t, tau_t = A Delta_t / 2,
+                // weighted by 1 / h_A; zero on boundary faces (their data are added below)
+                const T As = sA[s];
+                const bool in = kd == 0;
+                T* o = TS + (j * 2) * NS * NBT + s * NBT + t;
+                o[0] = in ? invh * As * (T(0.5) * (dm + dp) - pen * del) : T(0);
+                o[NS * NBT] = in ? invh * T(0.5) * As * del : T(0);
             }
         }
-        T* o = FC + ((fi * FPB + j) * 4) * NS * NBT + s * NBT + t;
-        o[0 * NS * NBT] = uo;
-        o[1 * NS * NBT] = del;
-        o[2 * NS * NBT] = dm;
-        o[3 * NS * NBT] = dp;
     }
     __syncthreads();
-    const bool modal = any_boundary == 0;
-    const T pen = c.pen_c * T((K + 1) * (K + 1)) * invh;
-    if (modal) {
-        // n3, c1, c2, c3 in modal form (orthonormal tangential basis, exact face
-        // quadrature): sigma_t = A (d_n U^-_t + d_n U^+_t) / 2 - pen A Delta_t,
-        // tau_t = A Delta_t / 2 (of the tangent in the JVP), weighted by 1 / h_A
-        constexpr int fl = F - 1;
-        constexpr int NM = SpeciesSet<3>::N;
-        for (int idx = tid; idx < FPB * NM * NBT; idx += P::NT) {
-            const int t = idx % NBT, ss = (idx / NBT) % NM, j = idx / (NBT * NM);
-            const int s = SpeciesSet<3>::s(ss);
-            const T* f = FC + ((fl * FPB + j) * 4) * NS * NBT + s * NBT + t;
-            const T del = f[1 * NS * NBT], dm = f[2 * NS * NBT], dp = f[3 * NS * NBT];
-            T As;   // c.A[s] without an indexed parameter load
-            switch (s) {
-                case 2: As = c.A[2]; break;
-                case 3: As = c.A[3]; break;
-                case 4: As = c.A[4]; break;
-                default: As = c.A[5]; break;
-            }
-            T* o = TS + (j * 2) * NS * NBT + s * NBT + t;
-            o[0] = kind[j] == 0 ? invh * As * (T(0.5) * (dm + dp) - pen * del) : T(0);
-            o[NS * NBT] = kind[j] == 0 ? invh * T(0.5) * As * del : T(0);
-        }
-        sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, 1, 1, T, 5>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT,
-                                                                   NQ1 * NB1, F * FPB * 4 * SpeciesSet<5>::N);
-        __syncthreads();
-        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1, T, 5>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1,
-                                                                   FPt, NQT, F * FPB * 4 * SpeciesSet<5>::N);
-    } else {
-        sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT,
-                                                           NQ1 * NB1, F * FPB * 4 * NS);
-        __syncthreads();
-        sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, FPt,
-                                                           NQT, F * FPB * 4 * NS);
-    }
+    sf_sym<0, NB1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FC, &tb.B[0][0], nullptr, nullptr, NBT, FT, NQ1 * NB1,
+                                                       F * FPB * 4 * N5);
+    __syncthreads();
+    sf_sym<1, NQ1, NB1, 1, NQ1, false, K + 1, false, 1, 1>(FT, &tb.B[0][0], nullptr, nullptr, NQ1 * NB1, FPt, NQT,
+                                                       F * FPB * 4 * N5);
     __syncthreads();
 
-    // pointwise fluxes: one face point per thread
+    // pointwise fluxes of n1, n2: one face point per thread
     if (tid < FPB * NQT) {
         const int p = tid % NQT, j = tid / NQT;
         const int kd = kind[j];
-        T sig[NS], tau[NS];
         const int p0 = p % NQ1, p1 = p / NQ1;
         const T Wp = tb.w[p0] * tb.w[p1] * invh;   // the element kernel accumulates the residual divided by |K|
         T uo[NS], del[NS], dm[NS], dp[NS];
         {
-            const T* base = FPt + (j * 4) * NS * NQT + p;
+            const T* base = FPt + (j * 4) * N5 * NQT + p;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                uo[s] = base[(0 * NS + s) * NQT];
-                del[s] = base[(1 * NS + s) * NQT];
-                dm[s] = base[(2 * NS + s) * NQT];
-                dp[s] = base[(3 * NS + s) * NQT];
+                const int ss = set5_slot(s);
+                uo[s] = ss < 0 ? T(0) : base[(0 * N5 + ss) * NQT];
+                del[s] = ss < 0 ? T(0) : base[(1 * N5 + ss) * NQT];
+                dm[s] = ss < 0 ? T(0) : base[(2 * N5 + ss) * NQT];
+                dp[s] = ss < 0 ? T(0) : base[(3 * N5 + ss) * NQT];
             }
         }
+        T sig[NS], tau[NS];
         if (kd == 0) {
             T uP[NS];
 #pragma unroll
@@ -297,25 +303,26 @@ __global__ void __launch_bounds__(128) face3_kernel(const Geo g, const TabP<T> t
                 face_point<T>(c, pen, uo, dm, uP, dp, del, sig, tau);
             } else {
                 T tuo[NS], tdel[NS], tdm[NS], tdp[NS], tuP[NS];
-                const T* base = FPt + ((FPB + j) * 4) * NS * NQT + p;
+                const T* base = FPt + ((FPB + j) * 4) * N5 * NQT + p;
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
-                    tuo[s] = base[(0 * NS + s) * NQT];
-                    tdel[s] = base[(1 * NS + s) * NQT];
-                    tdm[s] = base[(2 * NS + s) * NQT];
-                    tdp[s] = base[(3 * NS + s) * NQT];
+                    const int ss = set5_slot(s);
+                    tuo[s] = ss < 0 ? T(0) : base[(0 * N5 + ss) * NQT];
+                    tdel[s] = ss < 0 ? T(0) : base[(1 * N5 + ss) * NQT];
+                    tdm[s] = ss < 0 ? T(0) : base[(2 * N5 + ss) * NQT];
+                    tdp[s] = ss < 0 ? T(0) : base[(3 * N5 + ss) * NQT];
                     tuP[s] = tuo[s] - tdel[s];
                 }
                 face_point_lin<T>(c, pen, uo, dm, uP, dp, del, tuo, tdm, tuP, tdp, tdel, sig, tau);
             }
 #pragma unroll
-            for (int s = 0; s < NS; ++s) {
+            for (int s = 0; s < 2; ++s) {
                 sig[s] = Wp * sig[s];
                 tau[s] = Wp * tau[s];
             }
         } else {
 #pragma unroll
-            for (int s = 0; s < NS; ++s) {
+            for (int s = 0; s < 2; ++s) {
                 sig[s] = T(0);
                 tau[s] = T(0);
             }
@@ -329,30 +336,41 @@ __global__ void __launch_bounds__(128) face3_kernel(const Geo g, const TabP<T> t
                     boundary_point<T>(c, f, x, g, uo, sig, c.dth[7], false);
                 const T sg = kd == 2 ? -Wp : Wp;
 #pragma unroll
-                for (int s = 0; s < NS; ++s) sig[s] = sg * sig[s];
+                for (int s = 0; s < 2; ++s) sig[s] = sg * sig[s];
             }
         }
-        T* o = FS + (j * 2) * NS * NQT + p;
+        T* o = FS + (j * 2) * 2 * NQT + p;
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            o[(0 * NS + s) * NQT] = sig[s];
-            o[(1 * NS + s) * NQT] = tau[s];
+        for (int s = 0; s < 2; ++s) {
+            o[(0 * 2 + s) * NQT] = sig[s];
+            o[(1 * 2 + s) * NQT] = tau[s];
         }
     }
     __syncthreads();
-    if (modal) {
-        // n1, n2 through the face points
-        sf_sym<0, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1, T, 2>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1,
-                                                                  NB1 * NQ1, FPB * 2 * SpeciesSet<2>::N);
-        __syncthreads();
-        sf_sym<1, NB1, NQ1, 1, NB1, true, K + 1, false, 1, 1, T, 2>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1,
-                                                                  TS, NBT, FPB * 2 * SpeciesSet<2>::N);
-    } else {
-        sf_sym<0, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1,
-                                                          NB1 * NQ1, FPB * 2 * NS);
-        __syncthreads();
-        sf_sym<1, NB1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1, TS,
-                                                          NBT, FPB * 2 * NS);
+    sf_sym<0, NQ1, NQ1, 1, NB1, true, K + 1, false, 1, 1>(FS, &tb.B[0][0], nullptr, nullptr, NQT, TS1, NB1 * NQ1,
+                                                      FPB * 2 * 2);
+    __syncthreads();
+    sf_sym<1, NB1, NQ1, 1, NB1, true, K + 1, false, 1, 1, T, 2, true>(TS1, &tb.B[0][0], nullptr, nullptr, NB1 * NQ1,
+                                                                  TS, NBT, FPB * 2 * 2);
+    if constexpr (A == 1 && MODE == MODE_APPLY) {
+        // the c2 influx on Gamma_1 (Eq. 3), bc_sign A_c2 sigma on Gamma_{1,in}, tested over
+        // the points of the low-boundary faces (sigma of the owning cell: -W_p times the data)
+        for (int idx = tid; idx < FPB * NBT; idx += P::NT) {
+            const int j = idx / NBT, t = idx % NBT;
+            if (kind[j] != 2) continue;
+            const int t0 = t % NB1, t1 = t / NB1;
+            const long long cell = cp[j];
+            const T val = T(c.bc_sign) * sA[4] * T(c.sigma);
+            T acc = T(0);
+            for (int p1 = 0; p1 < NQ1; ++p1)
+                for (int p0 = 0; p0 < NQ1; ++p0) {
+                    const T x = T((cell % g.n[0]) * g.h[0]) + T(g.h[0]) * tb.xi[p0];
+                    const T s4 = (x >= T(g.g1in[0]) && x <= T(g.g1in[1])) ? val : T(0);
+                    const T Wp = tb.w[p0] * tb.w[p1] * invh;
+                    acc = fma(tb.B[p0][t0] * tb.B[p1][t1], -Wp * s4, acc);
+                }
+            TS[(j * 2) * NS * NBT + 4 * NBT + t] = acc;
+        }
     }
     __syncthreads();
     // coalesced store of the faces' tested fluxes

@@ -190,16 +190,18 @@ __global__ void __launch_bounds__(VT) k_mdot2_partial(long long n, int nv, const
     for (int jj = 0; jj < NVC; ++jj) aw[jj] = av[jj] = T(0);
     const long long np = n / W, stride = (long long)gridDim.x * VT;
     for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < np; i += stride) {
+        // all loads of the step issued before the first use (a short last chunk
+        // re-reads its last vector; those products are never stored)
         const Pack<T> wi = ld16(w + i * W), li = ld16(vl + i * W);
+        Pack<T> v[NVC];
+#pragma unroll
+        for (int jj = 0; jj < NVC; ++jj) v[jj] = ld16(V + (long long)(j0 + (jj < nj ? jj : nj - 1)) * ldv + i * W);
 #pragma unroll
         for (int jj = 0; jj < NVC; ++jj) {
-            if (jj < nj) {
-                const Pack<T> v = ld16(V + (j0 + jj) * ldv + i * W);
 #pragma unroll
-                for (int c = 0; c < W; ++c) {
-                    aw[jj] = fma(v.v[c], wi.v[c], aw[jj]);
-                    av[jj] = fma(v.v[c], li.v[c], av[jj]);
-                }
+            for (int c = 0; c < W; ++c) {
+                aw[jj] = fma(v[jj].v[c], wi.v[c], aw[jj]);
+                av[jj] = fma(v[jj].v[c], li.v[c], av[jj]);
             }
         }
         if (blockIdx.y == 0) {

@@ -1217,10 +1217,9 @@ static cudaError_t launch_one(const cdg2_mesh& m, const Coef& c, OpArgs<T> a, cu
         if (a.flags & CDG2_TF32) return launch_tc<MODE>(m, a, st);
     }
     a.fbuf = nullptr;
-    // Face-once for FP64 (bound by the FP64 pipe: halving the face arithmetic
-    // pays) and for 2D; the fused path stays for FP32 in 3D, where the extra
-    // launches and face loads cost more than the arithmetic they save.
-    constexpr bool face_once = MODE != MODE_VJP && (sizeof(T) == 8 || D == 2);
+    // Face-once (each face evaluated once, by the face kernels) for the apply
+    // and the JVP; the VJP keeps the fused path.
+    constexpr bool face_once = MODE != MODE_VJP;
     if constexpr (face_once) {
         cudaError_t e = launch_faces<D, K, MODE, T>(m, a, st);
         if (e != cudaSuccess) return e;

@@ -142,9 +142,13 @@ __device__ __forceinline__ void ld_x8(uint32_t a, float* v) {
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Round to the nearest TF32 value (ties away from zero) with two integer
-// operations (finite inputs; the conversion instruction is slower here).
+// operations (finite inputs), written as integer instructions so that they
+// stay on the integer pipe (the conversion instruction runs on the narrow
+// FP64 pipe here).
 __device__ __forceinline__ float to_tf32(float x) {
-    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+    uint32_t u;
+    asm("{\n\t.reg .u32 t;\n\tadd.u32 t, %1, 4096;\n\tand.b32 %0, t, 0xFFFFE000;\n\t}" : "=r"(u) : "r"(__float_as_uint(x)));
+    return __uint_as_float(u);
 }
 
 // One thread: expect `bytes` on the mbarrier and copy them from global to

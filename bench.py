@@ -47,9 +47,11 @@ def apply_flops_per_element(dim: int, k: int) -> int:
     n2..c3 in modal form (the nonzero entries of the 1D stiffness: same parity,
     both modes > 0); per axis the normal expansion of its two faces' tested
     fluxes.  Face kernel, one face per element and axis: normal contraction
-    (owning trace, jump, both normal derivatives), tangential interpolation of
-    4 fields, the pointwise face flux (126 per point, eight sensitivities
-    inverted together), tangential test of 2 fields.
+    (owning trace, jump, both normal derivatives) of all six species, the
+    modal diffusive fluxes of n3..c3 (9 per tangential mode and species),
+    tangential interpolation of the four traces of n1, n2, c1, c3, the
+    pointwise face flux of n1, n2 (about 90 per point, eight sensitivities
+    inverted together), tangential test of sigma and tau of n1, n2.
     """
     b, q, d, s = k + 1, k + 2, dim, 6
     H, mid = q // 2, q % 2
@@ -67,20 +69,20 @@ def apply_flops_per_element(dim: int, k: int) -> int:
         grads = b * fwd(-1) + q * (fwd(1) + fwd(-1))
         test_grad = q * (tr2 + tr(1)) + b * tr2
         test_val = q * tr(1) + b * tr(1)
-        tang = 4 * fwd(1) + 2 * tr(1)
+        interp, test = fwd(1), tr(1)
     else:
         values = b * b * fwd(1) + q * b * fwd(1) + q * q * fwd(1)
         grads = b * b * fwd(-1) + q * b * (fwd(1) + fwd(-1)) + q * q * (2 * fwd(1) + fwd(-1))
         test_grad = q * q * (tr2 + 2 * tr(1)) + q * b * (tr2 + tr(1)) + b * b * tr2
         test_val = q * q * tr(1) + q * b * tr(1) + b * b * tr(1)
-        tang = 4 * (b * fwd(1) + q * fwd(1)) + 2 * (q * tr(1) + b * tr(1))
+        interp, test = b * fwd(1) + q * fwd(1), q * tr(1) + b * tr(1)
     nz = [0] + [len(range(1 if a % 2 else 2, b, 2)) for a in range(1, b)]   # stiffness entries per row
     modal = sum(2 * nz[a] for a in range(b)) * d * b ** (d - 1) + 2 * b ** d
     normal = b ** (d - 1) * (2 * (5 * b - 2) + 1)
     expand = 8 * b ** d
     volume = 6 * values + 3 * grads + 2 * test_grad + 4 * test_val + 5 * modal
-    faces = s * d * (normal + tang + expand)
-    pointwise = q ** d * (43 + 28 * d) + d * q ** (d - 1) * 126
+    faces = d * (s * normal + 4 * 9 * b ** (d - 1) + 16 * interp + 4 * test + s * expand)
+    pointwise = q ** d * (43 + 28 * d) + d * q ** (d - 1) * 90
     return volume + faces + pointwise
 
 
@@ -88,9 +90,10 @@ def apply_flops_per_element(dim: int, k: int) -> int:
 # element kernels), from one ncu capture (profiles/), keyed by workload and
 # valid only for the kernel sources the counters were taken with (first 16 hex
 # of their sha256).
-NCU_TRAFFIC = {("2D 256x64 Q3 manufactured solution", "double"): (50636477, "6d354302f83ea1ce")}
+NCU_TRAFFIC = {("3D 128x32x32 Q2 seeded Gaussians", "double"): (1425502720, "9de59aa29ec1714e")}
 KERNEL_SOURCES = ("paper_1403_1157_gb300/csrc/operator.cu", "paper_1403_1157_gb300/csrc/elem_common.cuh",
-                  "paper_1403_1157_gb300/csrc/physics.cuh", "paper_1403_1157_gb300/csrc/tc_elem.cuh")
+                  "paper_1403_1157_gb300/csrc/physics.cuh", "paper_1403_1157_gb300/csrc/tc_elem.cuh",
+                  "paper_1403_1157_gb300/csrc/face3.cuh")
 
 
 def kernel_source_hash() -> str:
@@ -246,24 +249,24 @@ TC_FLOPS_PER_ELEMENT = {"apply": 2 * 128 * 64 * 15 + 2 * 64 * 128 * 12, "jvp": 2
 # divided by its elements), keyed by (dim, k, op, dtype) and valid only for the
 # kernel sources the counters were taken with (first 16 hex of their sha256).
 FLOPS_PER_ELEMENT = {
-    (3, 2, 'apply', 'f64'): (49387, '4183afe65d9b56bb'),
-    (3, 2, 'apply', 'f32'): (76207, '4183afe65d9b56bb'),
-    (3, 2, 'jvp', 'f64'): (74197, '4183afe65d9b56bb'),
-    (3, 2, 'jvp', 'f32'): (122393, '4183afe65d9b56bb'),
-    (3, 2, 'vjp', 'f64'): (126836, '4183afe65d9b56bb'),
-    (3, 2, 'vjp', 'f32'): (122345, '4183afe65d9b56bb'),
-    (3, 3, 'apply', 'f64'): (105688, '4183afe65d9b56bb'),
-    (3, 3, 'apply', 'f32'): (160596, '4183afe65d9b56bb'),
-    (3, 3, 'jvp', 'f64'): (158746, '4183afe65d9b56bb'),
-    (3, 3, 'jvp', 'f32'): (257828, '4183afe65d9b56bb'),
-    (3, 3, 'vjp', 'f64'): (266801, '4183afe65d9b56bb'),
-    (3, 3, 'vjp', 'f32'): (259292, '4183afe65d9b56bb'),
-    (2, 3, 'apply', 'f64'): (13700, '4183afe65d9b56bb'),
-    (2, 3, 'apply', 'f32'): (14605, '4183afe65d9b56bb'),
-    (2, 3, 'jvp', 'f64'): (20346, '4183afe65d9b56bb'),
-    (2, 3, 'jvp', 'f32'): (22794, '4183afe65d9b56bb'),
-    (2, 3, 'vjp', 'f64'): (32662, '4183afe65d9b56bb'),
-    (2, 3, 'vjp', 'f32'): (31423, '4183afe65d9b56bb'),
+    (3, 2, 'apply', 'f64'): (43229, '9de59aa29ec1714e'),
+    (3, 2, 'apply', 'f32'): (48076, '9de59aa29ec1714e'),
+    (3, 2, 'jvp', 'f64'): (64818, '9de59aa29ec1714e'),
+    (3, 2, 'jvp', 'f32'): (75684, '9de59aa29ec1714e'),
+    (3, 2, 'vjp', 'f64'): (126836, '9de59aa29ec1714e'),
+    (3, 2, 'vjp', 'f32'): (122861, '9de59aa29ec1714e'),
+    (3, 3, 'apply', 'f64'): (94278, '9de59aa29ec1714e'),
+    (3, 3, 'apply', 'f32'): (107102, '9de59aa29ec1714e'),
+    (3, 3, 'jvp', 'f64'): (138452, '9de59aa29ec1714e'),
+    (3, 3, 'jvp', 'f32'): (165149, '9de59aa29ec1714e'),
+    (3, 3, 'vjp', 'f64'): (266801, '9de59aa29ec1714e'),
+    (3, 3, 'vjp', 'f32'): (260326, '9de59aa29ec1714e'),
+    (2, 3, 'apply', 'f64'): (13299, '9de59aa29ec1714e'),
+    (2, 3, 'apply', 'f32'): (14206, '9de59aa29ec1714e'),
+    (2, 3, 'jvp', 'f64'): (19632, '9de59aa29ec1714e'),
+    (2, 3, 'jvp', 'f32'): (22050, '9de59aa29ec1714e'),
+    (2, 3, 'vjp', 'f64'): (32662, '9de59aa29ec1714e'),
+    (2, 3, 'vjp', 'f32'): (31681, '9de59aa29ec1714e'),
 }
 
 
@@ -848,11 +851,15 @@ def main():
                    "step": "one cdg2_apply (M^-1 L_h, FP64) over the whole mesh"},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
                      "frac": achieved_tf / peaks["fp64_tflops"], "traffic": ncu_traffic(w.name, "double"),
+                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one apply's launches (bytes), "
+                                     "ncu capture of the same workload; null once the kernel sources changed",
+                     "algorithmic_bytes": BYTES_PER_DOF[("apply", "f64")] * w.n_dof,
                      "peak_note": "FP64 FMA rate measured in this run by cdg2_probe_peak (FMA loop, 8 chains per "
                                   "thread, 8 x SMs blocks of 256 threads); achieved = flops of one apply / its "
                                   "event time (all its launches)",
                      "flops_per_apply": fl, "flops_source": fl_src,
-                     "kernels": f"{w.dim} x face_kernel<{w.dim},{w.k},0,A,double> + op_kernel<{w.dim},{w.k},0,double> (one apply)",
+                     "kernels": (f"3 x face3_kernel<{w.k},0,A,double>" if w.dim == 3 else
+                                 f"2 x face_kernel<2,{w.k},0,A,double>") + f" + op_kernel<{w.dim},{w.k},0,double> (one apply)",
                      "hbm_frac": head["hbm_frac"], "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_kind": kind,
                      "fp32_peak_tflops": peaks["fp32_tflops"]},
         "fp32": ops.pop("apply_f32"),

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(VT) k_mdot_partial(long long n, int nv, const 
 // (the newest basis vector, read from its slot in V), and with chunk 0 row
 // 2 nv = w . w.  One read of the chunk, w and V_last per block row.
 template <typename T>
-__global__ void __launch_bounds__(VT) k_mdot2_partial(long long n, int nv, const T* __restrict__ V, long long ldv,
+__global__ void __launch_bounds__(VT, sizeof(T) == 4 ? RED_BLOCKS / 152 : 1) k_mdot2_partial(long long n, int nv, const T* __restrict__ V, long long ldv,
                                                        const T* __restrict__ w, double* __restrict__ part) {
     constexpr int W = Pack<T>::W;
     __shared__ double sh[(2 * NVC + 1) * NWARP];

@@ -37,10 +37,11 @@ __device__ __forceinline__ void kappa_den(const CoefT<T>& c, const T u[NS], T* d
 // - A_s grad U_s and S(U) (Reading: the c1 row of S follows Eq. (1),
 // -alpha1 n1 c1 - alpha2 n2 c1 + f1 n3).  death1 = 0 drops the n1 death term
 // (the reduced model of Eq. (2), which keeps d1 n1 in the n3 equation).
-// MODAL: the diffusion of n2..c3 is applied elsewhere in modal form; only
+// MODAL = 1: the diffusion of n2..c3 is applied elsewhere in modal form; only
 // Phi_0 (with its diffusion) and the chemotactic part of Phi_1 are formed,
-// and only the gradients of n1, c1, c3 are read.
-template <int D, typename T, bool MODAL = false>
+// and only the gradients of n1, c1, c3 are read.  MODAL = 2: the diffusion of
+// n1 is modal too (Phi_0 is its chemotactic flux alone).
+template <int D, typename T, int MODAL = 0>
 __device__ __forceinline__ void volume_point(const CoefT<T>& c, const T u[NS], const T g[NS][D], T Phi[NS][D],
                                              T S[NS]) {
     T den[4], r[4];
@@ -52,8 +53,11 @@ __device__ __forceinline__ void volume_point(const CoefT<T>& c, const T u[NS], c
     for (int j = 0; j < D; ++j) {
         const T v1 = k11 * g[3][j] + k13 * g[5][j];
         const T v2 = k21 * g[3][j] - k22 * g[0][j];
-        Phi[0][j] = u[0] * v1 - T(c.A[0]) * g[0][j];
-        if constexpr (MODAL) {
+        if constexpr (MODAL == 2)
+            Phi[0][j] = u[0] * v1;
+        else
+            Phi[0][j] = u[0] * v1 - T(c.A[0]) * g[0][j];
+        if constexpr (MODAL >= 1) {
             Phi[1][j] = u[1] * v2;
         } else {
             Phi[1][j] = u[1] * v2 - T(c.A[1]) * g[1][j];
@@ -74,7 +78,7 @@ __device__ __forceinline__ void volume_point(const CoefT<T>& c, const T u[NS], c
 // along a tangent of the reaction coefficients (dth = d(d1, d2, gamma,
 // alpha1, alpha2, f1, k_ox, .)), when has_dth.  With kappa = a / (c + b):
 // d kappa = -kappa / (c + b) dc.
-template <int D, typename T, bool MODAL = false>
+template <int D, typename T, int MODAL = 0>
 __device__ __forceinline__ void volume_point_lin(const CoefT<T>& c, const T u[NS], const T g[NS][D], const T du[NS],
                                                  const T dg[NS][D], bool has_dth, T dPhi[NS][D],
                                                  T dS[NS]) {
@@ -92,8 +96,11 @@ __device__ __forceinline__ void volume_point_lin(const CoefT<T>& c, const T u[NS
         const T v2 = k21 * g[3][j] - k22 * g[0][j];
         const T dv1 = dk11 * g[3][j] + k11 * dg[3][j] + dk13 * g[5][j] + k13 * dg[5][j];
         const T dv2 = dk21 * g[3][j] + k21 * dg[3][j] - dk22 * g[0][j] - k22 * dg[0][j];
-        dPhi[0][j] = du[0] * v1 + u[0] * dv1 - T(c.A[0]) * dg[0][j];
-        if constexpr (MODAL) {
+        if constexpr (MODAL == 2)
+            dPhi[0][j] = du[0] * v1 + u[0] * dv1;
+        else
+            dPhi[0][j] = du[0] * v1 + u[0] * dv1 - T(c.A[0]) * dg[0][j];
+        if constexpr (MODAL >= 1) {
             dPhi[1][j] = du[1] * v2 + u[1] * dv2;
         } else {
             dPhi[1][j] = du[1] * v2 + u[1] * dv2 - T(c.A[1]) * dg[1][j];

@@ -11,7 +11,7 @@
 //      c2, then element);
 //   2. one thread issues the forward MMAs: point values of all six species
 //      and the gradients of n1, c1, c3 (the fluxes need no others: the
-//      diffusion of n2..c3 is applied in modal form) into tensor memory,
+//      diffusion of every species is applied in modal form) into tensor memory,
 //      lanes = points, columns = (quantity, species, element);
 //   3. the weighted, transposed test table image (64 modes x 128 points, the
 //      Gauss weights folded in) replaces the forward one; every thread owns
@@ -22,7 +22,7 @@
 //   4. the test MMAs (M = 64 modes) accumulate the volume residual in tensor
 //      memory; it goes to shared memory while bulk copies bring the tile's
 //      coefficients and the tested fluxes of its faces (the face kernels'
-//      buffer) into the freed table region; the modal diffusion of n2..c3 and
+//      buffer) into the freed table region; the modal diffusion of all species and
 //      the two tested face fluxes per axis are added from shared memory, and
 //      the epilogue (M^{-1}, alpha w + beta J w) stores.
 // Operands use the 128-byte-swizzled K-major layout (TF32 operands must be
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(512, 1) tc_elem_kernel(const Geo g, const TabP
                         gu[5][j] = gr[h2][0][j][2];
                     }
                     if constexpr (MODE == MODE_APPLY) {
-                        volume_point<D, float, true>(c, uu, gu, Phi, Sr);
+                        volume_point<D, float, 2>(c, uu, gu, Phi, Sr);
                         if (args.flags & CDG2_FORCING) {
                             const long long ge = e0 + e;
                             const long long ix = ge % g.n[0], iy = (ge / g.n[0]) % g.n[1];
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(512, 1) tc_elem_kernel(const Geo g, const TabP
                             dg[3][j] = gr[h2][F - 1][j][1];
                             dg[5][j] = gr[h2][F - 1][j][2];
                         }
-                        volume_point_lin<D, float, true>(c, uu, gu, du, dg, args.has_dtheta != 0, Phi, Sr);
+                        volume_point_lin<D, float, 2>(c, uu, gu, du, dg, args.has_dtheta != 0, Phi, Sr);
                     }
                 }
                 // test operands: K = point q; rows species x element
@@ -501,10 +501,11 @@ __global__ void __launch_bounds__(512, 1) tc_elem_kernel(const Geo g, const TabP
     const float* sC = reinterpret_cast<const float*>(sTab + EPI_COEF);   // [e][s][i] of the last field
     const float* sF = reinterpret_cast<const float*>(sTab);              // face records [axis][e][lo, hi][2][6][16]
 
-    // ---- modal diffusion of n2..c3 (exact on the orthonormal basis), from the field's coefficients ----
-    for (int idx = t; idx < NE * SpeciesSet<4>::N * NB; idx += NT) {
+    // ---- modal diffusion of all six species (exact on the orthonormal basis, in FP32: the
+    // diffusive fluxes stay off the TF32 contractions), from the field's coefficients ----
+    for (int idx = t; idx < NE * NS * NB; idx += NT) {
         const int i = idx % NB, es = idx / NB;
-        const int e = es / SpeciesSet<4>::N, s = SpeciesSet<4>::s(es % SpeciesSet<4>::N);
+        const int e = es / NS, s = es % NS;
         if (e >= ne_real) continue;
         const float* uf = sC + (e * NS + s) * NB;
         const double* ps = (MODE == MODE_JVP && args.pscale) ? args.pscale + s * NB : nullptr;

@@ -673,7 +673,7 @@ def main():
     ap.add_argument("--grad-config", type=int, default=2, help="workload of the gradient-through-steps timing")
     ap.add_argument("--assembled-config", type=int, default=2,
                     help="workload of the assembled-Jacobian comparison (-1: skip)")
-    ap.add_argument("--profile-solve", choices=["mixed", "fp64"], default=None,
+    ap.add_argument("--profile-solve", choices=["mixed", "mixed_tf32", "fp64"], default=None,
                     help="run one implicit step of the solve workload and exit (for ncu launch lists)")
     ap.add_argument("--profile-op", default=None,
                     help="cfg:op:dtype[:reps[:cells]] (several separated by ';'), e.g. 3:jvp:f32:1:16x8x8: only "
@@ -699,7 +699,7 @@ def main():
         w = I.workload(args.solve_config)
         mesh = G.cdg2_mesh_create(w.dim, w.cells, w.extent, w.periodic, w.k)
         U, p = make_inputs(G, w, I, mesh)
-        mixed = args.profile_solve == "mixed"
+        mixed = {"mixed": 1, "mixed_tf32": 2, "fp64": 0}[args.profile_solve]
         scheme = G.CDG2_SDIRK2 if w.k == 1 else G.CDG2_SDIRK3
         rc, st = G.cdg2_step(mesh, p, U, 0.0, w.dt, G.make_opts(scheme=scheme, mixed=mixed, newton_rtol=1e-10,
                                                                  gmres_rtol=1e-4 if mixed else 1e-3,

@@ -64,12 +64,15 @@ __global__ void __launch_bounds__(VT) k_add_into(long long n, const T* __restric
 
 constexpr int NWARP = VT / 32;
 
-// Sum of v over the block in a fixed order (warp shuffles, then the warps'
-// partials in warp order); the result is valid in thread 0.  sh: NWARP doubles.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
+// Sum of v over the block in a fixed order (warp shuffles in the type of
+// the thread's partial, then the warps' partials in FP64, in warp order); the
+// result is valid in thread 0.  sh: NWARP doubles.  (FP32 partials stay FP32
+// within the warp: FP64 adds run on GB300's narrow FP64 pipe.)
+template <typename A>
+__device__ __forceinline__ double block_sum(A v, double* sh) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = double(v);
     __syncthreads();
     double s = 0.0;
     if (threadIdx.x == 0)
@@ -78,10 +81,11 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return s;
 }
 
-// NR block sums at once: result r lands in res[r] (shared), valid after the
-// call for every thread.  sh: NR * NWARP doubles, res: NR doubles.
-template <int NR>
-__device__ __forceinline__ void block_sums(double (&v)[NR], double* sh, double* res) {
+// NR block sums at once (same order and precision rules as block_sum):
+// result r lands in res[r] (shared), valid after the call for every thread.
+// sh: NR * NWARP doubles, res: NR doubles.
+template <int NR, typename A>
+__device__ __forceinline__ void block_sums(A (&v)[NR], double* sh, double* res) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
@@ -90,7 +94,7 @@ __device__ __forceinline__ void block_sums(double (&v)[NR], double* sh, double* 
     }
     if (lane == 0) {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) sh[r * NWARP + warp] = v[r];
+        for (int r = 0; r < NR; ++r) sh[r * NWARP + warp] = double(v[r]);
     }
     __syncthreads();
     for (int r = threadIdx.x; r < NR; r += VT) {
@@ -162,11 +166,11 @@ __global__ void __launch_bounds__(VT) k_mdot_partial(long long n, int nv, const 
         if (with_self) accw = fma(wi, wi, accw);
     }
     for (int jj = 0; jj < nj; ++jj) {
-        const double s = block_sum(double(acc[jj]), sh);
+        const double s = block_sum(acc[jj], sh);
         if (threadIdx.x == 0) part[(long long)(j0 + jj) * gridDim.x + blockIdx.x] = s;
     }
     if (with_self) {
-        const double s = block_sum(double(accw), sh);
+        const double s = block_sum(accw, sh);
         if (threadIdx.x == 0) part[(long long)nv * gridDim.x + blockIdx.x] = s;
     }
 }
@@ -209,13 +213,13 @@ __global__ void __launch_bounds__(VT, sizeof(T) == 4 ? RED_BLOCKS / 152 : 1) k_m
             for (int c = 0; c < W; ++c) ww = fma(wi.v[c], wi.v[c], ww);
         }
     }
-    double acc[2 * NVC + 1];
+    T acc[2 * NVC + 1];
 #pragma unroll
     for (int jj = 0; jj < NVC; ++jj) {
-        acc[jj] = double(aw[jj]);
-        acc[NVC + jj] = double(av[jj]);
+        acc[jj] = aw[jj];
+        acc[NVC + jj] = av[jj];
     }
-    acc[2 * NVC] = double(ww);
+    acc[2 * NVC] = ww;
     block_sums<2 * NVC + 1>(acc, sh, res);
     if ((int)threadIdx.x < nj) {
         part[(long long)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = res[threadIdx.x];
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(VT) k_update_norm16(long long n, int nv, const
 #pragma unroll
         for (int c = 0; c < W; ++c) nrm = fma(acc.v[c], acc.v[c], nrm);
     }
-    const double s = block_sum(double(nrm), sh);
+    const double s = block_sum(nrm, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(VT) k_update_norm(long long n, int nv, const T
         w[i] = acc;
         nrm = fma(acc, acc, nrm);
     }
-    const double s = block_sum(double(nrm), sh);
+    const double s = block_sum(nrm, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 

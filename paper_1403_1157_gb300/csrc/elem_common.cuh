@@ -166,13 +166,15 @@ struct SpeciesSet<5> {
 // operations per line and matrix instead of 20.  SEL restricts the pass to
 // the species of SpeciesSet<SEL>: tensor t is then (t / N, species s(t % N))
 // of an element-major [..][6] layout, and nt counts only those tensors; with
-// IN_COMPACT the input holds only those tensors, back to back.
+// IN_COMPACT the input holds only those tensors, back to back.  The lines
+// are dealt to the CTA's threads, or, given first >= 0, to `step` threads
+// numbered from `first` (a warp working alone).
 template <int AX, int I0, int I1, int I2, int NO, bool TR, int LD, bool TWO, int P1, int P2, typename T, int SEL = 0,
           bool IN_COMPACT = false>
 __device__ __forceinline__ void sf_sym(const T* __restrict__ in1, const T* __restrict__ M1,
                                        const typename Ident<T>::type* __restrict__ in2,
                                        const typename Ident<T>::type* __restrict__ M2, int in_stride,
-                                       T* __restrict__ out, int out_stride, int nt) {
+                                       T* __restrict__ out, int out_stride, int nt, int first = -1, int step = 0) {
     constexpr int NI = AX == 0 ? I0 : (AX == 1 ? I1 : I2);
     constexpr int NQ = TR ? NI : NO;   // points
     constexpr int NM = TR ? NO : NI;   // modes
@@ -190,7 +192,8 @@ __device__ __forceinline__ void sf_sym(const T* __restrict__ in1, const T* __res
             if constexpr (TWO) m2[q][a] = M2[q * LD + a];
         }
     const int total = nt * NL;
-    for (int line = threadIdx.x; line < total; line += blockDim.x) {
+    const int l0 = first < 0 ? (int)threadIdx.x : first, dl = first < 0 ? (int)blockDim.x : step;
+    for (int line = l0; line < total; line += dl) {
         const int tt = line / NL;
         const int r = line - tt * NL;
         int ib, ob;

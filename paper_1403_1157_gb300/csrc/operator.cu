@@ -1117,7 +1117,31 @@ static cudaError_t launch_faces(const cdg2_mesh& m, OpArgs<T>& a, cudaStream_t s
         a.fb_off[ax] = off;
         if (ax < D) off += faces_of_axis(m.geo, ax) * per_face;
     }
-    if constexpr (D == 3) {
+    if constexpr (D == 3 && K == 3 && std::is_same<T, float>::value) {
+        // FP32 on Q3: one warp per face (issue-bound; no CTA barriers between phases)
+        using FPl = Face3WPlan<K, fields_of(MODE), T>;
+        constexpr size_t fsmem = FPl::smem_bytes();
+        static_assert(fsmem <= 227 * 1024, "face kernel shared memory exceeds 227 KB");
+        static DeviceOnce fattr;
+        cudaError_t e = once_per_device(fattr, [] {
+            cudaError_t r = cudaFuncSetAttribute(face3w_kernel<K, MODE, 0, T>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(face3w_kernel<K, MODE, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fsmem);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(face3w_kernel<K, MODE, 2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fsmem);
+            return r;
+        });
+        if (e != cudaSuccess) return e;
+        auto al16 = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+        const int bulk = FPl::BULK && al16(a.U[0]) && (fields_of(MODE) == 1 || al16(a.U[1]));
+        auto fgrid = [&](int ax) { return (unsigned)((faces_of_axis(m.geo, ax) + FPl::WARPS - 1) / FPl::WARPS); };
+        face3w_kernel<K, MODE, 0, T><<<fgrid(0), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a, bulk);
+        face3w_kernel<K, MODE, 1, T><<<fgrid(1), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a, bulk);
+        face3w_kernel<K, MODE, 2, T><<<fgrid(2), FPl::NT, fsmem, st>>>(m.geo, tab_of<T>(m), a, bulk);
+    } else if constexpr (D == 3) {
         using FPl = Face3Plan<K, fields_of(MODE), T>;
         constexpr size_t fsmem = FPl::smem_bytes();
         static_assert(fsmem <= 227 * 1024, "face kernel shared memory exceeds 227 KB");

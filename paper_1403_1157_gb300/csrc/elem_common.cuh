@@ -287,18 +287,26 @@ __device__ __forceinline__ int coef_index(int m, int b0, int b1) {
     }
 }
 
+// Cell coordinates of element e.  Element indices fit in 31 bits
+// (cdg2_mesh_create bounds E * 6 * n_b below 2^31), so the divisions are
+// 32-bit ones.
+__device__ __forceinline__ void cell_coords(const Geo& g, long long e, int c[3]) {
+    const unsigned u = (unsigned)e, n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+    const unsigned r = u / n0;
+    c[0] = (int)(u - r * n0);
+    c[1] = (int)(r % n1);
+    c[2] = (int)(r / n1);
+}
+
 // Neighbour of element e across face f (0: low side, 1: high side) of axis
 // a; -1 on a non-periodic boundary.
 __device__ __forceinline__ long long neighbour(const Geo& g, long long e, int a, int f) {
-    long long ix = e % g.n[0];
-    long long r = e / g.n[0];
-    long long iy = r % g.n[1];
-    long long iz = r / g.n[1];
-    long long c[3] = {ix, iy, iz};
-    long long v = c[a] + (f ? 1 : -1);
+    int c[3];
+    cell_coords(g, e, c);
+    int v = c[a] + (f ? 1 : -1);
     if (v < 0 || v >= g.n[a]) {
         if (!g.periodic[a]) return -1;
-        v = (v + g.n[a]) % g.n[a];
+        v = v < 0 ? v + g.n[a] : v - g.n[a];
     }
     c[a] = v;
     return c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);

@@ -380,10 +380,11 @@ __host__ __device__ inline long long faces_of_axis(const Geo& g, int a) {
 
 // Index of the low-boundary face of a cell in the first layer of axis a.
 __device__ __forceinline__ long long low_layer_index(const Geo& g, long long e, int a) {
-    const long long ix = e % g.n[0], iy = (e / g.n[0]) % g.n[1], iz = e / ((long long)g.n[0] * g.n[1]);
-    if (a == 0) return iy + (long long)g.n[1] * iz;
-    if (a == 1) return ix + (long long)g.n[0] * iz;
-    return ix + (long long)g.n[0] * iy;
+    int c[3];
+    cell_coords(g, e, c);
+    if (a == 0) return c[1] + (long long)g.n[1] * c[2];
+    if (a == 1) return c[0] + (long long)g.n[0] * c[2];
+    return c[0] + (long long)g.n[0] * c[1];
 }
 
 template <int D, int K, int MODE, int A, typename T>

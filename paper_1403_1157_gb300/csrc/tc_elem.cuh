@@ -32,6 +32,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "elem_common.cuh"
@@ -221,6 +222,7 @@ __global__ void __launch_bounds__(512, 1) tc_elem_kernel(const Geo g, const TabP
     STab<K, float>& tb = *reinterpret_cast<STab<K, float>*>(smem + SMALL_OFF);
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + SMALL_OFF + 1024 + 256);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SMALL_OFF + 1024 + 256 + 48);
+    float* sA = reinterpret_cast<float*>(smem + SMALL_OFF + 1024 + 256 + 64);   // A_s (diffusion coefficients)
     static_assert(sizeof(STab<K, float>) <= 1024, "tables of the face expansion exceed their slot");
     const int t = threadIdx.x;
     const long long e0 = (long long)blockIdx.x * NE;
@@ -242,6 +244,10 @@ __global__ void __launch_bounds__(512, 1) tc_elem_kernel(const Geo g, const TabP
         bulk_load(sbase, tables, TAB_BYTES, bar2);
     }
     load_tab<K, float>(tb, tab);
+    if (t == 0) {
+#pragma unroll
+        for (int sp = 0; sp < NS; ++sp) sA[sp] = c.A[sp];
+    }
     // coefficients of the 16 elements, TF32, species-major rows (tangent pre-scaled);
     // each thread's loads are issued together
     constexpr int CH = NE * NS * (NB / 4);   // 16-byte chunks per field
@@ -443,7 +449,10 @@ __global__ void __launch_bounds__(512, 1) tc_elem_kernel(const Geo g, const TabP
                     const long long nb = neighbour(g, ge, a, 0);
                     f = nb >= 0 ? nb : g.E + low_layer_index(g, ge, a);
                 }
-                const float* src = args.fbuf + args.fb_off[a] + f * (2 * NS * 16);
+                // (the axis' offset by selection: an indexed parameter access would copy the
+                // kernel's parameters to local memory)
+                const long long off = a == 0 ? args.fb_off[0] : (a == 1 ? args.fb_off[1] : args.fb_off[2]);
+                const float* src = args.fbuf + off + f * (2 * NS * 16);
                 asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                              :: "r"(sbase + (uint32_t)(((a * NE + e) * 2 + side) * FACE_REC)), "l"(src),
                                 "r"((uint32_t)FACE_REC), "r"(bar4)
@@ -501,59 +510,77 @@ __global__ void __launch_bounds__(512, 1) tc_elem_kernel(const Geo g, const TabP
     const float* sC = reinterpret_cast<const float*>(sTab + EPI_COEF);   // [e][s][i] of the last field
     const float* sF = reinterpret_cast<const float*>(sTab);              // face records [axis][e][lo, hi][2][6][16]
 
-    // ---- modal diffusion of all six species (exact on the orthonormal basis, in FP32: the
-    // diffusive fluxes stay off the TF32 contractions), from the field's coefficients ----
-    for (int idx = t; idx < NE * NS * NB; idx += NT) {
-        const int i = idx % NB, es = idx / NB;
-        const int e = es / NS, s = es % NS;
-        if (e >= ne_real) continue;
-        const float* uf = sC + (e * NS + s) * NB;
-        const double* ps = (MODE == MODE_JVP && args.pscale) ? args.pscale + s * NB : nullptr;
-        float acc = 0.f;
-        int stride = 1, rest = i;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            const int a = rest % 4;
-            rest /= 4;
-            const int base = i - a * stride;
-            for (int bb = (a & 1) ? 1 : 2; a > 0 && bb <= K; bb += 2) {
-                const int ci = base + bb * stride;
-                const float uv = ps ? uf[ci] * float(ps[ci]) : uf[ci];
-                acc = fma(tb.K1h[j][a][bb], uv, acc);
-            }
-            stride *= 4;
-        }
-        sR[(e * NS + s) * NB + i] = fma(-c.A[s], acc, sR[(e * NS + s) * NB + i]);
-    }
-    __syncthreads();
-    // ---- the two tested face fluxes per axis (from the staged records), M^{-1}, store ----
+    // ---- per (element, species, mode), one pass: the modal diffusion of all six species (exact on
+    // the orthonormal basis, in FP32: the diffusive fluxes stay off the TF32 contractions), from
+    // the field's coefficients; the two tested face fluxes per axis (from the staged records);
+    // M^{-1}; store ----
     const float scale = (args.flags & CDG2_MINV) ? 1.f : c.vol;
     const float alphaT = float(args.alpha), betaT = float(args.beta);
-    for (int idx = t; idx < NE * NS * NB; idx += NT) {
-        const int i = idx % NB, es = idx / NB, e = es / NS, s = es % NS;
-        if (e >= ne_real) continue;
-        const int a0 = i % 4, a1 = (i / 4) % 4, a2 = i / 16;
-        float acc = sR[idx];
+    const double* psg = MODE == MODE_JVP ? args.pscale : nullptr;
+    // NT is a multiple of NB: all of a thread's items share its mode i, so the mode's table
+    // entries are read from shared memory once, into registers
+    static_assert(NT % NB == 0, "a thread's items must share one mode");
+    const int i = t % NB;
+    const int am[3] = {i % 4, (i / 4) % 4, i / 16};
+    float k1[3][K], fe0[3], fd0[3], fe1[3], fd1[3];
+    int tt[3];
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            // normal mode m and tangential index t (the other two in increasing axis order)
-            const int m = a == 0 ? a0 : (a == 1 ? a1 : a2);
-            const int tt = a == 0 ? a1 + 4 * a2 : (a == 1 ? a0 + 4 * a2 : a0 + 4 * a1);
-            const float* lo = sF + ((a * NE + e) * 2 + 0) * (FACE_REC / 4) + s * 16 + tt;
-            const float* hi = sF + ((a * NE + e) * 2 + 1) * (FACE_REC / 4) + s * 16 + tt;
-            acc = fma(-tb.e[0][m], lo[0], acc);
-            acc = fma(tb.dh[a][0][m], lo[NS * 16], acc);
-            acc = fma(tb.e[1][m], hi[0], acc);
-            acc = fma(tb.dh[a][1][m], hi[NS * 16], acc);
-        }
-        if constexpr (MODE == MODE_JVP) {
-            float w = sC[idx];
-            if (args.pscale) w *= float(args.pscale[idx % (NS * NB)]);
-            args.out[e0 * (NS * NB) + idx] = alphaT * w + betaT * (acc * scale);
-        } else {
-            args.out[e0 * (NS * NB) + idx] = acc * scale;
-        }
+    for (int j = 0; j < D; ++j) {
+#pragma unroll
+        for (int bb = 1; bb <= K; ++bb) k1[j][bb - 1] = tb.K1h[j][am[j]][bb];
+        fe0[j] = -tb.e[0][am[j]];
+        fd0[j] = tb.dh[j][0][am[j]];
+        fe1[j] = tb.e[1][am[j]];
+        fd1[j] = tb.dh[j][1][am[j]];
+        // tangential index: the other two axes in increasing order
+        tt[j] = j == 0 ? am[1] + 4 * am[2] : (j == 1 ? am[0] + 4 * am[2] : am[0] + 4 * am[1]);
     }
+    // the loop with and without the tangent's pre-scale (a branch outside it, not per load)
+    auto items = [&](auto scaled) {
+        constexpr bool SCALED = decltype(scaled)::value;
+        for (int idx = t; idx < NE * NS * NB; idx += NT) {
+            const int es = idx / NB, e = es / NS, s = es % NS;
+            if (e >= ne_real) continue;
+            const float* uf = sC + es * NB;
+            float md = 0.f;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                // 1D stiffness of axis j: modes b of a_j's parity, both > 0
+                const int a = am[j];
+                const int stride = j == 0 ? 1 : (j == 1 ? 4 : 16);
+                const int base = i - a * stride;
+#pragma unroll
+                for (int bb = 1; bb <= K; ++bb) {
+                    if (a > 0 && ((a ^ bb) & 1) == 0) {
+                        const int ci = base + bb * stride;
+                        const float uv = SCALED ? uf[ci] * float(psg[s * NB + ci]) : uf[ci];
+                        md = fma(k1[j][bb - 1], uv, md);
+                    }
+                }
+            }
+            float acc = fma(-sA[s], md, sR[idx]);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float* lo = sF + ((a * NE + e) * 2 + 0) * (FACE_REC / 4) + s * 16 + tt[a];
+                const float* hi = sF + ((a * NE + e) * 2 + 1) * (FACE_REC / 4) + s * 16 + tt[a];
+                acc = fma(fe0[a], lo[0], acc);
+                acc = fma(fd0[a], lo[NS * 16], acc);
+                acc = fma(fe1[a], hi[0], acc);
+                acc = fma(fd1[a], hi[NS * 16], acc);
+            }
+            if constexpr (MODE == MODE_JVP) {
+                float w = sC[idx];
+                if (SCALED) w *= float(psg[idx % (NS * NB)]);
+                args.out[e0 * (NS * NB) + idx] = alphaT * w + betaT * (acc * scale);
+            } else {
+                args.out[e0 * (NS * NB) + idx] = acc * scale;
+            }
+        }
+    };
+    if (psg)
+        items(std::true_type{});
+    else
+        items(std::false_type{});
 }
 
 }  // namespace cdg2

@@ -517,6 +517,15 @@ __global__ void __launch_bounds__(128) face3w_kernel(const Geo g, const TabP<T> 
     // normal contraction (as in face3_kernel, one face)
     {
         constexpr int NLAST = NS * NBT, NFIRST = (F - 1) * N5 * NBT;
+        // the 1D trace and normal-derivative tables in registers (every item reads all of them)
+        T e0r[NB1], e1r[NB1], d0r[NB1], d1r[NB1];
+#pragma unroll
+        for (int m = 0; m < NB1; ++m) {
+            e0r[m] = tb.e[0][m];
+            e1r[m] = tb.e[1][m];
+            d0r[m] = tb.dh[A][0][m];
+            d1r[m] = tb.dh[A][1][m];
+        }
         for (int idx = lane; idx < NLAST + NFIRST; idx += 32) {
             int fi, s, t;
             if (idx < NLAST) {
@@ -533,35 +542,51 @@ __global__ void __launch_bounds__(128) face3w_kernel(const Geo g, const TabP<T> 
             const T* um = X + fi * CELL + s * NB;
             const T* up = X + (F + fi) * CELL + s * NB;
             T vm[NB1], vp[NB1];
-#pragma unroll
-            for (int m = 0; m < NB1; ++m) {
-                const int ci = coef_index<D, K, A>(m, b0, b1);
-                vm[m] = um[ci];
-                vp[m] = up[ci];
+            if constexpr (A == 0 && NB1 == 4 && sizeof(T) == 4) {
+                // normal axis x: a line's four coefficients are 16 contiguous bytes
+                const int c0 = coef_index<D, K, A>(0, b0, b1);
+                const float4 qm = *reinterpret_cast<const float4*>(um + c0);
+                const float4 qp = *reinterpret_cast<const float4*>(up + c0);
+                vm[0] = qm.x; vm[1] = qm.y; vm[2] = qm.z; vm[3] = qm.w;
+                vp[0] = qp.x; vp[1] = qp.y; vp[2] = qp.z; vp[3] = qp.w;
                 if (MODE == MODE_JVP && fi == 1 && ps) {
-                    vm[m] *= ps[s * NB + ci];
-                    vp[m] *= ps[s * NB + ci];
+#pragma unroll
+                    for (int m = 0; m < NB1; ++m) {
+                        vm[m] *= ps[s * NB + c0 + m];
+                        vp[m] *= ps[s * NB + c0 + m];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < NB1; ++m) {
+                    const int ci = coef_index<D, K, A>(m, b0, b1);
+                    vm[m] = um[ci];
+                    vp[m] = up[ci];
+                    if (MODE == MODE_JVP && fi == 1 && ps) {
+                        vm[m] *= ps[s * NB + ci];
+                        vp[m] *= ps[s * NB + ci];
+                    }
                 }
             }
             T uo = 0, del = 0, dm = 0, dp = 0;
             if (kd == 2) {
 #pragma unroll
-                for (int m = 0; m < NB1; ++m) uo = fma(tb.e[0][m], vp[m], uo);
+                for (int m = 0; m < NB1; ++m) uo = fma(e0r[m], vp[m], uo);
             } else {
 #pragma unroll
-                for (int m = 0; m < NB1; ++m) uo = fma(tb.e[1][m], vm[m], uo);
+                for (int m = 0; m < NB1; ++m) uo = fma(e1r[m], vm[m], uo);
             }
             if (kd == 0) {
                 del = vm[0] - vp[0];
 #pragma unroll
                 for (int m = 1; m < NB1; ++m) {
-                    del = fma(tb.e[1][m], vm[m], del);
-                    del = fma(-tb.e[0][m], vp[m], del);
+                    del = fma(e1r[m], vm[m], del);
+                    del = fma(-e0r[m], vp[m], del);
                 }
 #pragma unroll
                 for (int m = 0; m < NB1; ++m) {
-                    dm = fma(tb.dh[A][1][m], vm[m], dm);
-                    dp = fma(tb.dh[A][0][m], vp[m], dp);
+                    dm = fma(d1r[m], vm[m], dm);
+                    dp = fma(d0r[m], vp[m], dp);
                 }
             }
             const int ss = set5_slot(s);

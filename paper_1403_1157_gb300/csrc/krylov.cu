@@ -3,9 +3,9 @@
 // bandwidth-bound passes over DOF-length vectors with grid-stride loops;
 // every reduction is two-stage with a fixed partition and a fixed tree, so
 // results are bitwise reproducible (no atomics).  Dot products of FP32
-// vectors accumulate in FP32 within a thread and in FP64 across threads and
-// blocks (FP64 arithmetic per element would bind these kernels on GB300,
-// whose FP64 rate is 1/61 of its FP32 rate).
+// vectors accumulate in FP32 within a thread and within a warp, and in FP64
+// across warps and blocks (FP64 arithmetic per element would bind these
+// kernels on GB300, whose FP64 rate is 1/61 of its FP32 rate).
 #include <cstdint>
 #include <type_traits>
 
@@ -52,6 +52,17 @@ __global__ void __launch_bounds__(VT) k_convert(long long n, const S* src, doubl
     // the narrower of the two types carries the arithmetic
     using C = typename std::conditional<(sizeof(S) < sizeof(D)), S, D>::type;
     const C sc = C(scale);
+    if constexpr (std::is_same<S, float>::value && std::is_same<D, float>::value) {
+        // 16 bytes per access where both vectors allow it (same element-wise result)
+        if (n % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0 && reinterpret_cast<uintptr_t>(dst) % 16 == 0) {
+            const long long n4 = n / 4;
+            for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n4; i += (long long)gridDim.x * VT) {
+                const float4 x = reinterpret_cast<const float4*>(src)[i];
+                reinterpret_cast<float4*>(dst)[i] = make_float4(sc * x.x, sc * x.y, sc * x.z, sc * x.w);
+            }
+            return;
+        }
+    }
     for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
         dst[i] = D(sc * C(src[i]));
 }

@@ -158,6 +158,12 @@ __device__ __forceinline__ int dev_tau(const ApplyArgs& a, int j, long long i) {
     return 0;
 }
 
+// Elements per CTA of the block apply: a run long enough that the rows of the
+// inverse blocks, loaded into registers once per CTA (and again only where
+// the element type changes), are reused over many elements.
+template <int NB>
+constexpr int block_apply_run() { return 32 * (128 / NB); }
+
 // z = P^{-1} v for one species and a run of CH consecutive elements per CTA.
 // Thread (g, i), g < G = 128 / NB, owns output mode i of every G-th element
 // of the run and keeps row i of its element type's inverse block in
@@ -167,7 +173,7 @@ template <int NB, typename T>
 __global__ void __launch_bounds__(128) k_block_apply(const ApplyArgs a, const T* __restrict__ M,
                                                      const T* __restrict__ v, T* __restrict__ z) {
     constexpr int G = 128 / NB;
-    constexpr int CH = 8 * G;
+    constexpr int CH = block_apply_run<NB>();
     __shared__ __align__(16) T sv[CH][NB];
     __shared__ int stype[CH];
     const int s = blockIdx.y;
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(128) k_block_apply(const ApplyArgs a, const T*
 
 template <int NB, typename T>
 static void launch_nb(const ApplyArgs& a, const T* M, const T* v, T* z, cudaStream_t st) {
-    constexpr int CH = 8 * (128 / NB);
+    constexpr int CH = block_apply_run<NB>();
     const dim3 grid((unsigned)((a.E + CH - 1) / CH), NS);
     k_block_apply<NB, T><<<grid, 128, 0, st>>>(a, M, v, z);
 }

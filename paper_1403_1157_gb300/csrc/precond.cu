@@ -211,16 +211,19 @@ __global__ void __launch_bounds__(128) k_block_apply(const ApplyArgs a, const T*
         T acc = T(0);
         if constexpr (sizeof(T) == 4 && NB % 4 == 0) {
             // the row of the input slice read 16 bytes at a time (a broadcast
-            // to the warp): a quarter of the shared-memory instructions
+            // to the warp): a quarter of the shared-memory instructions; four
+            // independent partial sums instead of one chain of NB FMAs
             const float4* sv4 = reinterpret_cast<const float4*>(&sv[e][0]);
+            float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
             for (int j = 0; j < NB / 4; ++j) {
                 const float4 x = sv4[j];
-                acc = fma(m[4 * j], x.x, acc);
-                acc = fma(m[4 * j + 1], x.y, acc);
-                acc = fma(m[4 * j + 2], x.z, acc);
-                acc = fma(m[4 * j + 3], x.w, acc);
+                p0 = fma(m[4 * j], x.x, p0);
+                p1 = fma(m[4 * j + 1], x.y, p1);
+                p2 = fma(m[4 * j + 2], x.z, p2);
+                p3 = fma(m[4 * j + 3], x.w, p3);
             }
+            acc = (p0 + p1) + (p2 + p3);
         } else {
 #pragma unroll
             for (int j = 0; j < NB; ++j) acc = fma(m[j], sv[e][j], acc);

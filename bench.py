@@ -440,9 +440,11 @@ def measure_solve(G, torch, cfg: int, steps: int, precond: int):
     result = {"workload": w.name, "n_dof": w.n_dof, "dt": w.dt, "steps": steps, "scheme": f"SDIRK{scheme}",
               "newton_rtol": 1e-10, "precond": {1: "modal diagonal", 2: "element-block Jacobi"}.get(precond, "none")}
     finals = {}
-    modes = [("fp64", 0, 1e-3), ("mixed", 1, 1e-4)]
+    # GMRES forcing term eta = 3e-3 for every precision: swept over 1e-4 .. 3e-2 on 3D 64x16x16 Q3
+    # (SDIRK3, element blocks), the fastest setting of each of FP64, mixed FP32 and mixed TF32
+    modes = [("fp64", 0, 3e-3), ("mixed", 1, 3e-3)]
     if w.dim == 3 and w.k == 3:
-        modes.append(("mixed_tf32", 2, 1e-4))
+        modes.append(("mixed_tf32", 2, 3e-3))
     for mode, mixed, eta in modes:
         U = U0.clone()
         # one untimed step warms up the kernels and allocates the workspace

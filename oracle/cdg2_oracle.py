@@ -21,7 +21,9 @@ What it computes, with the passages it follows:
     by quadrature and inverted by a dense solve (no orthonormality shortcut);
   * the linearisation J(U) dU and its transpose via torch.func automatic
     differentiation of the same code (the definition of the derivative);
-  * SDIRK time stepping with Newton and GMRES (Sec. 3.2).
+  * SDIRK time stepping with Newton and GMRES (Sec. 3.2);
+  * the experimental order of convergence of Table 1 (Sec. 4), pinned to
+    the paper's printed column.
 
 Everything is evaluated densely: full tensor-product tabulation matrices,
 no sum factorisation, no fusion.  Readings where the paper is silent are
@@ -534,6 +536,12 @@ def l2_error(mesh: Mesh, U, func, npts=None):
     uh = torch.einsum("qi,esi->seq", phi, U)
     err = (uh - func(x)) ** 2
     return torch.sqrt(mesh.vol * torch.einsum("q,seq->s", wts, err))
+
+
+def eoc(errors):
+    """Experimental orders of convergence of a sequence of errors on meshes
+    refined by a factor 2 (Sec. 4, Table 1): EOC_l = log2(e_{l-1} / e_l)."""
+    return [math.log2(errors[l - 1] / errors[l]) for l in range(1, len(errors))]
 
 
 # ----------------------------------------------------------------------------

@@ -37,7 +37,7 @@
  *   the word is set (out is then undefined), clearing it.  With CDG2_ASYNC
  *   in flags they return as soon as the work is queued and leave the word
  *   set; the next call without CDG2_ASYNC on the mesh, or
- *   cdg2_mesh_status(), reports it.  The steps judge the converged stage
+ *   cdg2_mesh_status(), reports it.  The steps check the converged stage
  *   values: a stage value with y + chith <= 0 at a quadrature point returns
  *   CDG2_ERR_DOMAIN (U unchanged), while Newton may pass through iterates
  *   outside the domain on the way; the adjoint step reports stage values

@@ -235,8 +235,12 @@ int cdg2_mesh_status(const cdg2_mesh* mesh, void* stream);
  * pointwise model, the faces and the modal diffusion stay in FP32.  Meant
  * for the inner Krylov operator of the mixed solver: the JVP along a rough
  * tangent keeps about 5e-5 relative to FP64; on smooth states the apply of
- * n1 and n2 (whose fluxes go through the tensor cores) loses 1e-3 to 4e-3 to
- * the cancellation of the weak form.  Errors: INVALID_ARG,
+ * n1 and n2 (whose chemotactic fluxes go through the tensor cores; every
+ * species' diffusion is applied in FP32 modal form) loses up to about 2e-3
+ * to the cancellation of the weak form.  With CDG2_TF32, U and dU must be
+ * 16-byte aligned (else CDG2_ERR_CUDA, misaligned address); without it any
+ * element-aligned array is accepted (the face kernels then load without
+ * bulk copies).  Errors: INVALID_ARG,
  * CUDA, DOMAIN (y + chith <= 0 at a quadrature point; out undefined). */
 int cdg2_apply(const cdg2_mesh* mesh, const cdg2_params* params, const void* U, void* out,
                int flags, double t, void* stream);

@@ -239,117 +239,140 @@ __device__ __forceinline__ float f4c(const float4& x, int kk) {
     return kk == 0 ? x.x : (kk == 1 ? x.y : (kk == 2 ? x.z : x.w));
 }
 
-// z = P^{-1} v for NB = 64 (Q3 hexahedra) in FP32: one CTA of 64 threads per
-// (run of 64 elements, species), the run's input slices sx[e][j] and its
-// type's inverse block sm[j][i] = P^{-1}[i][j] staged in shared memory.
-// Register-tiled product: thread (rg, eg) accumulates the rows
-// {4rg..4rg+3, 32+4rg..32+4rg+3} of the 8 elements eg*8..eg*8+7, so every
-// value it reads from shared memory feeds 8 FMAs.  (One shared value per
-// FMA, as in k_block_apply, caps the product at the shared-memory delivery
-// rate of 32 values per cycle per SM: a quarter of the FP32 FMA rate.)  A
-// run with several element types is applied once per type present, each
-// pass storing the elements of its type; the blocks depend on the type only.
-// vec4: v and z are 16-byte aligned (16-byte global loads and stores).
-__global__ void __launch_bounds__(64) k_block_apply64(const ApplyArgs a, const float* __restrict__ M,
-                                                      const float* __restrict__ v, float* __restrict__ z, int vec4) {
-    constexpr int NB = 64, RUN = 64;
+// The type of element e (as dev_tau and the slots above) in 32-bit index
+// arithmetic (E * 6 * nb < 2^31 for every mesh) and with constant argument
+// indices: 64-bit divisions and indexed kernel-argument reads (a local copy
+// of the arguments) made the type computation a visible part of the apply.
+__device__ __forceinline__ int elem_type32(const ApplyArgs& a, long long e) {
+    unsigned rest = (unsigned)e;
+    int type = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j < a.dim) {
+            const unsigned nj = (unsigned)a.n[j];
+            const unsigned ij = rest % nj;
+            rest /= nj;
+            int tau = 0;
+            if (a.periodic[j]) tau = nj == 1 ? 4 : 0;
+            else if (nj == 1) tau = 3;
+            else if (ij == 0) tau = 1;
+            else if (ij == nj - 1) tau = 2;
+            const int sl = tau == 0 ? a.slot[j][0]
+                         : tau == 1 ? a.slot[j][1]
+                         : tau == 2 ? a.slot[j][2]
+                         : tau == 3 ? a.slot[j][3] : a.slot[j][4];
+            type += sl * a.stride[j];
+        }
+    }
+    return type;
+}
+
+// z = P^{-1} v for NB = 64 (Q3 hexahedra) in FP32: one CTA of 128 threads
+// per (run of 64 elements, species), the run's input slices sx[e][j] and an
+// element type's inverse block sm[j][i] = P^{-1}[i][j] staged in shared
+// memory.  Register-tiled product: thread (rg, eg) accumulates the rows
+// {4rg..4rg+3, 32+4rg..32+4rg+3} of the 4 elements 4eg..4eg+3, so a value
+// read from shared memory feeds 4 or 8 FMAs.  (One shared value per FMA, as
+// in k_block_apply, caps the product at the shared-memory delivery rate of
+// 32 values per cycle per SM: a quarter of the FP32 FMA rate.)  A run that
+// crosses a boundary layer holds several element types (fewer than 32: at
+// most 3 per axis); it is applied once per type present, each pass storing
+// the elements of its type.  The first element's block is staged with the
+// input.  vec4: v and z are 16-byte aligned (16-byte global accesses).
+__global__ void __launch_bounds__(128, 6) k_block_apply64(const ApplyArgs a, const float* __restrict__ M,
+                                                       const float* __restrict__ v, float* __restrict__ z, int vec4) {
+    constexpr int NB = 64, RUN = 64, NT = 128;
     __shared__ __align__(16) float sx[RUN][NB];
     __shared__ __align__(16) float sm[NB][NB];
     __shared__ int stype[RUN];
+    __shared__ unsigned smask;
     const int s = blockIdx.y, tid = threadIdx.x;
     const long long e0 = (long long)blockIdx.x * RUN;
     const int ne = (int)min((long long)RUN, a.E - e0);
+    int cur = elem_type32(a, e0);
+    if (tid == 0) smask = 0u;
+    if (tid < RUN) stype[tid] = tid < ne ? elem_type32(a, e0 + tid) : -1;   // padding: no type, never stored
+    {
+        const float4* Mg = reinterpret_cast<const float4*>(M + ((size_t)cur * NS + s) * NB * NB);
+        for (int q = tid; q < NB * NB / 4; q += NT) reinterpret_cast<float4*>(&sm[0][0])[q] = Mg[q];
+    }
     if (vec4) {
-        for (int idx = tid; idx < RUN * NB / 4; idx += RUN) {
+        for (int idx = tid; idx < RUN * NB / 4; idx += NT) {
             const int e = idx / (NB / 4), q = idx % (NB / 4);
             float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
             if (e < ne) x = reinterpret_cast<const float4*>(v + ((e0 + e) * NS + s) * NB)[q];
             reinterpret_cast<float4*>(&sx[e][0])[q] = x;
         }
     } else {
-        for (int idx = tid; idx < RUN * NB; idx += RUN) {
+        for (int idx = tid; idx < RUN * NB; idx += NT) {
             const int e = idx / NB, j = idx % NB;
             sx[e][j] = e < ne ? v[((e0 + e) * NS + s) * NB + j] : 0.f;
         }
     }
-    {
-        int type = -1;   // padding of a ragged last run: no type, never stored
-        if (tid < ne) {
-            long long rest = e0 + tid;
-            type = 0;
-            for (int j = 0; j < a.dim; ++j) {
-                const long long ij = rest % a.n[j];
-                rest /= a.n[j];
-                type += a.slot[j][dev_tau(a, j, ij)] * a.stride[j];
-            }
-        }
-        stype[tid] = type;
-    }
     __syncthreads();
+    if (tid < ne) atomicOr(&smask, 1u << stype[tid]);
+    __syncthreads();
+    unsigned left = smask;   // the types present (the same in every thread)
     const int rg = tid % 8, eg = tid / 8;   // a quarter warp shares eg: its x reads are broadcasts
-    int cur = -1;
     for (;;) {
-        // the next type of the run, in increasing order (the same in every thread)
-        int nxt = INT_MAX;
-        for (int e = 0; e < ne; ++e) {
-            const int t = stype[e];
-            if (t > cur && t < nxt) nxt = t;
-        }
-        if (nxt == INT_MAX) break;
-        cur = nxt;
-        __syncthreads();   // the previous type's block is read by no thread any more
-        const float4* Mg = reinterpret_cast<const float4*>(M + ((size_t)cur * NS + s) * NB * NB);
-        for (int q = tid; q < NB * NB / 4; q += RUN) reinterpret_cast<float4*>(&sm[0][0])[q] = Mg[q];
-        __syncthreads();
         bool mine = false;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) mine |= stype[eg * 8 + c] == cur;
-        if (!mine) continue;
-        float acc[8][8];
+        for (int c = 0; c < 4; ++c) mine |= stype[eg * 4 + c] == cur;
+        if (mine) {
+            float acc[4][8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
+            for (int c = 0; c < 4; ++c)
 #pragma unroll
-            for (int r = 0; r < 8; ++r) acc[c][r] = 0.f;
-#pragma unroll 2
-        for (int k = 0; k < NB; k += 4) {
-            float4 xr[8];
+                for (int r = 0; r < 8; ++r) acc[c][r] = 0.f;
+#pragma unroll 4
+            for (int k = 0; k < NB; k += 4) {
+                float4 xr[4];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) xr[c] = *reinterpret_cast<const float4*>(&sx[eg * 8 + c][k]);
+                for (int c = 0; c < 4; ++c) xr[c] = *reinterpret_cast<const float4*>(&sx[eg * 4 + c][k]);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const float4 m0 = *reinterpret_cast<const float4*>(&sm[k + kk][4 * rg]);
-                const float4 m1 = *reinterpret_cast<const float4*>(&sm[k + kk][32 + 4 * rg]);
+                for (int kk = 0; kk < 4; ++kk) {
+                    const float4 m0 = *reinterpret_cast<const float4*>(&sm[k + kk][4 * rg]);
+                    const float4 m1 = *reinterpret_cast<const float4*>(&sm[k + kk][32 + 4 * rg]);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const float x = f4c(xr[c], kk);
-                    acc[c][0] = fmaf(m0.x, x, acc[c][0]);
-                    acc[c][1] = fmaf(m0.y, x, acc[c][1]);
-                    acc[c][2] = fmaf(m0.z, x, acc[c][2]);
-                    acc[c][3] = fmaf(m0.w, x, acc[c][3]);
-                    acc[c][4] = fmaf(m1.x, x, acc[c][4]);
-                    acc[c][5] = fmaf(m1.y, x, acc[c][5]);
-                    acc[c][6] = fmaf(m1.z, x, acc[c][6]);
-                    acc[c][7] = fmaf(m1.w, x, acc[c][7]);
+                    for (int c = 0; c < 4; ++c) {
+                        const float x = f4c(xr[c], kk);
+                        acc[c][0] = fmaf(m0.x, x, acc[c][0]);
+                        acc[c][1] = fmaf(m0.y, x, acc[c][1]);
+                        acc[c][2] = fmaf(m0.z, x, acc[c][2]);
+                        acc[c][3] = fmaf(m0.w, x, acc[c][3]);
+                        acc[c][4] = fmaf(m1.x, x, acc[c][4]);
+                        acc[c][5] = fmaf(m1.y, x, acc[c][5]);
+                        acc[c][6] = fmaf(m1.z, x, acc[c][6]);
+                        acc[c][7] = fmaf(m1.w, x, acc[c][7]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int e = eg * 4 + c;
+                if (stype[e] != cur) continue;   // another type's pass, or padding
+                float* out = z + ((e0 + e) * NS + s) * NB;
+                if (vec4) {
+                    reinterpret_cast<float4*>(out + 4 * rg)[0] =
+                        make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+                    reinterpret_cast<float4*>(out + 32 + 4 * rg)[0] =
+                        make_float4(acc[c][4], acc[c][5], acc[c][6], acc[c][7]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        out[4 * rg + r] = acc[c][r];
+                        out[32 + 4 * rg + r] = acc[c][4 + r];
+                    }
                 }
             }
         }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int e = eg * 8 + c;
-            if (stype[e] != cur) continue;   // another type's pass (or padding: type -1)
-            float* out = z + ((e0 + e) * NS + s) * NB;
-            if (vec4) {
-                reinterpret_cast<float4*>(out + 4 * rg)[0] = make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
-                reinterpret_cast<float4*>(out + 32 + 4 * rg)[0] =
-                    make_float4(acc[c][4], acc[c][5], acc[c][6], acc[c][7]);
-            } else {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    out[4 * rg + r] = acc[c][r];
-                    out[32 + 4 * rg + r] = acc[c][4 + r];
-                }
-            }
-        }
+        left &= ~(1u << cur);
+        if (left == 0u) break;
+        cur = __ffs((int)left) - 1;
+        __syncthreads();   // the previous type's block is read by no thread any more
+        const float4* Mg = reinterpret_cast<const float4*>(M + ((size_t)cur * NS + s) * NB * NB);
+        for (int q = tid; q < NB * NB / 4; q += NT) reinterpret_cast<float4*>(&sm[0][0])[q] = Mg[q];
+        __syncthreads();
     }
 }
 
@@ -358,7 +381,7 @@ static void launch_nb(const ApplyArgs& a, const T* M, const T* v, T* z, cudaStre
     if constexpr (NB == 64 && sizeof(T) == 4) {
         auto al16 = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
         const dim3 grid((unsigned)((a.E + 63) / 64), NS);
-        k_block_apply64<<<grid, 64, 0, st>>>(a, M, v, z, al16(v) && al16(z) ? 1 : 0);
+        k_block_apply64<<<grid, 128, 0, st>>>(a, M, v, z, al16(v) && al16(z) ? 1 : 0);
         return;
     }
     constexpr int CH = block_apply_run<NB>();
